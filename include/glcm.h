@@ -1,0 +1,213 @@
+/*
+ * glcm.h -- C ABI of libglcm, a GB300 (sm_103a) library for the gray-level
+ * co-occurrence matrix (GLCM) of "Computation of gray-level co-occurrence
+ * matrix based on CUDA and its optimization" (Hong, Zheng, Pan, 2017).
+ *
+ * What is computed (Sec. I.A, Eq. 1): for an image f and an offset (dx, dy),
+ *
+ *     P[i][j] = #{ (x, y) : f(x, y) has level i, f(x + dx, y + dy) has level j }
+ *
+ * over every anchor (x, y) whose partner (x + dx, y + dy) lies inside the
+ * image.  x is the column, y the row (growing downwards), so the paper's
+ * directions 0/45/90/135 degrees at distance d (Eq. 2) are (d, 0), (d, -d),
+ * (0, -d), (-d, -d); diagonal distances are chessboard steps.  Pairs never
+ * wrap from one row into the next.  The bin of a pair is i * N + j with i
+ * the anchor's level (Eq. 3), one vote per pair, exact uint32 counts.
+ *
+ * Levels: a pixel v of b bits (b = 8 or 16) has level floor(v * N / 2^b)
+ * (the paper reduces images to N = 8, 16 or 32 levels without giving the
+ * mapping, Sec. I.A); with GLCM_INPUT_LEVELS the pixel already is its level
+ * and must be < N.
+ *
+ * Pointers.  Every image, count, normalized, feature or map pointer may be a
+ * host pointer (pageable or pinned) or a device pointer of the context's
+ * device; the library tells them apart with cudaPointerGetAttributes.  The
+ * caller owns all of them.  An image is `height` rows of `pitch_bytes` bytes
+ * each, pixels little-endian for uint16.
+ *
+ * Synchronicity.  A context created with a CUDA stream enqueues its work on
+ * that stream and returns as soon as everything is enqueued when all the
+ * call's pointers are device pointers; the caller synchronizes (the stream,
+ * or glcm_synchronize, which also reports device-detected errors).  Calls
+ * that read or write host memory, and every call on a context created
+ * without a stream, return after the results are in place.
+ *
+ * Errors.  Every function returns a glcm_status (0 = success); nothing is
+ * thrown across the ABI.  glcm_last_error() gives a message for the last
+ * failure on a context.  Pixels >= N in levels mode are skipped (their pairs
+ * are not counted) and the call, or the next glcm_synchronize, returns
+ * GLCM_ERR_RANGE; the kernels never trap.
+ */
+#ifndef GLCM_H
+#define GLCM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct glcm_ctx glcm_ctx;
+
+typedef enum {
+    GLCM_OK = 0,
+    GLCM_ERR_ARG = -1,         /* invalid argument                                */
+    GLCM_ERR_RANGE = -2,       /* a pixel >= N in GLCM_INPUT_LEVELS mode          */
+    GLCM_ERR_NOMEM = -3,       /* device or pinned memory could not be obtained   */
+    GLCM_ERR_UNSUPPORTED = -4, /* valid request outside what is implemented       */
+    GLCM_ERR_CUDA = -5,        /* a CUDA runtime call failed                      */
+    GLCM_ERR_TIMEOUT = -6,     /* a bounded device or host wait gave up           */
+    GLCM_ERR_BUSY = -7         /* admission refused: HBM budget or slots exhausted */
+} glcm_status;
+
+enum { GLCM_U8 = 0, GLCM_U16 = 1 };
+
+enum {
+    GLCM_SYMMETRIC = 1,    /* normalized / features use S = P + P^T           */
+    GLCM_NORMALIZE = 2,    /* write p = S / sum(S) as float32                 */
+    GLCM_INPUT_LEVELS = 4  /* pixels are levels already (must be < N)         */
+};
+
+#define GLCM_MAX_LEVELS 256
+#define GLCM_MAX_OFFSETS 64
+#define GLCM_N_FEATURES 14
+#define GLCM_N_WINDOW_MAPS 4
+#define GLCM_MAX_WINDOW_OFFSETS 8
+
+typedef struct {
+    int dx, dy; /* partner of anchor (x, y) is (x + dx, y + dy) */
+} glcm_offset;
+
+/* One image of a batch (glcm_compute_batch). */
+typedef struct {
+    const void *image;          /* height rows of pitch_bytes                      */
+    int width, height;
+    size_t pitch_bytes;
+    int dtype;                  /* GLCM_U8 or GLCM_U16                             */
+    int levels;                 /* N, 2..256                                       */
+    const glcm_offset *offsets; /* n_offsets entries (host memory)                 */
+    int n_offsets;              /* 1..GLCM_MAX_OFFSETS                             */
+    int flags;                  /* GLCM_SYMMETRIC | GLCM_INPUT_LEVELS              */
+    uint32_t *counts;           /* n_offsets x N x N, required                     */
+    float *normalized;          /* n_offsets x N x N or NULL                       */
+    float *features;            /* n_offsets x 14 or NULL                          */
+} glcm_desc;
+
+/* Create a context on CUDA device `device`.  `hbm_budget_bytes` caps the
+ * device memory the context may hold for staging and scratch (0 = 1 GiB).
+ * `cuda_stream` is a cudaStream_t to enqueue on, or NULL for a private
+ * stream with synchronous calls.  *out receives the context (owned by the
+ * caller, released with glcm_destroy).
+ * Errors: GLCM_ERR_ARG (out NULL, bad device), GLCM_ERR_CUDA, GLCM_ERR_NOMEM. */
+int glcm_create(glcm_ctx **out, int device, size_t hbm_budget_bytes, void *cuda_stream);
+
+/* Wait for all work enqueued by the context, free everything it owns.
+ * NULL is accepted.  Returns GLCM_OK or GLCM_ERR_CUDA. */
+int glcm_destroy(glcm_ctx *ctx);
+
+/* Message for the last failure on ctx ("" if none); valid until the next
+ * call on ctx.  With ctx == NULL: the last failure of glcm_create. */
+const char *glcm_last_error(const glcm_ctx *ctx);
+
+/* (dx, dy) of distance d >= 1 at theta in {0, 45, 90, 135} degrees, the
+ * directions of Eq. 2: (d,0), (d,-d), (0,-d), (-d,-d).  GLCM_ERR_ARG for
+ * any other theta or d < 1. */
+int glcm_offset_from_angle(int d, int theta_deg, glcm_offset *out);
+
+/* GLCMs of one image for n_offsets offsets (Eq. 1, all offsets fused in
+ * one pass over the image).
+ *   image       height rows of pitch_bytes; pitch_bytes >= width * bytes per pixel
+ *   levels      N in 2..256
+ *   offsets     host array of n_offsets (1..64) offsets, |dx| < 65536, |dy| < 65536
+ *   flags       GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS
+ *   counts      out: n_offsets x N x N uint32, row-major [offset][i][j]; always
+ *               the plain (non-symmetric) counts P
+ *   normalized  out (or NULL): n_offsets x N x N float32, p = S / sum(S) with
+ *               S = P + P^T if GLCM_SYMMETRIC else P; all zero for an empty GLCM.
+ *               Written only when GLCM_NORMALIZE is set.
+ * Host images are streamed to the device in row stripes with halo rows on a
+ * side stream, overlapped with the votes of earlier stripes (Sec. III,
+ * Eqs. 7-9).
+ * Errors: GLCM_ERR_ARG, GLCM_ERR_RANGE, GLCM_ERR_NOMEM (image staging over
+ * budget), GLCM_ERR_CUDA. */
+int glcm_compute(glcm_ctx *ctx, const void *image, int width, int height, size_t pitch_bytes,
+                 int dtype, int levels, const glcm_offset *offsets, int n_offsets, int flags,
+                 uint32_t *counts, float *normalized);
+
+/* The 14 Haralick texture features (named by the paper, Sec. I, as the use
+ * of each GLCM) of n_glcm count matrices.
+ *   counts    n_glcm x N x N uint32 (as written by glcm_compute)
+ *   flags     GLCM_SYMMETRIC: features of S = P + P^T, else of P
+ *   features  out: n_glcm x 14 float32 in the order asm, contrast,
+ *             correlation, sum of squares, inverse difference moment, sum
+ *             average, sum variance, sum entropy, entropy, difference
+ *             variance, difference entropy, information measures of
+ *             correlation 1 and 2, maximal correlation coefficient.
+ *             Natural logarithms; correlation is 1 when a marginal has zero
+ *             variance; an empty GLCM gives all zeros.
+ * float32 arithmetic with compensated sums; the correlation means and
+ * variances in float64.
+ * Errors: GLCM_ERR_ARG, GLCM_ERR_CUDA. */
+int glcm_features(glcm_ctx *ctx, const uint32_t *counts, int levels, int n_glcm, int flags,
+                  float *features);
+
+/* A batch of images (multispectral bands, many images of uneven sizes, all
+ * their offsets) in one persistent vote launch plus one epilogue launch,
+ * replayed from a cached CUDA graph when the same batch (same pointers,
+ * sizes and flags) comes again.  Per desc: counts always, normalized if
+ * non-NULL (GLCM_NORMALIZE implied), features if non-NULL.  Each desc's
+ * results equal those of a glcm_compute + glcm_features on that image alone.
+ * All image pointers must be device pointers or all host pointers.
+ * Errors: as glcm_compute, per the first failing desc. */
+int glcm_compute_batch(glcm_ctx *ctx, const glcm_desc *descs, int n);
+
+/* Local GLCMs of sliding win x win windows whose top-left pixels are
+ * (u*stride, v*stride), u < nwx = (width - win)/stride + 1,
+ * v < nwy = (height - win)/stride + 1; each window's GLCM counts the pairs
+ * with both pixels inside the window.
+ *   offsets   1..8 offsets with |dx|, |dy| < win
+ *   counts    out (or NULL): nwy x nwx x n_offsets x N x N uint32
+ *   maps      out (or NULL): 4 x n_offsets x nwy x nwx float32 -- contrast,
+ *             angular second moment, inverse difference moment, entropy of
+ *             each window's normalized GLCM (symmetric with GLCM_SYMMETRIC)
+ * Errors: GLCM_ERR_ARG, GLCM_ERR_UNSUPPORTED (window histograms larger than
+ * shared memory), GLCM_ERR_RANGE, GLCM_ERR_CUDA. */
+int glcm_windows(glcm_ctx *ctx, const void *image, int width, int height, size_t pitch_bytes,
+                 int dtype, int levels, int win, int stride, const glcm_offset *offsets,
+                 int n_offsets, int flags, uint32_t *counts, float *maps);
+
+/* Wait for the context's stream; report device-detected errors of the work
+ * enqueued since the last check (GLCM_ERR_RANGE, GLCM_ERR_TIMEOUT) and
+ * clear them. */
+int glcm_synchronize(glcm_ctx *ctx);
+
+/* Kernel timing: when enabled, CUDA events bracket every vote-kernel launch
+ * and glcm_get_timing returns the summed device milliseconds of the vote
+ * kernels completed since the last reset, how many vote launches that was,
+ * and how many kernels the context launched in total.  Reading synchronizes
+ * the context's stream. */
+int glcm_set_timing(glcm_ctx *ctx, int enable);
+int glcm_get_timing(glcm_ctx *ctx, double *vote_ms, long long *vote_launches,
+                    long long *kernel_launches, int reset);
+
+/* Vote-kernel tuning knobs for one (levels, offsets, pixel type) class, as
+ * chosen by the autotuner: threads per CTA (256..1024), log2 of private
+ * copies (-1 = vote into global memory, 0..5), counter packing (1 or 2),
+ * warp aggregation (0/1), rows per work item.  Passing threads <= 0 removes
+ * the override.  GLCM_ERR_ARG if the choice cannot hold the histograms. */
+int glcm_set_vote_config(glcm_ctx *ctx, int levels, int n_offsets, int dtype, int threads,
+                         int log2_copies, int pack, int aggregate, int band_rows);
+
+/* Scheme 1 of the paper (Sec. I.B): one thread per pixel and one global
+ * atomic per vote, one offset.  Ablation baseline with the same inputs and
+ * outputs as glcm_compute for one offset (device pointers only). */
+int glcm_compute_naive(glcm_ctx *ctx, const void *image, int width, int height,
+                       size_t pitch_bytes, int dtype, int levels, glcm_offset offset, int flags,
+                       uint32_t *counts);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GLCM_H */

@@ -1,0 +1,1195 @@
+// C ABI of libglcm (declared in include/glcm.h): contexts, argument checks,
+// work planning, the host-image stripe pipeline (Sec. III, Eqs. 7-9), batch
+// launches with a CUDA-graph cache, and kernel timing.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "glcm.h"
+#include "glcm_internal.cuh"
+
+using namespace glcm;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t cap = 0;
+};
+
+struct VoteCfg {
+    int threads = 1024;
+    int rshift = 5;
+    int pack = 1;
+    int agg = 0;
+    int band_rows = 0;  // 0: derived from the launch size
+};
+
+struct TimedPair {
+    cudaEvent_t a, b;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;
+    cudaEvent_t cap_a = nullptr, cap_b = nullptr;  // events recorded at capture
+    DevBuf jobs, offs, feat;
+    int n_vote_kernels = 0;
+    int n_kernels = 0;
+};
+
+// Host-side plan of one vote launch.
+struct VotePlan {
+    std::vector<VoteJob> jobs;
+    std::vector<VoteOffset> offs;
+    int n_items = 0;
+    int max_hist_words = 0;
+    int threads = 1024;
+    int bpp = 1;
+};
+
+}  // namespace
+
+struct glcm_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t copy_stream = nullptr;
+    size_t budget = 0, used = 0;
+    int sm_count = 0, smem_optin = 0;
+    unsigned* d_words = nullptr;  // [0] error bits, [1] work-item counter
+    DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
+    void* h_stage = nullptr;      // pinned table staging
+    size_t h_stage_cap = 0;
+    cudaEvent_t ev_stage = nullptr;
+    std::vector<cudaEvent_t> stripe_events;
+    std::string err;
+    bool timing = false;
+    std::vector<TimedPair> pool, pending;
+    double vote_ms = 0;
+    long long vote_launches = 0, kernel_launches = 0;
+    std::map<long long, VoteCfg> overrides;
+    std::unordered_map<std::string, GraphEntry> graphs;
+};
+
+namespace {
+
+int fail(glcm_ctx* c, int code, const char* fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(glcm_ctx* c, int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_error = buf;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(ctx, GLCM_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define TRY(expr)            \
+    do {                     \
+        int r_ = (expr);     \
+        if (r_ != GLCM_OK)   \
+            return r_;       \
+    } while (0)
+
+bool fault_injected(const char* what)
+{
+    const char* f = getenv("GLCM_FAULT");
+    return f && strcmp(f, what) == 0;
+}
+
+int ensure(glcm_ctx* ctx, DevBuf& b, size_t bytes)
+{
+    if (bytes == 0)
+        bytes = 16;
+    if (b.cap >= bytes)
+        return GLCM_OK;
+    size_t want = std::max(bytes, b.cap + b.cap / 2);
+    want = (want + 255) & ~(size_t)255;
+    if (fault_injected("alloc") || ctx->used - b.cap + want > ctx->budget) {
+        if (!fault_injected("alloc") && ctx->used - b.cap + bytes <= ctx->budget)
+            want = (bytes + 255) & ~(size_t)255;
+        else
+            return fail(ctx, GLCM_ERR_NOMEM, "device scratch of %zu bytes exceeds the budget (%zu of %zu used)",
+                        bytes, ctx->used, ctx->budget);
+    }
+    if (b.p) {
+        cudaStreamSynchronize(ctx->stream);
+        cudaFree(b.p);
+        ctx->used -= b.cap;
+        b.p = nullptr;
+        b.cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GLCM_ERR_NOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.cap = want;
+    ctx->used += want;
+    return GLCM_OK;
+}
+
+int ensure_stage(glcm_ctx* ctx, size_t bytes)
+{
+    if (ctx->h_stage_cap >= bytes)
+        return GLCM_OK;
+    if (ctx->h_stage) {
+        cudaEventSynchronize(ctx->ev_stage);
+        cudaFreeHost(ctx->h_stage);
+        ctx->h_stage = nullptr;
+        ctx->h_stage_cap = 0;
+    }
+    size_t want = std::max<size_t>(bytes, 1 << 16);
+    if (cudaMallocHost(&ctx->h_stage, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, GLCM_ERR_NOMEM, "cudaMallocHost(%zu) failed", want);
+    }
+    ctx->h_stage_cap = want;
+    return GLCM_OK;
+}
+
+bool is_device_ptr(const void* p)
+{
+    if (!p)
+        return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int ilog2_exact(int n)
+{
+    for (int k = 0; k < 31; ++k)
+        if ((1 << k) == n)
+            return k;
+    return -1;
+}
+
+long long cfg_key(int levels, int n_off, int bpp)
+{
+    return ((long long)levels << 20) | ((long long)n_off << 4) | bpp;
+}
+
+int hist_budget_words(const glcm_ctx* ctx)
+{
+    // Leave room for static shared memory and the per-SM reservation.
+    return (ctx->smem_optin - 4096) / 4;
+}
+
+// Default vote configuration: the most private copies (up to one per lane)
+// whose histograms fit one CTA's shared memory, preferring 32-bit counters.
+VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
+{
+    VoteCfg c;
+    const long long NN = (long long)levels * levels;
+    const long long budget = hist_budget_words(ctx);
+    int best_r = -1, best_pack = 1;
+    for (int pack = 1; pack <= 2; ++pack) {
+        const long long groups = (n_off + pack - 1) / pack;
+        for (int r = 5; r >= 0; --r) {
+            if (groups * NN * (1ll << r) <= budget) {
+                if (r > best_r) {
+                    best_r = r;
+                    best_pack = pack;
+                }
+                break;
+            }
+        }
+    }
+    if (best_r < 0) {
+        // Does a single offset fit?  Then the planner splits the offsets into
+        // several jobs; otherwise vote into global memory.
+        if (NN <= budget) {
+            best_r = 0;
+            best_pack = 1;
+        } else {
+            c.rshift = -1;
+            c.pack = 1;
+            c.agg = 1;
+            return c;
+        }
+    }
+    c.rshift = best_r;
+    c.pack = best_pack;
+    c.agg = 0;
+    return c;
+}
+
+VoteCfg get_cfg(const glcm_ctx* ctx, int levels, int n_off, int bpp)
+{
+    auto it = ctx->overrides.find(cfg_key(levels, n_off, bpp));
+    if (it != ctx->overrides.end())
+        return it->second;
+    return default_cfg(ctx, levels, n_off);
+}
+
+struct ImageSpec {
+    const uint8_t* img;  // device
+    long long pitch;
+    int W, H, bpp, levels, levels_mode;
+    const glcm_offset* offsets;
+    int n_off;
+    uint32_t* out;       // device counts, n_off*N*N
+    int y_begin, y_end;  // anchor rows of this launch
+};
+
+// Append the jobs of one image to a plan.
+int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
+{
+    const VoteCfg cfg = get_cfg(ctx, s.levels, s.n_off, s.bpp);
+    const int T = std::max(plan.threads, cfg.threads);
+    plan.threads = T;
+    plan.bpp = s.bpp;
+    const int nwarps = T / 32;
+    const long long NN = (long long)s.levels * s.levels;
+    const int PX = 16 / s.bpp;
+    // Offsets sorted by dy so a partner row is loaded once per distinct dy.
+    std::vector<int> order(s.n_off);
+    for (int k = 0; k < s.n_off; ++k)
+        order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return s.offsets[a].dy < s.offsets[b].dy; });
+    // Offsets per job so the job's histograms fit.
+    int per_job = s.n_off;
+    if (cfg.rshift >= 0) {
+        const long long words_per_group = NN << cfg.rshift;
+        const long long groups_fit = hist_budget_words(ctx) / words_per_group;
+        per_job = (int)std::max<long long>(1, std::min<long long>(s.n_off, groups_fit * cfg.pack));
+    } else {
+        per_job = s.n_off;
+    }
+    const int rows = s.y_end - s.y_begin;
+    const int strip_px = 32 * PX;
+    const int n_strips = std::max(1, (s.W + strip_px - 1) / strip_px);
+    int band = cfg.band_rows;
+    if (band <= 0) {
+        long long per = (long long)rows * n_strips / std::max(1, target_items);
+        band = (int)std::max<long long>(nwarps, ((per + nwarps - 1) / nwarps) * nwarps);
+    }
+    if (cfg.rshift >= 0 && cfg.pack == 2) {
+        // votes per 16-bit half per item: ceil(band/nwarps) * PX * (T / R) <= 65535
+        const long long max_rows_per_warp = 65535ll * (1 << cfg.rshift) / ((long long)PX * T);
+        band = (int)std::min<long long>(band, std::max<long long>(1, max_rows_per_warp) * nwarps);
+        if (max_rows_per_warp < 1)
+            return fail(ctx, GLCM_ERR_ARG, "vote config cannot bound 16-bit counters");
+    }
+    band = std::max(1, band);
+    const int n_bands = rows > 0 ? (rows + band - 1) / band : 0;
+    for (int o0 = 0; o0 < s.n_off; o0 += per_job) {
+        const int cnt = std::min(per_job, s.n_off - o0);
+        VoteJob j{};
+        j.img = s.img;
+        j.pitch = s.pitch;
+        j.W = s.W;
+        j.H = s.H;
+        j.bpp = s.bpp;
+        j.levels = s.levels;
+        j.log2n = ilog2_exact(s.levels);
+        j.levels_mode = s.levels_mode;
+        j.aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
+        j.n_off = cnt;
+        j.off0 = (int)plan.offs.size();
+        j.rshift = cfg.rshift;
+        j.pack = cfg.rshift >= 0 ? cfg.pack : 1;
+        j.agg = cfg.agg;
+        j.hist_words = cfg.rshift >= 0 ? (int)(((cnt + j.pack - 1) / j.pack) * NN << cfg.rshift) : 0;
+        j.item0 = plan.n_items;
+        j.n_strips = n_strips;
+        j.band_rows = band;
+        j.y_begin = s.y_begin;
+        j.y_end = s.y_end;
+        j.out = s.out;
+        for (int k = o0; k < o0 + cnt; ++k) {
+            VoteOffset vo{};
+            vo.dx = s.offsets[order[k]].dx;
+            vo.dy = s.offsets[order[k]].dy;
+            vo.slot = order[k];
+            plan.offs.push_back(vo);
+        }
+        plan.max_hist_words = std::max(plan.max_hist_words, j.hist_words);
+        plan.n_items += n_strips * n_bands;
+        if (n_strips * n_bands > 0)
+            plan.jobs.push_back(j);
+        else
+            plan.offs.resize(j.off0);
+    }
+    return GLCM_OK;
+}
+
+int check_image_args(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch, int dtype,
+                     int levels, const glcm_offset* offsets, int n_offsets)
+{
+    if (!image)
+        return fail(ctx, GLCM_ERR_ARG, "image is NULL");
+    if (width < 1 || height < 1)
+        return fail(ctx, GLCM_ERR_ARG, "width and height must be >= 1 (got %d x %d)", width, height);
+    if (dtype != GLCM_U8 && dtype != GLCM_U16)
+        return fail(ctx, GLCM_ERR_ARG, "dtype must be GLCM_U8 or GLCM_U16");
+    const int bpp = dtype == GLCM_U8 ? 1 : 2;
+    if (pitch < (size_t)width * bpp)
+        return fail(ctx, GLCM_ERR_ARG, "pitch_bytes %zu < width * %d", pitch, bpp);
+    if (levels > GLCM_MAX_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "levels %d > %d", levels, GLCM_MAX_LEVELS);
+    if (levels < 2)
+        return fail(ctx, GLCM_ERR_ARG, "levels must be in 2..256 (got %d)", levels);
+    if (!offsets || n_offsets < 1 || n_offsets > GLCM_MAX_OFFSETS)
+        return fail(ctx, GLCM_ERR_ARG, "need 1..%d offsets (got %d)", GLCM_MAX_OFFSETS, n_offsets);
+    for (int k = 0; k < n_offsets; ++k)
+        if (offsets[k].dx <= -65536 || offsets[k].dx >= 65536 || offsets[k].dy <= -65536 || offsets[k].dy >= 65536)
+            return fail(ctx, GLCM_ERR_ARG, "offset %d out of range", k);
+    return GLCM_OK;
+}
+
+int target_items(const glcm_ctx* ctx)
+{
+    return ctx->sm_count * 4;
+}
+
+int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
+{
+    const size_t smem = std::max<size_t>(16, (size_t)plan.max_hist_words * 4);
+    const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem));
+    return std::max(1, std::min(plan.n_items, ctx->sm_count * per_sm));
+}
+
+// Upload a plan's tables into the given device buffers (through pinned staging).
+int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob>& feats, DevBuf& djobs,
+                  DevBuf& doffs, DevBuf& dfeat)
+{
+    const size_t bj = plan.jobs.size() * sizeof(VoteJob);
+    const size_t bo = plan.offs.size() * sizeof(VoteOffset);
+    const size_t bf = feats.size() * sizeof(FeatJob);
+    TRY(ensure(ctx, djobs, bj));
+    TRY(ensure(ctx, doffs, bo));
+    TRY(ensure(ctx, dfeat, bf));
+    const size_t total = ((bj + 255) & ~(size_t)255) + ((bo + 255) & ~(size_t)255) + bf;
+    cudaEventSynchronize(ctx->ev_stage);
+    TRY(ensure_stage(ctx, total));
+    uint8_t* h = static_cast<uint8_t*>(ctx->h_stage);
+    const size_t oo = (bj + 255) & ~(size_t)255;
+    const size_t of = oo + ((bo + 255) & ~(size_t)255);
+    if (bj)
+        memcpy(h, plan.jobs.data(), bj);
+    if (bo)
+        memcpy(h + oo, plan.offs.data(), bo);
+    if (bf)
+        memcpy(h + of, feats.data(), bf);
+    if (bj)
+        CK(cudaMemcpyAsync(djobs.p, h, bj, cudaMemcpyHostToDevice, ctx->stream));
+    if (bo)
+        CK(cudaMemcpyAsync(doffs.p, h + oo, bo, cudaMemcpyHostToDevice, ctx->stream));
+    if (bf)
+        CK(cudaMemcpyAsync(dfeat.p, h + of, bf, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaEventRecord(ctx->ev_stage, ctx->stream));
+    return GLCM_OK;
+}
+
+__global__ void k_zero_job_outputs(const VoteJob* jobs, const VoteOffset* offs)
+{
+    const VoteJob j = jobs[blockIdx.x];
+    const long long NN = (long long)j.levels * j.levels;
+    for (int o = 0; o < j.n_off; ++o) {
+        uint32_t* dst = j.out + offs[j.off0 + o].slot * NN;
+        for (long long k = threadIdx.x; k < NN; k += blockDim.x)
+            dst[k] = 0u;
+    }
+}
+
+TimedPair take_pair(glcm_ctx* ctx)
+{
+    if (ctx->pool.empty()) {
+        TimedPair p;
+        cudaEventCreate(&p.a);
+        cudaEventCreate(&p.b);
+        return p;
+    }
+    TimedPair p = ctx->pool.back();
+    ctx->pool.pop_back();
+    return p;
+}
+
+// Enqueue zero (optional) + vote for a plan whose tables are at djobs/doffs.
+int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, bool zero,
+                 bool capturing, GraphEntry* ge)
+{
+    if (plan.jobs.empty())
+        return GLCM_OK;
+    if (zero) {
+        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, ctx->stream>>>(
+            static_cast<const VoteJob*>(djobs.p), static_cast<const VoteOffset*>(doffs.p));
+        CK(cudaGetLastError());
+        ctx->kernel_launches += capturing ? 0 : 1;
+        if (ge)
+            ge->n_kernels++;
+    }
+    CK(cudaMemsetAsync(ctx->d_words + 1, 0, sizeof(unsigned), ctx->stream));
+    VoteParams vp{};
+    vp.jobs = static_cast<const VoteJob*>(djobs.p);
+    vp.n_jobs = (int)plan.jobs.size();
+    vp.offs = static_cast<const VoteOffset*>(doffs.p);
+    vp.n_items = plan.n_items;
+    vp.max_hist_words = plan.max_hist_words;
+    vp.item_counter = ctx->d_words + 1;
+    vp.err = ctx->d_words;
+    const size_t smem = std::max<size_t>(16, (size_t)plan.max_hist_words * 4);
+    const int grid = grid_for(ctx, plan);
+    TimedPair tp{};
+    const bool time_it = ctx->timing && !capturing;
+    if (time_it) {
+        tp = take_pair(ctx);
+        CK(cudaEventRecord(tp.a, ctx->stream));
+    }
+    if (capturing && ge && ctx->timing) {
+        // Capture-time events; the graph's event nodes are re-pointed per replay.
+        if (!ge->cap_a) {
+            CK(cudaEventCreate(&ge->cap_a));
+            CK(cudaEventCreate(&ge->cap_b));
+        }
+        CK(cudaEventRecord(ge->cap_a, ctx->stream));
+    }
+    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, ctx->stream));
+    if (time_it) {
+        CK(cudaEventRecord(tp.b, ctx->stream));
+        ctx->pending.push_back(tp);
+    }
+    if (capturing && ge && ctx->timing)
+        CK(cudaEventRecord(ge->cap_b, ctx->stream));
+    if (!capturing) {
+        ctx->kernel_launches += 1;
+        ctx->vote_launches += 1;
+    }
+    if (ge) {
+        ge->n_kernels++;
+        ge->n_vote_kernels++;
+    }
+    return GLCM_OK;
+}
+
+int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const DevBuf& dfeat, int max_levels,
+                     bool capturing, GraphEntry* ge)
+{
+    if (feats.empty())
+        return GLCM_OK;
+    FeatParams fp{};
+    fp.jobs = static_cast<const FeatJob*>(dfeat.p);
+    fp.n_jobs = (int)feats.size();
+    fp.err = ctx->d_words;
+    if (max_levels > 64) {
+        bool any_feat = false;
+        for (const auto& f : feats)
+            any_feat |= f.features != nullptr;
+        if (any_feat) {
+            TRY(ensure(ctx, ctx->work, feats.size() * (size_t)max_levels * max_levels * sizeof(float)));
+            fp.work = static_cast<float*>(ctx->work.p);
+            fp.work_stride = (long long)max_levels * max_levels;
+        }
+    }
+    CK(launch_features(fp, max_levels, ctx->stream));
+    if (!capturing)
+        ctx->kernel_launches += 1;
+    if (ge)
+        ge->n_kernels++;
+    return GLCM_OK;
+}
+
+// Read (and clear) the device error word after synchronizing the stream.
+int collect_device_errors(glcm_ctx* ctx)
+{
+    CK(cudaStreamSynchronize(ctx->stream));
+    unsigned w = 0;
+    CK(cudaMemcpy(&w, ctx->d_words, sizeof w, cudaMemcpyDeviceToHost));
+    if (w) {
+        CK(cudaMemset(ctx->d_words, 0, sizeof(unsigned)));
+        if (w & kErrInternal)
+            return fail(ctx, GLCM_ERR_CUDA, "a kernel index check failed (error bits 0x%x)", w);
+        if (w & kErrTimeout)
+            return fail(ctx, GLCM_ERR_TIMEOUT, "a bounded device wait gave up (error bits 0x%x)", w);
+        if (w & kErrRange)
+            return fail(ctx, GLCM_ERR_RANGE, "a pixel >= levels in GLCM_INPUT_LEVELS mode; its pairs were skipped");
+    }
+    return GLCM_OK;
+}
+
+// Copy a host image into device staging, in row stripes on the copy stream;
+// returns the device image.  stripe_rows[k] are the row ends of the copies.
+int stage_host_image(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch, int bpp,
+                     DevBuf& dst, size_t& dpitch, const std::vector<int>& cuts)
+{
+    dpitch = (((size_t)width * bpp) + 15) & ~(size_t)15;
+    TRY(ensure(ctx, dst, dpitch * height));
+    int prev = 0;
+    while (ctx->stripe_events.size() < cuts.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->stripe_events.push_back(e);
+    }
+    for (size_t k = 0; k < cuts.size(); ++k) {
+        const int r1 = cuts[k];
+        if (r1 > prev) {
+            CK(cudaMemcpy2DAsync(static_cast<uint8_t*>(dst.p) + (size_t)prev * dpitch, dpitch,
+                                 static_cast<const uint8_t*>(image) + (size_t)prev * pitch, pitch,
+                                 (size_t)width * bpp, r1 - prev, cudaMemcpyHostToDevice, ctx->copy_stream));
+        }
+        CK(cudaEventRecord(ctx->stripe_events[k], ctx->copy_stream));
+        prev = std::max(prev, r1);
+    }
+    return GLCM_OK;
+}
+
+std::string batch_key(const glcm_desc* d, int n, const glcm_ctx* ctx)
+{
+    std::string k;
+    k.reserve((size_t)n * 96);
+    char buf[160];
+    for (int i = 0; i < n; ++i) {
+        snprintf(buf, sizeof buf, "%p,%d,%d,%zu,%d,%d,%d,%p,%p,%p|", d[i].image, d[i].width, d[i].height,
+                 d[i].pitch_bytes, d[i].dtype, d[i].levels, d[i].flags, (void*)d[i].counts,
+                 (void*)d[i].normalized, (void*)d[i].features);
+        k += buf;
+        for (int o = 0; o < d[i].n_offsets; ++o) {
+            snprintf(buf, sizeof buf, "%d:%d;", d[i].offsets[o].dx, d[i].offsets[o].dy);
+            k += buf;
+        }
+    }
+    k += ctx->timing ? "T" : "U";
+    for (const auto& kv : ctx->overrides) {
+        snprintf(buf, sizeof buf, "#%lld:%d,%d,%d,%d,%d", kv.first, kv.second.threads, kv.second.rshift,
+                 kv.second.pack, kv.second.agg, kv.second.band_rows);
+        k += buf;
+    }
+    return k;
+}
+
+void destroy_graph(GraphEntry& g)
+{
+    if (g.exec)
+        cudaGraphExecDestroy(g.exec);
+    if (g.cap_a)
+        cudaEventDestroy(g.cap_a);
+    if (g.cap_b)
+        cudaEventDestroy(g.cap_b);
+    for (DevBuf* b : {&g.jobs, &g.offs, &g.feat})
+        if (b->p)
+            cudaFree(b->p);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Public API
+// ---------------------------------------------------------------------------
+
+extern "C" int glcm_offset_from_angle(int d, int theta_deg, glcm_offset* out)
+{
+    if (!out || d < 1)
+        return GLCM_ERR_ARG;
+    switch (theta_deg) {
+        case 0: *out = {d, 0}; return GLCM_OK;
+        case 45: *out = {d, -d}; return GLCM_OK;
+        case 90: *out = {0, -d}; return GLCM_OK;
+        case 135: *out = {-d, -d}; return GLCM_OK;
+        default: return GLCM_ERR_ARG;
+    }
+}
+
+extern "C" const char* glcm_last_error(const glcm_ctx* ctx)
+{
+    return ctx ? ctx->err.c_str() : g_create_error.c_str();
+}
+
+extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, void* cuda_stream)
+{
+    glcm_ctx* ctx = nullptr;
+    if (!out)
+        return fail(nullptr, GLCM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(nullptr, GLCM_ERR_ARG, "no CUDA device %d", device);
+    }
+    if (cudaSetDevice(device) != cudaSuccess)
+        return fail(nullptr, GLCM_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    ctx = new glcm_ctx();
+    ctx->device = device;
+    ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)1 << 30;
+    cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    if (cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return fail(nullptr, GLCM_ERR_CUDA, "cudaStreamCreate failed");
+        }
+        ctx->own_stream = true;
+    }
+    if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
+        glcm_destroy(ctx);
+        return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
+    }
+    if (fault_injected("alloc") || cudaMalloc(&ctx->d_words, 64) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->d_words = nullptr;
+        glcm_destroy(ctx);
+        return fail(nullptr, GLCM_ERR_NOMEM, "could not allocate the context's device words");
+    }
+    cudaMemset(ctx->d_words, 0, 64);
+    cudaDeviceSynchronize();
+    *out = ctx;
+    return GLCM_OK;
+}
+
+extern "C" int glcm_destroy(glcm_ctx* ctx)
+{
+    if (!ctx)
+        return GLCM_OK;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream)
+        cudaStreamSynchronize(ctx->stream);
+    if (ctx->copy_stream)
+        cudaStreamSynchronize(ctx->copy_stream);
+    for (auto& kv : ctx->graphs)
+        destroy_graph(kv.second);
+    for (DevBuf* b : {&ctx->jobs, &ctx->offs, &ctx->feat, &ctx->work, &ctx->img, &ctx->counts, &ctx->norm,
+                      &ctx->featout, &ctx->maps})
+        if (b->p)
+            cudaFree(b->p);
+    if (ctx->d_words)
+        cudaFree(ctx->d_words);
+    if (ctx->h_stage)
+        cudaFreeHost(ctx->h_stage);
+    for (auto& p : ctx->pool) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto& p : ctx->pending) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    for (auto e : ctx->stripe_events)
+        cudaEventDestroy(e);
+    if (ctx->ev_stage)
+        cudaEventDestroy(ctx->ev_stage);
+    if (ctx->copy_stream)
+        cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->own_stream && ctx->stream)
+        cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return GLCM_OK;
+}
+
+extern "C" int glcm_synchronize(glcm_ctx* ctx)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    return collect_device_errors(ctx);
+}
+
+extern "C" int glcm_set_timing(glcm_ctx* ctx, int enable)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    ctx->timing = enable != 0;
+    return GLCM_OK;
+}
+
+extern "C" int glcm_get_timing(glcm_ctx* ctx, double* vote_ms, long long* vote_launches, long long* kernel_launches,
+                               int reset)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (auto& p : ctx->pending) {
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, p.a, p.b));
+        ctx->vote_ms += ms;
+        ctx->pool.push_back(p);
+    }
+    ctx->pending.clear();
+    if (vote_ms)
+        *vote_ms = ctx->vote_ms;
+    if (vote_launches)
+        *vote_launches = ctx->vote_launches;
+    if (kernel_launches)
+        *kernel_launches = ctx->kernel_launches;
+    if (reset) {
+        ctx->vote_ms = 0;
+        ctx->vote_launches = 0;
+        ctx->kernel_launches = 0;
+    }
+    return GLCM_OK;
+}
+
+extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, int dtype, int threads,
+                                    int log2_copies, int pack, int aggregate, int band_rows)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    const int bpp = dtype == GLCM_U16 ? 2 : 1;
+    const long long key = cfg_key(levels, n_offsets, bpp);
+    if (threads <= 0) {
+        ctx->overrides.erase(key);
+        return GLCM_OK;
+    }
+    if (threads % 32 || threads < 64 || threads > kMaxThreads || log2_copies < -1 || log2_copies > 5 ||
+        (pack != 1 && pack != 2) || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1)
+        return fail(ctx, GLCM_ERR_ARG, "invalid vote config");
+    if (log2_copies >= 0) {
+        const long long words = (long long)levels * levels << log2_copies;
+        if (words > hist_budget_words(ctx))
+            return fail(ctx, GLCM_ERR_ARG, "one offset's histograms need %lld words > %d", words,
+                        hist_budget_words(ctx));
+        if (pack == 2 && 65535ll * (1 << log2_copies) / ((16 / bpp) * (long long)threads) < 1)
+            return fail(ctx, GLCM_ERR_ARG, "16-bit counters cannot be bounded with this config");
+    }
+    VoteCfg c;
+    c.threads = threads;
+    c.rshift = log2_copies;
+    c.pack = pack;
+    c.agg = aggregate ? 1 : 0;
+    c.band_rows = band_rows;
+    ctx->overrides[key] = c;
+    return GLCM_OK;
+}
+
+extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes, int dtype,
+                            int levels, const glcm_offset* offsets, int n_offsets, int flags, uint32_t* counts,
+                            float* normalized)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, offsets, n_offsets));
+    if (!counts)
+        return fail(ctx, GLCM_ERR_ARG, "counts is NULL");
+    const int bpp = dtype == GLCM_U8 ? 1 : 2;
+    const bool dev_img = is_device_ptr(image);
+    const bool dev_counts = is_device_ptr(counts);
+    const bool want_norm = (flags & GLCM_NORMALIZE) && normalized;
+    const bool dev_norm = want_norm && is_device_ptr(normalized);
+    const size_t nn = (size_t)levels * levels;
+    uint32_t* d_counts = counts;
+    if (!dev_counts) {
+        TRY(ensure(ctx, ctx->counts, n_offsets * nn * 4));
+        d_counts = static_cast<uint32_t*>(ctx->counts.p);
+    }
+    float* d_norm = normalized;
+    if (want_norm && !dev_norm) {
+        TRY(ensure(ctx, ctx->norm, n_offsets * nn * 4));
+        d_norm = static_cast<float*>(ctx->norm.p);
+    }
+    int dymin = 0, dymax = 0;
+    for (int k = 0; k < n_offsets; ++k) {
+        dymin = std::min(dymin, offsets[k].dy);
+        dymax = std::max(dymax, offsets[k].dy);
+    }
+
+    // Stripes (Sec. III): anchor rows [r_k, r_{k+1}); stripe k's copy ends at
+    // r_{k+1} + max(dy, 0) so its partner rows are on the device.
+    std::vector<int> anchors_cut;
+    int n_stripes = 1;
+    if (!dev_img) {
+        const long long bytes = (long long)height * width * bpp;
+        n_stripes = (int)std::max<long long>(1, std::min<long long>(8, bytes / (4ll << 20)));
+        n_stripes = std::min(n_stripes, height);
+    }
+    for (int k = 1; k <= n_stripes; ++k)
+        anchors_cut.push_back((int)((long long)height * k / n_stripes));
+    const uint8_t* d_img = static_cast<const uint8_t*>(image);
+    size_t dpitch = pitch_bytes;
+    if (!dev_img) {
+        std::vector<int> copy_cut;
+        for (int r : anchors_cut)
+            copy_cut.push_back(std::min(height, r + dymax));
+        TRY(stage_host_image(ctx, image, width, height, pitch_bytes, bpp, ctx->img, dpitch, copy_cut));
+        d_img = static_cast<const uint8_t*>(ctx->img.p);
+    }
+    // Zero the counts once, then one vote launch per stripe.
+    CK(cudaMemsetAsync(d_counts, 0, n_offsets * nn * 4, ctx->stream));
+    int r0 = 0;
+    for (int k = 0; k < n_stripes; ++k) {
+        const int r1 = anchors_cut[k];
+        if (!dev_img)
+            CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[k], 0));
+        VotePlan plan;
+        ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
+                    offsets, n_offsets, d_counts, r0, r1};
+        TRY(plan_image(ctx, s, plan, target_items(ctx)));
+        std::vector<FeatJob> none;
+        TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
+        TRY(enqueue_vote(ctx, plan, ctx->jobs, ctx->offs, false, false, nullptr));
+        r0 = r1;
+    }
+    if (want_norm) {
+        std::vector<FeatJob> fj(n_offsets);
+        for (int o = 0; o < n_offsets; ++o)
+            fj[o] = FeatJob{d_counts + o * nn, d_norm + o * nn, nullptr, levels, (flags & GLCM_SYMMETRIC) ? 1 : 0};
+        VotePlan empty;
+        TRY(upload_tables(ctx, empty, fj, ctx->jobs, ctx->offs, ctx->feat));
+        TRY(enqueue_features(ctx, fj, ctx->feat, levels, false, nullptr));
+    }
+    if (!dev_counts)
+        CK(cudaMemcpyAsync(counts, d_counts, n_offsets * nn * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (want_norm && !dev_norm)
+        CK(cudaMemcpyAsync(normalized, d_norm, n_offsets * nn * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    const bool sync = ctx->own_stream || !dev_img || !dev_counts || (want_norm && !dev_norm);
+    if (sync)
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}
+
+extern "C" int glcm_compute_naive(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes,
+                                  int dtype, int levels, glcm_offset offset, int flags, uint32_t* counts)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, &offset, 1));
+    if (!is_device_ptr(image) || !is_device_ptr(counts))
+        return fail(ctx, GLCM_ERR_ARG, "glcm_compute_naive takes device pointers only");
+    const size_t nn = (size_t)levels * levels;
+    CK(cudaMemsetAsync(counts, 0, nn * 4, ctx->stream));
+    CK(launch_naive(static_cast<const uint8_t*>(image), (long long)pitch_bytes, width, height,
+                    dtype == GLCM_U8 ? 1 : 2, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0, offset.dx, offset.dy,
+                    counts, ctx->d_words, ctx->stream));
+    ctx->kernel_launches += 1;
+    if (ctx->own_stream)
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}
+
+extern "C" int glcm_features(glcm_ctx* ctx, const uint32_t* counts, int levels, int n_glcm, int flags,
+                             float* features)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (!counts || !features || n_glcm < 0 || levels < 2 || levels > GLCM_MAX_LEVELS)
+        return fail(ctx, GLCM_ERR_ARG, "glcm_features: bad arguments");
+    if (n_glcm == 0)
+        return GLCM_OK;
+    const size_t nn = (size_t)levels * levels;
+    const bool dev_c = is_device_ptr(counts), dev_f = is_device_ptr(features);
+    const uint32_t* d_c = counts;
+    float* d_f = features;
+    if (!dev_c) {
+        TRY(ensure(ctx, ctx->counts, n_glcm * nn * 4));
+        CK(cudaMemcpyAsync(ctx->counts.p, counts, n_glcm * nn * 4, cudaMemcpyHostToDevice, ctx->stream));
+        d_c = static_cast<const uint32_t*>(ctx->counts.p);
+    }
+    if (!dev_f) {
+        TRY(ensure(ctx, ctx->featout, (size_t)n_glcm * GLCM_N_FEATURES * 4));
+        d_f = static_cast<float*>(ctx->featout.p);
+    }
+    std::vector<FeatJob> fj(n_glcm);
+    for (int g = 0; g < n_glcm; ++g)
+        fj[g] = FeatJob{d_c + g * nn, nullptr, d_f + (size_t)g * GLCM_N_FEATURES, levels,
+                        (flags & GLCM_SYMMETRIC) ? 1 : 0};
+    VotePlan empty;
+    TRY(upload_tables(ctx, empty, fj, ctx->jobs, ctx->offs, ctx->feat));
+    TRY(enqueue_features(ctx, fj, ctx->feat, levels, false, nullptr));
+    if (!dev_f)
+        CK(cudaMemcpyAsync(features, d_f, (size_t)n_glcm * GLCM_N_FEATURES * 4, cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    if (ctx->own_stream || !dev_c || !dev_f)
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}
+
+namespace {
+
+// Build the plan and feature jobs of a batch whose images and outputs are on
+// the device.
+int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std::vector<FeatJob>& feats,
+               int& max_levels)
+{
+    max_levels = 2;
+    long long total_rows_strips = 0;
+    for (int i = 0; i < n; ++i) {
+        const int PX = descs[i].dtype == GLCM_U8 ? 16 : 8;
+        total_rows_strips += (long long)descs[i].height * ((descs[i].width + 32 * PX - 1) / (32 * PX));
+    }
+    for (int i = 0; i < n; ++i) {
+        const glcm_desc& d = descs[i];
+        const int bpp = d.dtype == GLCM_U8 ? 1 : 2;
+        // Work items in proportion to this image's share of the batch.
+        const long long rs = (long long)d.height * ((d.width + 32 * (16 / bpp) - 1) / (32 * (16 / bpp)));
+        const int tgt = (int)std::max<long long>(1, (long long)target_items(ctx) * 4 * rs /
+                                                        std::max<long long>(1, total_rows_strips));
+        ImageSpec s{static_cast<const uint8_t*>(d.image), (long long)d.pitch_bytes, d.width, d.height, bpp,
+                    d.levels, (d.flags & GLCM_INPUT_LEVELS) ? 1 : 0, d.offsets, d.n_offsets, d.counts, 0,
+                    d.height};
+        TRY(plan_image(ctx, s, plan, tgt));
+        max_levels = std::max(max_levels, d.levels);
+        const size_t nn = (size_t)d.levels * d.levels;
+        if (d.normalized || d.features) {
+            for (int o = 0; o < d.n_offsets; ++o)
+                feats.push_back(FeatJob{d.counts + o * nn, d.normalized ? d.normalized + o * nn : nullptr,
+                                        d.features ? d.features + (size_t)o * GLCM_N_FEATURES : nullptr, d.levels,
+                                        (d.flags & GLCM_SYMMETRIC) ? 1 : 0});
+        }
+    }
+    return GLCM_OK;
+}
+
+}  // namespace
+
+extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (n < 0 || (n > 0 && !descs))
+        return fail(ctx, GLCM_ERR_ARG, "bad batch");
+    if (n == 0)
+        return GLCM_OK;
+    bool all_dev = true, any_dev = false;
+    for (int i = 0; i < n; ++i) {
+        const glcm_desc& d = descs[i];
+        TRY(check_image_args(ctx, d.image, d.width, d.height, d.pitch_bytes, d.dtype, d.levels, d.offsets,
+                             d.n_offsets));
+        if (!d.counts)
+            return fail(ctx, GLCM_ERR_ARG, "desc %d: counts is NULL", i);
+        const bool dv = is_device_ptr(d.image) && is_device_ptr(d.counts) &&
+                        (!d.normalized || is_device_ptr(d.normalized)) && (!d.features || is_device_ptr(d.features));
+        all_dev &= dv;
+        any_dev |= dv;
+    }
+    if (!all_dev) {
+        // Host buffers: run each image through the stripe pipeline.
+        for (int i = 0; i < n; ++i) {
+            const glcm_desc& d = descs[i];
+            const int fl = d.flags | (d.normalized ? GLCM_NORMALIZE : 0);
+            TRY(glcm_compute(ctx, d.image, d.width, d.height, d.pitch_bytes, d.dtype, d.levels, d.offsets,
+                             d.n_offsets, fl, d.counts, d.normalized));
+            if (d.features)
+                TRY(glcm_features(ctx, d.counts, d.levels, d.n_offsets, d.flags & GLCM_SYMMETRIC, d.features));
+        }
+        return GLCM_OK;
+    }
+    const std::string key = batch_key(descs, n, ctx);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 16) {
+            cudaStreamSynchronize(ctx->stream);
+            for (auto& kv : ctx->graphs)
+                destroy_graph(kv.second);
+            ctx->graphs.clear();
+        }
+        VotePlan plan;
+        std::vector<FeatJob> feats;
+        int max_levels = 2;
+        TRY(plan_batch(ctx, descs, n, plan, feats, max_levels));
+        GraphEntry ge;
+        // Split the plan by pixel type: the vote kernel is templated on it.
+        VotePlan p8, p16;
+        for (int pass = 0; pass < 2; ++pass) {
+            VotePlan& dst = pass == 0 ? p8 : p16;
+            dst.threads = plan.threads;
+            dst.bpp = pass == 0 ? 1 : 2;
+            for (const VoteJob& j : plan.jobs) {
+                if (j.bpp != dst.bpp)
+                    continue;
+                VoteJob c = j;
+                const int cnt_items = (c.n_strips) * ((c.y_end - c.y_begin + c.band_rows - 1) / c.band_rows);
+                c.off0 = (int)dst.offs.size();
+                for (int k = 0; k < j.n_off; ++k)
+                    dst.offs.push_back(plan.offs[j.off0 + k]);
+                c.item0 = dst.n_items;
+                dst.n_items += cnt_items;
+                dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
+                dst.jobs.push_back(c);
+            }
+        }
+        // Tables: one device buffer each, p8's entries then p16's.
+        VotePlan all;
+        all.jobs = p8.jobs;
+        all.jobs.insert(all.jobs.end(), p16.jobs.begin(), p16.jobs.end());
+        for (size_t k = p8.jobs.size(); k < all.jobs.size(); ++k)
+            all.jobs[k].off0 += (int)p8.offs.size();
+        all.offs = p8.offs;
+        all.offs.insert(all.offs.end(), p16.offs.begin(), p16.offs.end());
+        TRY(upload_tables(ctx, all, feats, ge.jobs, ge.offs, ge.feat));
+        CK(cudaStreamSynchronize(ctx->stream));
+        DevBuf j16, o16;
+        j16.p = static_cast<VoteJob*>(ge.jobs.p) + p8.jobs.size();
+        o16.p = static_cast<VoteOffset*>(ge.offs.p);  // off0 already shifted
+        DevBuf j8 = ge.jobs;
+        // One direct run produces this call's results and sets every kernel
+        // attribute before capture.
+        if (!p8.jobs.empty())
+            TRY(enqueue_vote(ctx, p8, j8, ge.offs, true, false, nullptr));
+        if (!p16.jobs.empty())
+            TRY(enqueue_vote(ctx, p16, j16, o16, true, false, nullptr));
+        TRY(enqueue_features(ctx, feats, ge.feat, max_levels, false, nullptr));
+        TRY(collect_device_errors(ctx));
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+        int rc = GLCM_OK;
+        if (rc == GLCM_OK && !p8.jobs.empty())
+            rc = enqueue_vote(ctx, p8, j8, ge.offs, true, true, &ge);
+        if (rc == GLCM_OK && !p16.jobs.empty())
+            rc = enqueue_vote(ctx, p16, j16, o16, true, true, &ge);
+        if (rc == GLCM_OK)
+            rc = enqueue_features(ctx, feats, ge.feat, max_levels, true, &ge);
+        cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
+        if (rc != GLCM_OK) {
+            if (graph)
+                cudaGraphDestroy(graph);
+            destroy_graph(ge);
+            return rc;
+        }
+        CK(ce);
+        ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+        if (ce == cudaSuccess && ctx->timing) {
+            // Find the event-record nodes that bracket the first vote kernel.
+            size_t nnodes = 0;
+            cudaGraphGetNodes(graph, nullptr, &nnodes);
+            std::vector<cudaGraphNode_t> nodes(nnodes);
+            cudaGraphGetNodes(graph, nodes.data(), &nnodes);
+            for (auto nd : nodes) {
+                cudaGraphNodeType t;
+                cudaGraphNodeGetType(nd, &t);
+                if (t == cudaGraphNodeTypeEventRecord) {
+                    cudaEvent_t ev = nullptr;
+                    cudaGraphEventRecordNodeGetEvent(nd, &ev);
+                    if (ev == ge.cap_a)
+                        ge.ev_start = nd;
+                    else if (ev == ge.cap_b)
+                        ge.ev_stop = nd;
+                }
+            }
+        }
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            destroy_graph(ge);
+            return fail(ctx, GLCM_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ce));
+        }
+        it = ctx->graphs.emplace(key, ge).first;
+        // The direct run above already produced this batch's results.
+        return ctx->own_stream ? collect_device_errors(ctx) : GLCM_OK;
+    }
+    GraphEntry& ge = it->second;
+    TimedPair tp{};
+    const bool timed = ctx->timing && ge.ev_start && ge.ev_stop && ge.n_vote_kernels == 1;
+    if (timed) {
+        tp = take_pair(ctx);
+        CK(cudaGraphExecEventRecordNodeSetEvent(ge.exec, ge.ev_start, tp.a));
+        CK(cudaGraphExecEventRecordNodeSetEvent(ge.exec, ge.ev_stop, tp.b));
+    }
+    CK(cudaGraphLaunch(ge.exec, ctx->stream));
+    if (timed)
+        ctx->pending.push_back(tp);
+    ctx->kernel_launches += ge.n_kernels;
+    ctx->vote_launches += ge.n_vote_kernels;
+    if (ctx->own_stream)
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}
+
+extern "C" int glcm_windows(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes, int dtype,
+                            int levels, int win, int stride, const glcm_offset* offsets, int n_offsets, int flags,
+                            uint32_t* counts, float* maps)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, offsets, n_offsets));
+    if (n_offsets > GLCM_MAX_WINDOW_OFFSETS)
+        return fail(ctx, GLCM_ERR_ARG, "at most %d window offsets", GLCM_MAX_WINDOW_OFFSETS);
+    if (win < 1 || stride < 1 || win > width || win > height)
+        return fail(ctx, GLCM_ERR_ARG, "window %d / stride %d do not fit %d x %d", win, stride, width, height);
+    for (int k = 0; k < n_offsets; ++k)
+        if (abs(offsets[k].dx) >= win || abs(offsets[k].dy) >= win)
+            return fail(ctx, GLCM_ERR_ARG, "offset %d does not fit the window", k);
+    if (!counts && !maps)
+        return fail(ctx, GLCM_ERR_ARG, "need counts or maps");
+    const int bpp = dtype == GLCM_U8 ? 1 : 2;
+    const int nwx = (width - win) / stride + 1, nwy = (height - win) / stride + 1;
+    const size_t nn = (size_t)levels * levels;
+    const size_t n_counts = (size_t)nwx * nwy * n_offsets * nn;
+    const size_t n_maps = (size_t)GLCM_N_WINDOW_MAPS * n_offsets * nwx * nwy;
+    const bool dev_img = is_device_ptr(image);
+    const bool dev_c = counts && is_device_ptr(counts);
+    const bool dev_m = maps && is_device_ptr(maps);
+    const uint8_t* d_img = static_cast<const uint8_t*>(image);
+    size_t dpitch = pitch_bytes;
+    if (!dev_img) {
+        std::vector<int> cut{height};
+        TRY(stage_host_image(ctx, image, width, height, pitch_bytes, bpp, ctx->img, dpitch, cut));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[0], 0));
+        d_img = static_cast<const uint8_t*>(ctx->img.p);
+    }
+    uint32_t* d_c = counts;
+    float* d_m = maps;
+    if (counts && !dev_c) {
+        TRY(ensure(ctx, ctx->counts, n_counts * 4));
+        d_c = static_cast<uint32_t*>(ctx->counts.p);
+    }
+    if (maps && !dev_m) {
+        TRY(ensure(ctx, ctx->maps, n_maps * 4));
+        d_m = static_cast<float*>(ctx->maps.p);
+    }
+    WindowParams wp{};
+    wp.img = d_img;
+    wp.pitch = (long long)dpitch;
+    wp.W = width;
+    wp.H = height;
+    wp.bpp = bpp;
+    wp.levels = levels;
+    wp.levels_mode = (flags & GLCM_INPUT_LEVELS) ? 1 : 0;
+    wp.win = win;
+    wp.stride = stride;
+    wp.nwx = nwx;
+    wp.nwy = nwy;
+    wp.n_off = n_offsets;
+    for (int k = 0; k < n_offsets; ++k) {
+        wp.dx[k] = offsets[k].dx;
+        wp.dy[k] = offsets[k].dy;
+    }
+    wp.symmetric = (flags & GLCM_SYMMETRIC) ? 1 : 0;
+    wp.counts = d_c;
+    wp.maps = d_m;
+    wp.err = ctx->d_words;
+    cudaError_t e = launch_windows(wp, ctx->stream);
+    if (e == cudaErrorInvalidConfiguration) {
+        cudaGetLastError();
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "window histograms do not fit shared memory");
+    }
+    CK(e);
+    ctx->kernel_launches += 1;
+    if (counts && !dev_c)
+        CK(cudaMemcpyAsync(counts, d_c, n_counts * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (maps && !dev_m)
+        CK(cudaMemcpyAsync(maps, d_m, n_maps * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->own_stream || !dev_img || (counts && !dev_c) || (maps && !dev_m))
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}

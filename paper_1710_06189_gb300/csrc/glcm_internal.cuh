@@ -1,0 +1,113 @@
+// Internal structures shared by the host planner (glcm_capi.cu) and the
+// kernels.  Not part of the public ABI (include/glcm.h is).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace glcm {
+
+// Fast-path horizontal reach: a lane holds its own pixels plus one word of
+// quantized levels (4 levels) from each neighbouring lane.
+constexpr int kFastMaxDx = 4;
+constexpr int kMaxThreads = 1024;
+// Bounded spin limit for any device-side wait (none on the vote path today;
+// kept for the persistent serving kernels).
+constexpr long long kSpinLimit = 1ll << 26;
+
+// Device error bits written into the context's error word.
+enum : unsigned {
+    kErrRange = 1u,     // a pixel >= N in levels mode (pair skipped)
+    kErrInternal = 2u,  // an index check failed inside a kernel (access skipped)
+    kErrTimeout = 4u,   // a bounded wait gave up
+};
+
+// One histogram target: one image and the group of offsets voted together.
+struct VoteJob {
+    const uint8_t* img;
+    long long pitch;   // bytes between rows
+    int W, H;
+    int bpp;           // 1 (uint8) or 2 (uint16)
+    int levels;        // N
+    int log2n;         // log2(N) if N is a power of two, else -1
+    int levels_mode;   // pixels already are levels (< N)
+    int aligned;       // base and pitch are 16-byte aligned
+    int n_off;         // offsets in this job
+    int off0;          // first entry in the offsets table
+    int rshift;        // log2(copies): R = 1 << rshift private copies
+    int pack;          // 1: uint32 counters; 2: two uint16 counters per word
+    int agg;           // warp aggregation with match.any before each add
+    int hist_words;    // shared words this job uses: ceil(n_off/pack)*N*N*R
+    int item0;         // first work item of this job in the launch
+    int n_strips;      // column strips of 32 lanes x 16 bytes
+    int band_rows;     // anchor rows per work item
+    int y_begin, y_end;  // anchor rows voted by this job ([0, H) for a whole image)
+    uint32_t* out;     // counts: offset slot s at out + s*N*N
+};
+
+struct VoteOffset {
+    int dx, dy;
+    int slot;          // output GLCM index within the job
+    int pad;
+};
+
+// A work item: one column strip (32 lanes x 16 bytes) of one job and a band
+// of anchor rows; item k of job j is strip (k - item0) % n_strips of band
+// (k - item0) / n_strips.
+struct VoteItem {
+    int job, x0, y0, y1;
+};
+
+struct VoteParams {
+    const VoteJob* jobs;
+    int n_jobs;
+    const VoteOffset* offs;
+    int n_items;
+    int max_hist_words;
+    unsigned* item_counter;  // zeroed before each launch
+    unsigned* err;           // error bits (kErr*)
+};
+
+// Epilogue: symmetrize / normalize / Haralick features for one GLCM.
+struct FeatJob {
+    const uint32_t* counts;  // N*N
+    float* normalized;       // N*N or null
+    float* features;         // 14 or null
+    int levels;
+    int symmetric;
+};
+
+struct FeatParams {
+    const FeatJob* jobs;
+    int n_jobs;
+    float* work;             // scratch for large-N singular value sweeps
+    long long work_stride;   // floats per job in `work`
+    unsigned* err;
+};
+
+// Sliding-window local GLCMs.
+struct WindowParams {
+    const uint8_t* img;
+    long long pitch;
+    int W, H, bpp, levels, levels_mode;
+    int win, stride, nwx, nwy;
+    int n_off;
+    int dx[8], dy[8];
+    int symmetric;
+    uint32_t* counts;   // nwy*nwx*n_off*N*N or null
+    float* maps;        // 4*n_off*nwy*nwx or null  [map][offset][wy][wx]
+    unsigned* err;
+};
+
+// Launchers (defined in the .cu files).
+cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem,
+                        cudaStream_t s);
+cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
+                         int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
+                         cudaStream_t s);
+cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s);
+size_t features_smem_bytes(int max_levels);
+cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
+int vote_max_smem_optin();
+int vote_blocks_per_sm(int bpp, int threads, size_t smem);
+
+}  // namespace glcm

@@ -18,3 +18,22 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def gctx():
+    """A libglcm context on cuda:0 (private stream, synchronous calls)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1710_06189_gb300 import build as b
+    b.build()
+    import paper_1710_06189_gb300 as G
+    c = G.Context(0, hbm_budget_bytes=8 << 30)
+    yield c
+    c.close()
+
+
+def to_u32(t):
+    import numpy as np
+    return t.detach().cpu().numpy().view(np.uint32)

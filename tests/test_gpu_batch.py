@@ -1,0 +1,68 @@
+"""Batched launches: many images of uneven sizes and types in one persistent
+launch give, per image, exactly what the image gives alone; the graph
+replay gives the same again; the full contention sweep at 4096^2 (the
+benchmark's launch) matches the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import glcm_synth as S
+import oracle
+import paper_1710_06189_gb300 as G
+from conftest import to_u32
+from featcheck import assert_features, assert_normalized
+
+pytestmark = pytest.mark.gpu
+
+
+def _jobs(seed=0):
+    rng = np.random.default_rng(seed)
+    jobs = []
+    for k in range(9):
+        h, w = int(rng.integers(1, 700)), int(rng.integers(1, 1500))
+        u16 = k % 3 == 2
+        n = int(rng.choice([8, 16, 32, 64, 256]))
+        kind = ["iid", "smooth", "constant"][k % 3]
+        img = S.image(kind, 100 + k, h, w, np.uint16 if u16 else np.uint8, sigma=3.0)
+        offs = S.offsets_for((1, 2)) if k % 2 else S.CONTENTION_OFFSETS
+        jobs.append((img, n, offs, G.GLCM_SYMMETRIC if k % 2 else 0))
+    return jobs
+
+
+def test_batch_equals_alone_and_oracle(gctx):
+    jobs = _jobs()
+    spec = [dict(image=torch.from_numpy(im).cuda(), levels=n, offsets=o, flags=f, normalized=True, features=True)
+            for im, n, o, f in jobs]
+    for rep in range(3):  # first call captures, later calls replay the graph
+        outs = gctx.batch(spec)
+        torch.cuda.synchronize()
+        for (im, n, o, f), (c, nm, ft) in zip(jobs, outs):
+            P = oracle.glcm(im, n, o)
+            assert np.array_equal(to_u32(c), P), (im.shape, n, rep)
+            alone = gctx.compute(torch.from_numpy(im).cuda(), n, o, f)
+            fa = gctx.features(alone, n, symmetric=bool(f & 1))
+            torch.cuda.synchronize()
+            assert np.array_equal(to_u32(alone), P)
+            assert np.array_equal(ft.cpu().numpy(), fa.cpu().numpy())
+            sym = bool(f & 1)
+            Sm = oracle.symmetrize(P) if sym else P.astype(np.uint64)
+            assert_normalized(nm.cpu().numpy(), oracle.normalize(Sm))
+            assert_features(ft.cpu().numpy(), oracle.haralick_batch(P, sym), n)
+
+
+@pytest.mark.slow
+def test_contention_sweep_full_size(gctx):
+    """The benchmark's batch: 12 images of 4096^2, 4 offsets each, symmetric
+    normalized GLCMs and features, one graph launch."""
+    jobs = S.contention_jobs(4096)
+    spec = [dict(image=torch.from_numpy(j["image"]).cuda(), levels=j["levels"], offsets=j["offsets"],
+                 flags=G.GLCM_SYMMETRIC, normalized=True, features=True) for j in jobs]
+    gctx.batch(spec)
+    outs = gctx.batch(spec)  # graph replay
+    torch.cuda.synchronize()
+    for j, (c, nm, ft) in zip(jobs, outs):
+        P = oracle.glcm(j["image"], j["levels"], j["offsets"])
+        assert np.array_equal(to_u32(c), P), (j["kind"], j["levels"])
+        assert_features(ft.cpu().numpy(), oracle.haralick_batch(P, True), j["levels"],
+                        what=f'{j["kind"]} N={j["levels"]}')
+        assert_normalized(nm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)))

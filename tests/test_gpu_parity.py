@@ -1,0 +1,157 @@
+"""CUDA path vs the CPU oracle: counts bit-exact, epilogue within tolerance.
+
+Sizes span several column strips, several row bands and ragged tails; the
+edge cases are 1x1 images, offsets longer than the image (empty GLCMs),
+unaligned pitches, odd widths, non-power-of-two N, wide offsets that take the
+per-pixel path, and out-of-range pixels in levels mode."""
+import numpy as np
+import pytest
+import torch
+
+import glcm_synth as S
+import oracle
+import paper_1710_06189_gb300 as G
+from conftest import to_u32
+from featcheck import assert_features, assert_normalized
+
+pytestmark = pytest.mark.gpu
+
+C4 = S.CONTENTION_OFFSETS
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(gctx, img, n, offs, flags=0):
+    c = gctx.compute(dev(img), n, offs, flags)
+    torch.cuda.synchronize()
+    return to_u32(c)
+
+
+def test_plain_512_levels(gctx):
+    img, n, offs = S.plain_512()
+    got = run(gctx, img, n, offs, G.GLCM_INPUT_LEVELS)
+    want = oracle.glcm(img, n, offs, levels_mode=True)
+    assert np.array_equal(got, want)
+    assert int(got.sum()) == 511 * 512
+
+
+@pytest.mark.parametrize("kind", ["iid", "smooth", "constant"])
+@pytest.mark.parametrize("n", [8, 16, 32, 256])
+def test_contention_reduced(gctx, kind, n):
+    img = S.image(kind, 11 + n, 777, 1031, np.uint8, sigma=8.0)
+    got = run(gctx, img, n, C4)
+    assert np.array_equal(got, oracle.glcm(img, n, C4))
+
+
+@pytest.mark.parametrize("n", [8, 32])
+def test_u16_twelve_offsets(gctx, n):
+    img = S.iid(5, 333, 1111, np.uint16)
+    img[:, 600:] = S.smooth(6, 333, 511, 4.0, np.uint16)
+    offs = S.MULTISPECTRAL_OFFSETS
+    got = run(gctx, img, n, offs)
+    assert np.array_equal(got, oracle.glcm(img, n, offs))
+
+
+@pytest.mark.parametrize("h,w", [(1, 1), (1, 7), (5, 1), (3, 17), (40, 33), (65, 513), (130, 1000)])
+def test_small_and_ragged(gctx, h, w):
+    img = S.iid(h * 1000 + w, h, w, np.uint8)
+    offs = C4 + [(2, 0), (0, 3), (-4, 4), (4, -4)]
+    got = run(gctx, img, 16, offs)
+    assert np.array_equal(got, oracle.glcm(img, 16, offs))
+
+
+def test_unaligned_pitch_and_view(gctx):
+    base = S.iid(3, 70, 600, np.uint8)
+    view = torch.from_numpy(base).cuda()[:, 3:516]  # pitch 600, odd start: unaligned
+    c = gctx.compute(view, 32, C4)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_u32(c), oracle.glcm(np.ascontiguousarray(base[:, 3:516]), 32, C4))
+
+
+@pytest.mark.parametrize("n", [2, 3, 10, 100, 255])
+def test_non_power_of_two_levels(gctx, n):
+    img = S.smooth(n, 200, 700, 3.0, np.uint8)
+    for dt in (np.uint8, np.uint16):
+        im = img.astype(dt) * (257 if dt == np.uint16 else 1)
+        got = run(gctx, im, n, C4)
+        assert np.array_equal(got, oracle.glcm(im, n, C4)), dt
+
+
+def test_wide_offsets_and_positive_dy(gctx):
+    img = S.iid(9, 300, 900, np.uint8)
+    offs = [(7, 0), (-9, 2), (0, 12), (5, 5), (-30, -1), (600, 0), (0, 299), (1000, 0)]
+    got = run(gctx, img, 8, offs)
+    assert np.array_equal(got, oracle.glcm(img, 8, offs))
+
+
+def test_levels_mode_range_error_skips_pairs(gctx):
+    img = S.iid(4, 64, 640, np.uint8, 0, 8)
+    img[10, 100] = 9
+    img[33, 5] = 200
+    with pytest.raises(G.GlcmError) as ei:
+        gctx.compute(dev(img), 8, C4, G.GLCM_INPUT_LEVELS)
+    assert ei.value.status == G.binding.GLCM_ERR_RANGE
+    out = torch.empty((4, 8, 8), dtype=torch.int32, device="cuda")
+    with pytest.raises(G.GlcmError):
+        gctx.compute(dev(img), 8, C4, G.GLCM_INPUT_LEVELS, out=out)
+    want = oracle.glcm(img, 8, C4, levels_mode=True)
+    assert np.array_equal(to_u32(out), want)
+    # The context stays usable.
+    ok = S.iid(4, 64, 640, np.uint8, 0, 8)
+    assert np.array_equal(run(gctx, ok, 8, C4, G.GLCM_INPUT_LEVELS), oracle.glcm(ok, 8, C4, levels_mode=True))
+
+
+def test_u16_levels_mode(gctx):
+    img = S.iid(8, 90, 300, np.uint16, 0, 200)
+    got = run(gctx, img, 200, C4, G.GLCM_INPUT_LEVELS)
+    assert np.array_equal(got, oracle.glcm(img, 200, C4, levels_mode=True))
+
+
+def test_host_image_stripes(gctx):
+    img = S.smooth(21, 2100, 3000, 6.0, np.uint8)  # > 4 MiB: several stripes
+    offs = C4 + [(0, 2), (1, 3)]
+    c = torch.empty((len(offs), 32, 32), dtype=torch.int32)
+    G.glcm_compute(gctx.ctx, img, 3000, 2100, 3000, G.GLCM_U8, 32, offs, 0, c)
+    assert np.array_equal(c.numpy().view(np.uint32), oracle.glcm(img, 32, offs))
+
+
+@pytest.mark.parametrize("sym", [False, True])
+@pytest.mark.parametrize("n", [8, 32, 256])
+def test_normalize_and_features(gctx, sym, n):
+    img = S.image("smooth" if n != 256 else "iid", 30 + n, 400, 900, np.uint8, sigma=5.0)
+    flags = G.GLCM_SYMMETRIC if sym else 0
+    counts, norm = gctx.compute(dev(img), n, C4, flags, normalized=True)
+    feats = gctx.features(counts, n, symmetric=sym)
+    torch.cuda.synchronize()
+    P = oracle.glcm(img, n, C4)
+    assert np.array_equal(to_u32(counts), P)
+    Sm = oracle.symmetrize(P) if sym else P.astype(np.uint64)
+    assert_normalized(norm.cpu().numpy(), oracle.normalize(Sm), f"n={n} sym={sym}")
+    assert_features(feats.cpu().numpy(), oracle.haralick_batch(P, sym), n, what=f"n={n} sym={sym}")
+
+
+def test_features_of_special_matrices(gctx):
+    n = 16
+    mats = np.zeros((5, n, n), dtype=np.uint32)
+    mats[1, 3, 3] = 1000                        # one-hot
+    mats[2] = np.eye(n, dtype=np.uint32) * 7    # diagonal
+    mats[3] = 5                                 # uniform
+    px = np.arange(1, n + 1)
+    mats[4] = np.outer(px, px[::-1])            # independent
+    c = torch.from_numpy(mats.view(np.int32)).cuda()
+    f = gctx.features(c, n).cpu().numpy()
+    want = oracle.haralick_batch(mats, False)
+    assert_features(f, want, n, what="special")
+    assert np.all(f[0] == 0)
+
+
+def test_naive_scheme1_matches(gctx):
+    img = S.smooth(2, 300, 400, 4.0, np.uint8)
+    c = torch.empty((8, 8), dtype=torch.int32, device="cuda")
+    d = dev(img)
+    for off in C4:
+        G.glcm_compute_naive(gctx.ctx, d, 400, 300, 400, G.GLCM_U8, 8, off, 0, c)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_u32(c), oracle.glcm(img, 8, [off])[0])

@@ -1,0 +1,36 @@
+"""Sliding-window local GLCMs and maps vs the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import glcm_synth as S
+import oracle
+from conftest import to_u32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("sym", [False, True])
+def test_windows_counts_and_maps(gctx, sym):
+    img = S.smooth(3, 150, 203, 4.0, np.uint8)
+    offs = S.CONTENTION_OFFSETS
+    c, m = gctx.windows(torch.from_numpy(img).cuda(), 16, 15, 4, offs, flags=1 if sym else 0)
+    torch.cuda.synchronize()
+    want = oracle.window_glcm(img, 16, offs, 15, 4)
+    nwy, nwx = (150 - 15) // 4 + 1, (203 - 15) // 4 + 1
+    got = to_u32(c).reshape(nwy * nwx, 4, 16, 16)
+    assert np.array_equal(got, want)
+    maps = oracle.window_maps(want, symmetric=sym)  # (4, n_win, n_off)
+    g = m.cpu().numpy().reshape(4, 4, nwy * nwx).transpose(0, 2, 1).astype(np.float64)
+    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / 256, 1.0, 1.0])[:, None, None])
+    err = np.abs(g - maps) / scale
+    assert err.max() <= 1e-5, err.max()
+
+
+def test_windows_levels_and_u16(gctx):
+    img = S.iid(5, 40, 45, np.uint16)
+    offs = [(1, 0), (0, -2), (-3, 1)]
+    c, _ = gctx.windows(torch.from_numpy(img).cuda(), 32, 9, 3, offs, maps=False)
+    torch.cuda.synchronize()
+    want = oracle.window_glcm(img, 32, offs, 9, 3)
+    assert np.array_equal(to_u32(c).reshape(want.shape), want)
