@@ -290,7 +290,7 @@ def main():
 
     peak, peak_kind = load_peaks()
     avg_vote_ms = vote_ms / max(1, vote_n)
-    achieved = bytes_step / (avg_vote_ms * 1e-3) / 1e9 if vote_n else None
+    achieved = bytes_step / (avg_vote_ms * 1e-3) / 1e9 if (vote_n and avg_vote_ms > 0) else None
     traffic = profiled_traffic("vote_contention_4096.md")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -249,6 +249,155 @@ __device__ float jacobi_sigma_max(float* A, int m, int n, int* s_flag, float* s_
     return sqrtf(m2);
 }
 
+// Largest singular value of the m x n matrix A (column-major, leading dim m,
+// in global scratch) by Golub-Kahan-Lanczos bidiagonalization with full
+// reorthogonalization, then bisection (Sturm counts) on the 2K x 2K
+// zero-diagonal tridiagonal matrix whose eigenvalues are +-sigma(B_K).
+// U (kMaxLanczos x m) and V ((kMaxLanczos + 1) x n) live after A.
+constexpr int kMaxLanczos = 96;
+
+__device__ float block_dot(const float* x, const float* y, int len, float* s_red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    float s = 0.f;
+    for (int r = threadIdx.x; r < len; r += blockDim.x)
+        s = fmaf(x[r], y[r], s);
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0)
+        s_red[warp] = s;
+    __syncthreads();
+    float t = 0.f;
+    for (int w = 0; w < nw; ++w)
+        t += s_red[w];
+    __syncthreads();
+    return t;
+}
+
+// x -= sum_i <x, Q_i> Q_i over the first k rows of Q (twice, classical GS).
+__device__ void reorth(float* x, const float* Q, int k, int len, float* s_coef, float* s_red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int i = warp; i < k; i += nw) {
+            const float* q = Q + (long long)i * len;
+            float s = 0.f;
+            for (int r = lane; r < len; r += 32)
+                s = fmaf(x[r], q[r], s);
+            for (int o = 16; o > 0; o >>= 1)
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0)
+                s_coef[i] = s;
+        }
+        __syncthreads();
+        for (int r = threadIdx.x; r < len; r += blockDim.x) {
+            float v = x[r];
+            for (int i = 0; i < k; ++i)
+                v = fmaf(-s_coef[i], Q[(long long)i * len + r], v);
+            x[r] = v;
+        }
+        __syncthreads();
+    }
+    (void)s_red;
+}
+
+__device__ float lanczos_sigma_max(const float* A, int m, int n, float* U, float* V, float* s_coef, float* s_red,
+                                   float* s_ab)
+{
+    const int K = min(kMaxLanczos, min(m, n));
+    float* v0 = V;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        v0[c] = 1.f + 0.01f * (float)((c * 37) % 11);  // fixed, not orthogonal to anything special
+    __syncthreads();
+    float nv = sqrtf(block_dot(v0, v0, n, s_red));
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        v0[c] /= nv;
+    __syncthreads();
+    int steps = 0;
+    float beta = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float* uk = U + (long long)k * m;
+        const float* vk = V + (long long)k * n;
+        // u = A v_k - beta_k u_{k-1}
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            float s = 0.f;
+            for (int c = 0; c < n; ++c)
+                s = fmaf(A[(long long)c * m + r], vk[c], s);
+            if (k > 0)
+                s = fmaf(-beta, U[(long long)(k - 1) * m + r], s);
+            uk[r] = s;
+        }
+        __syncthreads();
+        reorth(uk, U, k, m, s_coef, s_red);
+        const float alpha = sqrtf(block_dot(uk, uk, m, s_red));
+        if (threadIdx.x == 0)
+            s_ab[2 * k] = alpha;
+        if (!(alpha > 1e-30f))
+            break;
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            uk[r] /= alpha;
+        __syncthreads();
+        steps = k + 1;
+        // v = A^T u_k - alpha_k v_k
+        float* vn = V + (long long)(k + 1) * n;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        for (int c = warp; c < n; c += nw) {
+            const float* col = A + (long long)c * m;
+            float s = 0.f;
+            for (int r = lane; r < m; r += 32)
+                s = fmaf(col[r], uk[r], s);
+            for (int o = 16; o > 0; o >>= 1)
+                s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (lane == 0)
+                vn[c] = s - alpha * vk[c];
+        }
+        __syncthreads();
+        reorth(vn, V, k + 1, n, s_coef, s_red);
+        beta = sqrtf(block_dot(vn, vn, n, s_red));
+        if (threadIdx.x == 0)
+            s_ab[2 * k + 1] = beta;
+        if (!(beta > 1e-30f) || k + 1 == K)
+            break;
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            vn[c] /= beta;
+        __syncthreads();
+    }
+    __syncthreads();
+    // Off-diagonals of the Golub-Kahan tridiagonal: alpha_0, beta_1, alpha_1, ...
+    __shared__ float s_sig;
+    if (threadIdx.x == 0) {
+        const int L = 2 * steps - 1;  // number of off-diagonal entries used
+        float hi = 0.f;
+        for (int t = 0; t < L; ++t)
+            hi = fmaxf(hi, s_ab[t]);
+        hi *= 2.f;
+        float lo = 0.f;
+        for (int it = 0; it < 60 && L > 0; ++it) {
+            const float x = 0.5f * (lo + hi);
+            // Sturm count of eigenvalues < x of the (L+1) x (L+1) matrix.
+            int cnt = 0;
+            float q = -x;
+            if (q < 0.f)
+                ++cnt;
+            for (int t = 0; t < L; ++t) {
+                const float b = s_ab[t];
+                if (q == 0.f)
+                    q = -1e-30f;
+                q = -x - b * b / q;
+                if (q < 0.f)
+                    ++cnt;
+            }
+            if (cnt >= L + 1)
+                hi = x;  // all eigenvalues below x
+            else
+                lo = x;
+        }
+        s_sig = L > 0 ? 0.5f * (lo + hi) : 0.f;
+    }
+    __syncthreads();
+    return s_sig;
+}
+
 __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
 {
     const FeatJob J = p.jobs[blockIdx.x];
@@ -392,8 +541,17 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
     block_reduce_d<3>(dv, dd);
 
     float mcc = 0.f;
-    if (nr >= 2 && have_work)
-        mcc = jacobi_sigma_max(A, nr, nc, &s_flag, s_red);
+    if (nr >= 2 && have_work) {
+        if (nr <= kSmemA && nc <= kSmemA) {
+            mcc = jacobi_sigma_max(A, nr, nc, &s_flag, s_red);
+        } else {
+            float* Uw = A + (long long)nr * nc;
+            float* Vw = Uw + (long long)kMaxLanczos * nr;
+            __shared__ float s_coef[kMaxLanczos + 1];
+            __shared__ float s_ab[2 * kMaxLanczos + 2];
+            mcc = lanczos_sigma_max(A, nr, nc, Uw, Vw, s_coef, s_red, s_ab);
+        }
+    }
     if (!have_work && threadIdx.x == 0)
         atomicOr(p.err, kErrInternal);
 
@@ -421,6 +579,11 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
 }
 
 }  // namespace
+
+long long features_work_floats(int levels)
+{
+    return (long long)levels * levels + (long long)(2 * kMaxLanczos + 2) * levels + 64;
+}
 
 size_t features_smem_bytes(int max_levels)
 {

@@ -468,7 +468,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
             CK(cudaEventCreate(&ge->cap_a));
             CK(cudaEventCreate(&ge->cap_b));
         }
-        CK(cudaEventRecord(ge->cap_a, ctx->stream));
+        CK(cudaEventRecordWithFlags(ge->cap_a, ctx->stream, cudaEventRecordExternal));
     }
     CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, ctx->stream));
     if (time_it) {
@@ -476,7 +476,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         ctx->pending.push_back(tp);
     }
     if (capturing && ge && ctx->timing)
-        CK(cudaEventRecord(ge->cap_b, ctx->stream));
+        CK(cudaEventRecordWithFlags(ge->cap_b, ctx->stream, cudaEventRecordExternal));
     if (!capturing) {
         ctx->kernel_launches += 1;
         ctx->vote_launches += 1;
@@ -502,9 +502,10 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
         for (const auto& f : feats)
             any_feat |= f.features != nullptr;
         if (any_feat) {
-            TRY(ensure(ctx, ctx->work, feats.size() * (size_t)max_levels * max_levels * sizeof(float)));
+            const long long per = features_work_floats(max_levels);
+            TRY(ensure(ctx, ctx->work, feats.size() * (size_t)per * sizeof(float)));
             fp.work = static_cast<float*>(ctx->work.p);
-            fp.work_stride = (long long)max_levels * max_levels;
+            fp.work_stride = per;
         }
     }
     CK(launch_features(fp, max_levels, ctx->stream));

@@ -106,6 +106,7 @@ cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int 
                          cudaStream_t s);
 cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s);
 size_t features_smem_bytes(int max_levels);
+long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
 int vote_max_smem_optin();
 int vote_blocks_per_sm(int bpp, int threads, size_t smem);
