@@ -38,6 +38,7 @@ struct TimedPair {
 };
 
 struct GraphEntry {
+    cudaGraph_t graph = nullptr;  // kept alive: its nodes address the exec's event records
     cudaGraphExec_t exec = nullptr;
     cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;
     cudaEvent_t cap_a = nullptr, cap_b = nullptr;  // events recorded at capture
@@ -588,6 +589,8 @@ void destroy_graph(GraphEntry& g)
 {
     if (g.exec)
         cudaGraphExecDestroy(g.exec);
+    if (g.graph)
+        cudaGraphDestroy(g.graph);
     if (g.cap_a)
         cudaEventDestroy(g.cap_a);
     if (g.cap_b)
@@ -1088,7 +1091,7 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
                 }
             }
         }
-        cudaGraphDestroy(graph);
+        ge.graph = graph;
         if (ce != cudaSuccess) {
             destroy_graph(ge);
             return fail(ctx, GLCM_ERR_CUDA, "cudaGraphInstantiate failed: %s", cudaGetErrorString(ce));
