@@ -191,13 +191,17 @@ int glcm_set_timing(glcm_ctx *ctx, int enable);
 int glcm_get_timing(glcm_ctx *ctx, double *vote_ms, long long *vote_launches,
                     long long *kernel_launches, int reset);
 
-/* Vote-kernel tuning knobs for one (levels, offsets, pixel type) class, as
- * chosen by the autotuner: threads per CTA (256..1024), log2 of private
- * copies (-1 = vote into global memory, 0..5), counter packing (1 or 2),
- * warp aggregation (0/1), rows per work item.  Passing threads <= 0 removes
- * the override.  GLCM_ERR_ARG if the choice cannot hold the histograms. */
+/* Vote-kernel configuration for one (levels, offsets, pixel type) class, as
+ * chosen by the autotuner: threads per CTA (64..1024, multiple of 32), log2
+ * of the private histogram copies per CTA (0..5; copy c serves lanes with
+ * lane % copies == c), the shared-memory layout (0: one row of copies per
+ * bin; 1: two offsets' rows interleaved per bin; 2: two offsets as 16-bit
+ * halves of one word), and anchor rows per work item (0 = derived).  Offsets
+ * that do not fit one CTA's shared memory together are split over several
+ * passes, and a histogram whose one level row does not fit is rejected.
+ * threads <= 0 removes the override.  Errors: GLCM_ERR_ARG. */
 int glcm_set_vote_config(glcm_ctx *ctx, int levels, int n_offsets, int dtype, int threads,
-                         int log2_copies, int pack, int aggregate, int band_rows);
+                         int log2_copies, int layout, int band_rows);
 
 /* Scheme 1 of the paper (Sec. I.B): one thread per pixel and one global
  * atomic per vote, one offset.  Ablation baseline with the same inputs and

@@ -65,7 +65,7 @@ _PROTOS = {
     "glcm_set_timing": (c_int, [c_void_p, c_int]),
     "glcm_get_timing": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_longlong),
                                 ctypes.POINTER(c_longlong), c_int]),
-    "glcm_set_vote_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
+    "glcm_set_vote_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
     "glcm_compute_naive": (c_int, [c_void_p, c_void_p, c_int, c_int, c_size_t, c_int, c_int, glcm_offset,
                                    c_int, c_void_p]),
 }
@@ -203,9 +203,9 @@ def glcm_get_timing(ctx, reset: bool = False):
     return ms.value, nv.value, nk.value
 
 
-def glcm_set_vote_config(ctx, levels, n_offsets, dtype, threads, log2_copies, pack, aggregate, band_rows):
+def glcm_set_vote_config(ctx, levels, n_offsets, dtype, threads, log2_copies, layout, band_rows=0):
     return _check(ctx, load().glcm_set_vote_config(ctx, int(levels), int(n_offsets), int(dtype), int(threads),
-                                                   int(log2_copies), int(pack), int(aggregate), int(band_rows)))
+                                                   int(log2_copies), int(layout), int(band_rows)))
 
 
 def glcm_compute_naive(ctx, image, width, height, pitch_bytes, dtype, levels, offset, flags, counts):

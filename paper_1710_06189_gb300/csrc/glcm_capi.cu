@@ -27,9 +27,8 @@ struct DevBuf {
 
 struct VoteCfg {
     int threads = 1024;
-    int rshift = 5;
-    int pack = 1;
-    int agg = 0;
+    int rshift = 5;     // log2 private copies
+    int layout = 1;     // see VoteJob::layout
     int band_rows = 0;  // 0: derived from the launch size
 };
 
@@ -200,43 +199,61 @@ int hist_budget_words(const glcm_ctx* ctx)
     return (ctx->smem_optin - 4096) / 4;
 }
 
-// Default vote configuration: the most private copies (up to one per lane)
-// whose histograms fit one CTA's shared memory, preferring 32-bit counters.
+// Offsets per histogram group and words per bin row of a group.
+int group_offsets(int layout) { return layout == 0 ? 1 : 2; }
+long long group_row_words(int layout, int rshift) { return (layout == 1 ? 2ll : 1ll) << rshift; }
+
+// How one image's offsets are split into jobs for a configuration: groups per
+// job, and anchor-level span per job (span < N splits the levels).
+struct JobShape {
+    int groups_per_job = 1, span = 0, jobs = 0;
+};
+
+JobShape job_shape(const glcm_ctx* ctx, int levels, int n_off, int layout, int rshift)
+{
+    JobShape s;
+    const long long budget = hist_budget_words(ctx);
+    const long long wrow = group_row_words(layout, rshift);
+    const int opg = group_offsets(layout);
+    const int groups = (n_off + opg - 1) / opg;
+    const long long per_group = (long long)levels * levels * wrow;
+    if (per_group <= budget) {
+        s.groups_per_job = (int)std::min<long long>(groups, budget / per_group);
+        s.span = levels;
+        s.jobs = (groups + s.groups_per_job - 1) / s.groups_per_job;
+    } else {
+        s.groups_per_job = 1;
+        s.span = (int)(budget / ((long long)levels * wrow));
+        if (s.span < 1)
+            return JobShape{1, 0, 0};
+        s.jobs = groups * ((levels + s.span - 1) / s.span);
+    }
+    return s;
+}
+
+// Default vote configuration from a cost model in units of one conflict-free
+// shared-memory reduction per pixel: each offset costs the bank-conflict
+// factor of its copy count (measured: 32 interleaved copies never conflict,
+// a single copy costs ~3x on random bins), each pass over the image ~0.6.
 VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
 {
-    VoteCfg c;
-    const long long NN = (long long)levels * levels;
-    const long long budget = hist_budget_words(ctx);
-    int best_r = -1, best_pack = 1;
-    for (int pack = 1; pack <= 2; ++pack) {
-        const long long groups = (n_off + pack - 1) / pack;
-        for (int r = 5; r >= 0; --r) {
-            if (groups * NN * (1ll << r) <= budget) {
-                if (r > best_r) {
-                    best_r = r;
-                    best_pack = pack;
-                }
-                break;
+    static const double conflict[6] = {3.0, 3.0, 2.8, 2.5, 2.0, 1.0};  // by log2 copies
+    VoteCfg best;
+    double best_cost = 1e30;
+    for (int r = 5; r >= 0; --r) {
+        for (int layout : {1, 0, 2}) {
+            const JobShape s = job_shape(ctx, levels, n_off, layout, r);
+            if (s.jobs <= 0)
+                continue;
+            const double cost = n_off * conflict[r] + 0.6 * s.jobs + (layout == 2 ? 0.05 * n_off : 0.0);
+            if (cost < best_cost - 1e-9) {
+                best_cost = cost;
+                best.rshift = r;
+                best.layout = layout;
             }
         }
     }
-    if (best_r < 0) {
-        // Does a single offset fit?  Then the planner splits the offsets into
-        // several jobs; otherwise vote into global memory.
-        if (NN <= budget) {
-            best_r = 0;
-            best_pack = 1;
-        } else {
-            c.rshift = -1;
-            c.pack = 1;
-            c.agg = 1;
-            return c;
-        }
-    }
-    c.rshift = best_r;
-    c.pack = best_pack;
-    c.agg = 0;
-    return c;
+    return best;
 }
 
 VoteCfg get_cfg(const glcm_ctx* ctx, int levels, int n_off, int bpp)
@@ -257,7 +274,9 @@ struct ImageSpec {
     int y_begin, y_end;  // anchor rows of this launch
 };
 
-// Append the jobs of one image to a plan.
+// Append the jobs of one image to a plan.  Jobs run in the order
+// (superband, offset group, level part): when an image needs several passes
+// each pass re-reads at most one superband (<= 24 MB), which stays in L2.
 int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
 {
     const VoteCfg cfg = get_cfg(ctx, s.levels, s.n_off, s.bpp);
@@ -265,23 +284,18 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     plan.threads = T;
     plan.bpp = s.bpp;
     const int nwarps = T / 32;
-    const long long NN = (long long)s.levels * s.levels;
     const int PX = 16 / s.bpp;
+    const JobShape shape = job_shape(ctx, s.levels, s.n_off, cfg.layout, cfg.rshift);
+    if (shape.jobs <= 0)
+        return fail(ctx, GLCM_ERR_ARG, "vote config cannot hold one level row of the histogram");
     // Offsets sorted by dy so a partner row is loaded once per distinct dy.
     std::vector<int> order(s.n_off);
     for (int k = 0; k < s.n_off; ++k)
         order[k] = k;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return s.offsets[a].dy < s.offsets[b].dy; });
-    // Offsets per job so the job's histograms fit.
-    int per_job = s.n_off;
-    if (cfg.rshift >= 0) {
-        const long long words_per_group = NN << cfg.rshift;
-        const long long groups_fit = hist_budget_words(ctx) / words_per_group;
-        per_job = (int)std::max<long long>(1, std::min<long long>(s.n_off, groups_fit * cfg.pack));
-    } else {
-        per_job = s.n_off;
-    }
+    const int opg = group_offsets(cfg.layout);
+    const int per_job = shape.groups_per_job * opg;
     const int rows = s.y_end - s.y_begin;
     const int strip_px = 32 * PX;
     const int n_strips = std::max(1, (s.W + strip_px - 1) / strip_px);
@@ -290,52 +304,72 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
         long long per = (long long)rows * n_strips / std::max(1, target_items);
         band = (int)std::max<long long>(nwarps, ((per + nwarps - 1) / nwarps) * nwarps);
     }
-    if (cfg.rshift >= 0 && cfg.pack == 2) {
+    if (cfg.layout == 2) {
         // votes per 16-bit half per item: ceil(band/nwarps) * PX * (T / R) <= 65535
         const long long max_rows_per_warp = 65535ll * (1 << cfg.rshift) / ((long long)PX * T);
-        band = (int)std::min<long long>(band, std::max<long long>(1, max_rows_per_warp) * nwarps);
         if (max_rows_per_warp < 1)
             return fail(ctx, GLCM_ERR_ARG, "vote config cannot bound 16-bit counters");
+        band = (int)std::min<long long>(band, max_rows_per_warp * nwarps);
     }
     band = std::max(1, band);
-    const int n_bands = rows > 0 ? (rows + band - 1) / band : 0;
-    for (int o0 = 0; o0 < s.n_off; o0 += per_job) {
-        const int cnt = std::min(per_job, s.n_off - o0);
-        VoteJob j{};
-        j.img = s.img;
-        j.pitch = s.pitch;
-        j.W = s.W;
-        j.H = s.H;
-        j.bpp = s.bpp;
-        j.levels = s.levels;
-        j.log2n = ilog2_exact(s.levels);
-        j.levels_mode = s.levels_mode;
-        j.aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
-        j.n_off = cnt;
-        j.off0 = (int)plan.offs.size();
-        j.rshift = cfg.rshift;
-        j.pack = cfg.rshift >= 0 ? cfg.pack : 1;
-        j.agg = cfg.agg;
-        j.hist_words = cfg.rshift >= 0 ? (int)(((cnt + j.pack - 1) / j.pack) * NN << cfg.rshift) : 0;
-        j.item0 = plan.n_items;
-        j.n_strips = n_strips;
-        j.band_rows = band;
-        j.y_begin = s.y_begin;
-        j.y_end = s.y_end;
-        j.out = s.out;
-        for (int k = o0; k < o0 + cnt; ++k) {
-            VoteOffset vo{};
-            vo.dx = s.offsets[order[k]].dx;
-            vo.dy = s.offsets[order[k]].dy;
-            vo.slot = order[k];
-            plan.offs.push_back(vo);
+    // Superbands only when the image takes several passes.
+    const int passes = ((s.n_off + per_job - 1) / per_job) * ((s.levels + shape.span - 1) / shape.span);
+    int sb_rows = rows;
+    if (passes > 1) {
+        const long long row_bytes = (long long)s.W * s.bpp;
+        const long long want = std::max<long long>(band, (24ll << 20) / std::max<long long>(1, row_bytes));
+        sb_rows = (int)std::min<long long>(rows, ((want + band - 1) / band) * band);
+    }
+    for (int sb0 = s.y_begin; sb0 < s.y_end; sb0 += sb_rows) {
+        const int sb1 = std::min(s.y_end, sb0 + sb_rows);
+        const int n_bands = (sb1 - sb0 + band - 1) / band;
+        for (int o0 = 0; o0 < s.n_off; o0 += per_job) {
+            const int cnt = std::min(per_job, s.n_off - o0);
+            for (int lv = 0; lv < s.levels; lv += shape.span) {
+                const int span = std::min(shape.span, s.levels - lv);
+                VoteJob j{};
+                j.img = s.img;
+                j.pitch = s.pitch;
+                j.W = s.W;
+                j.H = s.H;
+                j.bpp = s.bpp;
+                j.levels = s.levels;
+                j.log2n = ilog2_exact(s.levels);
+                j.levels_mode = s.levels_mode;
+                j.aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
+                j.n_off = cnt;
+                j.off0 = (int)plan.offs.size();
+                j.rshift = cfg.rshift;
+                j.layout = cfg.layout;
+                j.lv_lo = lv;
+                j.lv_span = span;
+                j.bytecode = (cfg.layout == 1 && cfg.rshift == 5 && span == s.levels && j.log2n >= 0 &&
+                              s.levels <= 16)
+                                 ? 1
+                                 : 0;
+                const int groups = (cnt + opg - 1) / opg;
+                j.hist_words = (int)((long long)groups * span * s.levels * group_row_words(cfg.layout, cfg.rshift));
+                j.item0 = plan.n_items;
+                j.n_strips = n_strips;
+                j.band_rows = band;
+                j.y_begin = sb0;
+                j.y_end = sb1;
+                j.out = s.out;
+                for (int k = o0; k < o0 + cnt; ++k) {
+                    VoteOffset vo{};
+                    vo.dx = s.offsets[order[k]].dx;
+                    vo.dy = s.offsets[order[k]].dy;
+                    vo.slot = order[k];
+                    plan.offs.push_back(vo);
+                }
+                plan.max_hist_words = std::max(plan.max_hist_words, j.hist_words);
+                plan.n_items += n_strips * n_bands;
+                if (n_strips * n_bands > 0)
+                    plan.jobs.push_back(j);
+                else
+                    plan.offs.resize(j.off0);
+            }
         }
-        plan.max_hist_words = std::max(plan.max_hist_words, j.hist_words);
-        plan.n_items += n_strips * n_bands;
-        if (n_strips * n_bands > 0)
-            plan.jobs.push_back(j);
-        else
-            plan.offs.resize(j.off0);
     }
     return GLCM_OK;
 }
@@ -578,8 +612,8 @@ std::string batch_key(const glcm_desc* d, int n, const glcm_ctx* ctx)
     }
     k += ctx->timing ? "T" : "U";
     for (const auto& kv : ctx->overrides) {
-        snprintf(buf, sizeof buf, "#%lld:%d,%d,%d,%d,%d", kv.first, kv.second.threads, kv.second.rshift,
-                 kv.second.pack, kv.second.agg, kv.second.band_rows);
+        snprintf(buf, sizeof buf, "#%lld:%d,%d,%d,%d", kv.first, kv.second.threads, kv.second.rshift,
+                 kv.second.layout, kv.second.band_rows);
         k += buf;
     }
     return k;
@@ -752,7 +786,7 @@ extern "C" int glcm_get_timing(glcm_ctx* ctx, double* vote_ms, long long* vote_l
 }
 
 extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, int dtype, int threads,
-                                    int log2_copies, int pack, int aggregate, int band_rows)
+                                    int log2_copies, int layout, int band_rows)
 {
     if (!ctx)
         return GLCM_ERR_ARG;
@@ -762,22 +796,17 @@ extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, in
         ctx->overrides.erase(key);
         return GLCM_OK;
     }
-    if (threads % 32 || threads < 64 || threads > kMaxThreads || log2_copies < -1 || log2_copies > 5 ||
-        (pack != 1 && pack != 2) || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1)
+    if (threads % 32 || threads < 64 || threads > kMaxThreads || log2_copies < 0 || log2_copies > 5 ||
+        layout < 0 || layout > 2 || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1 || band_rows < 0)
         return fail(ctx, GLCM_ERR_ARG, "invalid vote config");
-    if (log2_copies >= 0) {
-        const long long words = (long long)levels * levels << log2_copies;
-        if (words > hist_budget_words(ctx))
-            return fail(ctx, GLCM_ERR_ARG, "one offset's histograms need %lld words > %d", words,
-                        hist_budget_words(ctx));
-        if (pack == 2 && 65535ll * (1 << log2_copies) / ((16 / bpp) * (long long)threads) < 1)
-            return fail(ctx, GLCM_ERR_ARG, "16-bit counters cannot be bounded with this config");
-    }
+    if (job_shape(ctx, levels, n_offsets, layout, log2_copies).jobs <= 0)
+        return fail(ctx, GLCM_ERR_ARG, "one level row of the histograms does not fit shared memory");
+    if (layout == 2 && 65535ll * (1 << log2_copies) / ((16 / bpp) * (long long)threads) < 1)
+        return fail(ctx, GLCM_ERR_ARG, "16-bit counters cannot be bounded with this config");
     VoteCfg c;
     c.threads = threads;
     c.rshift = log2_copies;
-    c.pack = pack;
-    c.agg = aggregate ? 1 : 0;
+    c.layout = layout;
     c.band_rows = band_rows;
     ctx->overrides[key] = c;
     return GLCM_OK;

@@ -34,9 +34,11 @@ struct VoteJob {
     int n_off;         // offsets in this job
     int off0;          // first entry in the offsets table
     int rshift;        // log2(copies): R = 1 << rshift private copies
-    int pack;          // 1: uint32 counters; 2: two uint16 counters per word
-    int agg;           // warp aggregation with match.any before each add
-    int hist_words;    // shared words this job uses: ceil(n_off/pack)*N*N*R
+    int layout;        // 0: R words per bin; 1: two offsets' R words interleaved
+                       // per bin; 2: two offsets as 16-bit halves of R words
+    int bytecode;      // N <= 16 power of two, layout 1, R = 32, no level split
+    int lv_lo, lv_span;  // anchor levels [lv_lo, lv_lo + lv_span) counted
+    int hist_words;    // shared words this job uses
     int item0;         // first work item of this job in the launch
     int n_strips;      // column strips of 32 lanes x 16 bytes
     int band_rows;     // anchor rows per work item

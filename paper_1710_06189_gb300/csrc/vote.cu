@@ -6,27 +6,31 @@
 // pairing across the border, bins follow Eq. 3 with the anchor as the row.
 //
 // How (the paper's Scheme 2 copy strategy, Sec. II.A, redone for sm_103a):
-//  * Persistent CTAs (one or two per SM) pull work items -- a 16-byte-per-
-//    lane column strip of one image and a band of rows -- from a global
+//  * Persistent CTAs (one per SM, 1024 threads) pull work items -- a strip
+//    of 32 lanes x 16 bytes of one job and a band of rows -- from a global
 //    counter.  Each warp takes rows of the band; each lane owns 16 bytes of
-//    the row (16 uint8 or 8 uint16 pixels), read with one 128-bit
-//    non-coherent load, quantized in registers to packed level bytes.
+//    a row (16 uint8 or 8 uint16 pixels), read with one 128-bit
+//    non-coherent load and quantized in registers to packed level bytes.
 //  * The partner row of each distinct dy is read the same way; the 4 levels
 //    left and right of a lane come from its neighbours by shuffle, so every
 //    |dx| <= 4 partner is a byte extraction from registers.
 //  * Votes go into R private copies of the job's histograms in shared
-//    memory, interleaved so that copy c of bin b sits at word b*R + c and
-//    lane l always uses copy l mod R: with R = 32 every lane of a warp hits
-//    its own bank whatever the data (the paper's copies are contiguous, so
-//    equal bins of different copies share a bank).  With `pack` = 2, two
-//    offsets share a word as two 16-bit halves, halving the footprint; the
+//    memory, interleaved so that copy c of a bin is word c of the bin's
+//    R-word row and lane l always uses copy l mod R: with R = 32 every lane
+//    of a warp hits its own bank whatever the data (the paper's copies are
+//    contiguous, so equal bins of different copies share a bank).
+//    Layouts: (0) one R-word row per bin; (1) two offsets' rows interleaved
+//    per bin (R = 32: a bin is 256 bytes, so a byte code c addresses its bin
+//    as c << 8); (2) two offsets share each word as 16-bit halves -- the
 //    host bounds the votes per half between merges below 65536.
-//  * Optional warp aggregation (__match_any_sync + one popc-weighted add per
-//    distinct word) for single-copy histograms.
+//  * For N <= 16 (power of two) the 4 codes i*N + j of a word are formed
+//    with one shift and one OR, and each vote is one byte permute, one add
+//    and one shared-memory reduction.
+//  * A job may count only the anchors whose level lies in [lv_lo, lv_lo +
+//    lv_span): N = 256 histograms are split by anchor level so that each
+//    part fits one CTA's shared memory.
 //  * The merge (Sec. II.A, last step) sums the copies and adds each non-zero
 //    bin into the global uint32 counts once per CTA and job.
-//  * When a single offset's N*N uint32 histogram cannot fit shared memory
-//    (N = 256) the job votes straight into the global counts (L2 atomics).
 //  * Image edges, unaligned images, |dx| > 4 and out-of-range pixels in
 //    levels mode take a per-pixel path with full bounds checks.
 #include "glcm_internal.cuh"
@@ -118,12 +122,11 @@ __device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, uint32_t w0, u
     return r;
 }
 
-// Load the levels of pixels [xl, xl + PX) of row y into LW words.  Only whole
-// 4-pixel groups inside [0, W) are loaded (others read as 0 and are never
-// used by the fast path).
+// Levels of pixels [xl, xl + PX) of row y as LW words.  Only whole 4-pixel
+// groups inside [0, W) are loaded; the others read as 0 and are never used
+// by the fast path.
 template <int BPP>
-__device__ __forceinline__ void load_levels(const VoteJob& j, int y, int xl, uint32_t (&L)[4 / BPP],
-                                            bool& bad)
+__device__ __forceinline__ void load_levels(const VoteJob& j, int y, int xl, uint32_t (&L)[4 / BPP], bool& bad)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
@@ -166,69 +169,79 @@ __device__ __forceinline__ uint32_t load_group(const VoteJob& j, int y, int x, b
     return quant_u16x4(j, q.x, q.y, bad);
 }
 
+// Where offset o of a job votes: shared byte address of (bin 0, this lane's
+// copy), bytes between bins, and the increment (1 or 1 << 16).
 struct HistRef {
-    uint32_t base;    // shared byte address of copy c of this offset's first bin
-    uint32_t inc;     // 1 or 1 << 16
-    uint32_t stride;  // bytes between consecutive bins (4 * R)
+    uint32_t base;
+    uint32_t stride;
+    uint32_t inc;
 };
 
-// Vote the PX anchors of one lane for a compile-time dx, all pairs valid.
-template <int BPP, int DX>
+__device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hbase, int c)
+{
+    const uint32_t R = 1u << j.rshift;
+    const uint32_t NNs = (uint32_t)j.lv_span * (uint32_t)j.levels;
+    HistRef h;
+    if (j.layout == 1) {
+        h.base = hbase + 4u * (((uint32_t)(o >> 1) * NNs * 2u * R) + (uint32_t)(o & 1) * R + (uint32_t)c);
+        h.stride = 8u * R;
+        h.inc = 1u;
+    } else if (j.layout == 2) {
+        h.base = hbase + 4u * ((uint32_t)(o >> 1) * NNs * R + (uint32_t)c);
+        h.stride = 4u * R;
+        h.inc = (o & 1) ? 0x10000u : 1u;
+    } else {
+        h.base = hbase + 4u * ((uint32_t)o * NNs * R + (uint32_t)c);
+        h.stride = 4u * R;
+        h.inc = 1u;
+    }
+    return h;
+}
+
+// Fast vote of one lane's PX anchors for a compile-time dx (all pairs valid).
+template <int BPP, int DX, bool SPLIT>
 __device__ __forceinline__ void vote_fast(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                          int N, const HistRef& h)
+                                          uint32_t N, uint32_t lo, uint32_t span, const HistRef& h)
 {
     constexpr int PX = 16 / BPP;
 #pragma unroll
     for (int k = 0; k < PX; ++k) {
-        const uint32_t i = (A[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-        const int pb = k + DX + 4;  // byte of the extended partner row
-        const uint32_t jv = (B[pb >> 2] >> (8 * (pb & 3))) & 0xFFu;
-        const uint32_t bin = i * (uint32_t)N + jv;
-        red_shared_add(h.base + bin * h.stride, h.inc);
-    }
-}
-
-template <int BPP, int DX>
-__device__ __forceinline__ void vote_fast_agg(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                              int N, const HistRef& h, unsigned mask, int lane)
-{
-    constexpr int PX = 16 / BPP;
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const uint32_t i = (A[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-        const int pb = k + DX + 4;
-        const uint32_t jv = (B[pb >> 2] >> (8 * (pb & 3))) & 0xFFu;
-        const uint32_t bin = i * (uint32_t)N + jv;
-        const unsigned m = __match_any_sync(mask, bin);
-        if ((__ffs(m) - 1) == lane)
-            red_shared_add(h.base + bin * h.stride, h.inc * (uint32_t)__popc(m));
-    }
-}
-
-template <int BPP, int DX>
-__device__ __forceinline__ void vote_fast_global(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                                 int N, uint32_t* out, unsigned mask, int lane, int agg)
-{
-    constexpr int PX = 16 / BPP;
-#pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const uint32_t i = (A[k >> 2] >> (8 * (k & 3))) & 0xFFu;
-        const int pb = k + DX + 4;
-        const uint32_t jv = (B[pb >> 2] >> (8 * (pb & 3))) & 0xFFu;
-        const uint32_t bin = i * (uint32_t)N + jv;
-        if (agg) {
-            const unsigned m = __match_any_sync(mask, bin);
-            if ((__ffs(m) - 1) == lane)
-                red_global_add(out + bin, (uint32_t)__popc(m));
+        const uint32_t i = __byte_perm(A[k >> 2], 0u, 0x4440u | (uint32_t)(k & 3));
+        const int t = k + DX + 4;  // byte of the extended partner row
+        const uint32_t jv = __byte_perm(B[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+        if (SPLIT) {
+            const uint32_t ii = i - lo;
+            if (ii < span)
+                red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
         } else {
-            red_global_add(out + bin, 1u);
+            red_shared_add(h.base + (i * N + jv) * h.stride, h.inc);
         }
+    }
+}
+
+// N <= 16, power of two, layout 1 with 32 copies: code = (i << L) | j is a
+// byte and its bin starts at code << 8 bytes from the offset's base.
+template <int BPP, int DX>
+__device__ __forceinline__ void vote_bytecode(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
+                                             int L, uint32_t base)
+{
+    constexpr int LW = 4 / BPP;
+#pragma unroll
+    for (int m = 0; m < LW; ++m) {
+        const int t = 4 * m + DX + 4;
+        const int w0 = t >> 2, s = t & 3;
+        const uint32_t pw = s == 0 ? B[w0] : __funnelshift_r(B[w0], B[w0 + 1], 8 * s);
+        const uint32_t code = (A[m] << L) | pw;
+        red_shared_add(base + __byte_perm(code, 0u, 0x4404u), 1u);
+        red_shared_add(base + __byte_perm(code, 0u, 0x4414u), 1u);
+        red_shared_add(base + __byte_perm(code, 0u, 0x4424u), 1u);
+        red_shared_add(base + __byte_perm(code, 0u, 0x4434u), 1u);
     }
 }
 
 // Per-pixel path with full checks (edges, unaligned images, wide dx, bad levels).
 __device__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int px, const HistRef& h,
-                          uint32_t* gout, unsigned* err)
+                          unsigned* err)
 {
     const int yp = y + dy;
     if (y < 0 || y >= j.H || yp < 0 || yp >= j.H)
@@ -247,27 +260,27 @@ __device__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int p
             atomicOr(err, kErrRange);
             continue;
         }
-        const uint32_t bin = i * N + jv;
-        if (gout)
-            red_global_add(gout + bin, 1u);
-        else
-            red_shared_add(h.base + bin * h.stride, h.inc);
+        const uint32_t ii = i - (uint32_t)j.lv_lo;
+        if (ii >= (uint32_t)j.lv_span)
+            continue;
+        red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
     }
 }
 
 template <int BPP>
 __device__ __forceinline__ void dispatch_fast(int dx, const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                              int N, const HistRef& h, uint32_t* gout, int agg,
-                                              unsigned mask, int lane)
+                                              const VoteJob& j, const HistRef& h, bool bytecode)
 {
-#define GLCM_CASE(D)                                                        \
-    case D:                                                                 \
-        if (gout)                                                           \
-            vote_fast_global<BPP, D>(A, B, N, gout, mask, lane, agg);       \
-        else if (agg)                                                       \
-            vote_fast_agg<BPP, D>(A, B, N, h, mask, lane);                  \
-        else                                                                \
-            vote_fast<BPP, D>(A, B, N, h);                                  \
+    const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
+    const bool split = j.lv_span < j.levels;
+#define GLCM_CASE(D)                                            \
+    case D:                                                     \
+        if (bytecode)                                           \
+            vote_bytecode<BPP, D>(A, B, j.log2n, h.base);       \
+        else if (split)                                         \
+            vote_fast<BPP, D, true>(A, B, N, lo, span, h);      \
+        else                                                    \
+            vote_fast<BPP, D, false>(A, B, N, lo, span, h);     \
         break;
     switch (dx) {
         GLCM_CASE(-4)
@@ -285,15 +298,17 @@ __device__ __forceinline__ void dispatch_fast(int dx, const uint32_t (&A)[4 / BP
 #undef GLCM_CASE
 }
 
-// Sum the R copies of every word of the job's histograms into global counts,
-// then zero them.  Called by the whole CTA between __syncthreads().
+// Sum the R copies of every bin row of the job's histograms into the global
+// counts, then zero them.  Called by the whole CTA between __syncthreads().
 __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* hist)
 {
     const int R = 1 << j.rshift;
-    const int NN = j.levels * j.levels;
-    const int groups = (j.n_off + j.pack - 1) / j.pack;
-    const int rows = groups * NN;
+    const int N = j.levels;
+    const int NN = N * N;
+    const int NNs = j.lv_span * N;
+    const int rows = j.hist_words >> j.rshift;
     const int lane = threadIdx.x & 31;
+    const int out_bin0 = j.lv_lo * N;
     for (int w = threadIdx.x; w < rows; w += blockDim.x) {
         uint32_t lo = 0, hi = 0;
         uint32_t* base = hist + (long long)w * R;
@@ -301,20 +316,29 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
             const int c = (r + lane) & (R - 1);  // rotate so lanes hit distinct banks
             const uint32_t v = base[c];
             base[c] = 0u;
-            if (j.pack == 2) {
+            if (j.layout == 2) {
                 lo += v & 0xFFFFu;
                 hi += v >> 16;
             } else {
                 lo += v;
             }
         }
-        const int g = w / NN;
-        const int bin = w - g * NN;
-        const int o0 = g * j.pack;
-        if (lo)
-            red_global_add(j.out + (long long)offs[j.off0 + o0].slot * NN + bin, lo);
-        if (j.pack == 2 && hi && o0 + 1 < j.n_off)
-            red_global_add(j.out + (long long)offs[j.off0 + o0 + 1].slot * NN + bin, hi);
+        int o, bin;
+        if (j.layout == 1) {
+            const int pr = w >> 1;
+            o = (pr / NNs) * 2 + (w & 1);
+            bin = pr - (pr / NNs) * NNs;
+        } else if (j.layout == 2) {
+            o = (w / NNs) * 2;
+            bin = w - (w / NNs) * NNs;
+        } else {
+            o = w / NNs;
+            bin = w - o * NNs;
+        }
+        if (lo && o < j.n_off)
+            red_global_add(j.out + (long long)offs[j.off0 + o].slot * NN + out_bin0 + bin, lo);
+        if (j.layout == 2 && hi && o + 1 < j.n_off)
+            red_global_add(j.out + (long long)offs[j.off0 + o + 1].slot * NN + out_bin0 + bin, hi);
     }
 }
 
@@ -328,12 +352,9 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int xl = it.x0 + lane * PX;
-    const int N = j.levels;
-    const int NN = N * N;
-    const bool global_direct = j.rshift < 0;
-    const int R = global_direct ? 1 : (1 << j.rshift);
-    const int c = lane & (R - 1);
+    const int c = lane & ((1 << j.rshift) - 1);
     const uint32_t hbase = smem_u32(hist);
+    const bool bytecode = j.bytecode != 0;
     // A lane may use registers for all its pairs when its 4-pixel halos exist.
     const bool lane_interior = j.aligned && xl >= 4 && xl + PX + 4 <= j.W;
 
@@ -350,25 +371,15 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
             const int yp = y + of.dy;
             if (yp < 0 || yp >= j.H)
                 continue;
-            HistRef h;
-            uint32_t* gout = nullptr;
-            if (global_direct) {
-                gout = j.out + (long long)of.slot * NN;
-                h.base = 0; h.inc = 1; h.stride = 0;
-            } else {
-                const int g = j.pack == 2 ? (o >> 1) : o;
-                h.inc = (j.pack == 2 && (o & 1)) ? 0x10000u : 1u;
-                h.stride = 4u * (uint32_t)R;
-                h.base = hbase + 4u * (uint32_t)(g * NN * R + c);
-            }
-            const bool fast_dx = of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
+            const HistRef h = hist_ref(j, o, hbase, c);
             if (j.aligned && of.dy != cur_dy) {
                 // Partner row levels plus one 4-level halo word on each side.
                 bad_b = false;
                 uint32_t P[LW];
                 if (of.dy == 0) {
 #pragma unroll
-                    for (int w = 0; w < LW; ++w) P[w] = A[w];
+                    for (int w = 0; w < LW; ++w)
+                        P[w] = A[w];
                     bad_b = bad_a;
                 } else {
                     load_levels<BPP>(j, yp, xl, P, bad_b);
@@ -381,19 +392,21 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
                     right = load_group<BPP>(j, yp, xl + PX, bad_b);
                 B[0] = left;
 #pragma unroll
-                for (int w = 0; w < LW; ++w) B[w + 1] = P[w];
+                for (int w = 0; w < LW; ++w)
+                    B[w + 1] = P[w];
                 B[LW + 1] = right;
                 cur_dy = of.dy;
             }
-            // Neighbour halos may carry an out-of-range level: check them too.
-            const bool bad_any = __any_sync(0xffffffffu, bad_b) || bad_a;
-            const bool fast = lane_interior && fast_dx && !bad_a && !bad_b && !bad_any;
-            const unsigned fmask = __ballot_sync(0xffffffffu, fast);
-            if (fast) {
-                dispatch_fast<BPP>(of.dx, A, B, N, h, gout, j.agg, fmask, lane);
-            } else if (xl < j.W) {
-                vote_slow(j, of.dx, of.dy, y, xl, PX, h, gout, err);
+            bool fast = lane_interior && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
+            if (j.levels_mode) {
+                // Neighbour halos may carry an out-of-range level: check them too.
+                const bool bad_any = __any_sync(0xffffffffu, bad_b);
+                fast = fast && !bad_a && !bad_any;
             }
+            if (fast)
+                dispatch_fast<BPP>(of.dx, A, B, j, h, bytecode);
+            else if (xl < j.W)
+                vote_slow(j, of.dx, of.dy, y, xl, PX, h, err);
         }
     }
 }
@@ -405,8 +418,8 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_glcm_vote(VoteParams p)
     __shared__ int s_item, s_job;
     for (int i = threadIdx.x; i < p.max_hist_words; i += blockDim.x)
         hist[i] = 0u;
-    int cur = -1;       // job whose partial histogram is in shared memory
-    int acc = 0;        // rows per warp voted into 16-bit halves since the last merge
+    int cur = -1;  // job whose partial histogram is in shared memory
+    int acc = 0;   // rows per warp voted into 16-bit halves since the last merge
     __syncthreads();
     const int nwarps = blockDim.x >> 5;
     for (;;) {
@@ -440,31 +453,30 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_glcm_vote(VoteParams p)
             const int band = local / j.n_strips;
             const int strip = local - band * j.n_strips;
             it.job = job;
-            it.x0 = strip * 32 * (16 / j.bpp);
+            it.x0 = strip * 32 * (16 / BPP);
             it.y0 = j.y_begin + band * j.band_rows;
             it.y1 = min(j.y_end, it.y0 + j.band_rows);
         }
         const int rows_per_warp = (it.y1 - it.y0 + nwarps - 1) / nwarps;
         if (cur >= 0) {
             const VoteJob& cj = p.jobs[cur];
-            bool need = cur != it.job;
-            if (!need && cj.pack == 2 && cj.rshift >= 0) {
+            bool need = cur != job;
+            if (!need && cj.layout == 2) {
                 // Bound the votes per 16-bit half: threads per copy x pixels.
-                const long long per_half = (long long)(acc + rows_per_warp) * (16 / cj.bpp) *
-                                           (blockDim.x >> cj.rshift);
+                const long long per_half =
+                    (long long)(acc + rows_per_warp) * (16 / BPP) * (blockDim.x >> cj.rshift);
                 need = per_half > 65535;
             }
             if (need) {
-                if (cj.rshift >= 0)
-                    flush_hist(cj, p.offs, hist);
+                flush_hist(cj, p.offs, hist);
                 __syncthreads();
                 cur = -1;
                 acc = 0;
             }
         }
-        cur = it.job;
+        cur = job;
         acc += rows_per_warp;
-        if (j.rshift >= 0 && j.hist_words > p.max_hist_words) {
+        if (j.hist_words > p.max_hist_words) {
             if (threadIdx.x == 0)
                 atomicOr(p.err, kErrInternal);
         } else {
@@ -472,7 +484,7 @@ __global__ void __launch_bounds__(kMaxThreads, 1) k_glcm_vote(VoteParams p)
         }
         __syncthreads();
     }
-    if (cur >= 0 && p.jobs[cur].rshift >= 0)
+    if (cur >= 0)
         flush_hist(p.jobs[cur], p.offs, hist);
 }
 
@@ -508,20 +520,10 @@ __global__ void k_glcm_naive(const uint8_t* img, long long pitch, int W, int H, 
     }
 }
 
-}  // namespace
-
-int vote_max_smem_optin()
-{
-    int dev = 0, v = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    return v;
-}
-
 // Raise the dynamic shared-memory limit only when a launch needs more than
 // before, so no attribute call happens while a stream is being captured.
 template <int BPP>
-static cudaError_t vote_prepare(size_t smem)
+cudaError_t vote_prepare(size_t smem)
 {
     static size_t set_to = 0;
     if (smem <= set_to)
@@ -530,6 +532,16 @@ static cudaError_t vote_prepare(size_t smem)
     if (e == cudaSuccess)
         set_to = smem;
     return e;
+}
+
+}  // namespace
+
+int vote_max_smem_optin()
+{
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
 }
 
 int vote_blocks_per_sm(int bpp, int threads, size_t smem)

@@ -155,3 +155,28 @@ def test_naive_scheme1_matches(gctx):
         G.glcm_compute_naive(gctx.ctx, d, 400, 300, 400, G.GLCM_U8, 8, off, 0, c)
         torch.cuda.synchronize()
         assert np.array_equal(to_u32(c), oracle.glcm(img, 8, [off])[0])
+
+
+@pytest.mark.parametrize("n", [8, 16, 32, 64, 256])
+def test_every_vote_config_is_exact(gctx, n):
+    """All histogram layouts, copy counts, thread counts and level splits
+    give the same counts (the autotuner may pick any of them)."""
+    img = S.smooth(77, 300, 1100, 2.0, np.uint8)
+    img[:, 500:] = S.iid(78, 300, 600, np.uint8)
+    offs = C4 + [(2, -2)]
+    want = oracle.glcm(img, n, offs)
+    d = dev(img)
+    tried = 0
+    for threads in (1024, 256):
+        for r in (5, 3, 0):
+            for layout in (0, 1, 2):
+                try:
+                    G.glcm_set_vote_config(gctx.ctx, n, len(offs), G.GLCM_U8, threads, r, layout, 64)
+                except G.GlcmError:
+                    continue  # does not fit shared memory
+                c = gctx.compute(d, n, offs)
+                torch.cuda.synchronize()
+                assert np.array_equal(to_u32(c), want), (threads, r, layout)
+                tried += 1
+    G.glcm_set_vote_config(gctx.ctx, n, len(offs), G.GLCM_U8, 0, 0, 0, 0)
+    assert tried >= 3
