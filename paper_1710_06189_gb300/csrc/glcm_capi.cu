@@ -51,6 +51,7 @@ struct VotePlan {
     std::vector<VoteJob> jobs;
     std::vector<VoteOffset> offs;
     int n_items = 0;
+    double total_w = 0.0;
     int max_hist_words = 0;
     int threads = 1024;
     int bpp = 1;
@@ -242,6 +243,8 @@ VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
     double best_cost = 1e30;
     for (int r = 5; r >= 0; --r) {
         for (int layout : {1, 0, 2}) {
+            if (layout == 2 && 65535ll * (1 << r) / (16ll * 1024) < 64)
+                continue;  // 16-bit halves would force a merge every few rows
             const JobShape s = job_shape(ctx, levels, n_off, layout, r);
             if (s.jobs <= 0)
                 continue;
@@ -350,6 +353,12 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                 const int groups = (cnt + opg - 1) / opg;
                 j.hist_words = (int)((long long)groups * span * s.levels * group_row_words(cfg.layout, cfg.rshift));
                 j.item0 = plan.n_items;
+                j.n_job_items = n_strips * n_bands;
+                // Weight of an item: pixel loads plus expected votes (offsets x
+                // the share of anchor levels this job counts).
+                j.w_item = (float)((double)band * strip_px * (1.0 + (double)cnt * span / s.levels));
+                j.w0 = plan.total_w;
+                plan.total_w += (double)j.w_item * j.n_job_items;
                 j.n_strips = n_strips;
                 j.band_rows = band;
                 j.y_begin = sb0;
@@ -486,6 +495,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     vp.n_jobs = (int)plan.jobs.size();
     vp.offs = static_cast<const VoteOffset*>(doffs.p);
     vp.n_items = plan.n_items;
+    vp.total_w = plan.total_w;
     vp.max_hist_words = plan.max_hist_words;
     vp.item_counter = ctx->d_words + 1;
     vp.err = ctx->d_words;
@@ -1056,6 +1066,8 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
                 for (int k = 0; k < j.n_off; ++k)
                     dst.offs.push_back(plan.offs[j.off0 + k]);
                 c.item0 = dst.n_items;
+                c.w0 = dst.total_w;
+                dst.total_w += (double)c.w_item * c.n_job_items;
                 dst.n_items += cnt_items;
                 dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
                 dst.jobs.push_back(c);

@@ -40,6 +40,9 @@ struct VoteJob {
     int lv_lo, lv_span;  // anchor levels [lv_lo, lv_lo + lv_span) counted
     int hist_words;    // shared words this job uses
     int item0;         // first work item of this job in the launch
+    int n_job_items;   // work items of this job
+    float w_item;      // work weight of one item (static partition)
+    double w0;         // summed weight of all items before this job
     int n_strips;      // column strips of 32 lanes x 16 bytes
     int band_rows;     // anchor rows per work item
     int y_begin, y_end;  // anchor rows voted by this job ([0, H) for a whole image)
@@ -64,8 +67,9 @@ struct VoteParams {
     int n_jobs;
     const VoteOffset* offs;
     int n_items;
+    double total_w;          // summed weight of all items
     int max_hist_words;
-    unsigned* item_counter;  // zeroed before each launch
+    unsigned* item_counter;  // zeroed before each launch (unused by the static schedule)
     unsigned* err;           // error bits (kErr*)
 };
 

@@ -6,9 +6,10 @@
 // pairing across the border, bins follow Eq. 3 with the anchor as the row.
 //
 // How (the paper's Scheme 2 copy strategy, Sec. II.A, redone for sm_103a):
-//  * Persistent CTAs (one per SM, 1024 threads) pull work items -- a strip
-//    of 32 lanes x 16 bytes of one job and a band of rows -- from a global
-//    counter.  Each warp takes rows of the band; each lane owns 16 bytes of
+//  * Persistent CTAs (one per SM, 1024 threads) each take a contiguous,
+//    weight-balanced range of work items -- a strip of 32 lanes x 16 bytes
+//    of one job and a band of rows -- so a CTA spans few jobs and merges
+//    each once.  Each warp takes rows of the band; each lane owns 16 bytes of
 //    a row (16 uint8 or 8 uint16 pixels), read with one 128-bit
 //    non-coherent load and quantized in registers to packed level bytes.
 //  * The partner row of each distinct dy is read the same way; the 4 levels
@@ -411,45 +412,65 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
     }
 }
 
+// First item whose starting weight is >= w (items of a job all weigh w_item).
+__device__ int item_at(const VoteParams& p, double w)
+{
+    if (w <= 0.0)
+        return 0;
+    if (w >= p.total_w)
+        return p.n_items;
+    int lo = 0, hi = p.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.jobs[mid].w0 <= w)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    const VoteJob& j = p.jobs[lo];
+    long long k = (long long)ceil((w - j.w0) / (double)j.w_item);
+    k = k < 0 ? 0 : (k > j.n_job_items ? j.n_job_items : k);
+    return j.item0 + (int)k;
+}
+
+// Persistent CTAs with a static, weight-balanced partition: CTA b votes the
+// contiguous item range covering weights [W b / G, W (b + 1) / G), so it
+// touches only the few jobs that range spans and merges each once.
 template <int BPP>
 __global__ void __launch_bounds__(kMaxThreads, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(16) uint32_t hist[];
-    __shared__ int s_item, s_job;
+    __shared__ int s_k0, s_k1, s_job;
     for (int i = threadIdx.x; i < p.max_hist_words; i += blockDim.x)
         hist[i] = 0u;
+    if (threadIdx.x == 0) {
+        const double W = p.total_w;
+        s_k0 = item_at(p, W * (double)blockIdx.x / (double)gridDim.x);
+        s_k1 = blockIdx.x + 1 == gridDim.x ? p.n_items
+                                            : item_at(p, W * (double)(blockIdx.x + 1) / (double)gridDim.x);
+        int lo = 0, hi = p.n_jobs - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (p.jobs[mid].item0 <= s_k0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const int k0 = s_k0, k1 = s_k1;
+    int job = s_job;
     int cur = -1;  // job whose partial histogram is in shared memory
     int acc = 0;   // rows per warp voted into 16-bit halves since the last merge
-    __syncthreads();
     const int nwarps = blockDim.x >> 5;
-    for (;;) {
-        if (threadIdx.x == 0) {
-            const int k = (int)atomicAdd(p.item_counter, 1u);
-            int job = -1;
-            if (k < p.n_items) {
-                // Last job whose first item is <= k.
-                int lo = 0, hi = p.n_jobs - 1;
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (p.jobs[mid].item0 <= k)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                job = lo;
-            }
-            s_item = k;
-            s_job = job;
-        }
-        __syncthreads();
-        const int it_idx = s_item;
-        if (it_idx >= p.n_items)
-            break;
-        const int job = s_job;
+    for (int k = k0; k < k1; ++k) {
+        while (job + 1 < p.n_jobs && p.jobs[job + 1].item0 <= k)
+            ++job;
         const VoteJob j = p.jobs[job];
         VoteItem it;
         {
-            const int local = it_idx - j.item0;
+            const int local = k - j.item0;
             const int band = local / j.n_strips;
             const int strip = local - band * j.n_strips;
             it.job = job;
