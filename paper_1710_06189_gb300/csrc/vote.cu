@@ -32,8 +32,9 @@
 //    part fits one CTA's shared memory.
 //  * The merge (Sec. II.A, last step) sums the copies and adds each non-zero
 //    bin into the global uint32 counts once per CTA and job.
-//  * Image edges, unaligned images, |dx| > 4 and out-of-range pixels in
-//    levels mode take a per-pixel path with full bounds checks.
+//  * Warps touching an image edge vote with per-anchor validity masks;
+//    unaligned images, |dx| > 4 and out-of-range pixels in levels mode take
+//    a per-pixel path with full bounds checks.
 #include "glcm_internal.cuh"
 
 namespace glcm {
@@ -123,16 +124,41 @@ __device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, uint32_t w0, u
     return r;
 }
 
-// Levels of pixels [xl, xl + PX) of row y as LW words.  Only whole 4-pixel
-// groups inside [0, W) are loaded; the others read as 0 and are never used
-// by the fast path.
+// Levels of the 4 pixels starting at column x (x % 4 == 0); pixels outside
+// [0, W) read as level 0 and are masked out by the callers.
+template <int BPP>
+__device__ __forceinline__ uint32_t load_group(const VoteJob& j, int y, int x, bool& bad)
+{
+    if (x < 0 || x >= j.W)
+        return 0u;
+    const uint8_t* p = j.img + (long long)y * j.pitch + (long long)x * BPP;
+    if (x + 4 <= j.W) {
+        if (BPP == 1)
+            return quant_u8x4(j, __ldg(reinterpret_cast<const uint32_t*>(p)), bad);
+        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+        return quant_u16x4(j, q.x, q.y, bad);
+    }
+    // Ragged right edge: the 1..3 pixels inside, one at a time.
+    uint32_t r = 0;
+    for (int b = 0; b < 4 && x + b < j.W; ++b) {
+        const uint32_t v = BPP == 1 ? (uint32_t)__ldg(p + b)
+                                    : ((uint32_t)__ldg(p + 2 * b) | ((uint32_t)__ldg(p + 2 * b + 1) << 8));
+        const uint32_t q = level_of(j, v);
+        bad |= q >= (uint32_t)j.levels;
+        r |= (q & 0xFFu) << (8 * b);
+    }
+    return r;
+}
+
+// Levels of pixels [xl, xl + PX) of row y as LW words (one 128-bit load when
+// the whole lane lies inside the row).
 template <int BPP>
 __device__ __forceinline__ void load_levels(const VoteJob& j, int y, int xl, uint32_t (&L)[4 / BPP], bool& bad)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
-    const uint8_t* p = j.img + (long long)y * j.pitch + (long long)xl * BPP;
     if (xl + PX <= j.W) {
+        const uint8_t* p = j.img + (long long)y * j.pitch + (long long)xl * BPP;
         const uint4 r = ldg_v4(p);
         if (BPP == 1) {
             L[0] = quant_u8x4(j, r.x, bad);
@@ -145,29 +171,9 @@ __device__ __forceinline__ void load_levels(const VoteJob& j, int y, int xl, uin
         }
     } else {
 #pragma unroll
-        for (int w = 0; w < LW; ++w) {
-            L[w] = 0;
-            if (xl + 4 * w + 4 <= j.W) {
-                if (BPP == 1) {
-                    L[w] = quant_u8x4(j, __ldg(reinterpret_cast<const uint32_t*>(p + 4 * w)), bad);
-                } else {
-                    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p + 8 * w));
-                    L[w] = quant_u16x4(j, q.x, q.y, bad);
-                }
-            }
-        }
+        for (int w = 0; w < LW; ++w)
+            L[w] = load_group<BPP>(j, y, xl + 4 * w, bad);
     }
-}
-
-// Levels of the 4 pixels starting at column x (x % 4 == 0, whole group inside).
-template <int BPP>
-__device__ __forceinline__ uint32_t load_group(const VoteJob& j, int y, int x, bool& bad)
-{
-    const uint8_t* p = j.img + (long long)y * j.pitch + (long long)x * BPP;
-    if (BPP == 1)
-        return quant_u8x4(j, __ldg(reinterpret_cast<const uint32_t*>(p)), bad);
-    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-    return quant_u16x4(j, q.x, q.y, bad);
 }
 
 // Where offset o of a job votes: shared byte address of (bin 0, this lane's
@@ -199,10 +205,11 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
     return h;
 }
 
-// Fast vote of one lane's PX anchors for a compile-time dx (all pairs valid).
-template <int BPP, int DX, bool SPLIT>
+// Fast vote of one lane's PX anchors for a compile-time dx.  With MASKED,
+// only the anchors whose bit is set in `mask` vote (image edges).
+template <int BPP, int DX, bool SPLIT, bool MASKED>
 __device__ __forceinline__ void vote_fast(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                          uint32_t N, uint32_t lo, uint32_t span, const HistRef& h)
+                                          uint32_t N, uint32_t lo, uint32_t span, const HistRef& h, uint32_t mask)
 {
     constexpr int PX = 16 / BPP;
 #pragma unroll
@@ -210,11 +217,12 @@ __device__ __forceinline__ void vote_fast(const uint32_t (&A)[4 / BPP], const ui
         const uint32_t i = __byte_perm(A[k >> 2], 0u, 0x4440u | (uint32_t)(k & 3));
         const int t = k + DX + 4;  // byte of the extended partner row
         const uint32_t jv = __byte_perm(B[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
+        const bool on = !MASKED || ((mask >> k) & 1u);
         if (SPLIT) {
             const uint32_t ii = i - lo;
-            if (ii < span)
+            if (on && ii < span)
                 red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
-        } else {
+        } else if (on) {
             red_shared_add(h.base + (i * N + jv) * h.stride, h.inc);
         }
     }
@@ -222,9 +230,9 @@ __device__ __forceinline__ void vote_fast(const uint32_t (&A)[4 / BPP], const ui
 
 // N <= 16, power of two, layout 1 with 32 copies: code = (i << L) | j is a
 // byte and its bin starts at code << 8 bytes from the offset's base.
-template <int BPP, int DX>
+template <int BPP, int DX, bool MASKED>
 __device__ __forceinline__ void vote_bytecode(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                             int L, uint32_t base)
+                                             int L, uint32_t base, uint32_t mask)
 {
     constexpr int LW = 4 / BPP;
 #pragma unroll
@@ -233,15 +241,15 @@ __device__ __forceinline__ void vote_bytecode(const uint32_t (&A)[4 / BPP], cons
         const int w0 = t >> 2, s = t & 3;
         const uint32_t pw = s == 0 ? B[w0] : __funnelshift_r(B[w0], B[w0 + 1], 8 * s);
         const uint32_t code = (A[m] << L) | pw;
-        red_shared_add(base + __byte_perm(code, 0u, 0x4404u), 1u);
-        red_shared_add(base + __byte_perm(code, 0u, 0x4414u), 1u);
-        red_shared_add(base + __byte_perm(code, 0u, 0x4424u), 1u);
-        red_shared_add(base + __byte_perm(code, 0u, 0x4434u), 1u);
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+            if (!MASKED || ((mask >> (4 * m + b)) & 1u))
+                red_shared_add(base + __byte_perm(code, 0u, 0x4404u | (uint32_t)(b << 4)), 1u);
     }
 }
 
-// Per-pixel path with full checks (edges, unaligned images, wide dx, bad levels).
-__device__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int px, const HistRef& h,
+// Per-pixel path with full checks (unaligned images, wide dx, bad levels).
+__device__ __forceinline__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int px, const HistRef& h,
                           unsigned* err)
 {
     const int yp = y + dy;
@@ -268,20 +276,20 @@ __device__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int p
     }
 }
 
-template <int BPP>
+template <int BPP, bool MASKED>
 __device__ __forceinline__ void dispatch_fast(int dx, const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                              const VoteJob& j, const HistRef& h, bool bytecode)
+                                              const VoteJob& j, const HistRef& h, bool bytecode, uint32_t mask)
 {
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
     const bool split = j.lv_span < j.levels;
-#define GLCM_CASE(D)                                            \
-    case D:                                                     \
-        if (bytecode)                                           \
-            vote_bytecode<BPP, D>(A, B, j.log2n, h.base);       \
-        else if (split)                                         \
-            vote_fast<BPP, D, true>(A, B, N, lo, span, h);      \
-        else                                                    \
-            vote_fast<BPP, D, false>(A, B, N, lo, span, h);     \
+#define GLCM_CASE(D)                                                        \
+    case D:                                                                 \
+        if (bytecode)                                                       \
+            vote_bytecode<BPP, D, MASKED>(A, B, j.log2n, h.base, mask);     \
+        else if (split)                                                     \
+            vote_fast<BPP, D, true, MASKED>(A, B, N, lo, span, h, mask);    \
+        else                                                                \
+            vote_fast<BPP, D, false, MASKED>(A, B, N, lo, span, h, mask);   \
         break;
     switch (dx) {
         GLCM_CASE(-4)
@@ -344,8 +352,8 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
 }
 
 template <int BPP>
-__device__ void process_item(const VoteJob& j, const VoteOffset* offs, const VoteItem& it, uint32_t* hist,
-                             unsigned* err)
+__device__ __forceinline__ void process_item(const VoteJob& j, const VoteOffset* offs, const VoteItem& it,
+                                             uint32_t* hist, unsigned* err)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
@@ -356,8 +364,11 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
     const int c = lane & ((1 << j.rshift) - 1);
     const uint32_t hbase = smem_u32(hist);
     const bool bytecode = j.bytecode != 0;
-    // A lane may use registers for all its pairs when its 4-pixel halos exist.
-    const bool lane_interior = j.aligned && xl >= 4 && xl + PX + 4 <= j.W;
+    // Lanes whose anchors and 4-pixel halos all lie inside the row vote
+    // unmasked; a warp containing an edge lane votes with per-anchor masks.
+    const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
+    const bool warp_interior = __all_sync(0xffffffffu, lane_interior);
+    const int wrem = j.W - xl;  // pixels of this lane's row inside the image
 
     for (int y = it.y0 + warp; y < it.y1; y += nwarps) {
         bool bad_a = false;
@@ -387,9 +398,9 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
                 }
                 uint32_t left = __shfl_up_sync(0xffffffffu, P[LW - 1], 1);
                 uint32_t right = __shfl_down_sync(0xffffffffu, P[0], 1);
-                if (lane == 0 && xl >= 4)
+                if (lane == 0)
                     left = load_group<BPP>(j, yp, xl - 4, bad_b);
-                if (lane == 31 && xl + PX + 4 <= j.W)
+                if (lane == 31)
                     right = load_group<BPP>(j, yp, xl + PX, bad_b);
                 B[0] = left;
 #pragma unroll
@@ -398,16 +409,25 @@ __device__ void process_item(const VoteJob& j, const VoteOffset* offs, const Vot
                 B[LW + 1] = right;
                 cur_dy = of.dy;
             }
-            bool fast = lane_interior && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
+            bool fast = j.aligned && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
             if (j.levels_mode) {
                 // Neighbour halos may carry an out-of-range level: check them too.
-                const bool bad_any = __any_sync(0xffffffffu, bad_b);
-                fast = fast && !bad_a && !bad_any;
+                const bool bad_any = __any_sync(0xffffffffu, bad_b || bad_a);
+                fast = fast && !bad_any;
             }
-            if (fast)
-                dispatch_fast<BPP>(of.dx, A, B, j, h, bytecode);
-            else if (xl < j.W)
+            if (fast) {
+                // Anchors k with xl + k < W and 0 <= xl + k + dx < W (all of
+                // them for interior lanes).
+                uint32_t mask = (1u << PX) - 1u;
+                if (!warp_interior) {
+                    const int lo_k = max(0, -of.dx - xl);
+                    const int hi_k = min(min(PX, wrem), wrem - of.dx);
+                    mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
+                }
+                dispatch_fast<BPP, true>(of.dx, A, B, j, h, bytecode, mask);
+            } else if (xl < j.W) {
                 vote_slow(j, of.dx, of.dy, y, xl, PX, h, err);
+            }
         }
     }
 }
@@ -436,8 +456,8 @@ __device__ int item_at(const VoteParams& p, double w)
 // Persistent CTAs with a static, weight-balanced partition: CTA b votes the
 // contiguous item range covering weights [W b / G, W (b + 1) / G), so it
 // touches only the few jobs that range spans and merges each once.
-template <int BPP>
-__global__ void __launch_bounds__(kMaxThreads, 1) k_glcm_vote(VoteParams p)
+template <int BPP, int MAXT>
+__global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(16) uint32_t hist[];
     __shared__ int s_k0, s_k1, s_job;
@@ -543,16 +563,39 @@ __global__ void k_glcm_naive(const uint8_t* img, long long pitch, int W, int H, 
 
 // Raise the dynamic shared-memory limit only when a launch needs more than
 // before, so no attribute call happens while a stream is being captured.
-template <int BPP>
+template <int BPP, int MAXT>
 cudaError_t vote_prepare(size_t smem)
 {
     static size_t set_to = 0;
     if (smem <= set_to)
         return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_glcm_vote<BPP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_glcm_vote<BPP, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         set_to = smem;
     return e;
+}
+
+// Two register budgets: up to 1024 threads at 64 registers, or up to 512
+// threads at 128 registers.
+template <int BPP>
+cudaError_t vote_launch_t(const VoteParams& p, int grid, int threads, size_t smem, cudaStream_t s, int* occ)
+{
+    cudaError_t e;
+    if (threads > 512) {
+        if ((e = vote_prepare<BPP, 1024>(smem)) != cudaSuccess)
+            return e;
+        if (occ)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 1024>, threads, smem);
+        k_glcm_vote<BPP, 1024><<<grid, threads, smem, s>>>(p);
+    } else {
+        if ((e = vote_prepare<BPP, 512>(smem)) != cudaSuccess)
+            return e;
+        if (occ)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 512>, threads, smem);
+        k_glcm_vote<BPP, 512><<<grid, threads, smem, s>>>(p);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -568,31 +611,15 @@ int vote_max_smem_optin()
 int vote_blocks_per_sm(int bpp, int threads, size_t smem)
 {
     int n = 0;
-    if (bpp == 1) {
-        if (vote_prepare<1>(smem) != cudaSuccess)
-            return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_glcm_vote<1>, threads, smem);
-    } else {
-        if (vote_prepare<2>(smem) != cudaSuccess)
-            return 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_glcm_vote<2>, threads, smem);
-    }
-    return n;
+    cudaError_t e = bpp == 1 ? vote_launch_t<1>(VoteParams{}, 0, threads, smem, nullptr, &n)
+                             : vote_launch_t<2>(VoteParams{}, 0, threads, smem, nullptr, &n);
+    return e == cudaSuccess ? n : 1;
 }
 
 cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem, cudaStream_t s)
 {
-    cudaError_t e;
-    if (bpp == 1) {
-        if ((e = vote_prepare<1>(smem)) != cudaSuccess)
-            return e;
-        k_glcm_vote<1><<<grid, threads, smem, s>>>(p);
-    } else {
-        if ((e = vote_prepare<2>(smem)) != cudaSuccess)
-            return e;
-        k_glcm_vote<2><<<grid, threads, smem, s>>>(p);
-    }
-    return cudaGetLastError();
+    return bpp == 1 ? vote_launch_t<1>(p, grid, threads, smem, s, nullptr)
+                    : vote_launch_t<2>(p, grid, threads, smem, s, nullptr);
 }
 
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels, int levels_mode,
