@@ -26,7 +26,7 @@ struct DevBuf {
 };
 
 struct VoteCfg {
-    int threads = 1024;
+    int threads = 512;
     int rshift = 5;     // log2 private copies
     int layout = 1;     // see VoteJob::layout
     int band_rows = 0;  // 0: derived from the launch size
@@ -53,7 +53,7 @@ struct VotePlan {
     int n_items = 0;
     double total_w = 0.0;
     int max_hist_words = 0;
-    int threads = 1024;
+    int threads = 0;  // max over the plan's jobs
     int bpp = 1;
 };
 
@@ -243,7 +243,7 @@ VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
     double best_cost = 1e30;
     for (int r = 5; r >= 0; --r) {
         for (int layout : {1, 0, 2}) {
-            if (layout == 2 && 65535ll * (1 << r) / (16ll * 1024) < 64)
+            if (layout == 2 && 65535ll * (1 << r) / (16ll * 512) < 64)
                 continue;  // 16-bit halves would force a merge every few rows
             const JobShape s = job_shape(ctx, levels, n_off, layout, r);
             if (s.jobs <= 0)

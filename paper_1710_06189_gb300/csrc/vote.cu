@@ -351,84 +351,220 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
     }
 }
 
+// Per-offset vote parameters of the current job, staged in shared memory.
+struct OffInfo {
+    int dx, dy;
+    uint32_t base;    // shared byte address of (bin 0, copy 0)
+    uint32_t inc;     // 1 or 1 << 16
+};
+constexpr int kMaxJobOffsets = 64;
+
+// Raw (not yet quantized) bytes of one lane's row chunk and its halos.
+struct RawRow {
+    uint4 v;          // the lane's 16 bytes
+    uint2 l, r;       // 4 pixels left / right of the lane (lanes 0 and 31 only)
+};
+
+// One warp's row task: anchor row y, lane columns [xl, xl + PX).
+struct Task {
+    int y, xl;
+    bool valid;
+};
+
 template <int BPP>
-__device__ __forceinline__ void process_item(const VoteJob& j, const VoteOffset* offs, const VoteItem& it,
-                                             uint32_t* hist, unsigned* err)
+__device__ __forceinline__ Task task_of(const VoteJob& j, int k0, int t)
+{
+    constexpr int PX = 16 / BPP;
+    Task q;
+    const int item = k0 + t / j.band_rows;
+    const int rib = t - (t / j.band_rows) * j.band_rows;
+    const int local = item - j.item0;
+    const int band = local / j.n_strips;
+    const int strip = local - band * j.n_strips;
+    q.y = j.y_begin + band * j.band_rows + rib;
+    q.xl = strip * 32 * PX + (threadIdx.x & 31) * PX;
+    q.valid = q.y < j.y_end;
+    return q;
+}
+
+// Issue the loads of a lane's full chunk (and lane 0/31 halos) of row y.
+template <int BPP>
+__device__ __forceinline__ void fetch_raw(const VoteJob& j, int y, int xl, RawRow& r)
+{
+    constexpr int PX = 16 / BPP;
+    const int lane = threadIdx.x & 31;
+    const uint8_t* row = j.img + (long long)y * j.pitch;
+    r.v = make_uint4(0u, 0u, 0u, 0u);
+    r.l = make_uint2(0u, 0u);
+    r.r = make_uint2(0u, 0u);
+    if (xl + PX <= j.W)
+        r.v = ldg_v4(row + (long long)xl * BPP);
+    if (lane == 0 && xl >= 4) {
+        if (BPP == 1)
+            r.l.x = __ldg(reinterpret_cast<const uint32_t*>(row + xl - 4));
+        else
+            r.l = __ldg(reinterpret_cast<const uint2*>(row + 2ll * (xl - 4)));
+    }
+    if (lane == 31 && xl + PX + 4 <= j.W) {
+        if (BPP == 1)
+            r.r.x = __ldg(reinterpret_cast<const uint32_t*>(row + xl + PX));
+        else
+            r.r = __ldg(reinterpret_cast<const uint2*>(row + 2ll * (xl + PX)));
+    }
+}
+
+// Quantize a prefetched chunk into level words; lanes whose chunk is partial
+// (right image edge) load their groups now, byte-exact.
+template <int BPP>
+__device__ __forceinline__ void levels_of_raw(const VoteJob& j, int y, int xl, const RawRow& r,
+                                              uint32_t (&L)[4 / BPP], bool& bad)
+{
+    constexpr int PX = 16 / BPP;
+    if (xl + PX <= j.W) {
+        if (BPP == 1) {
+            L[0] = quant_u8x4(j, r.v.x, bad);
+            L[1 % (4 / BPP)] = quant_u8x4(j, r.v.y, bad);
+            L[2 % (4 / BPP)] = quant_u8x4(j, r.v.z, bad);
+            L[3 % (4 / BPP)] = quant_u8x4(j, r.v.w, bad);
+        } else {
+            L[0] = quant_u16x4(j, r.v.x, r.v.y, bad);
+            L[1] = quant_u16x4(j, r.v.z, r.v.w, bad);
+        }
+    } else {
+        load_levels<BPP>(j, y, xl, L, bad);
+    }
+}
+
+template <int BPP>
+__device__ __forceinline__ uint32_t halo_of_raw(const VoteJob& j, int y, int x, const uint2& raw, bool& bad)
+{
+    // Whole group inside the row: use the prefetched bytes; else exact loads.
+    if (x >= 0 && x + 4 <= j.W)
+        return BPP == 1 ? quant_u8x4(j, raw.x, bad) : quant_u16x4(j, raw.x, raw.y, bad);
+    return load_group<BPP>(j, y, x, bad);
+}
+
+// Vote every offset of one row task.  A is the anchor row; PA/PB (raw) are
+// the prefetched anchor row and first partner row (dy = dy1).
+template <int BPP>
+__device__ __forceinline__ void vote_task(const VoteJob& j, const OffInfo* s_off, int dy1, const Task& q,
+                                          const RawRow& ra, const RawRow& rb, unsigned* err)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
     const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int xl = it.x0 + lane * PX;
-    const int c = lane & ((1 << j.rshift) - 1);
-    const uint32_t hbase = smem_u32(hist);
+    const int xl = q.xl, y = q.y;
+    const uint32_t cbytes = 4u * (uint32_t)(lane & ((1 << j.rshift) - 1));
+    const uint32_t stride = (j.layout == 1 ? 8u : 4u) << j.rshift;
     const bool bytecode = j.bytecode != 0;
-    // Lanes whose anchors and 4-pixel halos all lie inside the row vote
-    // unmasked; a warp containing an edge lane votes with per-anchor masks.
     const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
     const bool warp_interior = __all_sync(0xffffffffu, lane_interior);
-    const int wrem = j.W - xl;  // pixels of this lane's row inside the image
-
-    for (int y = it.y0 + warp; y < it.y1; y += nwarps) {
-        bool bad_a = false;
-        uint32_t A[LW];
-        if (j.aligned)
-            load_levels<BPP>(j, y, xl, A, bad_a);
-        int cur_dy = 0x7fffffff;
-        uint32_t B[LW + 2];
-        bool bad_b = false;
-        for (int o = 0; o < j.n_off; ++o) {
-            const VoteOffset of = offs[j.off0 + o];
-            const int yp = y + of.dy;
-            if (yp < 0 || yp >= j.H)
-                continue;
-            const HistRef h = hist_ref(j, o, hbase, c);
-            if (j.aligned && of.dy != cur_dy) {
-                // Partner row levels plus one 4-level halo word on each side.
-                bad_b = false;
-                uint32_t P[LW];
-                if (of.dy == 0) {
-#pragma unroll
-                    for (int w = 0; w < LW; ++w)
-                        P[w] = A[w];
-                    bad_b = bad_a;
-                } else {
-                    load_levels<BPP>(j, yp, xl, P, bad_b);
-                }
-                uint32_t left = __shfl_up_sync(0xffffffffu, P[LW - 1], 1);
-                uint32_t right = __shfl_down_sync(0xffffffffu, P[0], 1);
-                if (lane == 0)
-                    left = load_group<BPP>(j, yp, xl - 4, bad_b);
-                if (lane == 31)
-                    right = load_group<BPP>(j, yp, xl + PX, bad_b);
-                B[0] = left;
+    const int wrem = j.W - xl;
+    bool bad_a = false;
+    uint32_t A[LW];
+    if (j.aligned)
+        levels_of_raw<BPP>(j, y, xl, ra, A, bad_a);
+    int cur_dy = 0x7fffffff;
+    uint32_t B[LW + 2];
+    bool bad_b = false;
+    for (int o = 0; o < j.n_off; ++o) {
+        const OffInfo of = s_off[o];
+        const int yp = y + of.dy;
+        if (yp < 0 || yp >= j.H)
+            continue;
+        HistRef h;
+        h.base = of.base + cbytes;
+        h.stride = stride;
+        h.inc = of.inc;
+        if (j.aligned && of.dy != cur_dy) {
+            bad_b = false;
+            uint32_t P[LW];
+            uint32_t left, right;
+            if (of.dy == 0) {
 #pragma unroll
                 for (int w = 0; w < LW; ++w)
-                    B[w + 1] = P[w];
-                B[LW + 1] = right;
-                cur_dy = of.dy;
+                    P[w] = A[w];
+                bad_b = bad_a;
+                left = halo_of_raw<BPP>(j, yp, xl - 4, ra.l, bad_b);
+                right = halo_of_raw<BPP>(j, yp, xl + PX, ra.r, bad_b);
+            } else if (of.dy == dy1) {
+                levels_of_raw<BPP>(j, yp, xl, rb, P, bad_b);
+                left = halo_of_raw<BPP>(j, yp, xl - 4, rb.l, bad_b);
+                right = halo_of_raw<BPP>(j, yp, xl + PX, rb.r, bad_b);
+            } else {
+                load_levels<BPP>(j, yp, xl, P, bad_b);
+                left = load_group<BPP>(j, yp, xl - 4, bad_b);
+                right = load_group<BPP>(j, yp, xl + PX, bad_b);
             }
-            bool fast = j.aligned && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
-            if (j.levels_mode) {
-                // Neighbour halos may carry an out-of-range level: check them too.
-                const bool bad_any = __any_sync(0xffffffffu, bad_b || bad_a);
-                fast = fast && !bad_any;
-            }
-            if (fast) {
-                // Anchors k with xl + k < W and 0 <= xl + k + dx < W (all of
-                // them for interior lanes).
-                uint32_t mask = (1u << PX) - 1u;
-                if (!warp_interior) {
-                    const int lo_k = max(0, -of.dx - xl);
-                    const int hi_k = min(min(PX, wrem), wrem - of.dx);
-                    mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
-                }
-                dispatch_fast<BPP, true>(of.dx, A, B, j, h, bytecode, mask);
-            } else if (xl < j.W) {
-                vote_slow(j, of.dx, of.dy, y, xl, PX, h, err);
+            // Lanes 1..31 take their left halo from the lane before, lanes
+            // 0..30 their right halo from the lane after.
+            const uint32_t up = __shfl_up_sync(0xffffffffu, P[LW - 1], 1);
+            const uint32_t down = __shfl_down_sync(0xffffffffu, P[0], 1);
+            B[0] = lane == 0 ? left : up;
+#pragma unroll
+            for (int w = 0; w < LW; ++w)
+                B[w + 1] = P[w];
+            B[LW + 1] = lane == 31 ? right : down;
+            cur_dy = of.dy;
+        }
+        bool fast = j.aligned && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
+        if (j.levels_mode) {
+            // Neighbour halos may carry an out-of-range level: check them too.
+            const bool bad_any = __any_sync(0xffffffffu, bad_b || bad_a);
+            fast = fast && !bad_any;
+        }
+        if (fast && warp_interior) {
+            dispatch_fast<BPP, false>(of.dx, A, B, j, h, bytecode, 0u);
+        } else if (fast) {
+            // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
+            const int lo_k = max(0, -of.dx - xl);
+            const int hi_k = min(min(PX, wrem), wrem - of.dx);
+            const uint32_t mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
+            dispatch_fast<BPP, true>(of.dx, A, B, j, h, bytecode, mask);
+        } else if (xl < j.W) {
+            vote_slow(j, of.dx, of.dy, y, xl, PX, h, err);
+        }
+    }
+}
+
+// All row tasks of items [ka, kb) of one job: warp w takes tasks w, w + nwarps,
+// ...; the loads of its next task are issued before it votes the current one.
+template <int BPP>
+__device__ __forceinline__ void vote_segment(const VoteJob& j, int ka, int kb, const OffInfo* s_off, int dy1,
+                                             unsigned* err)
+{
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int n_tasks = (kb - ka) * j.band_rows;
+    int t = warp;
+    if (t >= n_tasks)
+        return;
+    Task q = task_of<BPP>(j, ka, t);
+    RawRow ra, rb;
+    const bool pre_b = dy1 != 0;
+    if (q.valid && j.aligned) {
+        fetch_raw<BPP>(j, q.y, q.xl, ra);
+        if (pre_b && q.y + dy1 >= 0 && q.y + dy1 < j.H)
+            fetch_raw<BPP>(j, q.y + dy1, q.xl, rb);
+    }
+    for (; t < n_tasks; t += nwarps) {
+        const int tn = t + nwarps;
+        Task qn;
+        qn.valid = false;
+        RawRow na, nb;
+        if (tn < n_tasks) {
+            qn = task_of<BPP>(j, ka, tn);
+            if (qn.valid && j.aligned) {
+                fetch_raw<BPP>(j, qn.y, qn.xl, na);
+                if (pre_b && qn.y + dy1 >= 0 && qn.y + dy1 < j.H)
+                    fetch_raw<BPP>(j, qn.y + dy1, qn.xl, nb);
             }
         }
+        if (q.valid)
+            vote_task<BPP>(j, s_off, dy1, q, ra, rb, err);
+        q = qn;
+        ra = na;
+        rb = nb;
     }
 }
 
@@ -460,7 +596,8 @@ template <int BPP, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(16) uint32_t hist[];
-    __shared__ int s_k0, s_k1, s_job;
+    __shared__ int s_k0, s_k1, s_job, s_dy1;
+    __shared__ OffInfo s_off[kMaxJobOffsets];
     for (int i = threadIdx.x; i < p.max_hist_words; i += blockDim.x)
         hist[i] = 0u;
     if (threadIdx.x == 0) {
@@ -479,54 +616,51 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
         s_job = lo;
     }
     __syncthreads();
-    const int k0 = s_k0, k1 = s_k1;
+    const int k1 = s_k1;
+    int k = s_k0;
     int job = s_job;
-    int cur = -1;  // job whose partial histogram is in shared memory
-    int acc = 0;   // rows per warp voted into 16-bit halves since the last merge
+    const uint32_t hbase = smem_u32(hist);
     const int nwarps = blockDim.x >> 5;
-    for (int k = k0; k < k1; ++k) {
+    while (k < k1) {
         while (job + 1 < p.n_jobs && p.jobs[job + 1].item0 <= k)
             ++job;
         const VoteJob j = p.jobs[job];
-        VoteItem it;
-        {
-            const int local = k - j.item0;
-            const int band = local / j.n_strips;
-            const int strip = local - band * j.n_strips;
-            it.job = job;
-            it.x0 = strip * 32 * (16 / BPP);
-            it.y0 = j.y_begin + band * j.band_rows;
-            it.y1 = min(j.y_end, it.y0 + j.band_rows);
-        }
-        const int rows_per_warp = (it.y1 - it.y0 + nwarps - 1) / nwarps;
-        if (cur >= 0) {
-            const VoteJob& cj = p.jobs[cur];
-            bool need = cur != job;
-            if (!need && cj.layout == 2) {
-                // Bound the votes per 16-bit half: threads per copy x pixels.
-                const long long per_half =
-                    (long long)(acc + rows_per_warp) * (16 / BPP) * (blockDim.x >> cj.rshift);
-                need = per_half > 65535;
-            }
-            if (need) {
-                flush_hist(cj, p.offs, hist);
-                __syncthreads();
-                cur = -1;
-                acc = 0;
-            }
-        }
-        cur = job;
-        acc += rows_per_warp;
-        if (j.hist_words > p.max_hist_words) {
+        const int seg_end = min(k1, j.item0 + j.n_job_items);
+        if (j.hist_words > p.max_hist_words || j.n_off > kMaxJobOffsets) {
             if (threadIdx.x == 0)
                 atomicOr(p.err, kErrInternal);
-        } else {
-            process_item<BPP>(j, p.offs, it, hist, p.err);
+            k = seg_end;
+            continue;
+        }
+        // Stage the job's offsets (previous readers finished at the last barrier).
+        if (threadIdx.x < j.n_off) {
+            const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
+            const HistRef h = hist_ref(j, threadIdx.x, hbase, 0);
+            s_off[threadIdx.x] = OffInfo{vo.dx, vo.dy, h.base, h.inc};
+        }
+        if (threadIdx.x == 0) {
+            int d1 = 0;
+            for (int o = 0; o < j.n_off && d1 == 0; ++o)
+                d1 = p.offs[j.off0 + o].dy;
+            s_dy1 = d1;
         }
         __syncthreads();
+        // Items per merge: unbounded for 32-bit counters; 16-bit halves stay
+        // below 65536 votes (rows per warp x pixels x threads per copy).
+        int step = seg_end - k;
+        if (j.layout == 2) {
+            const long long rows_ok = 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift));
+            step = (int)max(1ll, min((long long)step, rows_ok * nwarps / j.band_rows));
+        }
+        for (int ka = k; ka < seg_end; ka += step) {
+            const int kb = min(seg_end, ka + step);
+            vote_segment<BPP>(j, ka, kb, s_off, s_dy1, p.err);
+            __syncthreads();
+            flush_hist(j, p.offs, hist);
+            __syncthreads();
+        }
+        k = seg_end;
     }
-    if (cur >= 0)
-        flush_hist(p.jobs[cur], p.offs, hist);
 }
 
 // Scheme 1 of the paper (Sec. I.B): one thread per anchor pixel, one global
