@@ -53,7 +53,8 @@ struct VotePlan {
     int n_items = 0;
     double total_w = 0.0;
     int max_hist_words = 0;
-    int threads = 0;  // max over the plan's jobs
+    int tile_rows = 0;  // max staged tile rows over the plan's jobs
+    int threads = 0;    // max over the plan's jobs
     int bpp = 1;
 };
 
@@ -194,10 +195,16 @@ long long cfg_key(int levels, int n_off, int bpp)
     return ((long long)levels << 20) | ((long long)n_off << 4) | bpp;
 }
 
+// Staged tiles: at most kTileRows rows (anchor band + dy halo) of
+// vote_row_bytes() bytes each, two buffers per CTA.
+constexpr int kTileRows = 48;
+constexpr int kDefaultBand = 32;
+
 int hist_budget_words(const glcm_ctx* ctx)
 {
-    // Leave room for static shared memory and the per-SM reservation.
-    return (ctx->smem_optin - 4096) / 4;
+    // Leave room for the two tile buffers, static shared memory and the
+    // per-block reservation.
+    return (ctx->smem_optin - 2 * kTileRows * vote_row_bytes() - 4096) / 4;
 }
 
 // Offsets per histogram group and words per bin row of a group.
@@ -302,11 +309,9 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     const int rows = s.y_end - s.y_begin;
     const int strip_px = 32 * PX;
     const int n_strips = std::max(1, (s.W + strip_px - 1) / strip_px);
-    int band = cfg.band_rows;
-    if (band <= 0) {
-        long long per = (long long)rows * n_strips / std::max(1, target_items);
-        band = (int)std::max<long long>(nwarps, ((per + nwarps - 1) / nwarps) * nwarps);
-    }
+    (void)target_items;
+    int band = cfg.band_rows > 0 ? cfg.band_rows : kDefaultBand;
+    band = std::min(band, kTileRows - kMaxDySpan);
     if (cfg.layout == 2) {
         // votes per 16-bit half per item: ceil(band/nwarps) * PX * (T / R) <= 65535
         const long long max_rows_per_warp = 65535ll * (1 << cfg.rshift) / ((long long)PX * T);
@@ -326,8 +331,21 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     for (int sb0 = s.y_begin; sb0 < s.y_end; sb0 += sb_rows) {
         const int sb1 = std::min(s.y_end, sb0 + sb_rows);
         const int n_bands = (sb1 - sb0 + band - 1) / band;
-        for (int o0 = 0; o0 < s.n_off; o0 += per_job) {
-            const int cnt = std::min(per_job, s.n_off - o0);
+        for (int o0 = 0; o0 < s.n_off;) {
+            // Up to per_job consecutive offsets (sorted by dy) whose dy range,
+            // with 0, spans at most kMaxDySpan rows; a lone wider offset is
+            // voted unstaged.
+            int cnt = 1;
+            int dmin = std::min(0, s.offsets[order[o0]].dy), dmax = std::max(0, s.offsets[order[o0]].dy);
+            while (o0 + cnt < s.n_off && cnt < per_job) {
+                const int d = s.offsets[order[o0 + cnt]].dy;
+                const int nmin = std::min(dmin, d), nmax = std::max(dmax, d);
+                if (nmax - nmin > kMaxDySpan && dmax - dmin <= kMaxDySpan)
+                    break;
+                dmin = nmin;
+                dmax = nmax;
+                ++cnt;
+            }
             for (int lv = 0; lv < s.levels; lv += shape.span) {
                 const int span = std::min(shape.span, s.levels - lv);
                 VoteJob j{};
@@ -363,7 +381,12 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                 j.band_rows = band;
                 j.y_begin = sb0;
                 j.y_end = sb1;
+                j.dy_min = dmin;
+                j.dy_max = dmax;
+                j.staged = (dmax - dmin <= kMaxDySpan) ? 1 : 0;
                 j.out = s.out;
+                if (j.staged)
+                    plan.tile_rows = std::max(plan.tile_rows, band + dmax - dmin);
                 for (int k = o0; k < o0 + cnt; ++k) {
                     VoteOffset vo{};
                     vo.dx = s.offsets[order[k]].dx;
@@ -378,6 +401,7 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                 else
                     plan.offs.resize(j.off0);
             }
+            o0 += cnt;
         }
     }
     return GLCM_OK;
@@ -412,9 +436,14 @@ int target_items(const glcm_ctx* ctx)
     return ctx->sm_count * 4;
 }
 
+size_t vote_smem(const VotePlan& plan)
+{
+    return std::max<size_t>(16, 2 * (size_t)plan.tile_rows * vote_row_bytes() + (size_t)plan.max_hist_words * 4);
+}
+
 int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 {
-    const size_t smem = std::max<size_t>(16, (size_t)plan.max_hist_words * 4);
+    const size_t smem = vote_smem(plan);
     const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem));
     return std::max(1, std::min(plan.n_items, ctx->sm_count * per_sm));
 }
@@ -497,9 +526,10 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     vp.n_items = plan.n_items;
     vp.total_w = plan.total_w;
     vp.max_hist_words = plan.max_hist_words;
+    vp.tile_bytes = plan.tile_rows * vote_row_bytes();
     vp.item_counter = ctx->d_words + 1;
     vp.err = ctx->d_words;
-    const size_t smem = std::max<size_t>(16, (size_t)plan.max_hist_words * 4);
+    const size_t smem = vote_smem(plan);
     const int grid = grid_for(ctx, plan);
     TimedPair tp{};
     const bool time_it = ctx->timing && !capturing;
@@ -1070,6 +1100,8 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
                 dst.total_w += (double)c.w_item * c.n_job_items;
                 dst.n_items += cnt_items;
                 dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
+                if (c.staged)
+                    dst.tile_rows = std::max(dst.tile_rows, c.band_rows + c.dy_max - c.dy_min);
                 dst.jobs.push_back(c);
             }
         }

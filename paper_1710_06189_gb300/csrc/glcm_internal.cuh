@@ -9,6 +9,8 @@ namespace glcm {
 // Fast-path horizontal reach: a lane holds its own pixels plus one word of
 // quantized levels (4 levels) from each neighbouring lane.
 constexpr int kFastMaxDx = 4;
+// Largest dy_max - dy_min a staged job may have (tile halo rows).
+constexpr int kMaxDySpan = 16;
 constexpr int kMaxThreads = 1024;
 // Bounded spin limit for any device-side wait (none on the vote path today;
 // kept for the persistent serving kernels).
@@ -46,6 +48,8 @@ struct VoteJob {
     int n_strips;      // column strips of 32 lanes x 16 bytes
     int band_rows;     // anchor rows per work item
     int y_begin, y_end;  // anchor rows voted by this job ([0, H) for a whole image)
+    int dy_min, dy_max;  // min(0, dy) and max(0, dy) over the job's offsets
+    int staged;          // tiles go through shared memory (dy_max - dy_min <= kMaxDySpan)
     uint32_t* out;     // counts: offset slot s at out + s*N*N
 };
 
@@ -68,6 +72,7 @@ struct VoteParams {
     const VoteOffset* offs;
     int n_items;
     double total_w;          // summed weight of all items
+    int tile_bytes;          // one staged tile buffer (two are allocated)
     int max_hist_words;
     unsigned* item_counter;  // zeroed before each launch (unused by the static schedule)
     unsigned* err;           // error bits (kErr*)
@@ -116,5 +121,6 @@ long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
 int vote_max_smem_optin();
 int vote_blocks_per_sm(int bpp, int threads, size_t smem);
+int vote_row_bytes();
 
 }  // namespace glcm

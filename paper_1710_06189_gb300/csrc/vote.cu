@@ -1,44 +1,52 @@
-// GLCM vote kernels: quantize -> partner lookup -> vote -> merge.
+// GLCM vote kernels: stage -> quantize -> partner lookup -> vote -> merge.
 //
 // What is computed (Sec. I.A, Eq. 1): for every anchor pixel (x, y) whose
 // partner (x + dx, y + dy) lies inside the image, with i and j the levels of
 // the two pixels, P[i][j] += 1.  Partner addressing follows Eq. 2 with no
 // pairing across the border, bins follow Eq. 3 with the anchor as the row.
 //
-// How (the paper's Scheme 2 copy strategy, Sec. II.A, redone for sm_103a):
-//  * Persistent CTAs (one per SM, 1024 threads) each take a contiguous,
-//    weight-balanced range of work items -- a strip of 32 lanes x 16 bytes
-//    of one job and a band of rows -- so a CTA spans few jobs and merges
-//    each once.  Each warp takes rows of the band; each lane owns 16 bytes of
-//    a row (16 uint8 or 8 uint16 pixels), read with one 128-bit
-//    non-coherent load and quantized in registers to packed level bytes.
-//  * The partner row of each distinct dy is read the same way; the 4 levels
-//    left and right of a lane come from its neighbours by shuffle, so every
-//    |dx| <= 4 partner is a byte extraction from registers.
+// How (the paper's Scheme 2 copy strategy, Sec. II.A, and its image
+// partitioning with halo, Sec. III, redone for sm_103a):
+//  * Work items are tiles: a strip of 512 bytes of a row range of one job
+//    (one image x one group of offsets x one anchor-level range).  Persistent
+//    CTAs (one per SM) each take a contiguous, weight-balanced range of
+//    items, so a CTA spans few jobs and merges each once.
+//  * A tile is staged into shared memory by TMA bulk copies
+//    (cp.async.bulk, one per row: 16 halo bytes + 512 + 16 halo bytes, plus
+//    the halo rows the offsets' dy need), double-buffered and completed on
+//    an mbarrier, so the copy of the next tile overlaps the votes of the
+//    current one.  Images whose base or pitch is not 16-byte aligned are
+//    staged by plain loads into the same layout.
+//  * Each lane reads its 16 bytes of a row (16 uint8 or 8 uint16 pixels) and
+//    the 4 pixels on each side from shared memory and quantizes them in
+//    registers to packed level bytes; the partner words of an offset are
+//    funnel shifts of the partner row's words.
 //  * Votes go into R private copies of the job's histograms in shared
 //    memory, interleaved so that copy c of a bin is word c of the bin's
-//    R-word row and lane l always uses copy l mod R: with R = 32 every lane
-//    of a warp hits its own bank whatever the data (the paper's copies are
+//    R-word row and lane l uses copy l mod R: with R = 32 every lane of a
+//    warp hits its own bank whatever the data (the paper's copies are
 //    contiguous, so equal bins of different copies share a bank).
 //    Layouts: (0) one R-word row per bin; (1) two offsets' rows interleaved
 //    per bin (R = 32: a bin is 256 bytes, so a byte code c addresses its bin
 //    as c << 8); (2) two offsets share each word as 16-bit halves -- the
-//    host bounds the votes per half between merges below 65536.
-//  * For N <= 16 (power of two) the 4 codes i*N + j of a word are formed
-//    with one shift and one OR, and each vote is one byte permute, one add
-//    and one shared-memory reduction.
-//  * A job may count only the anchors whose level lies in [lv_lo, lv_lo +
-//    lv_span): N = 256 histograms are split by anchor level so that each
-//    part fits one CTA's shared memory.
+//    merge comes before any half can reach 65536.
+//  * For N <= 16 (power of two) the 4 codes i*N + j of a word come from one
+//    shift and one OR; a vote is a byte permute, an add and a reduction.
 //  * The merge (Sec. II.A, last step) sums the copies and adds each non-zero
 //    bin into the global uint32 counts once per CTA and job.
-//  * Warps touching an image edge vote with per-anchor validity masks;
-//    unaligned images, |dx| > 4 and out-of-range pixels in levels mode take
-//    a per-pixel path with full bounds checks.
+//  * Edge lanes vote under per-anchor validity masks; |dx| > 4 and
+//    out-of-range pixels in levels mode take a per-pixel path with full
+//    bounds checks.  Every wait is bounded and reports a timeout bit.
 #include "glcm_internal.cuh"
 
 namespace glcm {
 namespace {
+
+constexpr int kStripBytes = 512;
+constexpr int kHaloBytes = 16;
+constexpr int kRowBytes = kStripBytes + 2 * kHaloBytes;
+constexpr int kMaxJobOffsets = 64;
+constexpr long long kTileWaitLimit = 1ll << 22;  // try_wait polls before a tile wait gives up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -50,17 +58,65 @@ __device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v)
     asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
+// Predicated reduction (no branch around it).
+__device__ __forceinline__ void red_shared_add_if(uint32_t addr, uint32_t v, uint32_t on)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr), "r"(v),
+        "r"(on));
+}
+
 __device__ __forceinline__ void red_global_add(uint32_t* p, uint32_t v)
 {
     asm volatile("red.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-__device__ __forceinline__ uint4 ldg_v4(const uint8_t* p)
+// ---- mbarrier + bulk copy (TMA) -------------------------------------------
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
 {
-    return __ldg(reinterpret_cast<const uint4*>(p));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
 
-// Raw pixel read with no alignment assumption.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Bounded wait for phase `parity` of `bar`; false (and the timeout bit) if
+// the limit is hit.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, unsigned* err)
+{
+    for (long long it = 0; it < kTileWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity))
+            return true;
+    atomicOr(err, kErrTimeout);
+    return false;
+}
+
+// ---- levels ----------------------------------------------------------------
+
 __device__ __forceinline__ uint32_t read_px(const VoteJob& j, int x, int y)
 {
     const uint8_t* row = j.img + (long long)y * j.pitch;
@@ -124,60 +180,82 @@ __device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, uint32_t w0, u
     return r;
 }
 
-// Levels of the 4 pixels starting at column x (x % 4 == 0); pixels outside
-// [0, W) read as level 0 and are masked out by the callers.
+// A staged row of the tile as this lane sees it: levels of its PX pixels
+// (LW words) with one 4-level halo word on each side.
 template <int BPP>
-__device__ __forceinline__ uint32_t load_group(const VoteJob& j, int y, int x, bool& bad)
+__device__ __forceinline__ void row_levels(const VoteJob& j, const uint8_t* trow, int lane, uint32_t (&A)[4 / BPP],
+                                           uint32_t& left, uint32_t& right, bool& bad)
 {
-    if (x < 0 || x >= j.W)
-        return 0u;
-    const uint8_t* p = j.img + (long long)y * j.pitch + (long long)x * BPP;
-    if (x + 4 <= j.W) {
-        if (BPP == 1)
-            return quant_u8x4(j, __ldg(reinterpret_cast<const uint32_t*>(p)), bad);
-        const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
-        return quant_u16x4(j, q.x, q.y, bad);
-    }
-    // Ragged right edge: the 1..3 pixels inside, one at a time.
-    uint32_t r = 0;
-    for (int b = 0; b < 4 && x + b < j.W; ++b) {
-        const uint32_t v = BPP == 1 ? (uint32_t)__ldg(p + b)
-                                    : ((uint32_t)__ldg(p + 2 * b) | ((uint32_t)__ldg(p + 2 * b + 1) << 8));
-        const uint32_t q = level_of(j, v);
-        bad |= q >= (uint32_t)j.levels;
-        r |= (q & 0xFFu) << (8 * b);
-    }
-    return r;
-}
-
-// Levels of pixels [xl, xl + PX) of row y as LW words (one 128-bit load when
-// the whole lane lies inside the row).
-template <int BPP>
-__device__ __forceinline__ void load_levels(const VoteJob& j, int y, int xl, uint32_t (&L)[4 / BPP], bool& bad)
-{
-    constexpr int PX = 16 / BPP;
-    constexpr int LW = PX / 4;
-    if (xl + PX <= j.W) {
-        const uint8_t* p = j.img + (long long)y * j.pitch + (long long)xl * BPP;
-        const uint4 r = ldg_v4(p);
-        if (BPP == 1) {
-            L[0] = quant_u8x4(j, r.x, bad);
-            L[1] = quant_u8x4(j, r.y, bad);
-            L[2 % LW] = quant_u8x4(j, r.z, bad);
-            L[3 % LW] = quant_u8x4(j, r.w, bad);
-        } else {
-            L[0] = quant_u16x4(j, r.x, r.y, bad);
-            L[1] = quant_u16x4(j, r.z, r.w, bad);
-        }
+    const uint8_t* c = trow + kHaloBytes + 16 * lane;
+    const uint4 v = *reinterpret_cast<const uint4*>(c);
+    if (BPP == 1) {
+        A[0] = quant_u8x4(j, v.x, bad);
+        A[1 % (4 / BPP)] = quant_u8x4(j, v.y, bad);
+        A[2 % (4 / BPP)] = quant_u8x4(j, v.z, bad);
+        A[3 % (4 / BPP)] = quant_u8x4(j, v.w, bad);
+        left = quant_u8x4(j, *reinterpret_cast<const uint32_t*>(c - 4), bad);
+        right = quant_u8x4(j, *reinterpret_cast<const uint32_t*>(c + 16), bad);
     } else {
-#pragma unroll
-        for (int w = 0; w < LW; ++w)
-            L[w] = load_group<BPP>(j, y, xl + 4 * w, bad);
+        A[0] = quant_u16x4(j, v.x, v.y, bad);
+        A[1] = quant_u16x4(j, v.z, v.w, bad);
+        const uint2 l = *reinterpret_cast<const uint2*>(c - 8);
+        const uint2 r = *reinterpret_cast<const uint2*>(c + 16);
+        left = quant_u16x4(j, l.x, l.y, bad);
+        right = quant_u16x4(j, r.x, r.y, bad);
     }
 }
 
-// Where offset o of a job votes: shared byte address of (bin 0, this lane's
-// copy), bytes between bins, and the increment (1 or 1 << 16).
+// Anchor levels only (no halos needed).
+template <int BPP>
+__device__ __forceinline__ void anchor_levels(const VoteJob& j, const uint8_t* trow, int lane,
+                                              uint32_t (&A)[4 / BPP], bool& bad)
+{
+    const uint4 v = *reinterpret_cast<const uint4*>(trow + kHaloBytes + 16 * lane);
+    if (BPP == 1) {
+        A[0] = quant_u8x4(j, v.x, bad);
+        A[1 % (4 / BPP)] = quant_u8x4(j, v.y, bad);
+        A[2 % (4 / BPP)] = quant_u8x4(j, v.z, bad);
+        A[3 % (4 / BPP)] = quant_u8x4(j, v.w, bad);
+    } else {
+        A[0] = quant_u16x4(j, v.x, v.y, bad);
+        A[1] = quant_u16x4(j, v.z, v.w, bad);
+    }
+}
+
+// Partner level words aligned with the anchor words: PW[m] holds the levels
+// of the partners of anchors 4m .. 4m + 3 for horizontal offset dx.
+template <int BPP>
+__device__ __forceinline__ void partner_words(int dx, const uint32_t (&B)[4 / BPP + 2], uint32_t (&PW)[4 / BPP])
+{
+    constexpr int LW = 4 / BPP;
+    // Byte t = 4m + dx + 4 of the extended row [left, B..., right].
+#define GLCM_PW(D)                                                                       \
+    case D:                                                                              \
+        _Pragma("unroll") for (int m = 0; m < LW; ++m)                                   \
+        {                                                                                \
+            constexpr int t0 = D + 4;                                                    \
+            const int t = 4 * m + t0;                                                    \
+            PW[m] = (t0 & 3) == 0 ? B[t >> 2] : __funnelshift_r(B[t >> 2], B[(t >> 2) + 1], 8 * (t0 & 3)); \
+        }                                                                                \
+        break;
+    switch (dx) {
+        GLCM_PW(-4)
+        GLCM_PW(-3)
+        GLCM_PW(-2)
+        GLCM_PW(-1)
+        GLCM_PW(0)
+        GLCM_PW(1)
+        GLCM_PW(2)
+        GLCM_PW(3)
+        GLCM_PW(4)
+        default:
+            break;
+    }
+#undef GLCM_PW
+}
+
+// Where offset o of a job votes: shared byte address of (bin 0, copy 0),
+// bytes between bins, and the increment (1 or 1 << 16).
 struct HistRef {
     uint32_t base;
     uint32_t stride;
@@ -205,53 +283,56 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
     return h;
 }
 
-// Fast vote of one lane's PX anchors for a compile-time dx.  With MASKED,
-// only the anchors whose bit is set in `mask` vote (image edges).
-template <int BPP, int DX, bool SPLIT, bool MASKED>
-__device__ __forceinline__ void vote_fast(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                          uint32_t N, uint32_t lo, uint32_t span, const HistRef& h, uint32_t mask)
+// Votes of one lane's PX anchors against partner words PW.  `mask` has a
+// bit per anchor that may vote (all set away from the image edges).
+template <int BPP>
+__device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)[4 / BPP],
+                                           const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask,
+                                           bool full)
 {
-    constexpr int PX = 16 / BPP;
+    constexpr int LW = 4 / BPP;
+    if (j.bytecode) {
+        const int L = j.log2n;
 #pragma unroll
-    for (int k = 0; k < PX; ++k) {
-        const uint32_t i = __byte_perm(A[k >> 2], 0u, 0x4440u | (uint32_t)(k & 3));
-        const int t = k + DX + 4;  // byte of the extended partner row
-        const uint32_t jv = __byte_perm(B[t >> 2], 0u, 0x4440u | (uint32_t)(t & 3));
-        const bool on = !MASKED || ((mask >> k) & 1u);
-        if (SPLIT) {
+        for (int m = 0; m < LW; ++m) {
+            const uint32_t code = (A[m] << L) | PW[m];
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t addr = h.base + __byte_perm(code, 0u, 0x4404u | (uint32_t)(b << 4));
+                if (full)
+                    red_shared_add(addr, 1u);
+                else
+                    red_shared_add_if(addr, 1u, (mask >> (4 * m + b)) & 1u);
+            }
+        }
+        return;
+    }
+    const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
+    const bool split = j.lv_span < j.levels;
+#pragma unroll
+    for (int m = 0; m < LW; ++m) {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
+            const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
             const uint32_t ii = i - lo;
-            if (on && ii < span)
-                red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
-        } else if (on) {
-            red_shared_add(h.base + (i * N + jv) * h.stride, h.inc);
+            uint32_t on = full ? 1u : ((mask >> (4 * m + b)) & 1u);
+            if (split)
+                on &= ii < span ? 1u : 0u;
+            const uint32_t addr = h.base + (ii * N + jv) * h.stride;
+            if (full && !split)
+                red_shared_add(addr, h.inc);
+            else
+                red_shared_add_if(addr, h.inc, on);
         }
     }
 }
 
-// N <= 16, power of two, layout 1 with 32 copies: code = (i << L) | j is a
-// byte and its bin starts at code << 8 bytes from the offset's base.
-template <int BPP, int DX, bool MASKED>
-__device__ __forceinline__ void vote_bytecode(const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                             int L, uint32_t base, uint32_t mask)
+// Per-pixel path with full checks (|dx| > 4, bad levels): reads the image.
+__device__ __noinline__ void vote_slow(const VoteJob* __restrict__ jp, int dx, int dy, int y, int xl, int px,
+                                       HistRef h, unsigned* err)
 {
-    constexpr int LW = 4 / BPP;
-#pragma unroll
-    for (int m = 0; m < LW; ++m) {
-        const int t = 4 * m + DX + 4;
-        const int w0 = t >> 2, s = t & 3;
-        const uint32_t pw = s == 0 ? B[w0] : __funnelshift_r(B[w0], B[w0 + 1], 8 * s);
-        const uint32_t code = (A[m] << L) | pw;
-#pragma unroll
-        for (int b = 0; b < 4; ++b)
-            if (!MASKED || ((mask >> (4 * m + b)) & 1u))
-                red_shared_add(base + __byte_perm(code, 0u, 0x4404u | (uint32_t)(b << 4)), 1u);
-    }
-}
-
-// Per-pixel path with full checks (unaligned images, wide dx, bad levels).
-__device__ __forceinline__ void vote_slow(const VoteJob& j, int dx, int dy, int y, int xl, int px, const HistRef& h,
-                          unsigned* err)
-{
+    const VoteJob& j = *jp;
     const int yp = y + dy;
     if (y < 0 || y >= j.H || yp < 0 || yp >= j.H)
         return;
@@ -274,37 +355,6 @@ __device__ __forceinline__ void vote_slow(const VoteJob& j, int dx, int dy, int 
             continue;
         red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
     }
-}
-
-template <int BPP, bool MASKED>
-__device__ __forceinline__ void dispatch_fast(int dx, const uint32_t (&A)[4 / BPP], const uint32_t (&B)[4 / BPP + 2],
-                                              const VoteJob& j, const HistRef& h, bool bytecode, uint32_t mask)
-{
-    const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
-    const bool split = j.lv_span < j.levels;
-#define GLCM_CASE(D)                                                        \
-    case D:                                                                 \
-        if (bytecode)                                                       \
-            vote_bytecode<BPP, D, MASKED>(A, B, j.log2n, h.base, mask);     \
-        else if (split)                                                     \
-            vote_fast<BPP, D, true, MASKED>(A, B, N, lo, span, h, mask);    \
-        else                                                                \
-            vote_fast<BPP, D, false, MASKED>(A, B, N, lo, span, h, mask);   \
-        break;
-    switch (dx) {
-        GLCM_CASE(-4)
-        GLCM_CASE(-3)
-        GLCM_CASE(-2)
-        GLCM_CASE(-1)
-        GLCM_CASE(0)
-        GLCM_CASE(1)
-        GLCM_CASE(2)
-        GLCM_CASE(3)
-        GLCM_CASE(4)
-        default:
-            break;
-    }
-#undef GLCM_CASE
 }
 
 // Sum the R copies of every bin row of the job's histograms into the global
@@ -351,221 +401,142 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
     }
 }
 
-// Per-offset vote parameters of the current job, staged in shared memory.
-struct OffInfo {
-    int dx, dy;
-    uint32_t base;    // shared byte address of (bin 0, copy 0)
-    uint32_t inc;     // 1 or 1 << 16
-};
-constexpr int kMaxJobOffsets = 64;
+// ---- tiles -------------------------------------------------------------------
 
-// Raw (not yet quantized) bytes of one lane's row chunk and its halos.
-struct RawRow {
-    uint4 v;          // the lane's 16 bytes
-    uint2 l, r;       // 4 pixels left / right of the lane (lanes 0 and 31 only)
+struct Tile {
+    int x0;          // first anchor column
+    int y0, y1;      // anchor rows
+    int ty0, ty1;    // image rows staged (anchor rows plus the dy halo)
 };
 
-// One warp's row task: anchor row y, lane columns [xl, xl + PX).
-struct Task {
-    int y, xl;
-    bool valid;
-};
-
-template <int BPP>
-__device__ __forceinline__ Task task_of(const VoteJob& j, int k0, int t)
+__device__ __forceinline__ Tile tile_of(const VoteJob& j, int k)
 {
-    constexpr int PX = 16 / BPP;
-    Task q;
-    const int item = k0 + t / j.band_rows;
-    const int rib = t - (t / j.band_rows) * j.band_rows;
-    const int local = item - j.item0;
+    Tile t;
+    const int local = k - j.item0;
     const int band = local / j.n_strips;
     const int strip = local - band * j.n_strips;
-    q.y = j.y_begin + band * j.band_rows + rib;
-    q.xl = strip * 32 * PX + (threadIdx.x & 31) * PX;
-    q.valid = q.y < j.y_end;
-    return q;
+    t.x0 = strip * (kStripBytes / j.bpp);
+    t.y0 = j.y_begin + band * j.band_rows;
+    t.y1 = min(j.y_end, t.y0 + j.band_rows);
+    t.ty0 = max(0, t.y0 + j.dy_min);
+    t.ty1 = min(j.H, t.y1 + j.dy_max);
+    return t;
 }
 
-// Issue the loads of a lane's full chunk (and lane 0/31 halos) of row y.
-template <int BPP>
-__device__ __forceinline__ void fetch_raw(const VoteJob& j, int y, int xl, RawRow& r)
+// Issue the bulk copies of a tile into `buf` (warp 0): each staged row is the
+// 16-byte-aligned byte range [x0*bpp - 16, x0*bpp + 528) clipped to the row's
+// 16-byte-rounded width.  Lane 0 announces the byte count first.
+__device__ __forceinline__ void issue_tile(const VoteJob& j, const Tile& t, uint8_t* buf, uint64_t* bar)
 {
-    constexpr int PX = 16 / BPP;
     const int lane = threadIdx.x & 31;
-    const uint8_t* row = j.img + (long long)y * j.pitch;
-    r.v = make_uint4(0u, 0u, 0u, 0u);
-    r.l = make_uint2(0u, 0u);
-    r.r = make_uint2(0u, 0u);
-    if (xl + PX <= j.W)
-        r.v = ldg_v4(row + (long long)xl * BPP);
-    if (lane == 0 && xl >= 4) {
-        if (BPP == 1)
-            r.l.x = __ldg(reinterpret_cast<const uint32_t*>(row + xl - 4));
-        else
-            r.l = __ldg(reinterpret_cast<const uint2*>(row + 2ll * (xl - 4)));
-    }
-    if (lane == 31 && xl + PX + 4 <= j.W) {
-        if (BPP == 1)
-            r.r.x = __ldg(reinterpret_cast<const uint32_t*>(row + xl + PX));
-        else
-            r.r = __ldg(reinterpret_cast<const uint2*>(row + 2ll * (xl + PX)));
-    }
-}
-
-// Quantize a prefetched chunk into level words; lanes whose chunk is partial
-// (right image edge) load their groups now, byte-exact.
-template <int BPP>
-__device__ __forceinline__ void levels_of_raw(const VoteJob& j, int y, int xl, const RawRow& r,
-                                              uint32_t (&L)[4 / BPP], bool& bad)
-{
-    constexpr int PX = 16 / BPP;
-    if (xl + PX <= j.W) {
-        if (BPP == 1) {
-            L[0] = quant_u8x4(j, r.v.x, bad);
-            L[1 % (4 / BPP)] = quant_u8x4(j, r.v.y, bad);
-            L[2 % (4 / BPP)] = quant_u8x4(j, r.v.z, bad);
-            L[3 % (4 / BPP)] = quant_u8x4(j, r.v.w, bad);
-        } else {
-            L[0] = quant_u16x4(j, r.v.x, r.v.y, bad);
-            L[1] = quant_u16x4(j, r.v.z, r.v.w, bad);
+    const int xb = t.x0 * j.bpp - kHaloBytes;
+    const int row_end = ((j.W * j.bpp) + 15) & ~15;
+    const int cb0 = max(0, xb), cb1 = min(row_end, xb + kRowBytes);
+    const int bytes = max(0, cb1 - cb0);
+    const int rows = max(0, t.ty1 - t.ty0);
+    if (lane == 0)
+        mbar_arrive_expect_tx(bar, (uint32_t)(bytes * rows));
+    __syncwarp();
+    if (bytes > 0) {
+        for (int r = lane; r < rows; r += 32) {
+            const uint8_t* src = j.img + (long long)(t.ty0 + r) * j.pitch + cb0;
+            bulk_copy_g2s(buf + r * kRowBytes + (cb0 - xb), src, (uint32_t)bytes, bar);
         }
-    } else {
-        load_levels<BPP>(j, y, xl, L, bad);
     }
 }
 
-template <int BPP>
-__device__ __forceinline__ uint32_t halo_of_raw(const VoteJob& j, int y, int x, const uint2& raw, bool& bad)
+// Unaligned images: the whole CTA copies the tile with plain loads.
+__device__ void fill_tile_plain(const VoteJob& j, const Tile& t, uint8_t* buf)
 {
-    // Whole group inside the row: use the prefetched bytes; else exact loads.
-    if (x >= 0 && x + 4 <= j.W)
-        return BPP == 1 ? quant_u8x4(j, raw.x, bad) : quant_u16x4(j, raw.x, raw.y, bad);
-    return load_group<BPP>(j, y, x, bad);
+    const int xb = t.x0 * j.bpp - kHaloBytes;
+    const int row_bytes = j.W * j.bpp;
+    const int rows = max(0, t.ty1 - t.ty0);
+    for (int e = threadIdx.x; e < rows * kRowBytes; e += blockDim.x) {
+        const int r = e / kRowBytes, b = e - r * kRowBytes;
+        const int col = xb + b;
+        uint8_t v = 0;
+        if (col >= 0 && col < row_bytes)
+            v = __ldg(j.img + (long long)(t.ty0 + r) * j.pitch + col);
+        buf[e] = v;
+    }
 }
 
-// Vote every offset of one row task.  A is the anchor row; PA/PB (raw) are
-// the prefetched anchor row and first partner row (dy = dy1).
+// Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps, ...
 template <int BPP>
-__device__ __forceinline__ void vote_task(const VoteJob& j, const OffInfo* s_off, int dy1, const Task& q,
-                                          const RawRow& ra, const RawRow& rb, unsigned* err)
+__device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
+                                          const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
-    const int lane = threadIdx.x & 31;
-    const int xl = q.xl, y = q.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int xl = t.x0 + lane * PX;
     const uint32_t cbytes = 4u * (uint32_t)(lane & ((1 << j.rshift) - 1));
-    const uint32_t stride = (j.layout == 1 ? 8u : 4u) << j.rshift;
-    const bool bytecode = j.bytecode != 0;
     const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
-    const bool warp_interior = __all_sync(0xffffffffu, lane_interior);
+    const bool full = __all_sync(0xffffffffu, lane_interior);
     const int wrem = j.W - xl;
-    bool bad_a = false;
-    uint32_t A[LW];
-    if (j.aligned)
-        levels_of_raw<BPP>(j, y, xl, ra, A, bad_a);
-    int cur_dy = 0x7fffffff;
-    uint32_t B[LW + 2];
-    bool bad_b = false;
-    for (int o = 0; o < j.n_off; ++o) {
-        const OffInfo of = s_off[o];
-        const int yp = y + of.dy;
-        if (yp < 0 || yp >= j.H)
-            continue;
-        HistRef h;
-        h.base = of.base + cbytes;
-        h.stride = stride;
-        h.inc = of.inc;
-        if (j.aligned && of.dy != cur_dy) {
-            bad_b = false;
-            uint32_t P[LW];
-            uint32_t left, right;
-            if (of.dy == 0) {
+    for (int y = t.y0 + warp; y < t.y1; y += nwarps) {
+        bool bad_a = false;
+        uint32_t A[LW];
+        anchor_levels<BPP>(j, buf + (y - t.ty0) * kRowBytes, lane, A, bad_a);
+        int cur_dy = 0x7fffffff;
+        uint32_t B[LW + 2];
+        bool bad_b = false;
+        for (int o = 0; o < j.n_off; ++o) {
+            const int2 d = s_off_d[o];
+            const int yp = y + d.y;
+            if (yp < 0 || yp >= j.H)
+                continue;
+            HistRef h = s_off_h[o];
+            h.base += cbytes;
+            if (d.y != cur_dy) {
+                bad_b = false;
+                uint32_t P[LW];
+                row_levels<BPP>(j, buf + (yp - t.ty0) * kRowBytes, lane, P, B[0], B[LW + 1], bad_b);
 #pragma unroll
                 for (int w = 0; w < LW; ++w)
-                    P[w] = A[w];
-                bad_b = bad_a;
-                left = halo_of_raw<BPP>(j, yp, xl - 4, ra.l, bad_b);
-                right = halo_of_raw<BPP>(j, yp, xl + PX, ra.r, bad_b);
-            } else if (of.dy == dy1) {
-                levels_of_raw<BPP>(j, yp, xl, rb, P, bad_b);
-                left = halo_of_raw<BPP>(j, yp, xl - 4, rb.l, bad_b);
-                right = halo_of_raw<BPP>(j, yp, xl + PX, rb.r, bad_b);
-            } else {
-                load_levels<BPP>(j, yp, xl, P, bad_b);
-                left = load_group<BPP>(j, yp, xl - 4, bad_b);
-                right = load_group<BPP>(j, yp, xl + PX, bad_b);
+                    B[w + 1] = P[w];
+                cur_dy = d.y;
             }
-            // Lanes 1..31 take their left halo from the lane before, lanes
-            // 0..30 their right halo from the lane after.
-            const uint32_t up = __shfl_up_sync(0xffffffffu, P[LW - 1], 1);
-            const uint32_t down = __shfl_down_sync(0xffffffffu, P[0], 1);
-            B[0] = lane == 0 ? left : up;
-#pragma unroll
-            for (int w = 0; w < LW; ++w)
-                B[w + 1] = P[w];
-            B[LW + 1] = lane == 31 ? right : down;
-            cur_dy = of.dy;
-        }
-        bool fast = j.aligned && of.dx >= -kFastMaxDx && of.dx <= kFastMaxDx;
-        if (j.levels_mode) {
-            // Neighbour halos may carry an out-of-range level: check them too.
-            const bool bad_any = __any_sync(0xffffffffu, bad_b || bad_a);
-            fast = fast && !bad_any;
-        }
-        if (fast && warp_interior) {
-            dispatch_fast<BPP, false>(of.dx, A, B, j, h, bytecode, 0u);
-        } else if (fast) {
-            // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
-            const int lo_k = max(0, -of.dx - xl);
-            const int hi_k = min(min(PX, wrem), wrem - of.dx);
-            const uint32_t mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
-            dispatch_fast<BPP, true>(of.dx, A, B, j, h, bytecode, mask);
-        } else if (xl < j.W) {
-            vote_slow(j, of.dx, of.dy, y, xl, PX, h, err);
+            bool fast = d.x >= -kFastMaxDx && d.x <= kFastMaxDx;
+            if (j.levels_mode) {
+                // A neighbour's halo may carry an out-of-range level: check all.
+                fast = fast && !__any_sync(0xffffffffu, bad_a || bad_b);
+            }
+            if (fast) {
+                uint32_t PW[LW];
+                partner_words<BPP>(d.x, B, PW);
+                uint32_t mask = 0xFFFFu;
+                if (!full) {
+                    // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
+                    const int lo_k = max(0, -d.x - xl);
+                    const int hi_k = min(min(PX, wrem), wrem - d.x);
+                    mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
+                }
+                vote_words<BPP>(j, A, PW, h, mask, full);
+            } else if (xl < j.W) {
+                vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
+            }
         }
     }
 }
 
-// All row tasks of items [ka, kb) of one job: warp w takes tasks w, w + nwarps,
-// ...; the loads of its next task are issued before it votes the current one.
+// Jobs whose offsets span too many rows to stage: per-pixel votes only.
 template <int BPP>
-__device__ __forceinline__ void vote_segment(const VoteJob& j, int ka, int kb, const OffInfo* s_off, int dy1,
-                                             unsigned* err)
+__device__ void vote_tile_unstaged(const VoteJob& j, const VoteJob* jg, const Tile& t, const HistRef* s_off_h,
+                                   const int2* s_off_d, unsigned* err)
 {
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int n_tasks = (kb - ka) * j.band_rows;
-    int t = warp;
-    if (t >= n_tasks)
+    constexpr int PX = 16 / BPP;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int xl = t.x0 + lane * PX;
+    const uint32_t cbytes = 4u * (uint32_t)(lane & ((1 << j.rshift) - 1));
+    if (xl >= j.W)
         return;
-    Task q = task_of<BPP>(j, ka, t);
-    RawRow ra, rb;
-    const bool pre_b = dy1 != 0;
-    if (q.valid && j.aligned) {
-        fetch_raw<BPP>(j, q.y, q.xl, ra);
-        if (pre_b && q.y + dy1 >= 0 && q.y + dy1 < j.H)
-            fetch_raw<BPP>(j, q.y + dy1, q.xl, rb);
-    }
-    for (; t < n_tasks; t += nwarps) {
-        const int tn = t + nwarps;
-        Task qn;
-        qn.valid = false;
-        RawRow na, nb;
-        if (tn < n_tasks) {
-            qn = task_of<BPP>(j, ka, tn);
-            if (qn.valid && j.aligned) {
-                fetch_raw<BPP>(j, qn.y, qn.xl, na);
-                if (pre_b && qn.y + dy1 >= 0 && qn.y + dy1 < j.H)
-                    fetch_raw<BPP>(j, qn.y + dy1, qn.xl, nb);
-            }
+    for (int y = t.y0 + warp; y < t.y1; y += nwarps)
+        for (int o = 0; o < j.n_off; ++o) {
+            HistRef h = s_off_h[o];
+            h.base += cbytes;
+            vote_slow(jg, s_off_d[o].x, s_off_d[o].y, y, xl, PX, h, err);
         }
-        if (q.valid)
-            vote_task<BPP>(j, s_off, dy1, q, ra, rb, err);
-        q = qn;
-        ra = na;
-        rb = nb;
-    }
 }
 
 // First item whose starting weight is >= w (items of a job all weigh w_item).
@@ -590,17 +561,24 @@ __device__ int item_at(const VoteParams& p, double w)
 }
 
 // Persistent CTAs with a static, weight-balanced partition: CTA b votes the
-// contiguous item range covering weights [W b / G, W (b + 1) / G), so it
-// touches only the few jobs that range spans and merges each once.
+// contiguous item range covering weights [W b / G, W (b + 1) / G).  Dynamic
+// shared memory: two tile buffers, then the histograms.
 template <int BPP, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
-    extern __shared__ __align__(16) uint32_t hist[];
-    __shared__ int s_k0, s_k1, s_job, s_dy1;
-    __shared__ OffInfo s_off[kMaxJobOffsets];
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ __align__(8) uint64_t s_bar[2];
+    __shared__ int s_k0, s_k1, s_job, s_ok;
+    __shared__ HistRef s_off_h[kMaxJobOffsets];
+    __shared__ int2 s_off_d[kMaxJobOffsets];
+    uint8_t* tiles = smem;
+    uint32_t* hist = reinterpret_cast<uint32_t*>(smem + 2 * p.tile_bytes);
     for (int i = threadIdx.x; i < p.max_hist_words; i += blockDim.x)
         hist[i] = 0u;
     if (threadIdx.x == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         const double W = p.total_w;
         s_k0 = item_at(p, W * (double)blockIdx.x / (double)gridDim.x);
         s_k1 = blockIdx.x + 1 == gridDim.x ? p.n_items
@@ -614,6 +592,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
                 hi = mid - 1;
         }
         s_job = lo;
+        s_ok = 1;
     }
     __syncthreads();
     const int k1 = s_k1;
@@ -621,41 +600,65 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
     int job = s_job;
     const uint32_t hbase = smem_u32(hist);
     const int nwarps = blockDim.x >> 5;
+    uint32_t uses[2] = {0u, 0u};  // completed phases per tile buffer
     while (k < k1) {
         while (job + 1 < p.n_jobs && p.jobs[job + 1].item0 <= k)
             ++job;
-        const VoteJob j = p.jobs[job];
+        const VoteJob* jg = p.jobs + job;
+        const VoteJob j = *jg;
         const int seg_end = min(k1, j.item0 + j.n_job_items);
-        if (j.hist_words > p.max_hist_words || j.n_off > kMaxJobOffsets) {
+        const int tile_need = j.staged ? (j.band_rows + j.dy_max - j.dy_min) * kRowBytes : 0;
+        if (j.hist_words > p.max_hist_words || j.n_off > kMaxJobOffsets || tile_need > p.tile_bytes) {
             if (threadIdx.x == 0)
                 atomicOr(p.err, kErrInternal);
             k = seg_end;
             continue;
         }
-        // Stage the job's offsets (previous readers finished at the last barrier).
         if (threadIdx.x < j.n_off) {
             const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
-            const HistRef h = hist_ref(j, threadIdx.x, hbase, 0);
-            s_off[threadIdx.x] = OffInfo{vo.dx, vo.dy, h.base, h.inc};
-        }
-        if (threadIdx.x == 0) {
-            int d1 = 0;
-            for (int o = 0; o < j.n_off && d1 == 0; ++o)
-                d1 = p.offs[j.off0 + o].dy;
-            s_dy1 = d1;
+            s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
+            s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
         }
         __syncthreads();
-        // Items per merge: unbounded for 32-bit counters; 16-bit halves stay
-        // below 65536 votes (rows per warp x pixels x threads per copy).
+        // Items per merge: unbounded for 32-bit counters; 16-bit halves must
+        // stay below 65536 votes (rows per warp x pixels x threads per copy).
         int step = seg_end - k;
         if (j.layout == 2) {
             const long long rows_ok = 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift));
             step = (int)max(1ll, min((long long)step, rows_ok * nwarps / j.band_rows));
         }
+        const bool tma = j.staged && j.aligned;
         for (int ka = k; ka < seg_end; ka += step) {
             const int kb = min(seg_end, ka + step);
-            vote_segment<BPP>(j, ka, kb, s_off, s_dy1, p.err);
-            __syncthreads();
+            if (tma && threadIdx.x < 32)
+                issue_tile(j, tile_of(j, ka), tiles, &s_bar[0]);
+            for (int kk = ka; kk < kb; ++kk) {
+                const int b = (kk - ka) & 1;
+                uint8_t* buf = tiles + b * p.tile_bytes;
+                const Tile t = tile_of(j, kk);
+                if (!j.staged) {
+                    vote_tile_unstaged<BPP>(j, jg, t, s_off_h, s_off_d, p.err);
+                    __syncthreads();
+                    continue;
+                }
+                if (tma) {
+                    // Prefetch the next tile into the other buffer (its last
+                    // readers passed the barrier at the end of the previous item).
+                    if (kk + 1 < kb && threadIdx.x < 32)
+                        issue_tile(j, tile_of(j, kk + 1), tiles + (b ^ 1) * p.tile_bytes, &s_bar[b ^ 1]);
+                    if (!mbar_wait_bounded(&s_bar[b], uses[b] & 1u, p.err))
+                        s_ok = 0;
+                    uses[b]++;
+                } else {
+                    fill_tile_plain(j, t, buf);
+                    // Plain stores before a later bulk copy reuses the buffer.
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                }
+                if (s_ok)
+                    vote_tile<BPP>(j, jg, t, buf, s_off_h, s_off_d, p.err);
+                __syncthreads();
+            }
             flush_hist(j, p.offs, hist);
             __syncthreads();
         }
@@ -741,6 +744,8 @@ int vote_max_smem_optin()
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     return v;
 }
+
+int vote_row_bytes() { return kRowBytes; }
 
 int vote_blocks_per_sm(int bpp, int threads, size_t smem)
 {
