@@ -283,15 +283,16 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
     return h;
 }
 
-// Votes of one lane's PX anchors against partner words PW.  `mask` has a
-// bit per anchor that may vote (all set away from the image edges).
-template <int BPP>
+// Votes of one lane's PX anchors against partner words PW.  FULL: every
+// anchor votes; else only those whose bit is set in `mask` (image edges).
+// BYTECODE: N <= 16 power of two, 32 interleaved copies, one byte per code.
+// SPLIT: only anchors with level in [lo, lo + span) vote.
+template <int BPP, bool BYTECODE, bool SPLIT, bool FULL>
 __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)[4 / BPP],
-                                           const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask,
-                                           bool full)
+                                           const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask)
 {
     constexpr int LW = 4 / BPP;
-    if (j.bytecode) {
+    if (BYTECODE) {
         const int L = j.log2n;
 #pragma unroll
         for (int m = 0; m < LW; ++m) {
@@ -299,7 +300,7 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 const uint32_t addr = h.base + __byte_perm(code, 0u, 0x4404u | (uint32_t)(b << 4));
-                if (full)
+                if (FULL)
                     red_shared_add(addr, 1u);
                 else
                     red_shared_add_if(addr, 1u, (mask >> (4 * m + b)) & 1u);
@@ -308,23 +309,47 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
         return;
     }
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
-    const bool split = j.lv_span < j.levels;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
             const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
             const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
-            const uint32_t ii = i - lo;
-            uint32_t on = full ? 1u : ((mask >> (4 * m + b)) & 1u);
-            if (split)
-                on &= ii < span ? 1u : 0u;
+            const uint32_t ii = SPLIT ? i - lo : i;
             const uint32_t addr = h.base + (ii * N + jv) * h.stride;
-            if (full && !split)
+            if (FULL && !SPLIT) {
                 red_shared_add(addr, h.inc);
-            else
+            } else {
+                uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
+                if (SPLIT)
+                    on &= ii < span ? 1u : 0u;
                 red_shared_add_if(addr, h.inc, on);
+            }
         }
+    }
+}
+
+template <int BPP>
+__device__ __forceinline__ void vote_words_dispatch(const VoteJob& j, const uint32_t (&A)[4 / BPP],
+                                                    const uint32_t (&PW)[4 / BPP], const HistRef& h,
+                                                    uint32_t mask, bool full)
+{
+    const bool split = j.lv_span < j.levels;
+    if (j.bytecode) {
+        if (full)
+            vote_words<BPP, true, false, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, true, false, false>(j, A, PW, h, mask);
+    } else if (split) {
+        if (full)
+            vote_words<BPP, false, true, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, true, false>(j, A, PW, h, mask);
+    } else {
+        if (full)
+            vote_words<BPP, false, false, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, false, false>(j, A, PW, h, mask);
     }
 }
 
@@ -512,7 +537,7 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
                     const int hi_k = min(min(PX, wrem), wrem - d.x);
                     mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
                 }
-                vote_words<BPP>(j, A, PW, h, mask, full);
+                vote_words_dispatch<BPP>(j, A, PW, h, mask, full);
             } else if (xl < j.W) {
                 vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
             }
