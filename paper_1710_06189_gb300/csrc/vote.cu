@@ -223,22 +223,35 @@ __device__ __forceinline__ void anchor_levels(const VoteJob& j, const uint8_t* t
 }
 
 // Partner level words aligned with the anchor words: PW[m] holds the levels
-// of the partners of anchors 4m .. 4m + 3 for horizontal offset dx in
-// [-4, 4]: bytes 4m + dx + 4 .. of the extended row [left, B..., right],
-// picked with selects and one funnel shift (no branches).
+// of the partners of anchors 4m .. 4m + 3 for horizontal offset dx.
 template <int BPP>
 __device__ __forceinline__ void partner_words(int dx, const uint32_t (&B)[4 / BPP + 2], uint32_t (&PW)[4 / BPP])
 {
     constexpr int LW = 4 / BPP;
-    const int t0 = dx + 4;       // 0..8
-    const int q = t0 >> 2;       // word offset 0..2
-    const uint32_t sh = 8u * (uint32_t)(t0 & 3);
-#pragma unroll
-    for (int m = 0; m < LW; ++m) {
-        const uint32_t lo = q == 0 ? B[m] : (q == 1 ? B[m + 1] : B[m + 2]);
-        const uint32_t hi = q == 0 ? B[m + 1] : (q == 1 ? B[m + 2] : (m + 3 < LW + 2 ? B[m + 3 < LW + 2 ? m + 3 : LW + 1] : 0u));
-        PW[m] = __funnelshift_r(lo, hi, sh);
+    // Byte t = 4m + dx + 4 of the extended row [left, B..., right].
+#define GLCM_PW(D)                                                                       \
+    case D:                                                                              \
+        _Pragma("unroll") for (int m = 0; m < LW; ++m)                                   \
+        {                                                                                \
+            constexpr int t0 = D + 4;                                                    \
+            const int t = 4 * m + t0;                                                    \
+            PW[m] = (t0 & 3) == 0 ? B[t >> 2] : __funnelshift_r(B[t >> 2], B[(t >> 2) + 1], 8 * (t0 & 3)); \
+        }                                                                                \
+        break;
+    switch (dx) {
+        GLCM_PW(-4)
+        GLCM_PW(-3)
+        GLCM_PW(-2)
+        GLCM_PW(-1)
+        GLCM_PW(0)
+        GLCM_PW(1)
+        GLCM_PW(2)
+        GLCM_PW(3)
+        GLCM_PW(4)
+        default:
+            break;
     }
+#undef GLCM_PW
 }
 
 // Where offset o of a job votes: shared byte address of (bin 0, copy 0),
@@ -313,6 +326,30 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
                 red_shared_add_if(addr, h.inc, on);
             }
         }
+    }
+}
+
+template <int BPP>
+__device__ __forceinline__ void vote_words_dispatch(const VoteJob& j, const uint32_t (&A)[4 / BPP],
+                                                    const uint32_t (&PW)[4 / BPP], const HistRef& h,
+                                                    uint32_t mask, bool full)
+{
+    const bool split = j.lv_span < j.levels;
+    if (j.bytecode) {
+        if (full)
+            vote_words<BPP, true, false, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, true, false, false>(j, A, PW, h, mask);
+    } else if (split) {
+        if (full)
+            vote_words<BPP, false, true, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, true, false>(j, A, PW, h, mask);
+    } else {
+        if (full)
+            vote_words<BPP, false, false, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, false, false>(j, A, PW, h, mask);
     }
 }
 
@@ -449,21 +486,19 @@ __device__ void fill_tile_plain(const VoteJob& j, const Tile& t, uint8_t* buf)
     }
 }
 
-// Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps,
-// ...  BYTECODE / SPLIT select the vote body, FULL means no lane of the warp
-// touches an image edge (both fixed for the whole tile).
-template <int BPP, bool BYTECODE, bool SPLIT, bool FULL>
-__device__ __noinline__ void vote_tile_v(const VoteJob* __restrict__ jg, const Tile t, const uint8_t* buf,
-                                         const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
+// Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps, ...
+template <int BPP>
+__device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
+                                          const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
 {
-    const VoteJob j = *jg;
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const int xl = t.x0 + lane * PX;
     const uint32_t cbytes = 4u * (uint32_t)(lane & ((1 << j.rshift) - 1));
+    const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
+    const bool full = __all_sync(0xffffffffu, lane_interior);
     const int wrem = j.W - xl;
-    const bool lmode = j.levels_mode != 0;
     for (int y = t.y0 + warp; y < t.y1; y += nwarps) {
         bool bad_a = false;
         uint32_t A[LW];
@@ -488,50 +523,25 @@ __device__ __noinline__ void vote_tile_v(const VoteJob* __restrict__ jg, const T
                 cur_dy = d.y;
             }
             bool fast = d.x >= -kFastMaxDx && d.x <= kFastMaxDx;
-            if (lmode)  // a neighbour's halo may carry an out-of-range level
+            if (j.levels_mode) {
+                // A neighbour's halo may carry an out-of-range level: check all.
                 fast = fast && !__any_sync(0xffffffffu, bad_a || bad_b);
+            }
             if (fast) {
                 uint32_t PW[LW];
                 partner_words<BPP>(d.x, B, PW);
                 uint32_t mask = 0xFFFFu;
-                if (!FULL) {
+                if (!full) {
                     // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
                     const int lo_k = max(0, -d.x - xl);
                     const int hi_k = min(min(PX, wrem), wrem - d.x);
                     mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
                 }
-                vote_words<BPP, BYTECODE, SPLIT, FULL>(j, A, PW, h, mask);
+                vote_words_dispatch<BPP>(j, A, PW, h, mask, full);
             } else if (xl < j.W) {
                 vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
             }
         }
-    }
-}
-
-template <int BPP>
-__device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
-                                          const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
-{
-    constexpr int PX = 16 / BPP;
-    // The tile's strip touches an edge iff its first lane or its last lane does.
-    const int xa = t.x0, xz = t.x0 + 31 * PX;
-    const bool full = xa >= 4 && xz + PX + 4 <= j.W;
-    const bool split = j.lv_span < j.levels;
-    if (j.bytecode) {
-        if (full)
-            vote_tile_v<BPP, true, false, true>(jg, t, buf, s_off_h, s_off_d, err);
-        else
-            vote_tile_v<BPP, true, false, false>(jg, t, buf, s_off_h, s_off_d, err);
-    } else if (split) {
-        if (full)
-            vote_tile_v<BPP, false, true, true>(jg, t, buf, s_off_h, s_off_d, err);
-        else
-            vote_tile_v<BPP, false, true, false>(jg, t, buf, s_off_h, s_off_d, err);
-    } else {
-        if (full)
-            vote_tile_v<BPP, false, false, true>(jg, t, buf, s_off_h, s_off_d, err);
-        else
-            vote_tile_v<BPP, false, false, false>(jg, t, buf, s_off_h, s_off_d, err);
     }
 }
 
