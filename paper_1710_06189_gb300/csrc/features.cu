@@ -301,8 +301,44 @@ __device__ void reorth(float* x, const float* Q, int k, int len, float* s_coef, 
     (void)s_red;
 }
 
+// Largest singular value of the K x K upper bidiagonal matrix with
+// diagonal alpha_k = ab[2k] and superdiagonal beta_k = ab[2k+1]: bisection
+// with Sturm counts on the zero-diagonal tridiagonal matrix whose
+// off-diagonals are alpha_0, beta_0, alpha_1, ... (eigenvalues +-sigma).
+__device__ float gk_sigma_max(const float* ab, int steps)
+{
+    const int L = 2 * steps - 1;
+    if (L <= 0)
+        return 0.f;
+    float hi = 0.f;
+    for (int t = 0; t < L; ++t)
+        hi = fmaxf(hi, ab[t]);
+    hi *= 2.f;
+    float lo = 0.f;
+    for (int it = 0; it < 60; ++it) {
+        const float x = 0.5f * (lo + hi);
+        int cnt = 0;
+        float q = -x;
+        if (q < 0.f)
+            ++cnt;
+        for (int t = 0; t < L; ++t) {
+            const float b = ab[t];
+            if (q == 0.f)
+                q = -1e-30f;
+            q = -x - b * b / q;
+            if (q < 0.f)
+                ++cnt;
+        }
+        if (cnt >= L + 1)
+            hi = x;  // all eigenvalues below x
+        else
+            lo = x;
+    }
+    return 0.5f * (lo + hi);
+}
+
 __device__ float lanczos_sigma_max(const float* A, int m, int n, float* U, float* V, float* s_coef, float* s_red,
-                                   float* s_ab)
+                                   float* s_ab, float* s_sig, int* s_stop)
 {
     const int K = min(kMaxLanczos, min(m, n));
     float* v0 = V;
@@ -358,44 +394,26 @@ __device__ float lanczos_sigma_max(const float* A, int m, int n, float* U, float
             s_ab[2 * k + 1] = beta;
         if (!(beta > 1e-30f) || k + 1 == K)
             break;
+        // Every 8 steps: stop once the top Ritz value moved by < 1e-7.
+        if (((k + 1) & 7) == 0) {
+            if (threadIdx.x == 0) {
+                const float sg = gk_sigma_max(s_ab, k + 1);
+                *s_stop = (k + 1 >= 16 && fabsf(sg - *s_sig) <= 1e-7f) ? 1 : 0;
+                *s_sig = sg;
+            }
+            __syncthreads();
+            if (*s_stop)
+                break;
+        }
         for (int c = threadIdx.x; c < n; c += blockDim.x)
             vn[c] /= beta;
         __syncthreads();
     }
     __syncthreads();
-    // Off-diagonals of the Golub-Kahan tridiagonal: alpha_0, beta_1, alpha_1, ...
-    __shared__ float s_sig;
-    if (threadIdx.x == 0) {
-        const int L = 2 * steps - 1;  // number of off-diagonal entries used
-        float hi = 0.f;
-        for (int t = 0; t < L; ++t)
-            hi = fmaxf(hi, s_ab[t]);
-        hi *= 2.f;
-        float lo = 0.f;
-        for (int it = 0; it < 60 && L > 0; ++it) {
-            const float x = 0.5f * (lo + hi);
-            // Sturm count of eigenvalues < x of the (L+1) x (L+1) matrix.
-            int cnt = 0;
-            float q = -x;
-            if (q < 0.f)
-                ++cnt;
-            for (int t = 0; t < L; ++t) {
-                const float b = s_ab[t];
-                if (q == 0.f)
-                    q = -1e-30f;
-                q = -x - b * b / q;
-                if (q < 0.f)
-                    ++cnt;
-            }
-            if (cnt >= L + 1)
-                hi = x;  // all eigenvalues below x
-            else
-                lo = x;
-        }
-        s_sig = L > 0 ? 0.5f * (lo + hi) : 0.f;
-    }
+    if (threadIdx.x == 0)
+        *s_sig = gk_sigma_max(s_ab, steps);
     __syncthreads();
-    return s_sig;
+    return *s_sig;
 }
 
 __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
@@ -549,7 +567,14 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
             float* Vw = Uw + (long long)kMaxLanczos * nr;
             __shared__ float s_coef[kMaxLanczos + 1];
             __shared__ float s_ab[2 * kMaxLanczos + 2];
-            mcc = lanczos_sigma_max(A, nr, nc, Uw, Vw, s_coef, s_red, s_ab);
+            __shared__ float s_sg;
+            __shared__ int s_stop;
+            if (threadIdx.x == 0) {
+                s_sg = -1.f;
+                s_stop = 0;
+            }
+            __syncthreads();
+            mcc = lanczos_sigma_max(A, nr, nc, Uw, Vw, s_coef, s_red, s_ab, &s_sg, &s_stop);
         }
     }
     if (!have_work && threadIdx.x == 0)

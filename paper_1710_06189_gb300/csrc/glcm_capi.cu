@@ -51,7 +51,8 @@ struct VotePlan {
     std::vector<VoteJob> jobs;
     std::vector<VoteOffset> offs;
     int n_items = 0;
-    double total_w = 0.0;
+    std::vector<int3> chunks;  // (job, first item, end item), job-major
+    size_t chunk_off = 0;      // byte offset of this plan's chunks in the jobs buffer
     int max_hist_words = 0;
     int tile_rows = 0;  // max staged tile rows over the plan's jobs
     int threads = 0;    // max over the plan's jobs
@@ -374,9 +375,14 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                 j.n_job_items = n_strips * n_bands;
                 // Weight of an item: pixel loads plus expected votes (offsets x
                 // the share of anchor levels this job counts).
-                j.w_item = (float)((double)band * strip_px * (1.0 + (double)cnt * span / s.levels));
-                j.w0 = plan.total_w;
-                plan.total_w += (double)j.w_item * j.n_job_items;
+                {
+                    // Chunk = enough items that their votes are ~10x the merge
+                    // (reading and clearing the job's shared histograms).
+                    const double votes_per_item = (double)band * strip_px * cnt * span / s.levels;
+                    const double merge = 2.0 * j.hist_words + 64.0;
+                    const double want = std::ceil(10.0 * merge / std::max(1.0, votes_per_item));
+                    j.chunk_items = (int)std::max(1.0, std::min<double>(n_strips * n_bands, want));
+                }
                 j.n_strips = n_strips;
                 j.band_rows = band;
                 j.y_begin = sb0;
@@ -445,14 +451,28 @@ int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 {
     const size_t smem = vote_smem(plan);
     const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem));
-    return std::max(1, std::min(plan.n_items, ctx->sm_count * per_sm));
+    return std::max(1, std::min((int)plan.chunks.size(), ctx->sm_count * per_sm));
+}
+
+// Split every job of a plan into chunks of chunk_items consecutive items.
+void build_chunks(VotePlan& plan)
+{
+    plan.chunks.clear();
+    for (int jb = 0; jb < (int)plan.jobs.size(); ++jb) {
+        const VoteJob& j = plan.jobs[jb];
+        const int cs = std::max(1, j.chunk_items);
+        for (int k = 0; k < j.n_job_items; k += cs)
+            plan.chunks.push_back(make_int3(jb, j.item0 + k, j.item0 + std::min(j.n_job_items, k + cs)));
+    }
 }
 
 // Upload a plan's tables into the given device buffers (through pinned staging).
+// The chunk table follows the jobs in `djobs`, 16-byte aligned.
 int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob>& feats, DevBuf& djobs,
                   DevBuf& doffs, DevBuf& dfeat)
 {
-    const size_t bj = plan.jobs.size() * sizeof(VoteJob);
+    const size_t bj0 = (plan.jobs.size() * sizeof(VoteJob) + 15) & ~(size_t)15;
+    const size_t bj = bj0 + plan.chunks.size() * sizeof(int3);
     const size_t bo = plan.offs.size() * sizeof(VoteOffset);
     const size_t bf = feats.size() * sizeof(FeatJob);
     TRY(ensure(ctx, djobs, bj));
@@ -464,8 +484,11 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
     uint8_t* h = static_cast<uint8_t*>(ctx->h_stage);
     const size_t oo = (bj + 255) & ~(size_t)255;
     const size_t of = oo + ((bo + 255) & ~(size_t)255);
-    if (bj)
-        memcpy(h, plan.jobs.data(), bj);
+    if (!plan.jobs.empty())
+        memcpy(h, plan.jobs.data(), plan.jobs.size() * sizeof(VoteJob));
+    if (!plan.chunks.empty())
+        memcpy(h + bj0, plan.chunks.data(), plan.chunks.size() * sizeof(int3));
+    const_cast<VotePlan&>(plan).chunk_off = bj0;
     if (bo)
         memcpy(h + oo, plan.offs.data(), bo);
     if (bf)
@@ -505,8 +528,8 @@ TimedPair take_pair(glcm_ctx* ctx)
 }
 
 // Enqueue zero (optional) + vote for a plan whose tables are at djobs/doffs.
-int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, bool zero,
-                 bool capturing, GraphEntry* ge)
+int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, const int3* dchunks,
+                 bool zero, bool capturing, GraphEntry* ge)
 {
     if (plan.jobs.empty())
         return GLCM_OK;
@@ -524,7 +547,8 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     vp.n_jobs = (int)plan.jobs.size();
     vp.offs = static_cast<const VoteOffset*>(doffs.p);
     vp.n_items = plan.n_items;
-    vp.total_w = plan.total_w;
+    vp.chunks = dchunks;
+    vp.n_chunks = (int)plan.chunks.size();
     vp.max_hist_words = plan.max_hist_words;
     vp.tile_bytes = plan.tile_rows * vote_row_bytes();
     vp.item_counter = ctx->d_words + 1;
@@ -915,9 +939,12 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
                     offsets, n_offsets, d_counts, r0, r1};
         TRY(plan_image(ctx, s, plan, target_items(ctx)));
+        build_chunks(plan);
         std::vector<FeatJob> none;
         TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
-        TRY(enqueue_vote(ctx, plan, ctx->jobs, ctx->offs, false, false, nullptr));
+        TRY(enqueue_vote(ctx, plan, ctx->jobs, ctx->offs,
+                         reinterpret_cast<const int3*>(static_cast<uint8_t*>(ctx->jobs.p) + plan.chunk_off), false,
+                         false, nullptr));
         r0 = r1;
     }
     if (want_norm) {
@@ -1096,8 +1123,6 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
                 for (int k = 0; k < j.n_off; ++k)
                     dst.offs.push_back(plan.offs[j.off0 + k]);
                 c.item0 = dst.n_items;
-                c.w0 = dst.total_w;
-                dst.total_w += (double)c.w_item * c.n_job_items;
                 dst.n_items += cnt_items;
                 dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
                 if (c.staged)
@@ -1113,27 +1138,34 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
             all.jobs[k].off0 += (int)p8.offs.size();
         all.offs = p8.offs;
         all.offs.insert(all.offs.end(), p16.offs.begin(), p16.offs.end());
+        // Chunks: p8's then p16's, each indexing jobs of its own sub-table.
+        build_chunks(p8);
+        build_chunks(p16);
+        all.chunks = p8.chunks;
+        all.chunks.insert(all.chunks.end(), p16.chunks.begin(), p16.chunks.end());
         TRY(upload_tables(ctx, all, feats, ge.jobs, ge.offs, ge.feat));
         CK(cudaStreamSynchronize(ctx->stream));
         DevBuf j16, o16;
         j16.p = static_cast<VoteJob*>(ge.jobs.p) + p8.jobs.size();
         o16.p = static_cast<VoteOffset*>(ge.offs.p);  // off0 already shifted
         DevBuf j8 = ge.jobs;
+        const int3* c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(ge.jobs.p) + all.chunk_off);
+        const int3* c16 = c8 + p8.chunks.size();
         // One direct run produces this call's results and sets every kernel
         // attribute before capture.
         if (!p8.jobs.empty())
-            TRY(enqueue_vote(ctx, p8, j8, ge.offs, true, false, nullptr));
+            TRY(enqueue_vote(ctx, p8, j8, ge.offs, c8, true, false, nullptr));
         if (!p16.jobs.empty())
-            TRY(enqueue_vote(ctx, p16, j16, o16, true, false, nullptr));
+            TRY(enqueue_vote(ctx, p16, j16, o16, c16, true, false, nullptr));
         TRY(enqueue_features(ctx, feats, ge.feat, max_levels, false, nullptr));
         TRY(collect_device_errors(ctx));
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
         int rc = GLCM_OK;
         if (rc == GLCM_OK && !p8.jobs.empty())
-            rc = enqueue_vote(ctx, p8, j8, ge.offs, true, true, &ge);
+            rc = enqueue_vote(ctx, p8, j8, ge.offs, c8, true, true, &ge);
         if (rc == GLCM_OK && !p16.jobs.empty())
-            rc = enqueue_vote(ctx, p16, j16, o16, true, true, &ge);
+            rc = enqueue_vote(ctx, p16, j16, o16, c16, true, true, &ge);
         if (rc == GLCM_OK)
             rc = enqueue_features(ctx, feats, ge.feat, max_levels, true, &ge);
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);

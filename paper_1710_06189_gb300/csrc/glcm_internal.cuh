@@ -43,8 +43,7 @@ struct VoteJob {
     int hist_words;    // shared words this job uses
     int item0;         // first work item of this job in the launch
     int n_job_items;   // work items of this job
-    float w_item;      // work weight of one item (static partition)
-    double w0;         // summed weight of all items before this job
+    int chunk_items;   // items per scheduling chunk
     int n_strips;      // column strips of 32 lanes x 16 bytes
     int band_rows;     // anchor rows per work item
     int y_begin, y_end;  // anchor rows voted by this job ([0, H) for a whole image)
@@ -71,10 +70,11 @@ struct VoteParams {
     int n_jobs;
     const VoteOffset* offs;
     int n_items;
-    double total_w;          // summed weight of all items
+    const int3* chunks;      // (job, first item, end item), job-major order
+    int n_chunks;
     int tile_bytes;          // one staged tile buffer (two are allocated)
     int max_hist_words;
-    unsigned* item_counter;  // zeroed before each launch (unused by the static schedule)
+    unsigned* item_counter;  // chunk counter, zeroed before each launch
     unsigned* err;           // error bits (kErr*)
 };
 

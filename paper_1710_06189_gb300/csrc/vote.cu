@@ -564,36 +564,19 @@ __device__ void vote_tile_unstaged(const VoteJob& j, const VoteJob* jg, const Ti
         }
 }
 
-// First item whose starting weight is >= w (items of a job all weigh w_item).
-__device__ int item_at(const VoteParams& p, double w)
-{
-    if (w <= 0.0)
-        return 0;
-    if (w >= p.total_w)
-        return p.n_items;
-    int lo = 0, hi = p.n_jobs - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.jobs[mid].w0 <= w)
-            lo = mid;
-        else
-            hi = mid - 1;
-    }
-    const VoteJob& j = p.jobs[lo];
-    long long k = (long long)ceil((w - j.w0) / (double)j.w_item);
-    k = k < 0 ? 0 : (k > j.n_job_items ? j.n_job_items : k);
-    return j.item0 + (int)k;
-}
-
-// Persistent CTAs with a static, weight-balanced partition: CTA b votes the
-// contiguous item range covering weights [W b / G, W (b + 1) / G).  Dynamic
-// shared memory: two tile buffers, then the histograms.
+// Persistent CTAs pull chunks -- runs of consecutive items of one job, sized
+// on the host so that a chunk's votes outweigh its merge -- from a global
+// counter.  Chunks are ordered job by job, so a CTA usually stays on one job
+// for several chunks and merges only when its job changes; pulling them
+// dynamically balances images whose contention makes items cost very
+// different times.  Dynamic shared memory: two tile buffers, then the
+// histograms.
 template <int BPP, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ int s_k0, s_k1, s_job, s_ok;
+    __shared__ int s_chunk, s_ok;
     __shared__ HistRef s_off_h[kMaxJobOffsets];
     __shared__ int2 s_off_d[kMaxJobOffsets];
     uint8_t* tiles = smem;
@@ -604,57 +587,60 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        const double W = p.total_w;
-        s_k0 = item_at(p, W * (double)blockIdx.x / (double)gridDim.x);
-        s_k1 = blockIdx.x + 1 == gridDim.x ? p.n_items
-                                            : item_at(p, W * (double)(blockIdx.x + 1) / (double)gridDim.x);
-        int lo = 0, hi = p.n_jobs - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (p.jobs[mid].item0 <= s_k0)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        s_job = lo;
         s_ok = 1;
     }
     __syncthreads();
-    const int k1 = s_k1;
-    int k = s_k0;
-    int job = s_job;
     const uint32_t hbase = smem_u32(hist);
     const int nwarps = blockDim.x >> 5;
     uint32_t uses[2] = {0u, 0u};  // completed phases per tile buffer
-    while (k < k1) {
-        while (job + 1 < p.n_jobs && p.jobs[job + 1].item0 <= k)
-            ++job;
-        const VoteJob* jg = p.jobs + job;
+    int cur = -1;                 // job whose partial histograms are in shared memory
+    long long acc_rows = 0;       // rows per warp voted into 16-bit halves since the last merge
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_chunk = (int)atomicAdd(p.item_counter, 1u);
+        __syncthreads();
+        const int c = s_chunk;
+        if (c >= p.n_chunks)
+            break;
+        const int3 ch = p.chunks[c];
+        const VoteJob* jg = p.jobs + ch.x;
         const VoteJob j = *jg;
-        const int seg_end = min(k1, j.item0 + j.n_job_items);
         const int tile_need = j.staged ? (j.band_rows + j.dy_max - j.dy_min) * kRowBytes : 0;
         if (j.hist_words > p.max_hist_words || j.n_off > kMaxJobOffsets || tile_need > p.tile_bytes) {
             if (threadIdx.x == 0)
                 atomicOr(p.err, kErrInternal);
-            k = seg_end;
+            __syncthreads();
             continue;
         }
-        if (threadIdx.x < j.n_off) {
-            const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
-            s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
-            s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
+        const long long rows_ok =
+            j.layout == 2 ? 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift)) : (1ll << 62);
+        const long long chunk_rows = (long long)(ch.z - ch.y) * j.band_rows / nwarps + 1;
+        if (cur >= 0 && (cur != ch.x || acc_rows + chunk_rows > rows_ok)) {
+            flush_hist(p.jobs[cur], p.offs, hist);
+            __syncthreads();
+            cur = -1;
         }
-        __syncthreads();
-        // Items per merge: unbounded for 32-bit counters; 16-bit halves must
-        // stay below 65536 votes (rows per warp x pixels x threads per copy).
-        int step = seg_end - k;
-        if (j.layout == 2) {
-            const long long rows_ok = 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift));
+        if (cur != ch.x) {
+            if (threadIdx.x < j.n_off) {
+                const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
+                s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
+                s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
+            }
+            __syncthreads();
+            cur = ch.x;
+            acc_rows = 0;
+        }
+        // Items per merge inside the chunk (16-bit halves only).
+        int step = ch.z - ch.y;
+        if (j.layout == 2)
             step = (int)max(1ll, min((long long)step, rows_ok * nwarps / j.band_rows));
-        }
         const bool tma = j.staged && j.aligned;
-        for (int ka = k; ka < seg_end; ka += step) {
-            const int kb = min(seg_end, ka + step);
+        for (int ka = ch.y; ka < ch.z; ka += step) {
+            const int kb = min(ch.z, ka + step);
+            if (ka > ch.y) {
+                flush_hist(j, p.offs, hist);
+                __syncthreads();
+            }
             if (tma && threadIdx.x < 32)
                 issue_tile(j, tile_of(j, ka), tiles, &s_bar[0]);
             for (int kk = ka; kk < kb; ++kk) {
@@ -684,11 +670,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
                     vote_tile<BPP>(j, jg, t, buf, s_off_h, s_off_d, p.err);
                 __syncthreads();
             }
-            flush_hist(j, p.offs, hist);
-            __syncthreads();
         }
-        k = seg_end;
+        acc_rows += chunk_rows;
     }
+    if (cur >= 0)
+        flush_hist(p.jobs[cur], p.offs, hist);
 }
 
 // Scheme 1 of the paper (Sec. I.B): one thread per anchor pixel, one global
