@@ -24,7 +24,9 @@
 //    (its square is the second eigenvalue of Q).  The known top pair
 //    (singular value 1, vectors sqrt(p_x), sqrt(p_y)) is removed exactly:
 //    A'(i,j) = (S*T - r*c) / (T sqrt(r c)), and the largest singular value
-//    of A' is found with one-sided (Hestenes) Jacobi rotations in float32.
+//    of A' is found by Golub-Kahan-Lanczos bidiagonalization with full
+//    reorthogonalization in float32, stopped when its top Ritz value
+//    settles (exact after min(rows, cols) steps).
 #include <cmath>
 
 #include "glcm_internal.cuh"
@@ -34,7 +36,12 @@ namespace {
 
 constexpr int kFeatThreads = 512;
 constexpr int kNumFeat = 14;
-constexpr int kSmemA = 64;  // support up to 64x64 keeps A' in shared memory
+constexpr int kMaxLanczos = 96;
+// A' and the Lanczos vectors stay in shared memory up to these sizes
+// (covers supports up to 128 x 128); larger ones use global scratch.
+constexpr int kSmemAFloats = 128 * 128;
+constexpr int kSmemUVFloats = (2 * kMaxLanczos + 1) * 128;
+constexpr int kColGroups = 4;
 
 struct DF {  // float value hi + lo (unevaluated sum)
     float hi, lo;
@@ -157,9 +164,9 @@ __device__ void block_reduce_d(double (&v)[K], double* scratch)
 
 __device__ __forceinline__ unsigned long long cell(const uint32_t* C, int N, int i, int j, int sym)
 {
-    unsigned long long s = C[i * N + j];
+    unsigned long long s = __ldg(C + i * N + j);
     if (sym)
-        s += C[j * N + i];
+        s += __ldg(C + j * N + i);
     return s;
 }
 
@@ -168,102 +175,18 @@ __device__ __forceinline__ float neg_plogp(float p)
     return p > 0.f ? -__fmul_rn(p, logf(p)) : 0.f;
 }
 
-// Largest singular value of the m x n matrix A (column-major, leading dim m)
-// by one-sided Jacobi: rotate column pairs until all are orthogonal, then
-// the column norms are the singular values.
-__device__ float jacobi_sigma_max(float* A, int m, int n, int* s_flag, float* s_red)
+__device__ __forceinline__ float warp_sum(float s)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    if (n <= 0 || m <= 0)
-        return 0.f;
-    const int np = (n + 1) & ~1;  // even number of players (one dummy if odd)
-    for (int sweep = 0; sweep < 40; ++sweep) {
-        if (threadIdx.x == 0)
-            *s_flag = 0;
-        __syncthreads();
-        for (int step = 0; step < np - 1; ++step) {
-            for (int k = warp; k < np / 2; k += nw) {
-                int a, b;
-                if (k == 0) {
-                    a = 0;
-                    b = (step % (np - 1)) + 1;
-                } else {
-                    a = ((step + k) % (np - 1)) + 1;
-                    b = ((step + np - 1 - k) % (np - 1)) + 1;
-                }
-                if (a >= n || b >= n)
-                    continue;
-                float* ca = A + (long long)a * m;
-                float* cb = A + (long long)b * m;
-                float al = 0.f, be = 0.f, ga = 0.f;
-                for (int r = lane; r < m; r += 32) {
-                    const float x = ca[r], y = cb[r];
-                    al = fmaf(x, x, al);
-                    be = fmaf(y, y, be);
-                    ga = fmaf(x, y, ga);
-                }
-                for (int o = 16; o > 0; o >>= 1) {
-                    al += __shfl_xor_sync(0xffffffffu, al, o);
-                    be += __shfl_xor_sync(0xffffffffu, be, o);
-                    ga += __shfl_xor_sync(0xffffffffu, ga, o);
-                }
-                if (fabsf(ga) > 4e-7f * sqrtf(al * be) && fabsf(ga) > 1e-30f) {
-                    const float zeta = (be - al) / (2.f * ga);
-                    const float t = copysignf(1.f, zeta) / (fabsf(zeta) + sqrtf(1.f + zeta * zeta));
-                    const float cs = rsqrtf(1.f + t * t);
-                    const float sn = cs * t;
-                    for (int r = lane; r < m; r += 32) {
-                        const float x = ca[r], y = cb[r];
-                        ca[r] = cs * x - sn * y;
-                        cb[r] = sn * x + cs * y;
-                    }
-                    if (lane == 0)
-                        *s_flag = 1;
-                }
-            }
-            __syncthreads();
-        }
-        const int rotated = *s_flag;
-        __syncthreads();
-        if (!rotated)
-            break;
-    }
-    // Column norms, maximum.
-    float best = 0.f;
-    for (int k = warp; k < n; k += nw) {
-        const float* ck = A + (long long)k * m;
-        float s = 0.f;
-        for (int r = lane; r < m; r += 32)
-            s = fmaf(ck[r], ck[r], s);
-        for (int o = 16; o > 0; o >>= 1)
-            s += __shfl_xor_sync(0xffffffffu, s, o);
-        best = fmaxf(best, s);
-    }
-    if (lane == 0)
-        s_red[warp] = best;
-    __syncthreads();
-    float m2 = 0.f;
-    for (int w = 0; w < nw; ++w)
-        m2 = fmaxf(m2, s_red[w]);
-    __syncthreads();
-    return sqrtf(m2);
-}
-
-// Largest singular value of the m x n matrix A (column-major, leading dim m,
-// in global scratch) by Golub-Kahan-Lanczos bidiagonalization with full
-// reorthogonalization, then bisection (Sturm counts) on the 2K x 2K
-// zero-diagonal tridiagonal matrix whose eigenvalues are +-sigma(B_K).
-// U (kMaxLanczos x m) and V ((kMaxLanczos + 1) x n) live after A.
-constexpr int kMaxLanczos = 96;
-
-__device__ float block_dot(const float* x, const float* y, int len, float* s_red)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    float s = 0.f;
-    for (int r = threadIdx.x; r < len; r += blockDim.x)
-        s = fmaf(x[r], y[r], s);
     for (int o = 16; o > 0; o >>= 1)
         s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// Sum over the block; every thread gets the result.
+__device__ float block_sum(float s, float* s_red)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    s = warp_sum(s);
     if (lane == 0)
         s_red[warp] = s;
     __syncthreads();
@@ -274,8 +197,64 @@ __device__ float block_dot(const float* x, const float* y, int len, float* s_red
     return t;
 }
 
-// x -= sum_i <x, Q_i> Q_i over the first k rows of Q (twice, classical GS).
-__device__ void reorth(float* x, const float* Q, int k, int len, float* s_coef, float* s_red)
+// y = A x for the m x n column-major A (leading dim m); x, y in shared memory.
+// Warps own 32-row blocks and split the columns into kColGroups strided
+// groups, four independent products in flight per lane.
+__device__ void matvec(const float* __restrict__ A, int m, int n, const float* x, float* y, float* part)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int rbs = (m + 31) >> 5;
+    const int groups = max(1, min(kColGroups, nw / rbs));
+    for (int w = warp; w < rbs * groups; w += nw) {
+        const int rb = w % rbs, g = w / rbs;
+        const int r = rb * 32 + lane;
+        if (r >= m)
+            continue;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int c = g;
+        for (; c + 3 * groups < n; c += 4 * groups) {
+            a0 = fmaf(A[(long long)c * m + r], x[c], a0);
+            a1 = fmaf(A[(long long)(c + groups) * m + r], x[c + groups], a1);
+            a2 = fmaf(A[(long long)(c + 2 * groups) * m + r], x[c + 2 * groups], a2);
+            a3 = fmaf(A[(long long)(c + 3 * groups) * m + r], x[c + 3 * groups], a3);
+        }
+        for (; c < n; c += groups)
+            a0 = fmaf(A[(long long)c * m + r], x[c], a0);
+        part[g * 256 + r] = (a0 + a1) + (a2 + a3);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < m; r += blockDim.x) {
+        float s = 0.f;
+        for (int g = 0; g < groups; ++g)
+            s += part[g * 256 + r];
+        y[r] = s;
+    }
+    __syncthreads();
+}
+
+// x = A^T y: one warp per column, lanes over the rows.
+__device__ void matvec_t(const float* __restrict__ A, int m, int n, const float* y, float* x)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int c = warp; c < n; c += nw) {
+        const float* col = A + (long long)c * m;
+        float a0 = 0.f, a1 = 0.f;
+        int r = lane;
+        for (; r + 32 < m; r += 64) {
+            a0 = fmaf(col[r], y[r], a0);
+            a1 = fmaf(col[r + 32], y[r + 32], a1);
+        }
+        if (r < m)
+            a0 = fmaf(col[r], y[r], a0);
+        const float s = warp_sum(a0 + a1);
+        if (lane == 0)
+            x[c] = s;
+    }
+    __syncthreads();
+}
+
+// v -= sum_i <v, Q_i> Q_i over rows i < k of Q (len-long rows), twice.
+__device__ void reorth(float* v, const float* __restrict__ Q, int k, int len, float* s_coef)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     for (int pass = 0; pass < 2; ++pass) {
@@ -283,22 +262,25 @@ __device__ void reorth(float* x, const float* Q, int k, int len, float* s_coef, 
             const float* q = Q + (long long)i * len;
             float s = 0.f;
             for (int r = lane; r < len; r += 32)
-                s = fmaf(x[r], q[r], s);
-            for (int o = 16; o > 0; o >>= 1)
-                s += __shfl_xor_sync(0xffffffffu, s, o);
+                s = fmaf(v[r], q[r], s);
+            s = warp_sum(s);
             if (lane == 0)
                 s_coef[i] = s;
         }
         __syncthreads();
         for (int r = threadIdx.x; r < len; r += blockDim.x) {
-            float v = x[r];
-            for (int i = 0; i < k; ++i)
-                v = fmaf(-s_coef[i], Q[(long long)i * len + r], v);
-            x[r] = v;
+            float a0 = v[r], a1 = 0.f;
+            int i = 0;
+            for (; i + 1 < k; i += 2) {
+                a0 = fmaf(-s_coef[i], Q[(long long)i * len + r], a0);
+                a1 = fmaf(-s_coef[i + 1], Q[(long long)(i + 1) * len + r], a1);
+            }
+            if (i < k)
+                a0 = fmaf(-s_coef[i], Q[(long long)i * len + r], a0);
+            v[r] = a0 + a1;
         }
         __syncthreads();
     }
-    (void)s_red;
 }
 
 // Largest singular value of the K x K upper bidiagonal matrix with
@@ -337,139 +319,223 @@ __device__ float gk_sigma_max(const float* ab, int steps)
     return 0.5f * (lo + hi);
 }
 
-__device__ float lanczos_sigma_max(const float* A, int m, int n, float* U, float* V, float* s_coef, float* s_red,
-                                   float* s_ab, float* s_sig, int* s_stop)
+struct LanczosWork {
+    float* xs;    // n floats, shared
+    float* ys;    // m floats, shared
+    float* part;  // kColGroups * 256 floats, shared
+    float* U;     // kMaxLanczos x m (shared or global)
+    float* V;     // (kMaxLanczos + 1) x n
+    float* coef;  // kMaxLanczos + 1, shared
+    float* red;   // 32, shared
+    float* ab;    // 2 kMaxLanczos + 2, shared
+    float* sig;   // shared scalar
+    int* stop;    // shared scalar
+};
+
+// Golub-Kahan-Lanczos bidiagonalization of the m x n matrix A with full
+// reorthogonalization; returns the top Ritz value (largest singular value).
+__device__ float lanczos_sigma_max(const float* A, int m, int n, const LanczosWork& w)
 {
     const int K = min(kMaxLanczos, min(m, n));
-    float* v0 = V;
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        v0[c] = 1.f + 0.01f * (float)((c * 37) % 11);  // fixed, not orthogonal to anything special
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        const float v = 1.f + 0.01f * (float)((c * 37) % 11);  // fixed start vector
+        w.xs[c] = v;
+    }
+    if (threadIdx.x == 0) {
+        *w.sig = -1.f;
+        *w.stop = 0;
+    }
     __syncthreads();
-    float nv = sqrtf(block_dot(v0, v0, n, s_red));
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        v0[c] /= nv;
-    __syncthreads();
+    {
+        float s = 0.f;
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            s = fmaf(w.xs[c], w.xs[c], s);
+        const float inv = rsqrtf(block_sum(s, w.red));
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            w.xs[c] *= inv;
+            w.V[c] = w.xs[c];
+        }
+        __syncthreads();
+    }
     int steps = 0;
     float beta = 0.f;
     for (int k = 0; k < K; ++k) {
-        float* uk = U + (long long)k * m;
-        const float* vk = V + (long long)k * n;
-        // u = A v_k - beta_k u_{k-1}
-        for (int r = threadIdx.x; r < m; r += blockDim.x) {
-            float s = 0.f;
-            for (int c = 0; c < n; ++c)
-                s = fmaf(A[(long long)c * m + r], vk[c], s);
-            if (k > 0)
-                s = fmaf(-beta, U[(long long)(k - 1) * m + r], s);
-            uk[r] = s;
-        }
+        // u_k = A v_k - beta_k u_{k-1}, reorthogonalized.
+        matvec(A, m, n, w.xs, w.ys, w.part);
+        if (k > 0)
+            for (int r = threadIdx.x; r < m; r += blockDim.x)
+                w.ys[r] = fmaf(-beta, w.U[(long long)(k - 1) * m + r], w.ys[r]);
         __syncthreads();
-        reorth(uk, U, k, m, s_coef, s_red);
-        const float alpha = sqrtf(block_dot(uk, uk, m, s_red));
+        reorth(w.ys, w.U, k, m, w.coef);
+        float s = 0.f;
+        for (int r = threadIdx.x; r < m; r += blockDim.x)
+            s = fmaf(w.ys[r], w.ys[r], s);
+        const float alpha = sqrtf(block_sum(s, w.red));
         if (threadIdx.x == 0)
-            s_ab[2 * k] = alpha;
+            w.ab[2 * k] = alpha;
         if (!(alpha > 1e-30f))
             break;
-        for (int r = threadIdx.x; r < m; r += blockDim.x)
-            uk[r] /= alpha;
+        const float ia = 1.f / alpha;
+        for (int r = threadIdx.x; r < m; r += blockDim.x) {
+            w.ys[r] *= ia;
+            w.U[(long long)k * m + r] = w.ys[r];
+        }
         __syncthreads();
         steps = k + 1;
-        // v = A^T u_k - alpha_k v_k
-        float* vn = V + (long long)(k + 1) * n;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        for (int c = warp; c < n; c += nw) {
-            const float* col = A + (long long)c * m;
-            float s = 0.f;
-            for (int r = lane; r < m; r += 32)
-                s = fmaf(col[r], uk[r], s);
-            for (int o = 16; o > 0; o >>= 1)
-                s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0)
-                vn[c] = s - alpha * vk[c];
-        }
+        // v_{k+1} = A^T u_k - alpha_k v_k, reorthogonalized.
+        matvec_t(A, m, n, w.ys, w.xs);
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            w.xs[c] = fmaf(-alpha, w.V[(long long)k * n + c], w.xs[c]);
         __syncthreads();
-        reorth(vn, V, k + 1, n, s_coef, s_red);
-        beta = sqrtf(block_dot(vn, vn, n, s_red));
+        reorth(w.xs, w.V, k + 1, n, w.coef);
+        s = 0.f;
+        for (int c = threadIdx.x; c < n; c += blockDim.x)
+            s = fmaf(w.xs[c], w.xs[c], s);
+        beta = sqrtf(block_sum(s, w.red));
         if (threadIdx.x == 0)
-            s_ab[2 * k + 1] = beta;
+            w.ab[2 * k + 1] = beta;
         if (!(beta > 1e-30f) || k + 1 == K)
             break;
-        // Every 8 steps: stop once the top Ritz value moved by < 1e-7.
-        if (((k + 1) & 7) == 0) {
-            if (threadIdx.x == 0) {
-                const float sg = gk_sigma_max(s_ab, k + 1);
-                *s_stop = (k + 1 >= 16 && fabsf(sg - *s_sig) <= 1e-7f) ? 1 : 0;
-                *s_sig = sg;
-            }
-            __syncthreads();
-            if (*s_stop)
-                break;
+        const float ib = 1.f / beta;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            w.xs[c] *= ib;
+            w.V[(long long)(k + 1) * n + c] = w.xs[c];
         }
-        for (int c = threadIdx.x; c < n; c += blockDim.x)
-            vn[c] /= beta;
+        // Every 8 steps: stop once the top Ritz value moved by < 1e-7.
+        if (((k + 1) & 7) == 0 && threadIdx.x == 0) {
+            const float sg = gk_sigma_max(w.ab, k + 1);
+            *w.stop = (k + 1 >= 16 && fabsf(sg - *w.sig) <= 1e-7f) ? 1 : 0;
+            *w.sig = sg;
+        }
         __syncthreads();
+        if (*w.stop)
+            break;
     }
     __syncthreads();
     if (threadIdx.x == 0)
-        *s_sig = gk_sigma_max(s_ab, steps);
+        *w.sig = gk_sigma_max(w.ab, steps);
     __syncthreads();
-    return *s_sig;
+    return *w.sig;
 }
 
-__global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
+// Dynamic shared memory layout for a launch whose largest N is `N`.
+struct FeatLayout {
+    size_t marg, maps, dscr, dd, xs, ys, part, a, uv, total;
+};
+
+__host__ __device__ inline FeatLayout feat_layout(int N)
+{
+    FeatLayout L;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = (o + bytes + 15) & ~(size_t)15;
+        return at;
+    };
+    const int K = N < kMaxLanczos ? N : kMaxLanczos;
+    const long long nn = (long long)N * N;
+    const long long uv = (2ll * K + 1) * N;
+    L.marg = take((size_t)5 * N * 8);
+    L.maps = take((size_t)2 * N * 4);
+    L.dscr = take(10 * 32 * sizeof(DF));
+    L.dd = take(6 * 32 * 8);
+    L.xs = take((size_t)N * 4);
+    L.ys = take((size_t)N * 4);
+    L.part = take((size_t)kColGroups * 256 * 4);
+    L.a = take((size_t)(nn < kSmemAFloats ? nn : kSmemAFloats) * 4);
+    L.uv = take((size_t)(uv < kSmemUVFloats ? uv : kSmemUVFloats) * 4);
+    L.total = o;
+    return L;
+}
+
+__global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int maxN)
 {
     const FeatJob J = p.jobs[blockIdx.x];
     const int N = J.levels;
     const int NN = N * N;
     const int sym = J.symmetric;
     const uint32_t* C = J.counts;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* rs = reinterpret_cast<unsigned long long*>(smem_raw);  // N
-    unsigned long long* cs = rs + N;                                           // N
-    unsigned long long* ss = cs + N;                                           // 2N
-    unsigned long long* ds = ss + 2 * N;                                       // N
-    int* rmap = reinterpret_cast<int*>(ds + N);                                // N (row -> support idx)
-    int* cmap = rmap + N;                                                      // N
-    DF* dscr = reinterpret_cast<DF*>(cmap + N);                                // 10 * 32
-    double* dd = reinterpret_cast<double*>(dscr + 10 * 32);                     // 6 * 32
-    float* fa = reinterpret_cast<float*>(dd + 6 * 32);                         // kSmemA^2
+    const FeatLayout Lo = feat_layout(maxN);
+    unsigned long long* rs = reinterpret_cast<unsigned long long*>(smem_raw + Lo.marg);  // N
+    unsigned long long* cs = rs + N;                                                    // N
+    unsigned long long* ss = cs + N;                                                    // 2N
+    unsigned long long* ds = ss + 2 * N;                                                // N
+    int* rmap = reinterpret_cast<int*>(smem_raw + Lo.maps);                             // N
+    int* cmap = rmap + N;                                                               // N
+    DF* dscr = reinterpret_cast<DF*>(smem_raw + Lo.dscr);
+    double* dd = reinterpret_cast<double*>(smem_raw + Lo.dd);
     __shared__ unsigned long long s_T, s_m[6];
-    __shared__ int s_nr, s_nc, s_flag;
-    __shared__ float s_red[32];
+    __shared__ int s_nr, s_nc, s_stop;
+    __shared__ float s_red[32], s_coef[kMaxLanczos + 1], s_ab[2 * kMaxLanczos + 2], s_sig;
 
     for (int k = threadIdx.x; k < 5 * N; k += blockDim.x)
         rs[k] = 0ull;
     __syncthreads();
-    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
-        const int i = t / N, j = t - (t / N) * N;
-        const unsigned long long s = cell(C, N, i, j, sym);
-        if (s) {
-            atomicAdd(&rs[i], s);
-            atomicAdd(&cs[j], s);
-            atomicAdd(&ss[i + j], s);
-            atomicAdd(&ds[i > j ? i - j : j - i], s);
+    // Exact integer marginals.  Warp w takes rows w, w + nwarps, ...; the row
+    // sum is a warp reduction, the other marginals shared atomics.
+    for (int i = warp; i < N; i += blockDim.x >> 5) {
+        unsigned long long rsum = 0;
+        for (int j = lane; j < N; j += 32) {
+            const unsigned long long s = cell(C, N, i, j, sym);
+            if (s) {
+                rsum += s;
+                atomicAdd(&cs[j], s);
+                atomicAdd(&ss[i + j], s);
+                atomicAdd(&ds[i > j ? i - j : j - i], s);
+            }
         }
+        for (int o = 16; o > 0; o >>= 1)
+            rsum += __shfl_xor_sync(0xffffffffu, rsum, o);
+        if (lane == 0)
+            rs[i] = rsum;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // Totals, integer moments and the support maps (warp 0).
+    if (warp == 0) {
         unsigned long long T = 0, m_i = 0, m_j = 0, c2 = 0, m_s = 0, m_d = 0;
         int nr = 0, nc = 0;
-        for (int k = 0; k < N; ++k) {
-            T += rs[k];
-            m_i += (unsigned long long)k * rs[k];
-            m_j += (unsigned long long)k * cs[k];
-            c2 += (unsigned long long)k * k * ds[k];
-            m_d += (unsigned long long)k * ds[k];
-            rmap[k] = rs[k] ? nr++ : -1;
-            cmap[k] = cs[k] ? nc++ : -1;
+        for (int k0 = 0; k0 < 2 * N; k0 += 32) {
+            const int k = k0 + lane;
+            const bool inN = k < N;
+            const unsigned long long r = inN ? rs[k] : 0ull, c = inN ? cs[k] : 0ull, d = inN ? ds[k] : 0ull;
+            const unsigned long long sv = k < 2 * N - 1 ? ss[k] : 0ull;
+            T += r;
+            m_i += (unsigned long long)k * r;
+            m_j += (unsigned long long)k * c;
+            c2 += (unsigned long long)k * k * d;
+            m_d += (unsigned long long)k * d;
+            m_s += (unsigned long long)k * sv;
+            const unsigned rb = __ballot_sync(0xffffffffu, r != 0ull);
+            const unsigned cb = __ballot_sync(0xffffffffu, c != 0ull);
+            const unsigned below = (1u << lane) - 1u;
+            if (inN) {
+                rmap[k] = r ? nr + __popc(rb & below) : -1;
+                cmap[k] = c ? nc + __popc(cb & below) : -1;
+            }
+            nr += __popc(rb);
+            nc += __popc(cb);
         }
-        for (int k = 0; k < 2 * N - 1; ++k)
-            m_s += (unsigned long long)k * ss[k];
-        s_T = T;
-        s_m[0] = m_i; s_m[1] = m_j; s_m[2] = c2; s_m[3] = m_s; s_m[4] = m_d;
-        s_nr = nr;
-        s_nc = nc;
+        for (int o = 16; o > 0; o >>= 1) {
+            T += __shfl_xor_sync(0xffffffffu, T, o);
+            m_i += __shfl_xor_sync(0xffffffffu, m_i, o);
+            m_j += __shfl_xor_sync(0xffffffffu, m_j, o);
+            c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+            m_s += __shfl_xor_sync(0xffffffffu, m_s, o);
+            m_d += __shfl_xor_sync(0xffffffffu, m_d, o);
+        }
+        if (lane == 0) {
+            s_T = T;
+            s_m[0] = m_i;
+            s_m[1] = m_j;
+            s_m[2] = c2;
+            s_m[3] = m_s;
+            s_m[4] = m_d;
+            s_nr = nr;
+            s_nc = nc;
+        }
     }
     __syncthreads();
     const unsigned long long T = s_T;
@@ -493,9 +559,17 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
     const double Td = (double)T;
     const double mux = (double)s_m[0] / Td, muy = (double)s_m[1] / Td;
     const int nr = s_nr, nc = s_nc;
-    // A' storage: shared memory when the support is small, else global scratch.
-    float* A = (nr <= kSmemA && nc <= kSmemA) ? fa : (p.work + (long long)blockIdx.x * p.work_stride);
-    const bool have_work = (nr <= kSmemA && nc <= kSmemA) || p.work != nullptr;
+    const int K = min(kMaxLanczos, min(nr, nc));
+    // A' and the Lanczos vectors: shared memory when they fit, else scratch.
+    float* gwork = p.work ? p.work + (long long)blockIdx.x * p.work_stride : nullptr;
+    const bool a_smem = (long long)nr * nc <= kSmemAFloats && (long long)nr * nc <= (long long)maxN * maxN;
+    const long long uv_need = (long long)K * nr + (long long)(K + 1) * nc;
+    const bool uv_smem = uv_need <= kSmemUVFloats &&
+                         uv_need <= (long long)(2 * min(maxN, kMaxLanczos) + 1) * maxN;
+    float* A = a_smem ? reinterpret_cast<float*>(smem_raw + Lo.a) : gwork;
+    float* UV = uv_smem ? reinterpret_cast<float*>(smem_raw + Lo.uv)
+                        : (gwork ? gwork + (long long)maxN * maxN : nullptr);
+    const bool have_work = A != nullptr && UV != nullptr;
 
     // Cell pass: normalized output, f1, f9, MI terms, covariance, A'.
     Kahan k_asm, k_ent, k_mi;
@@ -560,27 +634,23 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
 
     float mcc = 0.f;
     if (nr >= 2 && have_work) {
-        if (nr <= kSmemA && nc <= kSmemA) {
-            mcc = jacobi_sigma_max(A, nr, nc, &s_flag, s_red);
-        } else {
-            float* Uw = A + (long long)nr * nc;
-            float* Vw = Uw + (long long)kMaxLanczos * nr;
-            __shared__ float s_coef[kMaxLanczos + 1];
-            __shared__ float s_ab[2 * kMaxLanczos + 2];
-            __shared__ float s_sg;
-            __shared__ int s_stop;
-            if (threadIdx.x == 0) {
-                s_sg = -1.f;
-                s_stop = 0;
-            }
-            __syncthreads();
-            mcc = lanczos_sigma_max(A, nr, nc, Uw, Vw, s_coef, s_red, s_ab, &s_sg, &s_stop);
-        }
+        LanczosWork w;
+        w.xs = reinterpret_cast<float*>(smem_raw + Lo.xs);
+        w.ys = reinterpret_cast<float*>(smem_raw + Lo.ys);
+        w.part = reinterpret_cast<float*>(smem_raw + Lo.part);
+        w.U = UV;
+        w.V = UV + (long long)K * nr;
+        w.coef = s_coef;
+        w.red = s_red;
+        w.ab = s_ab;
+        w.sig = &s_sig;
+        w.stop = &s_stop;
+        mcc = lanczos_sigma_max(A, nr, nc, w);
     }
-    if (!have_work && threadIdx.x == 0)
+    if (!have_work && nr >= 2 && threadIdx.x == 0)
         atomicOr(p.err, kErrInternal);
 
-    if (threadIdx.x == 0 && feat) {
+    if (threadIdx.x == 0) {
         const double varx = dv[1] / Td, vary = dv[2] / Td;
         const double sdx = sqrt(varx), sdy = sqrt(vary);
         const float mi = fmaxf(0.f, v[2].hi + v[2].lo);
@@ -605,16 +675,17 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p)
 
 }  // namespace
 
+// Global scratch per GLCM for supports too large for shared memory: A' (N^2)
+// followed by the Lanczos vectors.
 long long features_work_floats(int levels)
 {
-    return (long long)levels * levels + (long long)(2 * kMaxLanczos + 2) * levels + 64;
+    const int K = levels < kMaxLanczos ? levels : kMaxLanczos;
+    return (long long)levels * levels + (2ll * K + 1) * levels + 64;
 }
 
 size_t features_smem_bytes(int max_levels)
 {
-    const int N = max_levels;
-    return (size_t)5 * N * 8 + (size_t)2 * N * 4 + 10 * 32 * sizeof(DF) + 6 * 32 * 8 +
-           (size_t)kSmemA * kSmemA * 4 + 64;
+    return feat_layout(max_levels).total;
 }
 
 cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
@@ -629,7 +700,7 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
             return e;
         set_to = smem;
     }
-    k_haralick<<<p.n_jobs, kFeatThreads, smem, s>>>(p);
+    k_haralick<<<p.n_jobs, kFeatThreads, smem, s>>>(p, max_levels);
     return cudaGetLastError();
 }
 
