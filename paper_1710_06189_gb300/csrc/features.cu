@@ -283,38 +283,55 @@ __device__ void reorth(float* v, const float* __restrict__ Q, int k, int len, fl
     }
 }
 
-// Largest singular value of the K x K upper bidiagonal matrix with
-// diagonal alpha_k = ab[2k] and superdiagonal beta_k = ab[2k+1]: bisection
-// with Sturm counts on the zero-diagonal tridiagonal matrix whose
-// off-diagonals are alpha_0, beta_0, alpha_1, ... (eigenvalues +-sigma).
-__device__ float gk_sigma_max(const float* ab, int steps)
+// Number of eigenvalues below x of the (L+1) x (L+1) zero-diagonal
+// tridiagonal matrix with off-diagonals ab[0..L) (Sturm sequence).
+__device__ __forceinline__ int sturm_below(const float* ab, int L, float x)
 {
+    int cnt = 0;
+    float q = -x;
+    if (q < 0.f)
+        ++cnt;
+    for (int t = 0; t < L; ++t) {
+        const float b = ab[t];
+        if (q == 0.f)
+            q = -1e-30f;
+        q = -x - __fdividef(b * b, q);
+        if (q < 0.f)
+            ++cnt;
+    }
+    return cnt;
+}
+
+// Largest singular value of the K x K upper bidiagonal matrix with
+// diagonal alpha_k = ab[2k] and superdiagonal beta_k = ab[2k+1], i.e. the
+// largest eigenvalue of the zero-diagonal tridiagonal matrix with
+// off-diagonals alpha_0, beta_0, alpha_1, ... (eigenvalues +-sigma).
+// Called by one whole warp: 32-way multisection, each lane testing one
+// point per round, until the bracket is below float resolution.
+__device__ float gk_sigma_max_warp(const float* ab, int steps)
+{
+    const int lane = threadIdx.x & 31;
     const int L = 2 * steps - 1;
     if (L <= 0)
         return 0.f;
     float hi = 0.f;
-    for (int t = 0; t < L; ++t)
+    for (int t = lane; t < L; t += 32)
         hi = fmaxf(hi, ab[t]);
+    for (int o = 16; o > 0; o >>= 1)
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     hi *= 2.f;
     float lo = 0.f;
-    for (int it = 0; it < 60; ++it) {
-        const float x = 0.5f * (lo + hi);
-        int cnt = 0;
-        float q = -x;
-        if (q < 0.f)
-            ++cnt;
-        for (int t = 0; t < L; ++t) {
-            const float b = ab[t];
-            if (q == 0.f)
-                q = -1e-30f;
-            q = -x - b * b / q;
-            if (q < 0.f)
-                ++cnt;
-        }
-        if (cnt >= L + 1)
-            hi = x;  // all eigenvalues below x
-        else
-            lo = x;
+    for (int round = 0; round < 8 && hi - lo > 1e-7f * hi; ++round) {
+        const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
+        const bool all_below = sturm_below(ab, L, x) >= L + 1;
+        const unsigned m = __ballot_sync(0xffffffffu, all_below);
+        // Points are increasing in lane; the first with all eigenvalues below
+        // x bounds the top eigenvalue from above.
+        const int first = m ? __ffs(m) - 1 : 32;
+        const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
+        const float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) / 33.f;
+        lo = nlo;
+        hi = nhi;
     }
     return 0.5f * (lo + hi);
 }
@@ -402,18 +419,24 @@ __device__ float lanczos_sigma_max(const float* A, int m, int n, const LanczosWo
             w.V[(long long)(k + 1) * n + c] = w.xs[c];
         }
         // Every 8 steps: stop once the top Ritz value moved by < 1e-7.
-        if (((k + 1) & 7) == 0 && threadIdx.x == 0) {
-            const float sg = gk_sigma_max(w.ab, k + 1);
-            *w.stop = (k + 1 >= 16 && fabsf(sg - *w.sig) <= 1e-7f) ? 1 : 0;
-            *w.sig = sg;
+        __syncthreads();
+        if (((k + 1) & 7) == 0 && threadIdx.x < 32) {
+            const float sg = gk_sigma_max_warp(w.ab, k + 1);
+            if (threadIdx.x == 0) {
+                *w.stop = (k + 1 >= 16 && fabsf(sg - *w.sig) <= 1e-7f) ? 1 : 0;
+                *w.sig = sg;
+            }
         }
         __syncthreads();
         if (*w.stop)
             break;
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        *w.sig = gk_sigma_max(w.ab, steps);
+    if (threadIdx.x < 32) {
+        const float sg = gk_sigma_max_warp(w.ab, steps);
+        if (threadIdx.x == 0)
+            *w.sig = sg;
+    }
     __syncthreads();
     return *w.sig;
 }
