@@ -210,6 +210,44 @@ int glcm_compute_naive(glcm_ctx *ctx, const void *image, int width, int height,
                        size_t pitch_bytes, int dtype, int levels, glcm_offset offset, int flags,
                        uint32_t *counts);
 
+/* GLCM counts of one device image without allocating anything (the paper has
+ * no counterpart; this is a deployment variant of glcm_compute).
+ *
+ * For callers that cannot call cudaMalloc while they run: real-time or
+ * embedded pipelines that reserve all memory up front, code running inside a
+ * custom allocator or memory pool that forbids nested allocation, and threads
+ * that must not block on the allocator.  glcm_create and the context entry
+ * points allocate tables and scratch on first use; this call does not.  It
+ * needs no context.
+ *
+ * The vote kernel's scratch (job, offset and chunk tables, the chunk counter,
+ * the error word; about 113 KB) is one fixed static device array present on
+ * every device that loads the library until the process exits.  The first call
+ * on a device, with that device current, looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+ * capture.  Every call reuses the array and clears the counter and error word
+ * it needs.  Calls are serialized by a process-wide mutex and each waits for
+ * its own work, but calls that overlap on the GPU through the same array (for
+ * example from another copy of the library in the same process) would race.
+ *
+ *   image      device pointer of the current device, height rows of pitch_bytes
+ *   offsets    host array of n_offsets (1..64) offsets
+ *   flags      GLCM_INPUT_LEVELS only (counts are always the plain P)
+ *   counts     device pointer, out: n_offsets x N x N uint32 (as glcm_compute)
+ *   cuda_stream  stream to run on (NULL: the legacy default stream); the call
+ *              returns after the counts are complete
+ *   errbuf     optional buffer for a message (errbuf_len bytes)
+ * Limits: at most GLCM_NOALLOC_MAX_JOBS histogram passes (offset groups x
+ * anchor-level parts) and GLCM_NOALLOC_MAX_CHUNKS scheduling chunks (chunks
+ * are made coarser to fit); larger requests return GLCM_ERR_UNSUPPORTED.
+ * Errors: GLCM_ERR_ARG (host pointers, bad sizes), GLCM_ERR_RANGE,
+ * GLCM_ERR_UNSUPPORTED, GLCM_ERR_CUDA, GLCM_ERR_TIMEOUT. */
+#define GLCM_NOALLOC_MAX_JOBS 128
+#define GLCM_NOALLOC_MAX_CHUNKS 8192
+int glcm_compute_noalloc(const void *image, int width, int height, size_t pitch_bytes, int dtype,
+                         int levels, const glcm_offset *offsets, int n_offsets, int flags,
+                         uint32_t *counts, void *cuda_stream, char *errbuf, size_t errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

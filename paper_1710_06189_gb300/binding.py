@@ -68,6 +68,8 @@ _PROTOS = {
     "glcm_set_vote_config": (c_int, [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_int]),
     "glcm_compute_naive": (c_int, [c_void_p, c_void_p, c_int, c_int, c_size_t, c_int, c_int, glcm_offset,
                                    c_int, c_void_p]),
+    "glcm_compute_noalloc": (c_int, [c_void_p, c_int, c_int, c_size_t, c_int, c_int, ctypes.POINTER(glcm_offset),
+                                     c_int, c_int, c_void_p, c_void_p, ctypes.c_char_p, c_size_t]),
 }
 
 _lib = None
@@ -212,3 +214,15 @@ def glcm_compute_naive(ctx, image, width, height, pitch_bytes, dtype, levels, of
     o = glcm_offset(int(offset[0]), int(offset[1]))
     return _check(ctx, load().glcm_compute_naive(ctx, _ptr(image), int(width), int(height), int(pitch_bytes),
                                                  int(dtype), int(levels), o, int(flags), _ptr(counts)))
+
+
+def glcm_compute_noalloc(image, width, height, pitch_bytes, dtype, levels, offsets, flags, counts, stream=None):
+    """GLCM counts with no allocation (static device scratch); device pointers only."""
+    offs = _offsets(offsets)
+    buf = ctypes.create_string_buffer(256)
+    st = load().glcm_compute_noalloc(_ptr(image), int(width), int(height), int(pitch_bytes), int(dtype),
+                                     int(levels), offs, len(offsets), int(flags), _ptr(counts),
+                                     None if not stream else int(stream), buf, 256)
+    if st != GLCM_OK:
+        raise GlcmError(st, buf.value.decode())
+    return st
