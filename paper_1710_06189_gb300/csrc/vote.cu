@@ -486,47 +486,7 @@ __device__ void fill_tile_plain(const VoteJob& j, const Tile& t, uint8_t* buf)
     }
 }
 
-// Partner words of two rows for the same dx (one dispatch for both).
-template <int BPP>
-__device__ __forceinline__ void partner_words2(int dx, const uint32_t (&B0)[4 / BPP + 2],
-                                               const uint32_t (&B1)[4 / BPP + 2], uint32_t (&P0)[4 / BPP],
-                                               uint32_t (&P1)[4 / BPP])
-{
-    constexpr int LW = 4 / BPP;
-#define GLCM_PW2(D)                                                                            \
-    case D:                                                                                    \
-        _Pragma("unroll") for (int m = 0; m < LW; ++m)                                         \
-        {                                                                                      \
-            constexpr int t0 = D + 4;                                                          \
-            const int t = 4 * m + t0;                                                          \
-            if ((t0 & 3) == 0) {                                                               \
-                P0[m] = B0[t >> 2];                                                            \
-                P1[m] = B1[t >> 2];                                                            \
-            } else {                                                                           \
-                P0[m] = __funnelshift_r(B0[t >> 2], B0[(t >> 2) + 1], 8 * (t0 & 3));           \
-                P1[m] = __funnelshift_r(B1[t >> 2], B1[(t >> 2) + 1], 8 * (t0 & 3));           \
-            }                                                                                  \
-        }                                                                                      \
-        break;
-    switch (dx) {
-        GLCM_PW2(-4)
-        GLCM_PW2(-3)
-        GLCM_PW2(-2)
-        GLCM_PW2(-1)
-        GLCM_PW2(0)
-        GLCM_PW2(1)
-        GLCM_PW2(2)
-        GLCM_PW2(3)
-        GLCM_PW2(4)
-        default:
-            break;
-    }
-#undef GLCM_PW2
-}
-
-// Votes of one staged tile.  Warp w takes the row pairs (y0 + 2w, y0 + 2w + 1),
-// (y0 + 2w + 2 nwarps, ...), so each offset's set-up (its parameters, the dx
-// dispatch, the partner rows) serves 2 x 16 votes per lane.
+// Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps, ...
 template <int BPP>
 __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
                                           const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
@@ -539,56 +499,37 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
     const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
     const bool full = __all_sync(0xffffffffu, lane_interior);
     const int wrem = j.W - xl;
-    for (int y = t.y0 + 2 * warp; y < t.y1; y += 2 * nwarps) {
-        const bool two = y + 1 < t.y1;  // warp-uniform
+    for (int y = t.y0 + warp; y < t.y1; y += nwarps) {
         bool bad_a = false;
-        uint32_t A0[LW], A1[LW];
-        anchor_levels<BPP>(j, buf + (y - t.ty0) * kRowBytes, lane, A0, bad_a);
-        if (two)
-            anchor_levels<BPP>(j, buf + (y + 1 - t.ty0) * kRowBytes, lane, A1, bad_a);
-        else
-#pragma unroll
-            for (int w = 0; w < LW; ++w)
-                A1[w] = 0u;
+        uint32_t A[LW];
+        anchor_levels<BPP>(j, buf + (y - t.ty0) * kRowBytes, lane, A, bad_a);
         int cur_dy = 0x7fffffff;
-        uint32_t B0[LW + 2], B1[LW + 2];
+        uint32_t B[LW + 2];
         bool bad_b = false;
-        bool v0 = false, v1 = false;
         for (int o = 0; o < j.n_off; ++o) {
             const int2 d = s_off_d[o];
             const int yp = y + d.y;
-            if (d.y != cur_dy) {
-                // Partner rows of the pair (rows outside the image are skipped).
-                bad_b = false;
-                v0 = yp >= 0 && yp < j.H;
-                v1 = two && yp + 1 >= 0 && yp + 1 < j.H;
-                uint32_t P[LW];
-                if (v0) {
-                    row_levels<BPP>(j, buf + (yp - t.ty0) * kRowBytes, lane, P, B0[0], B0[LW + 1], bad_b);
-#pragma unroll
-                    for (int w = 0; w < LW; ++w)
-                        B0[w + 1] = P[w];
-                }
-                if (v1) {
-                    row_levels<BPP>(j, buf + (yp + 1 - t.ty0) * kRowBytes, lane, P, B1[0], B1[LW + 1], bad_b);
-#pragma unroll
-                    for (int w = 0; w < LW; ++w)
-                        B1[w + 1] = P[w];
-                }
-                cur_dy = d.y;
-            }
-            if (!v0 && !v1)
+            if (yp < 0 || yp >= j.H)
                 continue;
             HistRef h = s_off_h[o];
             h.base += cbytes;
+            if (d.y != cur_dy) {
+                bad_b = false;
+                uint32_t P[LW];
+                row_levels<BPP>(j, buf + (yp - t.ty0) * kRowBytes, lane, P, B[0], B[LW + 1], bad_b);
+#pragma unroll
+                for (int w = 0; w < LW; ++w)
+                    B[w + 1] = P[w];
+                cur_dy = d.y;
+            }
             bool fast = d.x >= -kFastMaxDx && d.x <= kFastMaxDx;
             if (j.levels_mode) {
                 // A neighbour's halo may carry an out-of-range level: check all.
                 fast = fast && !__any_sync(0xffffffffu, bad_a || bad_b);
             }
             if (fast) {
-                uint32_t PW0[LW], PW1[LW];
-                partner_words2<BPP>(d.x, B0, B1, PW0, PW1);
+                uint32_t PW[LW];
+                partner_words<BPP>(d.x, B, PW);
                 uint32_t mask = 0xFFFFu;
                 if (!full) {
                     // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
@@ -596,15 +537,9 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
                     const int hi_k = min(min(PX, wrem), wrem - d.x);
                     mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
                 }
-                if (v0)
-                    vote_words_dispatch<BPP>(j, A0, PW0, h, mask, full);
-                if (v1)
-                    vote_words_dispatch<BPP>(j, A1, PW1, h, mask, full);
+                vote_words_dispatch<BPP>(j, A, PW, h, mask, full);
             } else if (xl < j.W) {
-                if (v0)
-                    vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
-                if (v1)
-                    vote_slow(jg, d.x, d.y, y + 1, xl, PX, h, err);
+                vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
             }
         }
     }
