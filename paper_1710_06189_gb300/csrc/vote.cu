@@ -53,23 +53,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Shared-memory reductions on a 32-bit shared address.  Written as atomics on
-// a shared-space pointer (the result unused, so they compile to reductions)
-// rather than inline assembly, so the compiler may schedule around them.
-__device__ __forceinline__ uint32_t* shared_ptr(uint32_t addr)
-{
-    return static_cast<uint32_t*>(__cvta_shared_to_generic(addr));
-}
-
 __device__ __forceinline__ void red_shared_add(uint32_t addr, uint32_t v)
 {
-    atomicAdd(shared_ptr(addr), v);
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v));
 }
 
+// Predicated reduction (no branch around it).
 __device__ __forceinline__ void red_shared_add_if(uint32_t addr, uint32_t v, uint32_t on)
 {
-    if (on)
-        atomicAdd(shared_ptr(addr), v);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.u32 p, %2, 0;\n\t@p red.shared.add.u32 [%0], %1;\n\t}" ::"r"(addr), "r"(v),
+        "r"(on));
 }
 
 __device__ __forceinline__ void red_global_add(uint32_t* p, uint32_t v)
