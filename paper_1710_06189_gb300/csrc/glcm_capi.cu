@@ -382,12 +382,6 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                     const double merge = 2.0 * j.hist_words + 64.0;
                     const double want = std::ceil(10.0 * merge / std::max(1.0, votes_per_item));
                     j.chunk_items = (int)std::max(1.0, std::min<double>(n_strips * n_bands, want));
-                    if (cfg.layout == 2) {
-                        // A chunk must stay below 65536 votes per 16-bit half.
-                        const long long rows_ok = 65535ll / ((long long)PX * (T >> cfg.rshift));
-                        const long long items_ok = std::max(1ll, rows_ok * nwarps / band - 1);
-                        j.chunk_items = (int)std::min<long long>(j.chunk_items, items_ok);
-                    }
                 }
                 j.n_strips = n_strips;
                 j.band_rows = band;

@@ -234,13 +234,6 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
             const double votes_per_item = (double)kNaBand * strip_px * cnt * span / levels;
             const double want = (10.0 * (2.0 * j.hist_words + 64.0)) / (votes_per_item > 1.0 ? votes_per_item : 1.0);
             j.chunk_items = want < 1.0 ? 1 : (want > j.n_job_items ? j.n_job_items : (int)want + 1);
-            if (layout == 2) {
-                // A chunk must stay below 65536 votes per 16-bit half.
-                const long long rows_ok = 65535ll / ((long long)PX * (kNaThreads >> rshift));
-                const long long items_ok = rows_ok * (kNaThreads / 32) / kNaBand - 1;
-                if (j.chunk_items > items_ok)
-                    j.chunk_items = items_ok < 1 ? 1 : (int)items_ok;
-            }
             j.n_strips = n_strips;
             j.band_rows = kNaBand;
             j.y_begin = 0;
@@ -263,10 +256,7 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     long long want_chunks = 0;
     for (int jb = 0; jb < n_jobs; ++jb)
         want_chunks += (h.jobs[jb].n_job_items + h.jobs[jb].chunk_items - 1) / h.jobs[jb].chunk_items;
-    long long scale = (want_chunks + kNaMaxChunks - 1) / kNaMaxChunks;
-    if (layout == 2 && scale > 1)
-        return na_fail(errbuf, errbuf_len, GLCM_ERR_UNSUPPORTED,
-                       "request needs more chunks than the static scratch holds (GLCM_NOALLOC_MAX_CHUNKS)");
+    const long long scale = (want_chunks + kNaMaxChunks - 1) / kNaMaxChunks;
     int n_chunks = 0;
     for (int jb = 0; jb < n_jobs; ++jb) {
         VoteJob& j = h.jobs[jb];

@@ -564,27 +564,19 @@ __device__ void vote_tile_unstaged(const VoteJob& j, const VoteJob* jg, const Ti
         }
 }
 
-__device__ __forceinline__ bool tile_ok(const VoteParams& p, const VoteJob& j)
-{
-    const int need = j.staged ? (j.band_rows + j.dy_max - j.dy_min) * kRowBytes : 0;
-    return j.hist_words <= p.max_hist_words && j.n_off <= kMaxJobOffsets && need <= p.tile_bytes;
-}
-
 // Persistent CTAs pull chunks -- runs of consecutive items of one job, sized
 // on the host so that a chunk's votes outweigh its merge -- from a global
 // counter.  Chunks are ordered job by job, so a CTA usually stays on one job
 // for several chunks and merges only when its job changes; pulling them
 // dynamically balances images whose contention makes items cost very
-// different times.  The next chunk is claimed one ahead, so the tile copy of
-// the next item is always in flight while the current item votes, across
-// chunk and job boundaries.  Dynamic shared memory: two tile buffers, then
-// the histograms.
+// different times.  Dynamic shared memory: two tile buffers, then the
+// histograms.
 template <int BPP, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ __align__(8) uint64_t s_bar[2];
-    __shared__ int s_grab, s_ok;
+    __shared__ int s_chunk, s_ok;
     __shared__ HistRef s_off_h[kMaxJobOffsets];
     __shared__ int2 s_off_d[kMaxJobOffsets];
     uint8_t* tiles = smem;
@@ -600,103 +592,89 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
     __syncthreads();
     const uint32_t hbase = smem_u32(hist);
     const int nwarps = blockDim.x >> 5;
-    auto grab = [&]() -> int {
-        if (threadIdx.x == 0)
-            s_grab = (int)atomicAdd(p.item_counter, 1u);
-        __syncthreads();
-        const int c = s_grab;
-        __syncthreads();
-        return c;
-    };
-    auto stage_offsets = [&](const VoteJob& j) {
-        if (threadIdx.x < j.n_off && threadIdx.x < kMaxJobOffsets) {
-            const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
-            s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
-            s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
-        }
-        if (threadIdx.x == 0 && !tile_ok(p, j)) {
-            atomicOr(p.err, kErrInternal);
-            s_ok = 0;
-        }
-        __syncthreads();
-    };
-    // Warp 0 starts the copy of item k of job j into buffer b; true if it did.
-    auto prefetch = [&](const VoteJob& j, int k, int b) -> bool {
-        if (!(j.staged && j.aligned && tile_ok(p, j)))
-            return false;
-        if (threadIdx.x < 32)
-            issue_tile(j, tile_of(j, k), tiles + b * p.tile_bytes, &s_bar[b]);
-        return true;
-    };
-
     uint32_t uses[2] = {0u, 0u};  // completed phases per tile buffer
-    int c_cur = grab();
-    if (c_cur >= p.n_chunks)
-        return;
-    int c_nxt = grab();
-    int3 ch = p.chunks[c_cur];
-    VoteJob j = p.jobs[ch.x];
-    stage_offsets(j);
-    long long acc_rows = 0;  // rows per warp voted into 16-bit halves since the last merge
-    int k = ch.y, b = 0;
-    bool issued = prefetch(j, k, b);
+    int cur = -1;                 // job whose partial histograms are in shared memory
+    long long acc_rows = 0;       // rows per warp voted into 16-bit halves since the last merge
     for (;;) {
-        // Start the copy of the item after this one (this chunk or the next).
-        bool nxt_issued = false;
-        if (k + 1 < ch.z) {
-            nxt_issued = prefetch(j, k + 1, b ^ 1);
-        } else if (c_nxt < p.n_chunks) {
-            const int3 nch = p.chunks[c_nxt];
-            nxt_issued = prefetch(p.jobs[nch.x], nch.y, b ^ 1);
-        }
-        const Tile t = tile_of(j, k);
-        uint8_t* buf = tiles + b * p.tile_bytes;
-        if (!j.staged) {
-            if (s_ok)
-                vote_tile_unstaged<BPP>(j, p.jobs + ch.x, t, s_off_h, s_off_d, p.err);
-        } else {
-            if (issued) {
-                if (!mbar_wait_bounded(&s_bar[b], uses[b] & 1u, p.err))
-                    s_ok = 0;
-                uses[b]++;
-            } else {
-                fill_tile_plain(j, t, buf);
-                // Plain stores before a later bulk copy reuses the buffer.
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-            }
-            if (s_ok)
-                vote_tile<BPP>(j, p.jobs + ch.x, t, buf, s_off_h, s_off_d, p.err);
-        }
+        if (threadIdx.x == 0)
+            s_chunk = (int)atomicAdd(p.item_counter, 1u);
         __syncthreads();
-        b ^= 1;
-        issued = nxt_issued;
-        if (++k < ch.z)
-            continue;
-        // End of the chunk: move to the next one (claimed earlier).
-        acc_rows += (long long)(ch.z - ch.y) * j.band_rows / nwarps + 1;
-        if (c_nxt >= p.n_chunks)
+        const int c = s_chunk;
+        if (c >= p.n_chunks)
             break;
-        const int3 nch = p.chunks[c_nxt];
-        c_cur = c_nxt;
-        c_nxt = grab();
+        const int3 ch = p.chunks[c];
+        const VoteJob* jg = p.jobs + ch.x;
+        const VoteJob j = *jg;
+        const int tile_need = j.staged ? (j.band_rows + j.dy_max - j.dy_min) * kRowBytes : 0;
+        if (j.hist_words > p.max_hist_words || j.n_off > kMaxJobOffsets || tile_need > p.tile_bytes) {
+            if (threadIdx.x == 0)
+                atomicOr(p.err, kErrInternal);
+            __syncthreads();
+            continue;
+        }
         const long long rows_ok =
             j.layout == 2 ? 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift)) : (1ll << 62);
-        const long long nrows = (long long)(nch.z - nch.y) * j.band_rows / nwarps + 1;
-        const bool job_change = nch.x != ch.x;
-        if (job_change || acc_rows + nrows > rows_ok) {
-            flush_hist(j, p.offs, hist);
+        const long long chunk_rows = (long long)(ch.z - ch.y) * j.band_rows / nwarps + 1;
+        if (cur >= 0 && (cur != ch.x || acc_rows + chunk_rows > rows_ok)) {
+            flush_hist(p.jobs[cur], p.offs, hist);
             __syncthreads();
+            cur = -1;
+        }
+        if (cur != ch.x) {
+            if (threadIdx.x < j.n_off) {
+                const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
+                s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
+                s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
+            }
+            __syncthreads();
+            cur = ch.x;
             acc_rows = 0;
         }
-        ch = nch;
-        k = ch.y;
-        if (job_change) {
-            j = p.jobs[ch.x];
-            stage_offsets(j);
+        // Items per merge inside the chunk (16-bit halves only).
+        int step = ch.z - ch.y;
+        if (j.layout == 2)
+            step = (int)max(1ll, min((long long)step, rows_ok * nwarps / j.band_rows));
+        const bool tma = j.staged && j.aligned;
+        for (int ka = ch.y; ka < ch.z; ka += step) {
+            const int kb = min(ch.z, ka + step);
+            if (ka > ch.y) {
+                flush_hist(j, p.offs, hist);
+                __syncthreads();
+            }
+            if (tma && threadIdx.x < 32)
+                issue_tile(j, tile_of(j, ka), tiles, &s_bar[0]);
+            for (int kk = ka; kk < kb; ++kk) {
+                const int b = (kk - ka) & 1;
+                uint8_t* buf = tiles + b * p.tile_bytes;
+                const Tile t = tile_of(j, kk);
+                if (!j.staged) {
+                    vote_tile_unstaged<BPP>(j, jg, t, s_off_h, s_off_d, p.err);
+                    __syncthreads();
+                    continue;
+                }
+                if (tma) {
+                    // Prefetch the next tile into the other buffer (its last
+                    // readers passed the barrier at the end of the previous item).
+                    if (kk + 1 < kb && threadIdx.x < 32)
+                        issue_tile(j, tile_of(j, kk + 1), tiles + (b ^ 1) * p.tile_bytes, &s_bar[b ^ 1]);
+                    if (!mbar_wait_bounded(&s_bar[b], uses[b] & 1u, p.err))
+                        s_ok = 0;
+                    uses[b]++;
+                } else {
+                    fill_tile_plain(j, t, buf);
+                    // Plain stores before a later bulk copy reuses the buffer.
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    __syncthreads();
+                }
+                if (s_ok)
+                    vote_tile<BPP>(j, jg, t, buf, s_off_h, s_off_d, p.err);
+                __syncthreads();
+            }
         }
+        acc_rows += chunk_rows;
     }
-    flush_hist(j, p.offs, hist);
+    if (cur >= 0)
+        flush_hist(p.jobs[cur], p.offs, hist);
 }
 
 // Scheme 1 of the paper (Sec. I.B): one thread per anchor pixel, one global
