@@ -287,7 +287,10 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
 // anchor votes; else only those whose bit is set in `mask` (image edges).
 // BYTECODE: N <= 16 power of two, 32 interleaved copies, one byte per code.
 // SPLIT: only anchors with level in [lo, lo + span) vote.
-template <int BPP, bool BYTECODE, bool SPLIT, bool FULL>
+// INC1: the increment is the constant 1 (every layout but the upper halves of
+// layout 2), which lets lanes of a warp that hit the same word be combined
+// into one update instead of serializing.
+template <int BPP, bool BYTECODE, bool SPLIT, bool FULL, bool INC1>
 __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)[4 / BPP],
                                            const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask)
 {
@@ -317,15 +320,40 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
             const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
             const uint32_t ii = SPLIT ? i - lo : i;
             const uint32_t addr = h.base + (ii * N + jv) * h.stride;
+            const uint32_t inc = INC1 ? 1u : h.inc;
             if (FULL && !SPLIT) {
-                red_shared_add(addr, h.inc);
+                red_shared_add(addr, inc);
             } else {
                 uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
                 if (SPLIT)
                     on &= ii < span ? 1u : 0u;
-                red_shared_add_if(addr, h.inc, on);
+                red_shared_add_if(addr, inc, on);
             }
         }
+    }
+}
+
+template <int BPP, bool INC1>
+__device__ __forceinline__ void vote_words_inc(const VoteJob& j, const uint32_t (&A)[4 / BPP],
+                                               const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask,
+                                               bool full)
+{
+    const bool split = j.lv_span < j.levels;
+    if (j.bytecode) {
+        if (full)
+            vote_words<BPP, true, false, true, true>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, true, false, false, true>(j, A, PW, h, mask);
+    } else if (split) {
+        if (full)
+            vote_words<BPP, false, true, true, INC1>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, true, false, INC1>(j, A, PW, h, mask);
+    } else {
+        if (full)
+            vote_words<BPP, false, false, true, INC1>(j, A, PW, h, mask);
+        else
+            vote_words<BPP, false, false, false, INC1>(j, A, PW, h, mask);
     }
 }
 
@@ -334,23 +362,10 @@ __device__ __forceinline__ void vote_words_dispatch(const VoteJob& j, const uint
                                                     const uint32_t (&PW)[4 / BPP], const HistRef& h,
                                                     uint32_t mask, bool full)
 {
-    const bool split = j.lv_span < j.levels;
-    if (j.bytecode) {
-        if (full)
-            vote_words<BPP, true, false, true>(j, A, PW, h, mask);
-        else
-            vote_words<BPP, true, false, false>(j, A, PW, h, mask);
-    } else if (split) {
-        if (full)
-            vote_words<BPP, false, true, true>(j, A, PW, h, mask);
-        else
-            vote_words<BPP, false, true, false>(j, A, PW, h, mask);
-    } else {
-        if (full)
-            vote_words<BPP, false, false, true>(j, A, PW, h, mask);
-        else
-            vote_words<BPP, false, false, false>(j, A, PW, h, mask);
-    }
+    if (h.inc == 1u)
+        vote_words_inc<BPP, true>(j, A, PW, h, mask, full);
+    else
+        vote_words_inc<BPP, false>(j, A, PW, h, mask, full);
 }
 
 // Per-pixel path with full checks (|dx| > 4, bad levels): reads the image.
