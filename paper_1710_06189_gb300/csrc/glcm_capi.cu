@@ -454,13 +454,15 @@ int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
     return std::max(1, std::min((int)plan.chunks.size(), ctx->sm_count * per_sm));
 }
 
-// Split every job of a plan into chunks of chunk_items consecutive items.
-void build_chunks(VotePlan& plan)
+// Split every job of a plan into chunks of chunk_items consecutive items,
+// capped so that the launch has at least ~3 chunks per CTA to balance.
+void build_chunks(VotePlan& plan, int ctas)
 {
     plan.chunks.clear();
+    const int cap = std::max(1, plan.n_items / std::max(1, 3 * ctas));
     for (int jb = 0; jb < (int)plan.jobs.size(); ++jb) {
         const VoteJob& j = plan.jobs[jb];
-        const int cs = std::max(1, j.chunk_items);
+        const int cs = std::max(1, std::min(j.chunk_items, cap));
         for (int k = 0; k < j.n_job_items; k += cs)
             plan.chunks.push_back(make_int3(jb, j.item0 + k, j.item0 + std::min(j.n_job_items, k + cs)));
     }
@@ -939,7 +941,7 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
                     offsets, n_offsets, d_counts, r0, r1};
         TRY(plan_image(ctx, s, plan, target_items(ctx)));
-        build_chunks(plan);
+        build_chunks(plan, ctx->sm_count);
         std::vector<FeatJob> none;
         TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
         TRY(enqueue_vote(ctx, plan, ctx->jobs, ctx->offs,
@@ -1139,8 +1141,8 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
         all.offs = p8.offs;
         all.offs.insert(all.offs.end(), p16.offs.begin(), p16.offs.end());
         // Chunks: p8's then p16's, each indexing jobs of its own sub-table.
-        build_chunks(p8);
-        build_chunks(p16);
+        build_chunks(p8, ctx->sm_count);
+        build_chunks(p16, ctx->sm_count);
         all.chunks = p8.chunks;
         all.chunks.insert(all.chunks.end(), p16.chunks.begin(), p16.chunks.end());
         TRY(upload_tables(ctx, all, feats, ge.jobs, ge.offs, ge.feat));

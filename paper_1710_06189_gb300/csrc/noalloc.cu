@@ -253,6 +253,12 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
         o0 += cnt;
     }
     // Chunks; if there are more than the scratch holds, make them coarser.
+    {
+        const int cap = n_items / (3 * sms) > 1 ? n_items / (3 * sms) : 1;  // >= ~3 chunks per CTA
+        for (int jb = 0; jb < n_jobs; ++jb)
+            if (h.jobs[jb].chunk_items > cap)
+                h.jobs[jb].chunk_items = cap;
+    }
     long long want_chunks = 0;
     for (int jb = 0; jb < n_jobs; ++jb)
         want_chunks += (h.jobs[jb].n_job_items + h.jobs[jb].chunk_items - 1) / h.jobs[jb].chunk_items;

@@ -610,9 +610,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
     uint32_t uses[2] = {0u, 0u};  // completed phases per tile buffer
     int cur = -1;                 // job whose partial histograms are in shared memory
     long long acc_rows = 0;       // rows per warp voted into 16-bit halves since the last merge
+    // Chunk b goes to CTA b; later chunks are claimed from the counter.
+    bool first = true;
     for (;;) {
         if (threadIdx.x == 0)
-            s_chunk = (int)atomicAdd(p.item_counter, 1u);
+            s_chunk = first ? (int)blockIdx.x : (int)gridDim.x + (int)atomicAdd(p.item_counter, 1u);
+        first = false;
         __syncthreads();
         const int c = s_chunk;
         if (c >= p.n_chunks)
