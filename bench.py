@@ -170,6 +170,124 @@ def run_reference(args):
     return 0
 
 
+SERVE_REQUESTS = 256
+SERVE_LOADS = (0.5, 0.9, 1.5)
+
+
+def _pace(target: float):
+    """Sleep, then spin, until perf_counter() reaches target."""
+    while True:
+        d = target - time.perf_counter()
+        if d <= 0:
+            return
+        if d > 0.0005:
+            time.sleep(d - 0.0003)
+
+
+def serving_leg(G, S, torch, local: int, n_req: int = SERVE_REQUESTS):
+    """Served stream: Poisson requests (seeded) of uint8 images, sides
+    log-uniform 256..8192, N in {8,16,32,64}, 1..12 offsets, iid/smooth 50/50,
+    from pinned host memory; counts + symmetric features back to pinned host
+    buffers.  The plain loop runs one request at a time through the public API
+    (copy in, launch, copy out, sync); the server batches continuously.  Both
+    see the same arrival times at loads of 0.5, 0.9 and 1.5 x the plain loop's
+    capacity, plus an all-at-once burst for saturation throughput.  Latency is
+    from a request's scheduled arrival to its results being in host memory."""
+    import numpy as np
+
+    reqs = S.request_stream(n_req, 1.0, lo=256, hi=8192)
+    crops = S.request_crops(reqs)
+    bases = {k: torch.from_numpy(S.image(k, S.serve_base_seed(k), S.SERVE_BASE_SIDE, S.SERVE_BASE_SIDE,
+                                         np.uint8, 8.0)).pin_memory() for k in ("iid", "smooth")}
+    views = [bases[r.kind][y0:y0 + r.side, x0:x0 + r.side] for r, (y0, x0) in zip(reqs, crops)]
+    outs = [(torch.empty((len(r.offsets), r.levels, r.levels), dtype=torch.int32).pin_memory(),
+             torch.empty((len(r.offsets), 14), dtype=torch.float32).pin_memory()) for r in reqs]
+    pairs = [pairs_of(r.side, r.side, r.offsets) for r in reqs]
+    total_pairs = float(sum(pairs))
+    unit_arrivals = [r.arrival_s for r in reqs]  # a rate-1 Poisson process
+    sym = G.GLCM_SYMMETRIC
+
+    ctx = G.Context(local, hbm_budget_bytes=2 << 30)
+
+    def plain_one(i):
+        r = reqs[i]
+        ctx.batch([dict(image=views[i], levels=r.levels, offsets=r.offsets, flags=sym, counts=outs[i][0],
+                        features=outs[i][1])])
+
+    for i in range(4):
+        plain_one(i)
+    t0 = time.perf_counter()
+    for i in range(n_req):
+        plain_one(i)
+    plain_s = time.perf_counter() - t0
+    capacity = n_req / plain_s
+
+    def plain_run(arr):
+        lat = []
+        t0 = time.perf_counter()
+        for i in range(n_req):
+            _pace(t0 + arr[i])
+            plain_one(i)
+            lat.append(time.perf_counter() - t0 - arr[i])
+        return lat, time.perf_counter() - t0
+
+    srv = G.Server(local, hbm_budget_bytes=8 << 30, lanes=2)
+
+    def served_run(arr):
+        tickets = [None] * n_req
+        lag = [0.0] * n_req
+        ready = threading.Semaphore(0)
+
+        def producer():
+            t0 = start[0]
+            for i in range(n_req):
+                r = reqs[i]
+                _pace(t0 + arr[i])
+                tickets[i] = srv.submit(views[i], r.levels, r.offsets, sym, counts=outs[i][0], features=outs[i][1])
+                lag[i] = time.perf_counter() - t0 - arr[i]
+                ready.release()
+
+        start = [time.perf_counter()]
+        th = threading.Thread(target=producer)
+        th.start()
+        lat = []
+        for i in range(n_req):
+            ready.acquire()
+            st, ms, _ = srv.wait(tickets[i])
+            if st != G.GLCM_OK:
+                raise RuntimeError(f"served request {i} failed ({st}): {srv.last_error()}")
+            lat.append(lag[i] + ms * 1e-3)
+        th.join()
+        return lat, time.perf_counter() - start[0]
+
+    served_run([0.0] * n_req)  # warm-up burst
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v) * 1e3, q))
+
+    out = {"requests": n_req, "mean_image_bytes": float(np.mean([r.side * r.side for r in reqs])),
+           "pairs": total_pairs, "plain_capacity_rps": capacity,
+           "plain_gpairs_s": total_pairs / plain_s / 1e9, "loads": []}
+    lat, el = served_run([0.0] * n_req)
+    out["served_burst_gpairs_s"] = total_pairs / el / 1e9
+    out["served_over_plain"] = out["served_burst_gpairs_s"] / out["plain_gpairs_s"]
+    for load in SERVE_LOADS:
+        arr = [a / (load * capacity) for a in unit_arrivals]
+        lp, elp = plain_run(arr)
+        ls, els = served_run(arr)
+        out["loads"].append({"load_x_plain_capacity": load, "rate_rps": load * capacity,
+                             "served": {"gpairs_s": total_pairs / els / 1e9, "p50_ms": pct(ls, 50),
+                                        "p99_ms": pct(ls, 99)},
+                             "plain": {"gpairs_s": total_pairs / elp / 1e9, "p50_ms": pct(lp, 50),
+                                       "p99_ms": pct(lp, 99)}})
+    st = srv.stats()
+    out["server_stats"] = {k: st[k] for k in ("batches", "max_batch", "kernel_launches", "arena_peak",
+                                             "completed", "failed")}
+    srv.close()
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -178,6 +296,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -309,6 +428,8 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if not args.no_serving:
+        line["serving"] = serving_leg(G, S, torch, local)
     if not args.no_cpu_baseline and world == 1:
         v, desc = oracle_sample(jobs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}

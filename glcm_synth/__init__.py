@@ -185,3 +185,24 @@ def request_stream(n: int, rate_per_s: float, lo: int = 256, hi: int = 8192, see
         kind = "iid" if rng.random() < 0.5 else "smooth"
         out.append(Request(r, t, side, n_lv, kind, seed + 1 + r, offs))
     return out
+
+
+SERVE_BASE_SIDE = 8192
+
+
+def request_crops(reqs, base_side: int = SERVE_BASE_SIDE, seed: int = BASE_SEED + 650):
+    """Top-left corner (y0, x0) of each request's side x side window inside a
+    base_side^2 image of its kind, uniform over the valid positions.  A
+    served request's pixels are that window of one of two base images
+    (``image(kind, serve_base_seed(kind), base_side, base_side)``)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for r in reqs:
+        span = base_side - r.side + 1
+        out.append((int(rng.integers(0, span)), int(rng.integers(0, span))))
+    return out
+
+
+def serve_base_seed(kind: str) -> int:
+    return BASE_SEED + 600 + ("iid", "smooth").index(kind)
+

@@ -162,6 +162,16 @@ int glcm_features(glcm_ctx *ctx, const uint32_t *counts, int levels, int n_glcm,
  * Errors: as glcm_compute, per the first failing desc. */
 int glcm_compute_batch(glcm_ctx *ctx, const glcm_desc *descs, int n);
 
+/* The same batch as glcm_compute_batch, launched directly (no graph is
+ * captured or cached) and never synchronized: the call returns once the
+ * table upload, the vote launches and the epilogue launch are enqueued on the
+ * context's stream.  For batches whose composition changes every call (a
+ * serving loop).  All pointers are device pointers; the caller keeps them
+ * valid until the stream has passed the work, and glcm_synchronize reports
+ * device-detected errors.
+ * Errors: GLCM_ERR_ARG (host pointers, bad descs), GLCM_ERR_NOMEM, GLCM_ERR_CUDA. */
+int glcm_enqueue_batch(glcm_ctx *ctx, const glcm_desc *descs, int n);
+
 /* Local GLCMs of sliding win x win windows whose top-left pixels are
  * (u*stride, v*stride), u < nwx = (width - win)/stride + 1,
  * v < nwy = (height - win)/stride + 1; each window's GLCM counts the pairs
@@ -247,6 +257,73 @@ int glcm_compute_naive(glcm_ctx *ctx, const void *image, int width, int height,
 int glcm_compute_noalloc(const void *image, int width, int height, size_t pitch_bytes, int dtype,
                          int levels, const glcm_offset *offsets, int n_offsets, int flags,
                          uint32_t *counts, void *cuda_stream, char *errbuf, size_t errbuf_len);
+
+/* ---- Serving: continuous batching of host requests ----------------------
+ *
+ * A server owns a device-memory arena of hbm_budget_bytes, `lanes` contexts
+ * (one CUDA stream each), a copy stream and one scheduler thread.  The paper
+ * overlaps the host-to-device copy of image stripes with the votes of
+ * earlier stripes over CUDA streams (Sec. III, Eqs. 7-9); the server applies
+ * the same overlap across requests.  Its scheduler repeatedly
+ *   - admits queued requests in arrival order while their device footprint
+ *     (pitched image + counts + normalized + features) fits in the free
+ *     arena, and enqueues their image copies on the copy stream;
+ *   - gives every admitted request not yet launched to the next idle lane as
+ *     one batch (at most max_batch requests): the lane waits for those
+ *     copies, runs the batch's votes and epilogue, and copies the results to
+ *     the requests' host buffers;
+ *   - retires finished batches, frees their arena space and wakes waiters.
+ * So requests that arrive while others are on the GPU join the next batch as
+ * lanes and memory free up, and copies overlap earlier batches' kernels.
+ * Each result equals that of glcm_compute (+ glcm_features) on the request
+ * alone.  Requests with GLCM_INPUT_LEVELS run as batches of one so that a
+ * GLCM_ERR_RANGE belongs to that request. */
+typedef struct glcm_server glcm_server;
+
+typedef struct {
+    long long submitted, completed, failed;
+    long long batches;          /* batches launched                              */
+    long long max_batch;        /* most requests in one batch                    */
+    long long kernel_launches;  /* kernels the lanes launched                    */
+    long long queue_peak;       /* most requests waiting for admission           */
+    size_t arena_bytes;         /* arena size                                    */
+    size_t arena_peak;          /* most arena bytes in use at once               */
+} glcm_server_counters;
+
+/* Create a server on `device`: an arena of hbm_budget_bytes (0 = 4 GiB),
+ * `lanes` compute streams (1..8; 0 = 2), at most max_batch requests per
+ * batch (0 = 256) and at most max_queue requests waiting for admission
+ * (0 = 4096).  Errors: GLCM_ERR_ARG, GLCM_ERR_NOMEM, GLCM_ERR_CUDA. */
+int glcm_server_create(glcm_server **out, int device, size_t hbm_budget_bytes, int lanes, int max_batch,
+                       int max_queue);
+
+/* Queue one request.  `request` is a glcm_desc whose image, counts and
+ * (optional) normalized and features pointers are HOST pointers -- pinned
+ * memory lets copies overlap; pageable memory works but blocks the
+ * scheduler during its copies.  The offsets are copied; the buffers must
+ * stay valid until the request completes.  *ticket receives its id (>= 1).
+ * Errors: GLCM_ERR_ARG (bad desc, device pointers), GLCM_ERR_NOMEM
+ * (footprint larger than the whole arena), GLCM_ERR_BUSY (admission queue
+ * full; retry later). */
+int glcm_server_submit(glcm_server *s, const glcm_desc *request, long long *ticket);
+
+/* Wait up to timeout_ms (< 0: no limit; 0: just check) for a request.  When
+ * it has completed, returns its status (GLCM_OK or the error that failed
+ * it), writes the milliseconds from its submission to its completion into
+ * *latency_ms (may be NULL) and forgets the ticket.  Returns GLCM_ERR_BUSY if
+ * it is still in flight, GLCM_ERR_ARG for an unknown ticket. */
+int glcm_server_wait(glcm_server *s, long long ticket, int timeout_ms, double *latency_ms);
+
+/* Counters since creation.  Errors: GLCM_ERR_ARG. */
+int glcm_server_stats(glcm_server *s, glcm_server_counters *out);
+
+/* Message for the last failure of a server call or request ("" if none);
+ * with s == NULL, of the last glcm_server_create. */
+const char *glcm_server_last_error(const glcm_server *s);
+
+/* Finish every admitted request, fail the ones still queued with
+ * GLCM_ERR_BUSY, stop the scheduler and free everything.  NULL is accepted. */
+int glcm_server_destroy(glcm_server *s);
 
 #ifdef __cplusplus
 }

@@ -10,13 +10,14 @@ up to 46340^2).
 from __future__ import annotations
 
 from . import binding
-from .binding import (GLCM_INPUT_LEVELS, GLCM_NORMALIZE, GLCM_SYMMETRIC, GLCM_U8, GLCM_U16, GlcmError,
+from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_INPUT_LEVELS, GLCM_NORMALIZE, GLCM_OK,
+                      GLCM_SYMMETRIC, GLCM_U8, GLCM_U16, GlcmError,
                       glcm_compute, glcm_compute_batch, glcm_compute_naive, glcm_create, glcm_destroy,
                       glcm_features, glcm_get_timing, glcm_last_error, glcm_offset_from_angle,
                       glcm_set_timing, glcm_set_vote_config, glcm_synchronize, glcm_windows)
 
 __all__ = [
-    "binding", "Context", "GlcmError", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_U8",
+    "binding", "Context", "Server", "GlcmError", "GLCM_OK", "GLCM_ERR_BUSY", "GLCM_ERR_NOMEM", "GLCM_ERR_RANGE", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_U8",
     "GLCM_U16", "glcm_compute", "glcm_compute_batch", "glcm_compute_naive", "glcm_create", "glcm_destroy",
     "glcm_features", "glcm_get_timing", "glcm_last_error", "glcm_offset_from_angle", "glcm_set_timing",
     "glcm_set_vote_config", "glcm_synchronize", "glcm_windows",
@@ -142,5 +143,90 @@ class Context:
         glcm_windows(self.ctx, src, w, h, pitch, dt, levels, win, stride, offsets, flags, c, m)
         return c, m
 
+    def enqueue_batch(self, jobs):
+        """glcm_enqueue_batch: the batch launched directly, no graph, no sync;
+        jobs as for batch() with device tensors only."""
+        torch = _torch()
+        descs, outs = [], []
+        for jb in jobs:
+            src, w, h, pitch, dt = image_args(jb["image"])
+            n, N = len(jb["offsets"]), jb["levels"]
+            c = jb.get("counts")
+            if c is None:
+                c = self._empty((n, N, N), torch.int32)
+            nm = jb.get("normalized")
+            nm = self._empty((n, N, N), torch.float32) if nm is True else (nm if nm is not False else None)
+            ft = jb.get("features")
+            ft = self._empty((n, 14), torch.float32) if ft is True else (ft if ft is not False else None)
+            descs.append(binding.make_desc(src, w, h, pitch, dt, N, jb["offsets"], jb.get("flags", 0), c, nm, ft))
+            outs.append((c, nm, ft))
+        binding.glcm_enqueue_batch(self.ctx, descs)
+        self._keep = descs
+        return outs
+
     def synchronize(self):
         glcm_synchronize(self.ctx)
+
+
+class Server:
+    """Continuous-batching GLCM server on one device (glcm_server_*).
+
+    submit() queues a host image and returns a ticket; wait() returns
+    (status, latency_ms, (counts, normalized, features)).  Outputs are
+    allocated in pinned host memory unless given.  The image and the outputs
+    are kept referenced here until the request is waited for."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, lanes: int = 0, max_batch: int = 0,
+                 max_queue: int = 0):
+        self.server = binding.glcm_server_create(device, hbm_budget_bytes, lanes, max_batch, max_queue)
+        self._live = {}
+
+    def submit(self, image, levels: int, offsets, flags: int = 0, counts=None, normalized=False, features=False,
+               pin: bool = True):
+        torch = _torch()
+        src, w, h, pitch, dt = image_args(image)
+        n = len(offsets)
+
+        def host(shape, dtype):
+            t = torch.empty(shape, dtype=dtype)
+            return t.pin_memory() if pin else t
+
+        c = counts if counts is not None else host((n, levels, levels), torch.int32)
+        nm = normalized if not isinstance(normalized, bool) else (host((n, levels, levels), torch.float32)
+                                                                  if normalized else None)
+        ft = features if not isinstance(features, bool) else (host((n, 14), torch.float32) if features else None)
+        desc = binding.make_desc(src, w, h, pitch, dt, levels, offsets, flags, c, nm, ft)
+        t = binding.glcm_server_submit(self.server, desc)
+        self._live[t] = (desc, image, (c, nm, ft))
+        return t
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        st, lat = binding.glcm_server_wait(self.server, ticket, timeout_ms)
+        if st == GLCM_ERR_BUSY:
+            return st, None, None
+        _, _, outs = self._live.pop(ticket)
+        return st, lat, outs
+
+    def stats(self):
+        return binding.glcm_server_stats(self.server)
+
+    def last_error(self):
+        return binding.glcm_server_last_error(self.server)
+
+    def close(self):
+        if self.server is not None:
+            binding.glcm_server_destroy(self.server)
+            self.server = None
+            self._live.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -44,6 +44,12 @@ class glcm_desc(ctypes.Structure):
                 ("features", c_void_p)]
 
 
+class glcm_server_stats_t(ctypes.Structure):
+    _fields_ = [("submitted", c_longlong), ("completed", c_longlong), ("failed", c_longlong),
+                ("batches", c_longlong), ("max_batch", c_longlong), ("kernel_launches", c_longlong),
+                ("queue_peak", c_longlong), ("arena_bytes", c_size_t), ("arena_peak", c_size_t)]
+
+
 class GlcmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"glcm status {status}: {message}")
@@ -59,6 +65,13 @@ _PROTOS = {
                              ctypes.POINTER(glcm_offset), c_int, c_int, c_void_p, c_void_p]),
     "glcm_features": (c_int, [c_void_p, c_void_p, c_int, c_int, c_int, c_void_p]),
     "glcm_compute_batch": (c_int, [c_void_p, ctypes.POINTER(glcm_desc), c_int]),
+    "glcm_enqueue_batch": (c_int, [c_void_p, ctypes.POINTER(glcm_desc), c_int]),
+    "glcm_server_create": (c_int, [ctypes.POINTER(c_void_p), c_int, c_size_t, c_int, c_int, c_int]),
+    "glcm_server_submit": (c_int, [c_void_p, ctypes.POINTER(glcm_desc), ctypes.POINTER(c_longlong)]),
+    "glcm_server_wait": (c_int, [c_void_p, c_longlong, c_int, ctypes.POINTER(c_double)]),
+    "glcm_server_stats": (c_int, [c_void_p, ctypes.POINTER(glcm_server_stats_t)]),
+    "glcm_server_last_error": (ctypes.c_char_p, [c_void_p]),
+    "glcm_server_destroy": (c_int, [c_void_p]),
     "glcm_windows": (c_int, [c_void_p, c_void_p, c_int, c_int, c_size_t, c_int, c_int, c_int, c_int,
                              ctypes.POINTER(glcm_offset), c_int, c_int, c_void_p, c_void_p]),
     "glcm_synchronize": (c_int, [c_void_p]),
@@ -181,6 +194,59 @@ def make_desc(image, width, height, pitch_bytes, dtype, levels, offsets, flags, 
 def glcm_compute_batch(ctx, descs):
     arr = (glcm_desc * len(descs))(*[d[0] if isinstance(d, tuple) else d for d in descs])
     return _check(ctx, load().glcm_compute_batch(ctx, arr, len(descs)))
+
+
+def glcm_enqueue_batch(ctx, descs):
+    """Direct (graph-free, unsynchronized) batch launch; device pointers only."""
+    arr = (glcm_desc * len(descs))(*[d[0] if isinstance(d, tuple) else d for d in descs])
+    return _check(ctx, load().glcm_enqueue_batch(ctx, arr, len(descs)))
+
+
+def _check_server(server, status: int):
+    if status != GLCM_OK:
+        msg = load().glcm_server_last_error(server)
+        raise GlcmError(status, msg.decode() if msg else "")
+    return status
+
+
+def glcm_server_create(device=0, hbm_budget_bytes=0, lanes=0, max_batch=0, max_queue=0):
+    out = c_void_p()
+    _check_server(None, load().glcm_server_create(ctypes.byref(out), int(device), int(hbm_budget_bytes),
+                                                  int(lanes), int(max_batch), int(max_queue)))
+    return out
+
+
+def glcm_server_submit(server, desc):
+    """Queue one request (a make_desc tuple with host pointers); returns its ticket."""
+    t = c_longlong()
+    d = desc[0] if isinstance(desc, tuple) else desc
+    _check_server(server, load().glcm_server_submit(server, ctypes.byref(d), ctypes.byref(t)))
+    return t.value
+
+
+def glcm_server_wait(server, ticket, timeout_ms=-1):
+    """(status, latency_ms); status GLCM_ERR_BUSY means still in flight.  A
+    failed request's status is returned, not raised."""
+    lat = c_double()
+    st = load().glcm_server_wait(server, int(ticket), int(timeout_ms), ctypes.byref(lat))
+    if st == GLCM_ERR_ARG:
+        _check_server(server, st)
+    return st, lat.value
+
+
+def glcm_server_stats(server):
+    st = glcm_server_stats_t()
+    _check_server(server, load().glcm_server_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in st._fields_}
+
+
+def glcm_server_last_error(server) -> str:
+    m = load().glcm_server_last_error(server)
+    return m.decode() if m else ""
+
+
+def glcm_server_destroy(server):
+    return load().glcm_server_destroy(server)
 
 
 def glcm_windows(ctx, image, width, height, pitch_bytes, dtype, levels, win, stride, offsets, flags,

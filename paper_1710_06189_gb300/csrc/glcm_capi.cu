@@ -1061,6 +1061,73 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
     return GLCM_OK;
 }
 
+
+// A device batch split by pixel type (the vote kernel is templated on it),
+// with its tables uploaded: p8's jobs, offsets and chunks first, then p16's.
+struct SplitBatch {
+    VotePlan p8, p16;
+    std::vector<FeatJob> feats;
+    int max_levels = 2;
+    DevBuf j16, o16;                       // views into the uploaded tables
+    const int3* c8 = nullptr;
+    const int3* c16 = nullptr;
+};
+
+int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, DevBuf& djobs, DevBuf& doffs,
+                  DevBuf& dfeat)
+{
+    VotePlan plan;
+    TRY(plan_batch(ctx, descs, n, plan, sb.feats, sb.max_levels));
+    for (int pass = 0; pass < 2; ++pass) {
+        VotePlan& dst = pass == 0 ? sb.p8 : sb.p16;
+        dst.threads = plan.threads;
+        dst.bpp = pass == 0 ? 1 : 2;
+        for (const VoteJob& j : plan.jobs) {
+            if (j.bpp != dst.bpp)
+                continue;
+            VoteJob c = j;
+            const int cnt_items = (c.n_strips) * ((c.y_end - c.y_begin + c.band_rows - 1) / c.band_rows);
+            c.off0 = (int)dst.offs.size();
+            for (int k = 0; k < j.n_off; ++k)
+                dst.offs.push_back(plan.offs[j.off0 + k]);
+            c.item0 = dst.n_items;
+            dst.n_items += cnt_items;
+            dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
+            if (c.staged)
+                dst.tile_rows = std::max(dst.tile_rows, c.band_rows + c.dy_max - c.dy_min);
+            dst.jobs.push_back(c);
+        }
+    }
+    VotePlan all;
+    all.jobs = sb.p8.jobs;
+    all.jobs.insert(all.jobs.end(), sb.p16.jobs.begin(), sb.p16.jobs.end());
+    for (size_t k = sb.p8.jobs.size(); k < all.jobs.size(); ++k)
+        all.jobs[k].off0 += (int)sb.p8.offs.size();
+    all.offs = sb.p8.offs;
+    all.offs.insert(all.offs.end(), sb.p16.offs.begin(), sb.p16.offs.end());
+    build_chunks(sb.p8, ctx->sm_count);
+    build_chunks(sb.p16, ctx->sm_count);
+    all.chunks = sb.p8.chunks;
+    all.chunks.insert(all.chunks.end(), sb.p16.chunks.begin(), sb.p16.chunks.end());
+    TRY(upload_tables(ctx, all, sb.feats, djobs, doffs, dfeat));
+    sb.j16.p = static_cast<VoteJob*>(djobs.p) + sb.p8.jobs.size();
+    sb.o16.p = doffs.p;  // p16's off0 are already shifted past p8's offsets
+    sb.c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(djobs.p) + all.chunk_off);
+    sb.c16 = sb.c8 + sb.p8.chunks.size();
+    return GLCM_OK;
+}
+
+// Enqueue a prepared batch: zero + vote per pixel type, then the epilogue.
+int enqueue_batch(glcm_ctx* ctx, const SplitBatch& sb, const DevBuf& djobs, const DevBuf& doffs, const DevBuf& dfeat,
+                  bool capturing, GraphEntry* ge)
+{
+    if (!sb.p8.jobs.empty())
+        TRY(enqueue_vote(ctx, sb.p8, djobs, doffs, sb.c8, true, capturing, ge));
+    if (!sb.p16.jobs.empty())
+        TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, capturing, ge));
+    return enqueue_features(ctx, sb.feats, dfeat, sb.max_levels, capturing, ge);
+}
+
 }  // namespace
 
 extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
@@ -1105,71 +1172,23 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
                 destroy_graph(kv.second);
             ctx->graphs.clear();
         }
-        VotePlan plan;
-        std::vector<FeatJob> feats;
-        int max_levels = 2;
-        TRY(plan_batch(ctx, descs, n, plan, feats, max_levels));
         GraphEntry ge;
-        // Split the plan by pixel type: the vote kernel is templated on it.
-        VotePlan p8, p16;
-        for (int pass = 0; pass < 2; ++pass) {
-            VotePlan& dst = pass == 0 ? p8 : p16;
-            dst.threads = plan.threads;
-            dst.bpp = pass == 0 ? 1 : 2;
-            for (const VoteJob& j : plan.jobs) {
-                if (j.bpp != dst.bpp)
-                    continue;
-                VoteJob c = j;
-                const int cnt_items = (c.n_strips) * ((c.y_end - c.y_begin + c.band_rows - 1) / c.band_rows);
-                c.off0 = (int)dst.offs.size();
-                for (int k = 0; k < j.n_off; ++k)
-                    dst.offs.push_back(plan.offs[j.off0 + k]);
-                c.item0 = dst.n_items;
-                dst.n_items += cnt_items;
-                dst.max_hist_words = std::max(dst.max_hist_words, c.hist_words);
-                if (c.staged)
-                    dst.tile_rows = std::max(dst.tile_rows, c.band_rows + c.dy_max - c.dy_min);
-                dst.jobs.push_back(c);
-            }
-        }
-        // Tables: one device buffer each, p8's entries then p16's.
-        VotePlan all;
-        all.jobs = p8.jobs;
-        all.jobs.insert(all.jobs.end(), p16.jobs.begin(), p16.jobs.end());
-        for (size_t k = p8.jobs.size(); k < all.jobs.size(); ++k)
-            all.jobs[k].off0 += (int)p8.offs.size();
-        all.offs = p8.offs;
-        all.offs.insert(all.offs.end(), p16.offs.begin(), p16.offs.end());
-        // Chunks: p8's then p16's, each indexing jobs of its own sub-table.
-        build_chunks(p8, ctx->sm_count);
-        build_chunks(p16, ctx->sm_count);
-        all.chunks = p8.chunks;
-        all.chunks.insert(all.chunks.end(), p16.chunks.begin(), p16.chunks.end());
-        TRY(upload_tables(ctx, all, feats, ge.jobs, ge.offs, ge.feat));
-        CK(cudaStreamSynchronize(ctx->stream));
-        DevBuf j16, o16;
-        j16.p = static_cast<VoteJob*>(ge.jobs.p) + p8.jobs.size();
-        o16.p = static_cast<VoteOffset*>(ge.offs.p);  // off0 already shifted
-        DevBuf j8 = ge.jobs;
-        const int3* c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(ge.jobs.p) + all.chunk_off);
-        const int3* c16 = c8 + p8.chunks.size();
+        SplitBatch sb;
         // One direct run produces this call's results and sets every kernel
         // attribute before capture.
-        if (!p8.jobs.empty())
-            TRY(enqueue_vote(ctx, p8, j8, ge.offs, c8, true, false, nullptr));
-        if (!p16.jobs.empty())
-            TRY(enqueue_vote(ctx, p16, j16, o16, c16, true, false, nullptr));
-        TRY(enqueue_features(ctx, feats, ge.feat, max_levels, false, nullptr));
-        TRY(collect_device_errors(ctx));
+        int rc0 = prepare_batch(ctx, descs, n, sb, ge.jobs, ge.offs, ge.feat);
+        if (rc0 == GLCM_OK)
+            rc0 = enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, false, nullptr);
+        if (rc0 == GLCM_OK)
+            rc0 = collect_device_errors(ctx);
+        if (rc0 != GLCM_OK) {
+            cudaStreamSynchronize(ctx->stream);
+            destroy_graph(ge);
+            return rc0;
+        }
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        int rc = GLCM_OK;
-        if (rc == GLCM_OK && !p8.jobs.empty())
-            rc = enqueue_vote(ctx, p8, j8, ge.offs, c8, true, true, &ge);
-        if (rc == GLCM_OK && !p16.jobs.empty())
-            rc = enqueue_vote(ctx, p16, j16, o16, c16, true, true, &ge);
-        if (rc == GLCM_OK)
-            rc = enqueue_features(ctx, feats, ge.feat, max_levels, true, &ge);
+        const int rc = enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, true, &ge);
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (rc != GLCM_OK) {
             if (graph)
@@ -1223,6 +1242,30 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
     if (ctx->own_stream)
         return collect_device_errors(ctx);
     return GLCM_OK;
+}
+
+extern "C" int glcm_enqueue_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    if (n < 0 || (n > 0 && !descs))
+        return fail(ctx, GLCM_ERR_ARG, "bad batch");
+    if (n == 0)
+        return GLCM_OK;
+    for (int i = 0; i < n; ++i) {
+        const glcm_desc& d = descs[i];
+        TRY(check_image_args(ctx, d.image, d.width, d.height, d.pitch_bytes, d.dtype, d.levels, d.offsets,
+                             d.n_offsets));
+        if (!d.counts)
+            return fail(ctx, GLCM_ERR_ARG, "desc %d: counts is NULL", i);
+        if (!is_device_ptr(d.image) || !is_device_ptr(d.counts) || (d.normalized && !is_device_ptr(d.normalized)) ||
+            (d.features && !is_device_ptr(d.features)))
+            return fail(ctx, GLCM_ERR_ARG, "desc %d: glcm_enqueue_batch takes device pointers only", i);
+    }
+    SplitBatch sb;
+    TRY(prepare_batch(ctx, descs, n, sb, ctx->jobs, ctx->offs, ctx->feat));
+    return enqueue_batch(ctx, sb, ctx->jobs, ctx->offs, ctx->feat, false, nullptr);
 }
 
 extern "C" int glcm_windows(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes, int dtype,
