@@ -27,6 +27,12 @@
 //    of A' is found by Golub-Kahan-Lanczos bidiagonalization with full
 //    reorthogonalization in float32, stopped when its top Ritz value
 //    settles (exact after min(rows, cols) steps).
+//  * Symmetric GLCMs with N > 128 (A' symmetric, too large for shared
+//    memory as a full matrix) keep A' as its upper 32 x 32 blocks in shared
+//    memory and find max |eigenvalue| of A' -- its largest singular value --
+//    by symmetric Lanczos without reorthogonalization: in finite precision
+//    the extreme Ritz values still converge (lost orthogonality only adds
+//    copies of converged values), so no basis has to be stored.
 #include <cmath>
 
 #include "glcm_internal.cuh"
@@ -42,6 +48,13 @@ constexpr int kMaxLanczos = 96;
 constexpr int kSmemAFloats = 128 * 128;
 constexpr int kSmemUVFloats = (2 * kMaxLanczos + 1) * 128;
 constexpr int kColGroups = 4;
+// Blocked symmetric path: N <= kBigN, 32 x 32 blocks padded to 33 columns.
+constexpr int kBigN = 256;
+constexpr int kBigNB = kBigN / 32;
+constexpr int kBigTiles = kBigNB * (kBigNB + 1) / 2;
+constexpr int kTileFloats = 32 * 33;
+constexpr int kMaxSymSteps = 384;
+constexpr int kMaxLevelsPerLane = 256 / 32;  // N <= 256
 
 struct DF {  // float value hi + lo (unevaluated sum)
     float hi, lo;
@@ -441,9 +454,322 @@ __device__ float lanczos_sigma_max(const float* A, int m, int n, const LanczosWo
     return *w.sig;
 }
 
+// ---- Blocked symmetric path (symmetric GLCMs with 128 < N <= 256) ----------
+//
+// A' is kept as its upper 32 x 32 blocks (I <= J), each padded to 33 columns
+// so that a lane can walk either a row or a column of a block without bank
+// conflicts.  Levels outside the support give zero rows and columns of A',
+// which only add zero eigenvalues.
+
+// (I, J) of upper block t in row-major order of the upper triangle.
+__device__ __forceinline__ void tile_of(int t, int nb, int& I, int& J)
+{
+    I = 0;
+    while (t >= nb - I) {
+        t -= nb - I;
+        ++I;
+    }
+    J = I + t;
+}
+
+__device__ __forceinline__ int tile_index(int I, int J, int nb)
+{
+    return I * nb - I * (I - 1) / 2 + (J - I);
+}
+
+// Cell pass of a symmetric GLCM: S = P + P^T staged block by block (both
+// global reads coalesced), the cell sums (an off-diagonal block stands for
+// itself and its mirror image, whose terms are equal, so they count twice),
+// the normalized output, and A' written over each staged block.
+// Requires T < 2^32 so that every S entry fits 32 bits.
+__device__ void sym_cell_pass(const FeatJob& J, int N, unsigned long long T, const unsigned long long* rs,
+                              const unsigned long long* cs, double mux, double muy, float* blk, Kahan& k_asm,
+                              Kahan& k_ent, Kahan& k_mi, double& cov)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nb = (N + 31) >> 5;
+    const int ntiles = nb * (nb + 1) / 2;
+    const uint32_t* C = J.counts;
+    const float Tf = (float)T;
+    for (int t = warp; t < ntiles; t += nw) {
+        int I, Jb;
+        tile_of(t, nb, I, Jb);
+        uint32_t* Bu = reinterpret_cast<uint32_t*>(blk + (size_t)t * kTileFloats);
+        float* Bf = blk + (size_t)t * kTileFloats;
+        const int jc = Jb * 32 + lane;
+        const int ic = I * 32 + lane;
+        // Block (I, Jb) of P first (all 32 rows), then block (Jb, I) added
+        // transposed; 16 loads in flight per batch.
+        for (int r0 = 0; r0 < 32; r0 += 16) {
+            uint32_t va[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                const int i = I * 32 + r0 + u;
+                va[u] = (i < N && jc < N) ? __ldg(C + (size_t)i * N + jc) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                Bu[(r0 + u) * 33 + lane] = va[u];
+        }
+        __syncwarp();
+        for (int r0 = 0; r0 < 32; r0 += 16) {
+            uint32_t vb[16];
+#pragma unroll
+            for (int u = 0; u < 16; ++u) {
+                // Row Jb*32 + r of P, column I*32 + lane: P(j, i) for S(i, j).
+                const int iT = Jb * 32 + r0 + u;
+                vb[u] = (iT < N && ic < N) ? __ldg(C + (size_t)iT * N + ic) : 0u;
+            }
+#pragma unroll
+            for (int u = 0; u < 16; ++u)
+                Bu[lane * 33 + r0 + u] += vb[u];
+        }
+        __syncwarp();
+        const bool twice = I != Jb;
+        for (int r = 0; r < 32; ++r) {
+            const int i = I * 32 + r;
+            float a = 0.f;
+            if (i < N && jc < N) {
+                const unsigned long long sv = Bu[r * 33 + lane];
+                const float pv = __fdiv_rn((float)sv, Tf);
+                if (J.normalized) {
+                    J.normalized[(size_t)i * N + jc] = pv;
+                    if (twice)
+                        J.normalized[(size_t)jc * N + i] = pv;
+                }
+                if (sv) {
+                    const float t1 = __fmul_rn(pv, pv), t2 = neg_plogp(pv);
+                    const double tc = ((double)i - mux) * ((double)jc - muy) * (double)sv;
+                    k_asm.add(twice ? 2.f * t1 : t1);
+                    k_ent.add(twice ? 2.f * t2 : t2);
+                    cov += twice ? 2.0 * tc : tc;
+                }
+                const unsigned long long ri = rs[i], cj = cs[jc];
+                if (ri && cj) {
+                    const float rc = __fmul_rn((float)ri, (float)cj);
+                    float numf;
+                    if (T < (1ull << 31))
+                        numf = (float)((long long)(sv * T) - (long long)(ri * cj));
+                    else
+                        numf = __fsub_rn(__fmul_rn((float)sv, Tf), rc);
+                    const float x = __fdiv_rn(numf, rc);
+                    const float q = __fmul_rn(__fdiv_rn((float)ri, Tf), __fdiv_rn((float)cj, Tf));
+                    const float tm = __fmul_rn(q, phi(x));
+                    k_mi.add(twice ? 2.f * tm : tm);
+                    a = __fdiv_rn(numf, __fmul_rn(Tf, sqrtf(rc)));
+                }
+            }
+            Bf[r * 33 + lane] = a;
+        }
+    }
+    __syncthreads();
+}
+
+// y = A' x over the blocked upper triangle (x, y: nb * 32 floats).  Block
+// (I, J) gives B x_J to y_I and, off the diagonal, B^T x_I to y_J; the
+// pieces are summed per element in a fixed order (deterministic).
+__device__ void sym_block_matvec(const float* blk, int nb, const float* x, float* y, float* bpart)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int ntiles = nb * (nb + 1) / 2;
+    for (int t = warp; t < ntiles; t += nw) {
+        int I, Jb;
+        tile_of(t, nb, I, Jb);
+        const float* B = blk + (size_t)t * kTileFloats;
+        const float* xJ = x + Jb * 32;
+        const float* xI = x + I * 32;
+        float r0 = 0.f, r1 = 0.f, c0 = 0.f, c1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; k += 4) {
+            // Vector entries as broadcast float4 loads; block rows and
+            // columns as conflict-free scalar loads.
+            const float4 vj = *reinterpret_cast<const float4*>(xJ + k);
+            const float4 vi = *reinterpret_cast<const float4*>(xI + k);
+            r0 = fmaf(B[lane * 33 + k], vj.x, r0);
+            r1 = fmaf(B[lane * 33 + k + 1], vj.y, r1);
+            r0 = fmaf(B[lane * 33 + k + 2], vj.z, r0);
+            r1 = fmaf(B[lane * 33 + k + 3], vj.w, r1);
+            c0 = fmaf(B[k * 33 + lane], vi.x, c0);
+            c1 = fmaf(B[(k + 1) * 33 + lane], vi.y, c1);
+            c0 = fmaf(B[(k + 2) * 33 + lane], vi.z, c0);
+            c1 = fmaf(B[(k + 3) * 33 + lane], vi.w, c1);
+        }
+        bpart[t * 32 + lane] = r0 + r1;
+        bpart[(kBigTiles + t) * 32 + lane] = c0 + c1;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nb * 32; e += blockDim.x) {
+        const int I = e >> 5, l = e & 31;
+        float acc = 0.f;
+        for (int Jb = 0; Jb < nb; ++Jb)
+            acc += Jb >= I ? bpart[tile_index(I, Jb, nb) * 32 + l]
+                           : bpart[(kBigTiles + tile_index(Jb, I, nb)) * 32 + l];
+        y[e] = acc;
+    }
+    __syncthreads();
+}
+
+// Eigenvalues below x of the L x L symmetric tridiagonal matrix with
+// diagonal al[] and off-diagonal be[] (Sturm sequence).
+__device__ __forceinline__ int tri_count_below(const float* al, const float* be, int L, float x)
+{
+    int cnt = 0;
+    float d = al[0] - x;
+    if (d < 0.f)
+        ++cnt;
+    for (int t = 1; t < L; ++t) {
+        if (d == 0.f)
+            d = -1e-30f;
+        d = (al[t] - x) - __fdividef(be[t - 1] * be[t - 1], d);
+        if (d < 0.f)
+            ++cnt;
+    }
+    return cnt;
+}
+
+// One end of the spectrum of that tridiagonal matrix (upper: the largest
+// eigenvalue, else the smallest), by 32-way multisection of its Gershgorin
+// interval (one whole warp).
+__device__ float tri_extreme_warp(const float* al, const float* be, int L, bool upper)
+{
+    const int lane = threadIdx.x & 31;
+    if (L <= 0)
+        return 0.f;
+    float lo = 3.4e38f, hi = -3.4e38f;
+    for (int t = lane; t < L; t += 32) {
+        const float b0 = t > 0 ? fabsf(be[t - 1]) : 0.f, b1 = t + 1 < L ? fabsf(be[t]) : 0.f;
+        lo = fminf(lo, al[t] - b0 - b1);
+        hi = fmaxf(hi, al[t] + b0 + b1);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    float a = lo, b = hi;
+    for (int round = 0; round < 10 && b - a > 1e-7f * fmaxf(fabsf(a), fabsf(b)); ++round) {
+        const float x = a + (b - a) * (float)(lane + 1) / 33.f;
+        const int below = tri_count_below(al, be, L, x);
+        if (upper) {
+            const unsigned m = __ballot_sync(0xffffffffu, below >= L);
+            const int first = m ? __ffs(m) - 1 : 32;  // first point above every eigenvalue
+            const float na = first == 0 ? a : a + (b - a) * (float)first / 33.f;
+            const float nb = first == 32 ? b : a + (b - a) * (float)(first + 1) / 33.f;
+            a = na;
+            b = nb;
+        } else {
+            const unsigned m = __ballot_sync(0xffffffffu, below == 0);
+            const int last = m ? 31 - __clz(m) : -1;  // last point below every eigenvalue
+            const float na = last < 0 ? a : a + (b - a) * (float)(last + 1) / 33.f;
+            const float nb = last == 31 ? b : a + (b - a) * (float)(last + 2) / 33.f;
+            a = na;
+            b = nb;
+        }
+    }
+    return 0.5f * (a + b);
+}
+
+// max(|lambda_max|, |lambda_min|) of the tridiagonal matrix: warps 0 and 1
+// search the two ends at once; the result is in *out after the call (every
+// thread of the block must call).
+__device__ void tri_absmax_block(const float* al, const float* be, int L, float* ends, float* out)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 2) {
+        const float e = tri_extreme_warp(al, be, L, warp == 0);
+        if (lane == 0)
+            ends[warp] = e;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        *out = fmaxf(fabsf(ends[0]), fabsf(ends[1]));
+    __syncthreads();
+}
+
+// Largest |eigenvalue| of the blocked symmetric A' (N levels) by Lanczos
+// without reorthogonalization; stops once the estimate moved by less than
+// 4e-7 of itself over 8 steps (after at least 16) or after kMaxSymSteps.
+__device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* tri, float* bpart, float* s_red,
+                                    float* s_sig, int* s_stop)
+{
+    const int nb = (N + 31) >> 5, n = nb * 32;
+    float* q = qv;
+    float* qp = qv + kBigN;
+    float* y = qv + 2 * kBigN;
+    float* al = tri;
+    float* be = tri + kMaxSymSteps;
+    float* ends = tri + 2 * kMaxSymSteps;  // 3 floats
+    for (int c = threadIdx.x; c < n; c += blockDim.x) {
+        // Fixed zero-mean pseudo-random start (multiplicative hash of c): a
+        // near-constant start would be almost orthogonal to the top
+        // eigenvectors of a deflated A' and could stall on a lower one.
+        const unsigned h = (unsigned)c * 2654435761u + 12345u;
+        q[c] = c < N ? (float)h * 2.3283064e-10f - 0.5f : 0.f;
+        qp[c] = 0.f;
+    }
+    if (threadIdx.x == 0) {
+        *s_sig = -1.f;
+        *s_stop = 0;
+    }
+    float ss = 0.f;
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        ss = fmaf(q[c], q[c], ss);
+    const float inv = rsqrtf(block_sum(ss, s_red));
+    for (int c = threadIdx.x; c < n; c += blockDim.x)
+        q[c] *= inv;
+    __syncthreads();
+    float beta = 0.f;
+    int L = 0;
+    for (int k = 0; k < kMaxSymSteps; ++k) {
+        sym_block_matvec(blk, nb, q, y, bpart);
+        float d = 0.f;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const float w = fmaf(-beta, qp[c], y[c]);
+            y[c] = w;
+            d = fmaf(w, q[c], d);
+        }
+        const float alpha = block_sum(d, s_red);
+        float s2 = 0.f;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            const float w = fmaf(-alpha, q[c], y[c]);
+            y[c] = w;
+            s2 = fmaf(w, w, s2);
+        }
+        const float bn = sqrtf(block_sum(s2, s_red));
+        if (threadIdx.x == 0) {
+            al[k] = alpha;
+            be[k] = bn;
+        }
+        L = k + 1;
+        if (!(bn > 1e-30f))
+            break;  // invariant subspace: the tridiagonal matrix is exact
+        const float ib = 1.f / bn;
+        for (int c = threadIdx.x; c < n; c += blockDim.x) {
+            qp[c] = q[c];
+            q[c] = y[c] * ib;
+        }
+        beta = bn;
+        __syncthreads();
+        if ((L & 7) == 0 && L >= 16) {
+            tri_absmax_block(al, be, L, ends, ends + 2);
+            if (threadIdx.x == 0) {
+                *s_stop = fabsf(ends[2] - *s_sig) <= 4e-7f * ends[2] ? 1 : 0;
+                *s_sig = ends[2];
+            }
+            __syncthreads();
+            if (*s_stop)
+                break;
+        }
+    }
+    __syncthreads();
+    tri_absmax_block(al, be, L, ends, ends + 2);
+    return ends[2];
+}
+
 // Dynamic shared memory layout for a launch whose largest N is `N`.
 struct FeatLayout {
     size_t marg, maps, dscr, dd, xs, ys, part, a, uv, total;
+    // Blocked symmetric path (N > 128), overlapping a and uv.
+    size_t blk, bpart, qv, tri;
 };
 
 __host__ __device__ inline FeatLayout feat_layout(int N)
@@ -465,8 +791,20 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     L.xs = take((size_t)N * 4);
     L.ys = take((size_t)N * 4);
     L.part = take((size_t)kColGroups * 256 * 4);
+    const size_t u0 = o;
     L.a = take((size_t)(nn < kSmemAFloats ? nn : kSmemAFloats) * 4);
     L.uv = take((size_t)(uv < kSmemUVFloats ? uv : kSmemUVFloats) * 4);
+    const size_t u1 = o;
+    L.blk = L.bpart = L.qv = L.tri = 0;
+    if (N > 128) {
+        o = u0;
+        const int nb = (N + 31) / 32;
+        L.blk = take((size_t)nb * (nb + 1) / 2 * kTileFloats * 4);
+        L.bpart = take((size_t)2 * kBigTiles * 32 * 4);
+        L.qv = take((size_t)3 * kBigN * 4);
+        L.tri = take((size_t)(2 * kMaxSymSteps + 4) * 4);
+        o = o > u1 ? o : u1;
+    }
     L.total = o;
     return L;
 }
@@ -497,12 +835,24 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     for (int k = threadIdx.x; k < 5 * N; k += blockDim.x)
         rs[k] = 0ull;
     __syncthreads();
-    // Exact integer marginals.  Warp w takes rows w, w + nwarps, ...; the row
-    // sum is a warp reduction, the other marginals shared atomics.
+    // Exact integer marginals of P.  Warp w takes rows w, w + nwarps, ...; the
+    // row sum is a warp reduction, the other marginals shared atomics.  For
+    // S = P + P^T they follow from P's without reading P^T: the row (= column)
+    // sums of S are P's row plus column sums, and the i+j and |i-j| sums of S
+    // are twice P's.
     for (int i = warp; i < N; i += blockDim.x >> 5) {
+        // All of the row's loads are issued before the first atomic.
+        uint32_t v[kMaxLevelsPerLane];
+#pragma unroll
+        for (int u = 0; u < kMaxLevelsPerLane; ++u) {
+            const int j = lane + 32 * u;
+            v[u] = j < N ? __ldg(C + i * N + j) : 0u;
+        }
         unsigned long long rsum = 0;
-        for (int j = lane; j < N; j += 32) {
-            const unsigned long long s = cell(C, N, i, j, sym);
+#pragma unroll
+        for (int u = 0; u < kMaxLevelsPerLane; ++u) {
+            const int j = lane + 32 * u;
+            const unsigned long long s = v[u];
             if (s) {
                 rsum += s;
                 atomicAdd(&cs[j], s);
@@ -516,6 +866,18 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
             rs[i] = rsum;
     }
     __syncthreads();
+    if (sym) {
+        for (int k = threadIdx.x; k < 2 * N - 1; k += blockDim.x) {
+            if (k < N) {
+                const unsigned long long t = rs[k] + cs[k];
+                rs[k] = t;
+                cs[k] = t;
+                ds[k] *= 2ull;
+            }
+            ss[k] *= 2ull;
+        }
+        __syncthreads();
+    }
     // Totals, integer moments and the support maps (warp 0).
     if (warp == 0) {
         unsigned long long T = 0, m_i = 0, m_j = 0, c2 = 0, m_s = 0, m_d = 0;
@@ -583,6 +945,9 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     const double mux = (double)s_m[0] / Td, muy = (double)s_m[1] / Td;
     const int nr = s_nr, nc = s_nc;
     const int K = min(kMaxLanczos, min(nr, nc));
+    // Symmetric GLCMs too large for a full A' in shared memory take the
+    // blocked path (every S entry < 2^32 when T < 2^32).
+    const bool big_sym = sym && N > 128 && N <= kBigN && maxN > 128 && T < (1ull << 32);
     // A' and the Lanczos vectors: shared memory when they fit, else scratch.
     float* gwork = p.work ? p.work + (long long)blockIdx.x * p.work_stride : nullptr;
     const bool a_smem = (long long)nr * nc <= kSmemAFloats && (long long)nr * nc <= (long long)maxN * maxN;
@@ -592,12 +957,15 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     float* A = a_smem ? reinterpret_cast<float*>(smem_raw + Lo.a) : gwork;
     float* UV = uv_smem ? reinterpret_cast<float*>(smem_raw + Lo.uv)
                         : (gwork ? gwork + (long long)maxN * maxN : nullptr);
-    const bool have_work = A != nullptr && UV != nullptr;
+    const bool have_work = big_sym || (A != nullptr && UV != nullptr);
+    float* blk = reinterpret_cast<float*>(smem_raw + Lo.blk);
 
     // Cell pass: normalized output, f1, f9, MI terms, covariance, A'.
     Kahan k_asm, k_ent, k_mi;
     double cov = 0.0;
-    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
+    if (big_sym)
+        sym_cell_pass(J, N, T, rs, cs, mux, muy, blk, k_asm, k_ent, k_mi, cov);
+    for (int t = threadIdx.x; !big_sym && t < NN; t += blockDim.x) {
         const int i = t / N, j = t - (t / N) * N;
         const unsigned long long s = cell(C, N, i, j, sym);
         const float pv = __fdiv_rn((float)s, Tf);
@@ -656,7 +1024,11 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     block_reduce_d<3>(dv, dd);
 
     float mcc = 0.f;
-    if (nr >= 2 && have_work) {
+    if (big_sym && nr >= 2) {
+        mcc = sym_lanczos_absmax(blk, N, reinterpret_cast<float*>(smem_raw + Lo.qv),
+                                 reinterpret_cast<float*>(smem_raw + Lo.tri),
+                                 reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop);
+    } else if (nr >= 2 && have_work) {
         LanczosWork w;
         w.xs = reinterpret_cast<float*>(smem_raw + Lo.xs);
         w.ys = reinterpret_cast<float*>(smem_raw + Lo.ys);

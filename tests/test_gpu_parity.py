@@ -132,6 +132,24 @@ def test_normalize_and_features(gctx, sym, n):
     assert_features(feats.cpu().numpy(), oracle.haralick_batch(P, sym), n, what=f"n={n} sym={sym}")
 
 
+@pytest.mark.parametrize("n", [129, 160, 200, 255, 256])
+def test_symmetric_features_large_levels(gctx, n):
+    """Symmetric GLCMs with N > 128: A' kept blockwise, symmetric Lanczos."""
+    imgs = [S.iid(n, 300, 700, np.uint8), S.smooth(n + 1, 300, 700, 2.0, np.uint8),
+            S.smooth(n + 2, 300, 700, 8.0, np.uint8), (S.iid(n + 3, 200, 300, np.uint8) & 0xF0),
+            (np.indices((64, 96)).sum(0) % 2 * 255).astype(np.uint8),   # checkerboard: f14 = 1
+            S.iid(n + 4, 2, 2, np.uint8), S.constant(50, 60)]
+    offs = [(1, 0), (1, -1), (0, -1), (-1, -1), (3, -3)]
+    for k, img in enumerate(imgs):
+        counts, norm = gctx.compute(dev(img), n, offs, G.GLCM_SYMMETRIC, normalized=True)
+        feats = gctx.features(counts, n, symmetric=True)
+        torch.cuda.synchronize()
+        P = oracle.glcm(img, n, offs)
+        assert np.array_equal(to_u32(counts), P)
+        assert_normalized(norm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)), f"n={n} img={k}")
+        assert_features(feats.cpu().numpy(), oracle.haralick_batch(P, True), n, what=f"n={n} img={k}")
+
+
 def test_features_of_special_matrices(gctx):
     n = 16
     mats = np.zeros((5, n, n), dtype=np.uint32)
