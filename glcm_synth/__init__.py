@@ -120,16 +120,18 @@ def contention_jobs(side: int = 4096, levels=CONTENTION_LEVELS, kinds=CONTENTION
     return jobs
 
 
+def multispectral_band(b: int, side: int = 8192, n_bands: int = 8, sigma: float = 16.0) -> np.ndarray:
+    """Band b of the multispectral stack: iid over 0..65535 for the first
+    half of the bands, smooth (sigma px) for the rest."""
+    seed = BASE_SEED + 200 + b
+    if b < n_bands // 2:
+        return iid(seed, side, side, np.uint16)
+    return smooth(seed, side, side, sigma, np.uint16)
+
+
 def multispectral_bands(side: int = 8192, n_bands: int = 8, sigma: float = 16.0):
     """8 uint16 bands: 0-3 iid over 0..65535, 4-7 smooth (sigma px)."""
-    bands = []
-    for b in range(n_bands):
-        seed = BASE_SEED + 200 + b
-        if b < n_bands // 2:
-            bands.append(iid(seed, side, side, np.uint16))
-        else:
-            bands.append(smooth(seed, side, side, sigma, np.uint16))
-    return bands
+    return [multispectral_band(b, side, n_bands, sigma) for b in range(n_bands)]
 
 
 MULTISPECTRAL_OFFSETS = offsets_for((1, 2, 4))

@@ -158,7 +158,11 @@ int glcm_features(glcm_ctx *ctx, const uint32_t *counts, int levels, int n_glcm,
  * sizes and flags) comes again.  Per desc: counts always, normalized if
  * non-NULL (GLCM_NORMALIZE implied), features if non-NULL.  Each desc's
  * results equal those of a glcm_compute + glcm_features on that image alone.
- * All image pointers must be device pointers or all host pointers.
+ * Host images (and host results) may be mixed with device ones: host images
+ * are copied once into device staging on a side stream in groups of about
+ * equal bytes, each group's votes starting as soon as its copies are in
+ * (Sec. III's overlap of copies with earlier votes); the call then returns
+ * after the host results are written.
  * Errors: as glcm_compute, per the first failing desc. */
 int glcm_compute_batch(glcm_ctx *ctx, const glcm_desc *descs, int n);
 

@@ -2,6 +2,7 @@
 // work planning, the host-image stripe pipeline (Sec. III, Eqs. 7-9), batch
 // launches with a CUDA-graph cache, and kernel timing.
 #include <algorithm>
+#include <array>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
@@ -42,6 +43,7 @@ struct GraphEntry {
     cudaGraphNode_t ev_start = nullptr, ev_stop = nullptr;
     cudaEvent_t cap_a = nullptr, cap_b = nullptr;  // events recorded at capture
     DevBuf jobs, offs, feat;
+    DevBuf jobs2, offs2, feat2;  // second part of a split batch
     int n_vote_kernels = 0;
     int n_kernels = 0;
 };
@@ -57,6 +59,7 @@ struct VotePlan {
     int tile_rows = 0;  // max staged tile rows over the plan's jobs
     int threads = 0;    // max over the plan's jobs
     int bpp = 1;
+    int max_ctas = 0;   // grid cap (0: every SM), leaves SMs to a concurrent kernel
 };
 
 }  // namespace
@@ -66,10 +69,14 @@ struct glcm_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;
+    cudaStream_t side_stream = nullptr;  // epilogues overlapped with votes in split batches
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
     unsigned* d_words = nullptr;  // [0] error bits, [1] work-item counter
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
+    DevBuf hb_img, hb_out;        // host-buffer batches: staged images, device results
+    std::vector<std::array<DevBuf, 3>> hb_tab;  // host-buffer batches: tables per group
     void* h_stage = nullptr;      // pinned table staging
     size_t h_stage_cap = 0;
     cudaEvent_t ev_stage = nullptr;
@@ -137,6 +144,8 @@ int ensure(glcm_ctx* ctx, DevBuf& b, size_t bytes)
     }
     if (b.p) {
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->side_stream)
+            cudaStreamSynchronize(ctx->side_stream);
         cudaFree(b.p);
         ctx->used -= b.cap;
         b.p = nullptr;
@@ -451,7 +460,10 @@ int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 {
     const size_t smem = vote_smem(plan);
     const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem));
-    return std::max(1, std::min((int)plan.chunks.size(), ctx->sm_count * per_sm));
+    int ctas = ctx->sm_count * per_sm;
+    if (plan.max_ctas > 0)
+        ctas = std::min(ctas, plan.max_ctas * per_sm);
+    return std::max(1, std::min((int)plan.chunks.size(), ctas));
 }
 
 // Split every job of a plan into chunks of chunk_items consecutive items,
@@ -531,19 +543,21 @@ TimedPair take_pair(glcm_ctx* ctx)
 
 // Enqueue zero (optional) + vote for a plan whose tables are at djobs/doffs.
 int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, const int3* dchunks,
-                 bool zero, bool capturing, GraphEntry* ge)
+                 bool zero, bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
 {
     if (plan.jobs.empty())
         return GLCM_OK;
+    if (!st)
+        st = ctx->stream;
     if (zero) {
-        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, ctx->stream>>>(
-            static_cast<const VoteJob*>(djobs.p), static_cast<const VoteOffset*>(doffs.p));
+        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, st>>>(static_cast<const VoteJob*>(djobs.p),
+                                                                   static_cast<const VoteOffset*>(doffs.p));
         CK(cudaGetLastError());
         ctx->kernel_launches += capturing ? 0 : 1;
         if (ge)
             ge->n_kernels++;
     }
-    CK(cudaMemsetAsync(ctx->d_words + 1, 0, sizeof(unsigned), ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_words + 1, 0, sizeof(unsigned), st));
     VoteParams vp{};
     vp.jobs = static_cast<const VoteJob*>(djobs.p);
     vp.n_jobs = (int)plan.jobs.size();
@@ -561,23 +575,13 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     const bool time_it = ctx->timing && !capturing;
     if (time_it) {
         tp = take_pair(ctx);
-        CK(cudaEventRecord(tp.a, ctx->stream));
+        CK(cudaEventRecord(tp.a, st));
     }
-    if (capturing && ge && ctx->timing) {
-        // Capture-time events; the graph's event nodes are re-pointed per replay.
-        if (!ge->cap_a) {
-            CK(cudaEventCreate(&ge->cap_a));
-            CK(cudaEventCreate(&ge->cap_b));
-        }
-        CK(cudaEventRecordWithFlags(ge->cap_a, ctx->stream, cudaEventRecordExternal));
-    }
-    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, ctx->stream));
+    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st));
     if (time_it) {
-        CK(cudaEventRecord(tp.b, ctx->stream));
+        CK(cudaEventRecord(tp.b, st));
         ctx->pending.push_back(tp);
     }
-    if (capturing && ge && ctx->timing)
-        CK(cudaEventRecordWithFlags(ge->cap_b, ctx->stream, cudaEventRecordExternal));
     if (!capturing) {
         ctx->kernel_launches += 1;
         ctx->vote_launches += 1;
@@ -589,11 +593,27 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     return GLCM_OK;
 }
 
+// Capture-time timing events around a graph's vote kernels; the graph's
+// event nodes are re-pointed per replay.
+int capture_mark(glcm_ctx* ctx, GraphEntry* ge, bool start)
+{
+    if (!ge || !ctx->timing)
+        return GLCM_OK;
+    if (!ge->cap_a) {
+        CK(cudaEventCreate(&ge->cap_a));
+        CK(cudaEventCreate(&ge->cap_b));
+    }
+    CK(cudaEventRecordWithFlags(start ? ge->cap_a : ge->cap_b, ctx->stream, cudaEventRecordExternal));
+    return GLCM_OK;
+}
+
 int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const DevBuf& dfeat, int max_levels,
-                     bool capturing, GraphEntry* ge)
+                     bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
 {
     if (feats.empty())
         return GLCM_OK;
+    if (!st)
+        st = ctx->stream;
     FeatParams fp{};
     fp.jobs = static_cast<const FeatJob*>(dfeat.p);
     fp.n_jobs = (int)feats.size();
@@ -609,7 +629,7 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
             fp.work_stride = per;
         }
     }
-    CK(launch_features(fp, max_levels, ctx->stream));
+    CK(launch_features(fp, max_levels, st));
     if (!capturing)
         ctx->kernel_launches += 1;
     if (ge)
@@ -695,7 +715,7 @@ void destroy_graph(GraphEntry& g)
         cudaEventDestroy(g.cap_a);
     if (g.cap_b)
         cudaEventDestroy(g.cap_b);
-    for (DevBuf* b : {&g.jobs, &g.offs, &g.feat})
+    for (DevBuf* b : {&g.jobs, &g.offs, &g.feat, &g.jobs2, &g.offs2, &g.feat2})
         if (b->p)
             cudaFree(b->p);
 }
@@ -752,6 +772,9 @@ extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, 
         ctx->own_stream = true;
     }
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
         glcm_destroy(ctx);
         return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
@@ -777,12 +800,18 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaStreamSynchronize(ctx->stream);
     if (ctx->copy_stream)
         cudaStreamSynchronize(ctx->copy_stream);
+    if (ctx->side_stream)
+        cudaStreamSynchronize(ctx->side_stream);
     for (auto& kv : ctx->graphs)
         destroy_graph(kv.second);
     for (DevBuf* b : {&ctx->jobs, &ctx->offs, &ctx->feat, &ctx->work, &ctx->img, &ctx->counts, &ctx->norm,
-                      &ctx->featout, &ctx->maps})
+                      &ctx->featout, &ctx->maps, &ctx->hb_img, &ctx->hb_out})
         if (b->p)
             cudaFree(b->p);
+    for (auto& t : ctx->hb_tab)
+        for (DevBuf& b : t)
+            if (b.p)
+                cudaFree(b.p);
     if (ctx->d_words)
         cudaFree(ctx->d_words);
     if (ctx->h_stage)
@@ -801,6 +830,12 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaEventDestroy(ctx->ev_stage);
     if (ctx->copy_stream)
         cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->side_stream)
+        cudaStreamDestroy(ctx->side_stream);
+    if (ctx->ev_fork)
+        cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join)
+        cudaEventDestroy(ctx->ev_join);
     if (ctx->own_stream && ctx->stream)
         cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1121,11 +1156,197 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
 int enqueue_batch(glcm_ctx* ctx, const SplitBatch& sb, const DevBuf& djobs, const DevBuf& doffs, const DevBuf& dfeat,
                   bool capturing, GraphEntry* ge)
 {
+    if (capturing)
+        TRY(capture_mark(ctx, ge, true));
     if (!sb.p8.jobs.empty())
         TRY(enqueue_vote(ctx, sb.p8, djobs, doffs, sb.c8, true, capturing, ge));
     if (!sb.p16.jobs.empty())
         TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, capturing, ge));
+    if (capturing)
+        TRY(capture_mark(ctx, ge, false));
     return enqueue_features(ctx, sb.feats, dfeat, sb.max_levels, capturing, ge);
+}
+
+// A batch split in two: the images whose epilogue is expensive (features of
+// N > 64) vote first; their epilogue then runs on the side stream on a few
+// SMs while the rest of the batch votes on the others, and the rest's
+// epilogue follows.
+int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, SplitBatch& r, const DevBuf* tr,
+                        bool capturing, GraphEntry* ge)
+{
+    if (capturing)
+        TRY(capture_mark(ctx, ge, true));
+    if (!h.p8.jobs.empty())
+        TRY(enqueue_vote(ctx, h.p8, th[0], th[1], h.c8, true, capturing, ge));
+    if (!h.p16.jobs.empty())
+        TRY(enqueue_vote(ctx, h.p16, h.j16, h.o16, h.c16, true, capturing, ge));
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
+    TRY(enqueue_features(ctx, h.feats, th[2], h.max_levels, capturing, ge, ctx->side_stream));
+    const int reserve = std::min((int)h.feats.size(), ctx->sm_count / 4);
+    r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - reserve);
+    if (!r.p8.jobs.empty())
+        TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge));
+    if (!r.p16.jobs.empty())
+        TRY(enqueue_vote(ctx, r.p16, r.j16, r.o16, r.c16, true, capturing, ge));
+    if (capturing)
+        TRY(capture_mark(ctx, ge, false));
+    TRY(enqueue_features(ctx, r.feats, tr[2], r.max_levels, capturing, ge));
+    CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    return GLCM_OK;
+}
+
+// A batch with host buffers.  Every host image is copied once into device
+// staging on the copy stream, in groups of about equal bytes; each group's
+// votes start as soon as its own copies are in, so the copies of later
+// groups overlap the votes of earlier ones (the paper overlaps the copies of
+// image parts with the votes of earlier parts over streams, Sec. III).
+// Images with expensive epilogues (features of N > 64) come first, and their
+// groups' epilogues run on the side stream on a few SMs reserved from the
+// votes.  Results come back to the host buffers once, at the end.
+int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
+{
+    std::vector<glcm_desc> descs;
+    descs.reserve(n);
+    int n_heavy_glcm = 0;
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i = 0; i < n; ++i) {
+            const bool heavy = descs_in[i].features && descs_in[i].levels > 64;
+            if (heavy == (pass == 0)) {
+                descs.push_back(descs_in[i]);
+                n_heavy_glcm += heavy ? descs_in[i].n_offsets : 0;
+            }
+        }
+    std::vector<glcm_desc> dd(descs);
+    std::vector<size_t> img_off(n), dpitch(n);
+    std::vector<char> host_img(n), heavy(n);
+    size_t ib = 0, ob = 0;
+    auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    struct OutMap {
+        size_t counts, norm, feat;
+    };
+    std::vector<OutMap> om(n);
+    for (int i = 0; i < n; ++i) {
+        const glcm_desc& d = descs[i];
+        const int bpp = d.dtype == GLCM_U8 ? 1 : 2;
+        heavy[i] = d.features && d.levels > 64;
+        host_img[i] = !is_device_ptr(d.image);
+        dpitch[i] = (((size_t)d.width * bpp) + 15) & ~(size_t)15;
+        img_off[i] = ib;
+        if (host_img[i])
+            ib += r256(dpitch[i] * d.height);
+        const size_t nn = (size_t)d.levels * d.levels;
+        om[i].counts = om[i].norm = om[i].feat = (size_t)-1;
+        if (!is_device_ptr(d.counts)) {
+            om[i].counts = ob;
+            ob += r256(d.n_offsets * nn * 4);
+        }
+        if (d.normalized && !is_device_ptr(d.normalized)) {
+            om[i].norm = ob;
+            ob += r256(d.n_offsets * nn * 4);
+        }
+        if (d.features && !is_device_ptr(d.features)) {
+            om[i].feat = ob;
+            ob += r256((size_t)d.n_offsets * GLCM_N_FEATURES * 4);
+        }
+    }
+    TRY(ensure(ctx, ctx->hb_img, ib));
+    TRY(ensure(ctx, ctx->hb_out, ob));
+    uint8_t* gi = static_cast<uint8_t*>(ctx->hb_img.p);
+    uint8_t* go = static_cast<uint8_t*>(ctx->hb_out.p);
+    for (int i = 0; i < n; ++i) {
+        if (host_img[i]) {
+            dd[i].image = gi + img_off[i];
+            dd[i].pitch_bytes = dpitch[i];
+        }
+        if (om[i].counts != (size_t)-1)
+            dd[i].counts = reinterpret_cast<uint32_t*>(go + om[i].counts);
+        if (om[i].norm != (size_t)-1)
+            dd[i].normalized = reinterpret_cast<float*>(go + om[i].norm);
+        if (om[i].feat != (size_t)-1)
+            dd[i].features = reinterpret_cast<float*>(go + om[i].feat);
+    }
+    // Groups of consecutive images with about equal bytes.
+    const int G = std::min(n, 3);
+    std::vector<int> gend;
+    {
+        const size_t total = std::max<size_t>(1, ib);
+        size_t acc = 0;
+        int g = 1;
+        for (int i = 0; i < n; ++i) {
+            acc += host_img[i] ? r256(dpitch[i] * descs[i].height) : 0;
+            if ((acc * G >= total * g && (int)gend.size() < G - 1) || i == n - 1) {
+                gend.push_back(i + 1);
+                ++g;
+            }
+        }
+    }
+    while (ctx->stripe_events.size() < gend.size()) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->stripe_events.push_back(e);
+    }
+    if (ctx->hb_tab.size() < gend.size())
+        ctx->hb_tab.resize(gend.size());
+    int first = 0;
+    for (size_t g = 0; g < gend.size(); ++g) {
+        for (int i = first; i < gend[g]; ++i) {
+            if (!host_img[i])
+                continue;
+            const int bpp = descs[i].dtype == GLCM_U8 ? 1 : 2;
+            CK(cudaMemcpy2DAsync(gi + img_off[i], dpitch[i], descs[i].image, descs[i].pitch_bytes,
+                                 (size_t)descs[i].width * bpp, descs[i].height, cudaMemcpyHostToDevice,
+                                 ctx->copy_stream));
+        }
+        CK(cudaEventRecord(ctx->stripe_events[g], ctx->copy_stream));
+        first = gend[g];
+    }
+    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
+    bool forked = false;
+    first = 0;
+    for (size_t g = 0; g < gend.size(); ++g) {
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[g], 0));
+        auto& tab = ctx->hb_tab[g];
+        SplitBatch sb;
+        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sb, tab[0], tab[1], tab[2]));
+        if (reserve > 0)
+            sb.p8.max_ctas = sb.p16.max_ctas = ctx->sm_count - reserve;
+        if (!sb.p8.jobs.empty())
+            TRY(enqueue_vote(ctx, sb.p8, tab[0], tab[1], sb.c8, true, false, nullptr));
+        if (!sb.p16.jobs.empty())
+            TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, false, nullptr));
+        bool group_heavy = false;
+        for (int i = first; i < gend[g]; ++i)
+            group_heavy |= heavy[i] != 0;
+        if (group_heavy) {
+            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+            CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
+            TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr, ctx->side_stream));
+            forked = true;
+        } else {
+            TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr));
+        }
+        first = gend[g];
+    }
+    if (forked) {
+        CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    }
+    for (int i = 0; i < n; ++i) {
+        const size_t nn = (size_t)descs[i].levels * descs[i].levels;
+        if (om[i].counts != (size_t)-1)
+            CK(cudaMemcpyAsync(descs[i].counts, dd[i].counts, descs[i].n_offsets * nn * 4, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+        if (om[i].norm != (size_t)-1)
+            CK(cudaMemcpyAsync(descs[i].normalized, dd[i].normalized, descs[i].n_offsets * nn * 4,
+                               cudaMemcpyDeviceToHost, ctx->stream));
+        if (om[i].feat != (size_t)-1)
+            CK(cudaMemcpyAsync(descs[i].features, dd[i].features,
+                               (size_t)descs[i].n_offsets * GLCM_N_FEATURES * 4, cudaMemcpyDeviceToHost,
+                               ctx->stream));
+    }
+    return collect_device_errors(ctx);
 }
 
 }  // namespace
@@ -1151,8 +1372,10 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
         all_dev &= dv;
         any_dev |= dv;
     }
+    if (!all_dev && n > 1)
+        return run_host_batch(ctx, descs, n);
     if (!all_dev) {
-        // Host buffers: run each image through the stripe pipeline.
+        // One image with host buffers: the stripe pipeline.
         for (int i = 0; i < n; ++i) {
             const glcm_desc& d = descs[i];
             const int fl = d.flags | (d.normalized ? GLCM_NORMALIZE : 0);
@@ -1173,22 +1396,40 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
             ctx->graphs.clear();
         }
         GraphEntry ge;
-        SplitBatch sb;
+        SplitBatch sb, sb2;
+        // Expensive epilogues (features of N > 64) overlap the other images'
+        // votes when the batch has both kinds.
+        std::vector<glcm_desc> heavy, rest;
+        for (int i = 0; i < n; ++i)
+            (descs[i].features && descs[i].levels > 64 ? heavy : rest).push_back(descs[i]);
+        const bool split = !heavy.empty() && !rest.empty();
         // One direct run produces this call's results and sets every kernel
         // attribute before capture.
-        int rc0 = prepare_batch(ctx, descs, n, sb, ge.jobs, ge.offs, ge.feat);
+        int rc0;
+        if (split) {
+            rc0 = prepare_batch(ctx, heavy.data(), (int)heavy.size(), sb, ge.jobs, ge.offs, ge.feat);
+            if (rc0 == GLCM_OK)
+                rc0 = prepare_batch(ctx, rest.data(), (int)rest.size(), sb2, ge.jobs2, ge.offs2, ge.feat2);
+        } else {
+            rc0 = prepare_batch(ctx, descs, n, sb, ge.jobs, ge.offs, ge.feat);
+        }
+        const DevBuf th[3] = {ge.jobs, ge.offs, ge.feat};
+        const DevBuf tr[3] = {ge.jobs2, ge.offs2, ge.feat2};
         if (rc0 == GLCM_OK)
-            rc0 = enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, false, nullptr);
+            rc0 = split ? enqueue_batch_split(ctx, sb, th, sb2, tr, false, nullptr)
+                        : enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, false, nullptr);
         if (rc0 == GLCM_OK)
             rc0 = collect_device_errors(ctx);
         if (rc0 != GLCM_OK) {
             cudaStreamSynchronize(ctx->stream);
+            cudaStreamSynchronize(ctx->side_stream);
             destroy_graph(ge);
             return rc0;
         }
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-        const int rc = enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, true, &ge);
+        const int rc = split ? enqueue_batch_split(ctx, sb, th, sb2, tr, true, &ge)
+                             : enqueue_batch(ctx, sb, ge.jobs, ge.offs, ge.feat, true, &ge);
         cudaError_t ce = cudaStreamEndCapture(ctx->stream, &graph);
         if (rc != GLCM_OK) {
             if (graph)
@@ -1228,7 +1469,7 @@ extern "C" int glcm_compute_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
     }
     GraphEntry& ge = it->second;
     TimedPair tp{};
-    const bool timed = ctx->timing && ge.ev_start && ge.ev_stop && ge.n_vote_kernels == 1;
+    const bool timed = ctx->timing && ge.ev_start && ge.ev_stop;
     if (timed) {
         tp = take_pair(ctx);
         CK(cudaGraphExecEventRecordNodeSetEvent(ge.exec, ge.ev_start, tp.a));

@@ -403,11 +403,22 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
 {
     const int R = 1 << j.rshift;
     const int N = j.levels;
-    const int NN = N * N;
+    const long long NN = (long long)N * N;
     const int NNs = j.lv_span * N;
     const int rows = j.hist_words >> j.rshift;
     const int lane = threadIdx.x & 31;
     const int out_bin0 = j.lv_lo * N;
+    // Row w of the histograms is bin `bin` of offset group g: layout 1 pairs
+    // two offsets' rows (w = 2 (g NNs + bin) + parity), the others have one
+    // row per bin.  Advanced incrementally, without a division per row.
+    const int per = j.layout == 1 ? 2 : 1;
+    const int par = (int)threadIdx.x % per;
+    const int step = (int)blockDim.x / per;
+    int u = (int)threadIdx.x / per;
+    int g = u / NNs, bin = u - g * NNs;
+    int cur_o = -1;
+    uint32_t* dst_lo = nullptr;
+    uint32_t* dst_hi = nullptr;
     for (int w = threadIdx.x; w < rows; w += blockDim.x) {
         uint32_t lo = 0, hi = 0;
         uint32_t* base = hist + (long long)w * R;
@@ -422,22 +433,23 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
                 lo += v;
             }
         }
-        int o, bin;
-        if (j.layout == 1) {
-            const int pr = w >> 1;
-            o = (pr / NNs) * 2 + (w & 1);
-            bin = pr - (pr / NNs) * NNs;
-        } else if (j.layout == 2) {
-            o = (w / NNs) * 2;
-            bin = w - (w / NNs) * NNs;
-        } else {
-            o = w / NNs;
-            bin = w - o * NNs;
+        const int o = j.layout == 1 ? 2 * g + par : (j.layout == 2 ? 2 * g : g);
+        if (o != cur_o) {
+            cur_o = o;
+            dst_lo = o < j.n_off ? j.out + (long long)offs[j.off0 + o].slot * NN + out_bin0 : nullptr;
+            dst_hi = (j.layout == 2 && o + 1 < j.n_off)
+                         ? j.out + (long long)offs[j.off0 + o + 1].slot * NN + out_bin0
+                         : nullptr;
         }
-        if (lo && o < j.n_off)
-            red_global_add(j.out + (long long)offs[j.off0 + o].slot * NN + out_bin0 + bin, lo);
-        if (j.layout == 2 && hi && o + 1 < j.n_off)
-            red_global_add(j.out + (long long)offs[j.off0 + o + 1].slot * NN + out_bin0 + bin, hi);
+        if (lo && dst_lo)
+            red_global_add(dst_lo + bin, lo);
+        if (hi && dst_hi)
+            red_global_add(dst_hi + bin, hi);
+        bin += step;
+        while (bin >= NNs) {
+            bin -= NNs;
+            ++g;
+        }
     }
 }
 

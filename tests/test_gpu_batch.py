@@ -66,3 +66,34 @@ def test_contention_sweep_full_size(gctx):
         assert_features(ft.cpu().numpy(), oracle.haralick_batch(P, True), j["levels"],
                         what=f'{j["kind"]} N={j["levels"]}')
         assert_normalized(nm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)))
+
+
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_batch(gctx, pinned):
+    """A batch from host memory (images and results), mixed with one device
+    image: staged in groups on the copy stream; every result equals the
+    oracle and the same batch from device memory."""
+    jobs = _jobs(7)
+    spec_h, spec_d = [], []
+    for k, (im, n, o, f) in enumerate(jobs):
+        t = torch.from_numpy(np.ascontiguousarray(im))
+        if pinned:
+            t = t.pin_memory()
+        img = t.cuda() if k == 3 else t   # one device image in the mix
+        outs = [torch.empty((len(o), n, n), dtype=torch.int32), torch.empty((len(o), n, n), dtype=torch.float32),
+                torch.empty((len(o), 14), dtype=torch.float32)]
+        if pinned:
+            outs = [x.pin_memory() for x in outs]
+        spec_h.append(dict(image=img, levels=n, offsets=o, flags=f, counts=outs[0], normalized=outs[1],
+                           features=outs[2]))
+        spec_d.append(dict(image=torch.from_numpy(im).cuda(), levels=n, offsets=o, flags=f, normalized=True,
+                           features=True))
+    for rep in range(2):
+        gctx.batch(spec_h)
+        dev = gctx.batch(spec_d)
+        torch.cuda.synchronize()
+        for (im, n, o, f), h, (c, nm, ft) in zip(jobs, spec_h, dev):
+            P = oracle.glcm(im, n, o)
+            assert np.array_equal(h["counts"].numpy().view(np.uint32), P), (im.shape, n, rep)
+            assert np.array_equal(h["features"].numpy(), ft.cpu().numpy())
+            assert np.array_equal(h["normalized"].numpy(), nm.cpu().numpy())

@@ -1,0 +1,140 @@
+"""Full-size parity for the multispectral, local-texture, uneven-batch and
+served-stream workloads, in the launch configurations a user (and the
+benchmark) uses: one batched launch for all bands / images, the window
+kernel over the whole image, the continuous-batching server.
+
+Counts are compared bit for bit with the oracle everywhere it can compute
+them in seconds (all GLCMs of the bands and the 1000 images; a seeded sample
+of the windows and of the served requests); the rest are checked through
+properties that hold at any size (per-window pair totals).  The oracle runs
+in threads (its C loops release the GIL)."""
+import json
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+import pytest
+import torch
+
+import glcm_synth as S
+import oracle
+import paper_1710_06189_gb300 as G
+from conftest import to_u32
+from featcheck import FEATURE_TOL, assert_normalized, feature_errors, relative_errors
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+THREADS = max(1, min(16, os.cpu_count() or 1))
+
+
+def _pool_map(fn, items):
+    with ThreadPoolExecutor(THREADS) as ex:
+        return list(ex.map(fn, items))
+
+
+def _report(name, payload):
+    d = os.environ.get("GLCM_REPORT_DIR")
+    if d:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, name), "w") as f:
+            json.dump(payload, f, indent=1)
+
+
+def test_multispectral_8_bands_8192_u16(gctx):
+    """8 bands of 8192^2 uint16 (4 iid, 4 smooth sigma 16), N = 32, 12 offsets
+    (d in {1, 2, 4} x 4 angles), symmetric normalized GLCMs and all 14
+    features, one batched launch.  Per-feature error against float64."""
+    bands = _pool_map(S.multispectral_band, range(8))
+    offs = S.MULTISPECTRAL_OFFSETS
+    n = 32
+    spec = [dict(image=torch.from_numpy(b).cuda(), levels=n, offsets=offs, flags=G.GLCM_SYMMETRIC,
+                 normalized=True, features=True) for b in bands]
+    outs = gctx.batch(spec)
+    torch.cuda.synchronize()
+    want = _pool_map(lambda b: oracle.glcm(b, n, offs), bands)
+    errs, rels = [], []
+    for k, (P, (c, nm, ft)) in enumerate(zip(want, outs)):
+        assert np.array_equal(to_u32(c), P), f"band {k}"
+        assert_normalized(nm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)), f"band {k}")
+        F = oracle.haralick_batch(P, True)
+        errs.append(feature_errors(ft.cpu().numpy(), F, n))
+        rels.append(relative_errors(ft.cpu().numpy(), F))
+    e = np.stack(errs)
+    r = np.stack(rels)
+    per = {name: float(e[:, i].max()) for i, name in enumerate(oracle.FEATURE_NAMES)}
+    rel = {name: float(r[:, i].max()) for i, name in enumerate(oracle.FEATURE_NAMES)}
+    _report("multispectral_feature_errors.json", {"glcms": 8 * len(offs), "max_scaled_error": per,
+                                                   "max_relative_error": rel})
+    print("per-feature max scaled error:", json.dumps(per))
+    assert e.max() <= FEATURE_TOL, per
+
+
+def test_windows_2048_full(gctx):
+    """2048^2 smooth (sigma 4), N = 16, 15 x 15 windows at stride 4 (259,081
+    windows), 4 offsets: per-window totals everywhere, counts and maps of a
+    seeded sample of windows against the oracle."""
+    img = S.window_image()
+    offs = S.CONTENTION_OFFSETS
+    n, win, st = 16, 15, 4
+    c, m = gctx.windows(torch.from_numpy(img).cuda(), n, win, st, offs, flags=G.GLCM_SYMMETRIC)
+    torch.cuda.synchronize()
+    nwy = nwx = (2048 - win) // st + 1
+    assert nwy * nwx == 259081
+    cnt = c.view(torch.int32).reshape(nwy * nwx, 4, n * n)
+    totals = cnt.sum(dim=2, dtype=torch.int64).cpu().numpy()
+    for k, (dx, dy) in enumerate(offs):
+        assert np.all(totals[:, k] == (win - abs(dx)) * (win - abs(dy)))
+    rng = np.random.default_rng(S.BASE_SEED + 31)
+    idx = rng.choice(nwy * nwx, size=4096, replace=False)
+    wins = np.stack([idx // nwx, idx % nwx], axis=1)
+    want = oracle.window_glcm(img, n, offs, win, st, windows=wins)
+    got = to_u32(c).reshape(nwy * nwx, 4, n, n)[idx]
+    assert np.array_equal(got, want)
+    maps = oracle.window_maps(want, symmetric=True)  # (4 maps, n_win, n_off)
+    g = m.cpu().numpy().reshape(4, 4, nwy * nwx)[:, :, idx].transpose(0, 2, 1).astype(np.float64)
+    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / (n * n), 1.0, 1.0])[:, None, None])
+    assert (np.abs(g - maps) / scale).max() <= 1e-5
+
+
+def test_uneven_batch_1000_images(gctx):
+    """1000 square uint8 images, sides log-uniform 64..2048, N in {8, 16, 32},
+    4 offsets, one batched launch: every GLCM against the oracle."""
+    recipe = S.uneven_batch()
+    imgs = _pool_map(lambda r: S.image(r["kind"], r["seed"], r["side"], r["side"], np.uint8, 4.0), recipe)
+    spec = [dict(image=torch.from_numpy(im).cuda(), levels=r["levels"], offsets=r["offsets"],
+                 flags=G.GLCM_SYMMETRIC, normalized=False, features=True) for im, r in zip(imgs, recipe)]
+    for _ in range(2):  # captured, then replayed from the graph
+        outs = gctx.batch(spec)
+        torch.cuda.synchronize()
+    want = _pool_map(lambda a: oracle.glcm(a[0], a[1]["levels"], a[1]["offsets"]), list(zip(imgs, recipe)))
+    worst = 0.0
+    for k, (P, r, (c, _, ft)) in enumerate(zip(want, recipe, outs)):
+        assert np.array_equal(to_u32(c), P), f"image {k} side {r['side']} N {r['levels']}"
+        if k % 10 == 0:
+            worst = max(worst, float(feature_errors(ft.cpu().numpy(), oracle.haralick_batch(P, True),
+                                                    r["levels"]).max()))
+    assert worst <= FEATURE_TOL
+
+
+def test_served_stream_full_sizes():
+    """Served requests of the full stream recipe (sides log-uniform
+    256..8192, N in {8..64}, 1..12 offsets, iid/smooth), submitted at once to
+    the server; a seeded sample of 24 requests against the oracle."""
+    reqs = S.request_stream(24, 1000.0, lo=256, hi=8192, seed=S.BASE_SEED + 77)
+    crops = S.request_crops(reqs)
+    bases = {k: S.image(k, S.serve_base_seed(k), S.SERVE_BASE_SIDE, S.SERVE_BASE_SIDE, np.uint8, 8.0)
+             for k in ("iid", "smooth")}
+    pinned = {k: torch.from_numpy(v).pin_memory() for k, v in bases.items()}
+    with G.Server(0, hbm_budget_bytes=4 << 30, lanes=2) as srv:
+        ts = []
+        for r, (y0, x0) in zip(reqs, crops):
+            view = pinned[r.kind][y0:y0 + r.side, x0:x0 + r.side]
+            ts.append(srv.submit(view, r.levels, r.offsets, G.GLCM_SYMMETRIC, features=True))
+        res = [srv.wait(t) for t in ts]
+    want = _pool_map(lambda a: oracle.glcm(bases[a[0].kind][a[1][0]:a[1][0] + a[0].side,
+                                                            a[1][1]:a[1][1] + a[0].side], a[0].levels, a[0].offsets),
+                     list(zip(reqs, crops)))
+    for r, (st, lat, (c, _, ft)), P in zip(reqs, res, want):
+        assert st == G.GLCM_OK
+        assert np.array_equal(c.numpy().view(np.uint32), P), (r.side, r.levels, r.offsets)
+        assert feature_errors(ft.numpy(), oracle.haralick_batch(P, True), r.levels).max() <= FEATURE_TOL
