@@ -82,13 +82,13 @@ def load_peaks():
 
 
 def profiled_traffic(name: str):
-    """Per-launch DRAM bytes of the vote kernel from the committed ncu summary,
+    """DRAM bytes of a step's vote launches from the committed ncu summary,
     valid only while the kernel source is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
-    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m = re.search(r"traffic_bytes_per_step:\s*([0-9.eE+]+)", text)
     s = re.search(r"vote_source_sha256:\s*([0-9a-f]{64})", text)
     if not m or not s:
         return None

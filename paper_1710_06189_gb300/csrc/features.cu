@@ -203,9 +203,10 @@ __device__ float block_sum(float s, float* s_red)
     if (lane == 0)
         s_red[warp] = s;
     __syncthreads();
-    float t = 0.f;
-    for (int w = 0; w < nw; ++w)
-        t += s_red[w];
+    // Every warp reduces the partials the same way; lane 0's total is
+    // broadcast so that all threads hold the same value.
+    float t = lane < nw ? s_red[lane] : 0.f;
+    t = __shfl_sync(0xffffffffu, warp_sum(t), 0);
     __syncthreads();
     return t;
 }
@@ -282,15 +283,19 @@ __device__ void reorth(float* v, const float* __restrict__ Q, int k, int len, fl
         }
         __syncthreads();
         for (int r = threadIdx.x; r < len; r += blockDim.x) {
-            float a0 = v[r], a1 = 0.f;
+            // Four independent chains so that the loads of a group issue together.
+            float a0 = v[r], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+            const float* q = Q + r;
             int i = 0;
-            for (; i + 1 < k; i += 2) {
-                a0 = fmaf(-s_coef[i], Q[(long long)i * len + r], a0);
-                a1 = fmaf(-s_coef[i + 1], Q[(long long)(i + 1) * len + r], a1);
+            for (; i + 3 < k; i += 4) {
+                a0 = fmaf(-s_coef[i], q[(long long)i * len], a0);
+                a1 = fmaf(-s_coef[i + 1], q[(long long)(i + 1) * len], a1);
+                a2 = fmaf(-s_coef[i + 2], q[(long long)(i + 2) * len], a2);
+                a3 = fmaf(-s_coef[i + 3], q[(long long)(i + 3) * len], a3);
             }
-            if (i < k)
-                a0 = fmaf(-s_coef[i], Q[(long long)i * len + r], a0);
-            v[r] = a0 + a1;
+            for (; i < k; ++i)
+                a0 = fmaf(-s_coef[i], q[(long long)i * len], a0);
+            v[r] = (a0 + a1) + (a2 + a3);
         }
         __syncthreads();
     }
@@ -315,15 +320,65 @@ __device__ __forceinline__ int sturm_below(const float* ab, int L, float x)
     return cnt;
 }
 
-// Largest singular value of the K x K upper bidiagonal matrix with
-// diagonal alpha_k = ab[2k] and superdiagonal beta_k = ab[2k+1], i.e. the
-// largest eigenvalue of the zero-diagonal tridiagonal matrix with
-// off-diagonals alpha_0, beta_0, alpha_1, ... (eigenvalues +-sigma).
-// Called by one whole warp: 32-way multisection, each lane testing one
-// point per round, until the bracket is below float resolution.
-__device__ float gk_sigma_max_warp(const float* ab, int steps)
+// Multisection of one end of a spectrum by the warps [w0, w0 + nw): each of
+// the 32 nw points of a round tests whether every eigenvalue (upper) or none
+// (lower) lies below it, and the bracket shrinks to the interval between the
+// two neighbouring points where the answer changes.  A fixed number of rounds,
+// so that every thread of the block passes the same barriers; the returned
+// midpoint is meaningful in the calling warps.  s_msk: 2 x 32 words.
+template <class F>
+__device__ float block_multisect(F below, int n_eig, float a, float b, bool upper, int w0, int nw, int rounds,
+                                 unsigned (*s_msk)[32])
 {
-    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const bool mine = warp >= w0 && warp < w0 + nw;
+    const int P = 32 * nw;
+    const float den = (float)(P + 1);
+    for (int r = 0; r < rounds; ++r) {
+        if (mine) {
+            const int pt = (warp - w0) * 32 + lane;
+            const float x = a + (b - a) * (float)(pt + 1) / den;
+            const int c = below(x);
+            const unsigned m = __ballot_sync(0xffffffffu, upper ? c >= n_eig : c == 0);
+            if (lane == 0)
+                s_msk[r & 1][warp - w0 + (upper ? 0 : 16)] = m;
+        }
+        __syncthreads();
+        if (mine) {
+            const unsigned* mk = s_msk[r & 1] + (upper ? 0 : 16);
+            float na, nb;
+            if (upper) {
+                int idx = P;  // first point above every eigenvalue
+                for (int w = nw - 1; w >= 0; --w)
+                    if (mk[w])
+                        idx = 32 * w + __ffs(mk[w]) - 1;
+                na = idx == 0 ? a : a + (b - a) * (float)idx / den;
+                nb = idx == P ? b : a + (b - a) * (float)(idx + 1) / den;
+            } else {
+                int idx = -1;  // last point below every eigenvalue
+                for (int w = 0; w < nw; ++w)
+                    if (mk[w])
+                        idx = 32 * w + 31 - __clz(mk[w]);
+                na = idx < 0 ? a : a + (b - a) * (float)(idx + 1) / den;
+                nb = idx == P - 1 ? b : a + (b - a) * (float)(idx + 2) / den;
+            }
+            a = na;
+            b = nb;
+        }
+    }
+    return 0.5f * (a + b);
+}
+
+// The Golub-Kahan bidiagonal matrix after k steps has diagonal alpha_i =
+// ab[2i] and superdiagonal beta_i = ab[2i+1]; its singular values are the
+// non-negative eigenvalues of the zero-diagonal tridiagonal matrix with
+// off-diagonals alpha_0, beta_0, alpha_1, ... (eigenvalues +-sigma).
+// Largest singular value of that bidiagonal matrix by the whole block: three
+// rounds of 32 nw-way multisection of [0, 2 max(ab)] (the largest
+// eigenvalue of the zero-diagonal tridiagonal matrix); every thread returns it.
+__device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk)[32])
+{
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int L = 2 * steps - 1;
     if (L <= 0)
         return 0.f;
@@ -333,20 +388,8 @@ __device__ float gk_sigma_max_warp(const float* ab, int steps)
     for (int o = 16; o > 0; o >>= 1)
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     hi *= 2.f;
-    float lo = 0.f;
-    for (int round = 0; round < 8 && hi - lo > 1e-7f * hi; ++round) {
-        const float x = lo + (hi - lo) * (float)(lane + 1) / 33.f;
-        const bool all_below = sturm_below(ab, L, x) >= L + 1;
-        const unsigned m = __ballot_sync(0xffffffffu, all_below);
-        // Points are increasing in lane; the first with all eigenvalues below
-        // x bounds the top eigenvalue from above.
-        const int first = m ? __ffs(m) - 1 : 32;
-        const float nlo = first == 0 ? lo : lo + (hi - lo) * (float)first / 33.f;
-        const float nhi = first == 32 ? hi : lo + (hi - lo) * (float)(first + 1) / 33.f;
-        lo = nlo;
-        hi = nhi;
-    }
-    return 0.5f * (lo + hi);
+    auto below = [&](float x) { return sturm_below(ab, L, x); };
+    return block_multisect(below, L + 1, 0.f, hi, true, 0, nw < 16 ? nw : 16, 3, s_msk);
 }
 
 struct LanczosWork {
@@ -360,6 +403,7 @@ struct LanczosWork {
     float* ab;    // 2 kMaxLanczos + 2, shared
     float* sig;   // shared scalar
     int* stop;    // shared scalar
+    unsigned (*msk)[32];  // shared 2 x 32 words for the multisection
 };
 
 // Golub-Kahan-Lanczos bidiagonalization of the m x n matrix A with full
@@ -433,25 +477,19 @@ __device__ float lanczos_sigma_max(const float* A, int m, int n, const LanczosWo
         }
         // Every 8 steps: stop once the top Ritz value moved by < 1e-7.
         __syncthreads();
-        if (((k + 1) & 7) == 0 && threadIdx.x < 32) {
-            const float sg = gk_sigma_max_warp(w.ab, k + 1);
+        if (((k + 1) & 7) == 0) {
+            const float sg = gk_sigma_max_block(w.ab, k + 1, w.msk);
             if (threadIdx.x == 0) {
                 *w.stop = (k + 1 >= 16 && fabsf(sg - *w.sig) <= 1e-7f) ? 1 : 0;
                 *w.sig = sg;
             }
+            __syncthreads();
+            if (*w.stop)
+                break;
         }
-        __syncthreads();
-        if (*w.stop)
-            break;
     }
     __syncthreads();
-    if (threadIdx.x < 32) {
-        const float sg = gk_sigma_max_warp(w.ab, steps);
-        if (threadIdx.x == 0)
-            *w.sig = sg;
-    }
-    __syncthreads();
-    return *w.sig;
+    return gk_sigma_max_block(w.ab, steps, w.msk);
 }
 
 // ---- Blocked symmetric path (symmetric GLCMs with 128 < N <= 256) ----------
@@ -627,14 +665,15 @@ __device__ __forceinline__ int tri_count_below(const float* al, const float* be,
     return cnt;
 }
 
-// One end of the spectrum of that tridiagonal matrix (upper: the largest
-// eigenvalue, else the smallest), by 32-way multisection of its Gershgorin
-// interval (one whole warp).
-__device__ float tri_extreme_warp(const float* al, const float* be, int L, bool upper)
+// max(|lambda_max|, |lambda_min|) of the tridiagonal matrix: the first half
+// of the warps searches the top end, the second half the bottom end, four
+// rounds each; the result is in *out after the call (every thread of the
+// block must call).
+__device__ void tri_absmax_block(const float* al, const float* be, int L, float* ends, float* out,
+                                 unsigned (*s_msk)[32])
 {
-    const int lane = threadIdx.x & 31;
-    if (L <= 0)
-        return 0.f;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int half = nw / 2 < 16 ? nw / 2 : 16;
     float lo = 3.4e38f, hi = -3.4e38f;
     for (int t = lane; t < L; t += 32) {
         const float b0 = t > 0 ? fabsf(be[t - 1]) : 0.f, b1 = t + 1 < L ? fabsf(be[t]) : 0.f;
@@ -645,40 +684,13 @@ __device__ float tri_extreme_warp(const float* al, const float* be, int L, bool 
         lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, o));
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     }
-    float a = lo, b = hi;
-    for (int round = 0; round < 10 && b - a > 1e-7f * fmaxf(fabsf(a), fabsf(b)); ++round) {
-        const float x = a + (b - a) * (float)(lane + 1) / 33.f;
-        const int below = tri_count_below(al, be, L, x);
-        if (upper) {
-            const unsigned m = __ballot_sync(0xffffffffu, below >= L);
-            const int first = m ? __ffs(m) - 1 : 32;  // first point above every eigenvalue
-            const float na = first == 0 ? a : a + (b - a) * (float)first / 33.f;
-            const float nb = first == 32 ? b : a + (b - a) * (float)(first + 1) / 33.f;
-            a = na;
-            b = nb;
-        } else {
-            const unsigned m = __ballot_sync(0xffffffffu, below == 0);
-            const int last = m ? 31 - __clz(m) : -1;  // last point below every eigenvalue
-            const float na = last < 0 ? a : a + (b - a) * (float)(last + 1) / 33.f;
-            const float nb = last == 31 ? b : a + (b - a) * (float)(last + 2) / 33.f;
-            a = na;
-            b = nb;
-        }
-    }
-    return 0.5f * (a + b);
-}
-
-// max(|lambda_max|, |lambda_min|) of the tridiagonal matrix: warps 0 and 1
-// search the two ends at once; the result is in *out after the call (every
-// thread of the block must call).
-__device__ void tri_absmax_block(const float* al, const float* be, int L, float* ends, float* out)
-{
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp < 2) {
-        const float e = tri_extreme_warp(al, be, L, warp == 0);
-        if (lane == 0)
-            ends[warp] = e;
-    }
+    if (L <= 0)
+        lo = hi = 0.f;
+    auto below = [&](float x) { return tri_count_below(al, be, L, x); };
+    const bool up = warp < half;
+    const float e = block_multisect(below, L, lo, hi, up, up ? 0 : half, half, 4, s_msk);
+    if (lane == 0 && (warp == 0 || warp == half))
+        ends[up ? 0 : 1] = e;
     __syncthreads();
     if (threadIdx.x == 0)
         *out = fmaxf(fabsf(ends[0]), fabsf(ends[1]));
@@ -689,7 +701,7 @@ __device__ void tri_absmax_block(const float* al, const float* be, int L, float*
 // without reorthogonalization; stops once the estimate moved by less than
 // 4e-7 of itself over 8 steps (after at least 16) or after kMaxSymSteps.
 __device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* tri, float* bpart, float* s_red,
-                                    float* s_sig, int* s_stop)
+                                    float* s_sig, int* s_stop, unsigned (*s_msk)[32])
 {
     const int nb = (N + 31) >> 5, n = nb * 32;
     float* q = qv;
@@ -750,7 +762,7 @@ __device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* t
         beta = bn;
         __syncthreads();
         if ((L & 7) == 0 && L >= 16) {
-            tri_absmax_block(al, be, L, ends, ends + 2);
+            tri_absmax_block(al, be, L, ends, ends + 2, s_msk);
             if (threadIdx.x == 0) {
                 *s_stop = fabsf(ends[2] - *s_sig) <= 4e-7f * ends[2] ? 1 : 0;
                 *s_sig = ends[2];
@@ -761,7 +773,7 @@ __device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* t
         }
     }
     __syncthreads();
-    tri_absmax_block(al, be, L, ends, ends + 2);
+    tri_absmax_block(al, be, L, ends, ends + 2, s_msk);
     return ends[2];
 }
 
@@ -831,6 +843,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     __shared__ unsigned long long s_T, s_m[6];
     __shared__ int s_nr, s_nc, s_stop;
     __shared__ float s_red[32], s_coef[kMaxLanczos + 1], s_ab[2 * kMaxLanczos + 2], s_sig;
+    __shared__ unsigned s_msk[2][32];
 
     for (int k = threadIdx.x; k < 5 * N; k += blockDim.x)
         rs[k] = 0ull;
@@ -1027,7 +1040,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     if (big_sym && nr >= 2) {
         mcc = sym_lanczos_absmax(blk, N, reinterpret_cast<float*>(smem_raw + Lo.qv),
                                  reinterpret_cast<float*>(smem_raw + Lo.tri),
-                                 reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop);
+                                 reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop, s_msk);
     } else if (nr >= 2 && have_work) {
         LanczosWork w;
         w.xs = reinterpret_cast<float*>(smem_raw + Lo.xs);
@@ -1040,6 +1053,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
         w.ab = s_ab;
         w.sig = &s_sig;
         w.stop = &s_stop;
+        w.msk = s_msk;
         mcc = lanczos_sigma_max(A, nr, nc, w);
     }
     if (!have_work && nr >= 2 && threadIdx.x == 0)
