@@ -317,6 +317,81 @@ def serving_leg(G, S, torch, local: int, n_req: int = SERVE_REQUESTS):
     return out
 
 
+def _timed(stream, fn, warm=2, reps=5):
+    """Milliseconds per call of fn() on `stream` (CUDA events, after warm-up)."""
+    import torch
+    for _ in range(warm):
+        fn()
+    stream.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def other_workloads(G, S, torch, local: int):
+    """Device-resident throughput of the other workload shapes (each through
+    the same public calls a user makes, inputs already in HBM):
+    plain 512^2 N=8 levels-mode single offset; 8 bands of 8192^2 uint16 x 12
+    offsets with symmetric normalized GLCMs and features in one batch; the
+    2048^2 sliding-window texture maps (259,081 windows x 4 offsets); 1000
+    uneven uint8 images (64..2048) in one batch."""
+    import numpy as np
+    from concurrent.futures import ThreadPoolExecutor
+    out = {}
+    stream = torch.cuda.Stream(device=local)
+    ctx = G.Context(local, hbm_budget_bytes=8 << 30, stream=stream)
+    with torch.cuda.stream(stream):
+        # Plain method: one small image per call.
+        img, n, offs = S.plain_512()
+        d = torch.from_numpy(img).cuda(local)
+        c = torch.empty((1, n, n), dtype=torch.int32, device=f"cuda:{local}")
+        ms = _timed(stream, lambda: ctx.compute(d, n, offs, G.GLCM_INPUT_LEVELS, out=c), warm=3, reps=50)
+        out["plain_512"] = {"us_per_image": ms * 1e3, "gpairs_s": pairs_of(512, 512, offs) / (ms * 1e-3) / 1e9}
+        # Multispectral bands.
+        with ThreadPoolExecutor(8) as ex:
+            bands = list(ex.map(S.multispectral_band, range(8)))
+        offs = S.MULTISPECTRAL_OFFSETS
+        spec = [dict(image=torch.from_numpy(b).cuda(local), levels=32, offsets=offs, flags=G.GLCM_SYMMETRIC,
+                     normalized=True, features=True) for b in bands]
+        outs = ctx.batch(spec)
+        spec = [dict(s_, counts=o[0], normalized=o[1], features=o[2]) for s_, o in zip(spec, outs)]
+        ms = _timed(stream, lambda: ctx.batch(spec))
+        pairs = 8 * pairs_of(8192, 8192, offs)
+        out["multispectral_8x8192_u16"] = {"ms_per_batch": ms, "gpairs_s": pairs / (ms * 1e-3) / 1e9,
+                                           "hbm_read_gbs": 8 * 8192 * 8192 * 2 / (ms * 1e-3) / 1e9}
+        del spec, outs, bands
+        # Sliding-window texture maps.
+        wimg = torch.from_numpy(S.window_image()).cuda(local)
+        offs = S.CONTENTION_OFFSETS
+        nw = ((2048 - 15) // 4 + 1) ** 2
+        cw = torch.empty((509, 509, 4, 16, 16), dtype=torch.int32, device=f"cuda:{local}")
+        mw = torch.empty((4, 4, 509, 509), dtype=torch.float32, device=f"cuda:{local}")
+        src, w, h, pitch, dt = G.image_args(wimg)
+        ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
+                                                    G.GLCM_SYMMETRIC, cw, mw))
+        wp = nw * sum((15 - abs(dx)) * (15 - abs(dy)) for dx, dy in offs)
+        out["windows_2048_15x15_s4"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3), "gpairs_s": wp / (ms * 1e-3) / 1e9}
+        del cw, mw
+        # 1000 uneven images.
+        recipe = S.uneven_batch()
+        with ThreadPoolExecutor(8) as ex:
+            imgs = list(ex.map(lambda r: S.image(r["kind"], r["seed"], r["side"], r["side"], np.uint8, 4.0), recipe))
+        spec = [dict(image=torch.from_numpy(im).cuda(local), levels=r["levels"], offsets=r["offsets"],
+                     flags=G.GLCM_SYMMETRIC, normalized=False, features=True) for im, r in zip(imgs, recipe)]
+        outs = ctx.batch(spec)
+        spec = [dict(s_, counts=o[0], features=o[2]) for s_, o in zip(spec, outs)]
+        ms = _timed(stream, lambda: ctx.batch(spec))
+        pairs = sum(pairs_of(r["side"], r["side"], r["offsets"]) for r in recipe)
+        out["uneven_1000"] = {"ms_per_batch": ms, "gpairs_s": pairs / (ms * 1e-3) / 1e9}
+    stream.synchronize()
+    ctx.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -326,6 +401,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
     ap.add_argument("--no-tune", action="store_true", help="use the planner's default vote configurations")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -469,6 +545,8 @@ def main():
     }
     if not args.no_serving:
         line["serving"] = serving_leg(G, S, torch, local)
+    if not args.no_extra:
+        line["other_workloads"] = other_workloads(G, S, torch, local)
     if not args.no_cpu_baseline and world == 1:
         v, desc = oracle_sample(jobs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
