@@ -517,8 +517,31 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
     return GLCM_OK;
 }
 
-__global__ void k_zero_job_outputs(const VoteJob* jobs, const VoteOffset* offs)
+// Zero the jobs' output GLCMs and the vote kernel's chunk counter.  (A kernel
+// rather than memsets: on the copy engines a memset would queue behind the
+// image copies of a host-buffer batch.)
+__global__ void k_clear_word(unsigned* w) { *w = 0u; }
+
+__global__ void k_zero_words(uint32_t* p, long long n)
 {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x)
+        p[k] = 0u;
+}
+
+// Zero n words on `st` with a kernel (see k_zero_job_outputs for why).
+int zero_words(glcm_ctx* ctx, uint32_t* p, long long n, cudaStream_t st)
+{
+    const int grid = (int)std::min<long long>(std::max<long long>(1, (n + 255) / 256), 4ll * ctx->sm_count);
+    k_zero_words<<<grid, 256, 0, st>>>(p, n);
+    CK(cudaGetLastError());
+    ctx->kernel_launches += 1;
+    return GLCM_OK;
+}
+
+__global__ void k_zero_job_outputs(const VoteJob* jobs, const VoteOffset* offs, unsigned* counter)
+{
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+        *counter = 0u;
     const VoteJob j = jobs[blockIdx.x];
     const long long NN = (long long)j.levels * j.levels;
     for (int o = 0; o < j.n_off; ++o) {
@@ -550,14 +573,15 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     if (!st)
         st = ctx->stream;
     if (zero) {
-        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, st>>>(static_cast<const VoteJob*>(djobs.p),
-                                                                   static_cast<const VoteOffset*>(doffs.p));
-        CK(cudaGetLastError());
-        ctx->kernel_launches += capturing ? 0 : 1;
-        if (ge)
-            ge->n_kernels++;
+        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, st>>>(
+            static_cast<const VoteJob*>(djobs.p), static_cast<const VoteOffset*>(doffs.p), ctx->d_words + 1);
+    } else {
+        k_clear_word<<<1, 1, 0, st>>>(ctx->d_words + 1);
     }
-    CK(cudaMemsetAsync(ctx->d_words + 1, 0, sizeof(unsigned), st));
+    CK(cudaGetLastError());
+    ctx->kernel_launches += capturing ? 0 : 1;
+    if (ge)
+        ge->n_kernels++;
     VoteParams vp{};
     vp.jobs = static_cast<const VoteJob*>(djobs.p);
     vp.n_jobs = (int)plan.jobs.size();
@@ -655,6 +679,19 @@ int collect_device_errors(glcm_ctx* ctx)
     return GLCM_OK;
 }
 
+// Host-to-device copy of `rows` image rows: one flat copy when source and
+// destination rows are equally spaced (the bytes between a row's end and the
+// next row's start are copied along and never read), else a 2-D copy.
+cudaError_t copy_rows_h2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
+                          cudaStream_t st)
+{
+    if (rows <= 0)
+        return cudaSuccess;
+    if (dpitch == spitch)
+        return cudaMemcpyAsync(dst, src, spitch * (size_t)(rows - 1) + row_bytes, cudaMemcpyHostToDevice, st);
+    return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, rows, cudaMemcpyHostToDevice, st);
+}
+
 // Copy a host image into device staging, in row stripes on the copy stream;
 // returns the device image.  stripe_rows[k] are the row ends of the copies.
 int stage_host_image(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch, int bpp,
@@ -671,9 +708,9 @@ int stage_host_image(glcm_ctx* ctx, const void* image, int width, int height, si
     for (size_t k = 0; k < cuts.size(); ++k) {
         const int r1 = cuts[k];
         if (r1 > prev) {
-            CK(cudaMemcpy2DAsync(static_cast<uint8_t*>(dst.p) + (size_t)prev * dpitch, dpitch,
-                                 static_cast<const uint8_t*>(image) + (size_t)prev * pitch, pitch,
-                                 (size_t)width * bpp, r1 - prev, cudaMemcpyHostToDevice, ctx->copy_stream));
+            CK(copy_rows_h2d(static_cast<uint8_t*>(dst.p) + (size_t)prev * dpitch, dpitch,
+                             static_cast<const uint8_t*>(image) + (size_t)prev * pitch, pitch, (size_t)width * bpp,
+                             r1 - prev, ctx->copy_stream));
         }
         CK(cudaEventRecord(ctx->stripe_events[k], ctx->copy_stream));
         prev = std::max(prev, r1);
@@ -966,7 +1003,7 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         d_img = static_cast<const uint8_t*>(ctx->img.p);
     }
     // Zero the counts once, then one vote launch per stripe.
-    CK(cudaMemsetAsync(d_counts, 0, n_offsets * nn * 4, ctx->stream));
+    TRY(zero_words(ctx, d_counts, (long long)n_offsets * nn, ctx->stream));
     int r0 = 0;
     for (int k = 0; k < n_stripes; ++k) {
         const int r1 = anchors_cut[k];
@@ -1012,7 +1049,7 @@ extern "C" int glcm_compute_naive(glcm_ctx* ctx, const void* image, int width, i
     if (!is_device_ptr(image) || !is_device_ptr(counts))
         return fail(ctx, GLCM_ERR_ARG, "glcm_compute_naive takes device pointers only");
     const size_t nn = (size_t)levels * levels;
-    CK(cudaMemsetAsync(counts, 0, nn * 4, ctx->stream));
+    TRY(zero_words(ctx, counts, (long long)nn, ctx->stream));
     CK(launch_naive(static_cast<const uint8_t*>(image), (long long)pitch_bytes, width, height,
                     dtype == GLCM_U8 ? 1 : 2, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0, offset.dx, offset.dy,
                     counts, ctx->d_words, ctx->stream));
@@ -1289,29 +1326,36 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
     }
     if (ctx->hb_tab.size() < gend.size())
         ctx->hb_tab.resize(gend.size());
+    // Plans and tables of every group first: their uploads must not queue
+    // behind the image copies on a copy engine.
+    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
+    std::vector<SplitBatch> sbs(gend.size());
     int first = 0;
+    for (size_t g = 0; g < gend.size(); ++g) {
+        auto& tab = ctx->hb_tab[g];
+        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sbs[g], tab[0], tab[1], tab[2]));
+        if (reserve > 0)
+            sbs[g].p8.max_ctas = sbs[g].p16.max_ctas = ctx->sm_count - reserve;
+        first = gend[g];
+    }
+    first = 0;
     for (size_t g = 0; g < gend.size(); ++g) {
         for (int i = first; i < gend[g]; ++i) {
             if (!host_img[i])
                 continue;
             const int bpp = descs[i].dtype == GLCM_U8 ? 1 : 2;
-            CK(cudaMemcpy2DAsync(gi + img_off[i], dpitch[i], descs[i].image, descs[i].pitch_bytes,
-                                 (size_t)descs[i].width * bpp, descs[i].height, cudaMemcpyHostToDevice,
-                                 ctx->copy_stream));
+            CK(copy_rows_h2d(gi + img_off[i], dpitch[i], descs[i].image, descs[i].pitch_bytes,
+                             (size_t)descs[i].width * bpp, descs[i].height, ctx->copy_stream));
         }
         CK(cudaEventRecord(ctx->stripe_events[g], ctx->copy_stream));
         first = gend[g];
     }
-    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
     bool forked = false;
     first = 0;
     for (size_t g = 0; g < gend.size(); ++g) {
         CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[g], 0));
         auto& tab = ctx->hb_tab[g];
-        SplitBatch sb;
-        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sb, tab[0], tab[1], tab[2]));
-        if (reserve > 0)
-            sb.p8.max_ctas = sb.p16.max_ctas = ctx->sm_count - reserve;
+        SplitBatch& sb = sbs[g];
         if (!sb.p8.jobs.empty())
             TRY(enqueue_vote(ctx, sb.p8, tab[0], tab[1], sb.c8, true, false, nullptr));
         if (!sb.p16.jobs.empty())
