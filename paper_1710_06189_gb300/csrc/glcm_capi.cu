@@ -679,18 +679,63 @@ int collect_device_errors(glcm_ctx* ctx)
     return GLCM_OK;
 }
 
-// Host-to-device copy of `rows` image rows: one flat copy when source and
-// destination rows are equally spaced (the bytes between a row's end and the
-// next row's start are copied along and never read), else a 2-D copy.
-cudaError_t copy_rows_h2d(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
-                          cudaStream_t st)
+// Image rows from host memory to the device (see copy_rows_to_device).
+__global__ void k_copy_rows(uint8_t* __restrict__ dst, size_t dpitch, const uint8_t* __restrict__ src, size_t spitch,
+                            size_t row_bytes, int rows, int vec)
 {
-    if (rows <= 0)
+    const size_t units = row_bytes / vec;
+    const long long total = (long long)units * rows;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long r = k / (long long)units;
+        const size_t u = (size_t)(k - r * (long long)units) * vec;
+        const uint8_t* s = src + r * spitch + u;
+        uint8_t* d = dst + r * dpitch + u;
+        if (vec == 16)
+            *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(s);
+        else if (vec == 4)
+            *reinterpret_cast<uint32_t*>(d) = *reinterpret_cast<const uint32_t*>(s);
+        else
+            *d = *s;
+    }
+}
+
+}  // namespace
+
+// Host-to-device copy of `rows` image rows.  Registered (pinned) host memory
+// that the device can address, with 16-byte aligned rows, is read by a copy
+// kernel on a few SMs: on GB300
+// (host memory behind the chip-to-chip link) copy-engine transfers from host
+// memory held back the kernels of other streams until every queued transfer
+// had finished, while a copy kernel overlaps them.  Other host memory takes
+// cudaMemcpyAsync (one flat copy when both sides have the same pitch) or
+// cudaMemcpy2DAsync.
+cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes,
+                                      int rows, cudaStream_t st)
+{
+    if (rows <= 0 || row_bytes == 0)
         return cudaSuccess;
+    cudaPointerAttributes pa;
+    if (cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
+        // 16-byte units only: narrower reads over the link are far slower than
+        // a copy-engine transfer.
+        const uintptr_t a = reinterpret_cast<uintptr_t>(pa.devicePointer), b = reinterpret_cast<uintptr_t>(dst);
+        if ((a | b | spitch | dpitch | row_bytes) % 16 == 0) {
+            const long long units = (long long)(row_bytes / 16) * rows;
+            const int grid = (int)std::max<long long>(1, std::min<long long>(24, (units + 511) / 512));
+            k_copy_rows<<<grid, 512, 0, st>>>(static_cast<uint8_t*>(dst), dpitch,
+                                              static_cast<const uint8_t*>(pa.devicePointer), spitch, row_bytes, rows,
+                                              16);
+            return cudaGetLastError();
+        }
+    }
+    cudaGetLastError();
     if (dpitch == spitch)
         return cudaMemcpyAsync(dst, src, spitch * (size_t)(rows - 1) + row_bytes, cudaMemcpyHostToDevice, st);
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, rows, cudaMemcpyHostToDevice, st);
 }
+
+namespace {
 
 // Copy a host image into device staging, in row stripes on the copy stream;
 // returns the device image.  stripe_rows[k] are the row ends of the copies.
@@ -708,9 +753,9 @@ int stage_host_image(glcm_ctx* ctx, const void* image, int width, int height, si
     for (size_t k = 0; k < cuts.size(); ++k) {
         const int r1 = cuts[k];
         if (r1 > prev) {
-            CK(copy_rows_h2d(static_cast<uint8_t*>(dst.p) + (size_t)prev * dpitch, dpitch,
-                             static_cast<const uint8_t*>(image) + (size_t)prev * pitch, pitch, (size_t)width * bpp,
-                             r1 - prev, ctx->copy_stream));
+            CK(copy_rows_to_device(static_cast<uint8_t*>(dst.p) + (size_t)prev * dpitch, dpitch,
+                                   static_cast<const uint8_t*>(image) + (size_t)prev * pitch, pitch,
+                                   (size_t)width * bpp, r1 - prev, ctx->copy_stream));
         }
         CK(cudaEventRecord(ctx->stripe_events[k], ctx->copy_stream));
         prev = std::max(prev, r1);
@@ -1344,8 +1389,8 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
             if (!host_img[i])
                 continue;
             const int bpp = descs[i].dtype == GLCM_U8 ? 1 : 2;
-            CK(copy_rows_h2d(gi + img_off[i], dpitch[i], descs[i].image, descs[i].pitch_bytes,
-                             (size_t)descs[i].width * bpp, descs[i].height, ctx->copy_stream));
+            CK(copy_rows_to_device(gi + img_off[i], dpitch[i], descs[i].image, descs[i].pitch_bytes,
+                                   (size_t)descs[i].width * bpp, descs[i].height, ctx->copy_stream));
         }
         CK(cudaEventRecord(ctx->stripe_events[g], ctx->copy_stream));
         first = gend[g];

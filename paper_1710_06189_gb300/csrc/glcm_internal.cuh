@@ -122,5 +122,9 @@ cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
 int vote_max_smem_optin();
 int vote_blocks_per_sm(int bpp, int threads, size_t smem);
 int vote_row_bytes();
+// Host image rows to the device on `st` (a copy kernel for registered host
+// memory, else cudaMemcpy(2D)Async); defined in glcm_capi.cu.
+cudaError_t copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
+                                cudaStream_t st);
 
 }  // namespace glcm

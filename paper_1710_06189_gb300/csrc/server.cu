@@ -26,6 +26,7 @@
 
 #include "arena.h"
 #include "glcm.h"
+#include "glcm_internal.cuh"
 
 namespace {
 
@@ -178,14 +179,8 @@ bool admit(glcm_server* s)
     }
     for (Req* r : take) {
         const int bpp = r->d.dtype == GLCM_U8 ? 1 : 2;
-        // One flat copy when the rows are equally spaced on both sides.
-        const size_t row_bytes = (size_t)r->d.width * bpp;
-        cudaError_t e = r->dpitch == r->d.pitch_bytes
-                            ? cudaMemcpyAsync(s->base + r->off, r->d.image,
-                                              r->dpitch * (size_t)(r->d.height - 1) + row_bytes,
-                                              cudaMemcpyHostToDevice, s->copy)
-                            : cudaMemcpy2DAsync(s->base + r->off, r->dpitch, r->d.image, r->d.pitch_bytes, row_bytes,
-                                                r->d.height, cudaMemcpyHostToDevice, s->copy);
+        cudaError_t e = glcm::copy_rows_to_device(s->base + r->off, r->dpitch, r->d.image, r->d.pitch_bytes,
+                                                  (size_t)r->d.width * bpp, r->d.height, s->copy);
         r->copied = take_event(s);
         if (e == cudaSuccess && r->copied)
             e = cudaEventRecord(r->copied, s->copy);
