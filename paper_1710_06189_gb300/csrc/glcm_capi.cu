@@ -679,53 +679,79 @@ int collect_device_errors(glcm_ctx* ctx)
     return GLCM_OK;
 }
 
-// Image rows from host memory to the device (see copy_rows_to_device).
+// Image rows from host memory to the device (see copy_rows_to_device).  The
+// destination rows are 16-byte aligned; thread k of a row writes destination
+// bytes [16k, 16k + 16) from two aligned 16-byte source blocks realigned by
+// funnel shifts.  Only blocks that hold at least one byte of the row are read,
+// so no read leaves the pages of the caller's rows; destination bytes past
+// row_bytes (up to the next 16) are don't-care padding.
 __global__ void k_copy_rows(uint8_t* __restrict__ dst, size_t dpitch, const uint8_t* __restrict__ src, size_t spitch,
-                            size_t row_bytes, int rows, int vec)
+                            size_t row_bytes, int rows)
 {
-    const size_t units = row_bytes / vec;
+    const size_t units = (row_bytes + 15) / 16;
     const long long total = (long long)units * rows;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x) {
         const long long r = k / (long long)units;
-        const size_t u = (size_t)(k - r * (long long)units) * vec;
-        const uint8_t* s = src + r * spitch + u;
-        uint8_t* d = dst + r * dpitch + u;
-        if (vec == 16)
-            *reinterpret_cast<uint4*>(d) = *reinterpret_cast<const uint4*>(s);
-        else if (vec == 4)
-            *reinterpret_cast<uint32_t*>(d) = *reinterpret_cast<const uint32_t*>(s);
-        else
-            *d = *s;
+        const size_t u = (size_t)(k - r * (long long)units);
+        const uintptr_t row = reinterpret_cast<uintptr_t>(src) + (uintptr_t)(r * (long long)spitch);
+        const uintptr_t first = row + 16 * u;
+        const uintptr_t b0 = first & ~(uintptr_t)15;
+        const uintptr_t last_blk = (row + row_bytes - 1) & ~(uintptr_t)15;
+        const uint4 x = *reinterpret_cast<const uint4*>(b0);
+        const uint4 y = b0 + 16 <= last_blk ? *reinterpret_cast<const uint4*>(b0 + 16) : make_uint4(0, 0, 0, 0);
+        const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+        const unsigned off = (unsigned)(first & 15);
+        const unsigned q = off >> 2, sh = 8 * (off & 3);
+        uint32_t o[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            // words q + i and q + i + 1 of the 8, selected without dynamic indexing
+            uint32_t lo = w[i], hi = w[i + 1];
+            if (q == 1) {
+                lo = w[i + 1];
+                hi = w[i + 2];
+            } else if (q == 2) {
+                lo = w[i + 2];
+                hi = w[i + 3];
+            } else if (q == 3) {
+                lo = w[i + 3];
+                hi = i + 4 < 8 ? w[i + 4] : 0u;
+            }
+            o[i] = __funnelshift_r(lo, hi, sh);
+        }
+        *reinterpret_cast<uint4*>(dst + r * (long long)dpitch + 16 * u) = make_uint4(o[0], o[1], o[2], o[3]);
     }
 }
 
 }  // namespace
 
 // Host-to-device copy of `rows` image rows.  Registered (pinned) host memory
-// that the device can address, with 16-byte aligned rows, is read by a copy
-// kernel on a few SMs: on GB300
+// that the device can address is read by a copy kernel on a few SMs (16-byte
+// aligned reads, realigned on the device): on GB300
 // (host memory behind the chip-to-chip link) copy-engine transfers from host
 // memory held back the kernels of other streams until every queued transfer
 // had finished, while a copy kernel overlaps them.  Other host memory takes
 // cudaMemcpyAsync (one flat copy when both sides have the same pitch) or
-// cudaMemcpy2DAsync.
+// cudaMemcpy2DAsync, as does every copy when allow_kernel is false (the
+// serving loop: its lanes' vote launches fill every SM, and copy CTAs waiting
+// for SMs cost more there than the copy engine's hold-back; measured).
 cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes,
-                                      int rows, cudaStream_t st)
+                                      int rows, cudaStream_t st, bool allow_kernel)
 {
     if (rows <= 0 || row_bytes == 0)
         return cudaSuccess;
     cudaPointerAttributes pa;
-    if (cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost && pa.devicePointer) {
-        // 16-byte units only: narrower reads over the link are far slower than
-        // a copy-engine transfer.
-        const uintptr_t a = reinterpret_cast<uintptr_t>(pa.devicePointer), b = reinterpret_cast<uintptr_t>(dst);
-        if ((a | b | spitch | dpitch | row_bytes) % 16 == 0) {
-            const long long units = (long long)(row_bytes / 16) * rows;
+    if (allow_kernel && cudaPointerGetAttributes(&pa, src) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
+        pa.devicePointer) {
+        // The destination side must allow 16-byte stores; the source side may
+        // start anywhere.
+        const uintptr_t b = reinterpret_cast<uintptr_t>(dst);
+        if ((b | dpitch) % 16 == 0 && dpitch >= ((row_bytes + 15) & ~(size_t)15)) {
+            const long long units = (long long)((row_bytes + 15) / 16) * rows;
             const int grid = (int)std::max<long long>(1, std::min<long long>(24, (units + 511) / 512));
             k_copy_rows<<<grid, 512, 0, st>>>(static_cast<uint8_t*>(dst), dpitch,
-                                              static_cast<const uint8_t*>(pa.devicePointer), spitch, row_bytes, rows,
-                                              16);
+                                              static_cast<const uint8_t*>(pa.devicePointer), spitch, row_bytes, rows);
             return cudaGetLastError();
         }
     }

@@ -125,6 +125,6 @@ int vote_row_bytes();
 // Host image rows to the device on `st` (a copy kernel for registered host
 // memory, else cudaMemcpy(2D)Async); defined in glcm_capi.cu.
 cudaError_t copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
-                                cudaStream_t st);
+                                cudaStream_t st, bool allow_kernel = true);
 
 }  // namespace glcm

@@ -180,7 +180,7 @@ bool admit(glcm_server* s)
     for (Req* r : take) {
         const int bpp = r->d.dtype == GLCM_U8 ? 1 : 2;
         cudaError_t e = glcm::copy_rows_to_device(s->base + r->off, r->dpitch, r->d.image, r->d.pitch_bytes,
-                                                  (size_t)r->d.width * bpp, r->d.height, s->copy);
+                                                  (size_t)r->d.width * bpp, r->d.height, s->copy, false);
         r->copied = take_event(s);
         if (e == cudaSuccess && r->copied)
             e = cudaEventRecord(r->copied, s->copy);

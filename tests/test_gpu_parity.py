@@ -117,6 +117,26 @@ def test_host_image_stripes(gctx):
     assert np.array_equal(c.numpy().view(np.uint32), oracle.glcm(img, 32, offs))
 
 
+@pytest.mark.parametrize("x0,w", [(0, 3000), (3, 2999), (13, 1501), (16, 37)])
+def test_host_image_pinned_views(gctx, x0, w):
+    """Pinned host images, also views whose rows start at any byte and have
+    any length: staged by the copy kernel (aligned 16-byte reads realigned on
+    the device), through the stripe pipeline and through a host batch."""
+    base = torch.from_numpy(S.smooth(22, 2100, 3100, 6.0, np.uint8)).pin_memory()
+    view = base[5:2105 - 5, x0:x0 + w]
+    img = view.numpy()
+    offs = C4 + [(0, 2), (-3, 1)]
+    c = torch.empty((len(offs), 32, 32), dtype=torch.int32)
+    G.glcm_compute(gctx.ctx, view, w, view.shape[0], view.stride(0), G.GLCM_U8, 32, offs, 0, c)
+    want = oracle.glcm(img, 32, offs)
+    assert np.array_equal(c.numpy().view(np.uint32), want)
+    outs = gctx.batch([dict(image=view, levels=32, offsets=offs, counts=torch.empty_like(c)),
+                       dict(image=view, levels=16, offsets=offs, counts=torch.empty((len(offs), 16, 16),
+                                                                                    dtype=torch.int32))])
+    assert np.array_equal(outs[0][0].numpy().view(np.uint32), want)
+    assert np.array_equal(outs[1][0].numpy().view(np.uint32), oracle.glcm(img, 16, offs))
+
+
 @pytest.mark.parametrize("sym", [False, True])
 @pytest.mark.parametrize("n", [8, 32, 256])
 def test_normalize_and_features(gctx, sym, n):
