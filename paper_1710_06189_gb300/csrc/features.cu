@@ -392,6 +392,110 @@ __device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk
     return block_multisect(below, L + 1, 0.f, hi, true, 0, nw < 16 ? nw : 16, 3, s_msk);
 }
 
+// Reduce-scatter over the lanes of a warp: on entry every lane holds 32
+// values p[0..31]; on exit p[0] of lane l is the sum over all lanes of their
+// p[l] (recursive halving: 31 shuffles for 32 sums).
+__device__ __forceinline__ float warp_reduce_scatter32(float (&p)[32])
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const bool hi = (lane & o) != 0;
+#pragma unroll
+        for (int j = 0; j < o; ++j) {
+            const float keep = hi ? p[j + o] : p[j];
+            const float send = hi ? p[j] : p[j + o];
+            p[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+    }
+    return p[0];
+}
+
+// x -= sum_{i<k} <x, Q_i> Q_i, twice; x and the rows Q_i hold one entry per
+// lane (Q in shared memory, rows of 32).  One warp, no block barriers.
+__device__ __forceinline__ float warp_reorth32(float x, const float* Q, int k)
+{
+    const int lane = threadIdx.x & 31;
+    for (int pass = 0; pass < 2; ++pass) {
+        float q[32], pr[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+            q[i] = i < k ? Q[i * 32 + lane] : 0.f;
+            pr[i] = x * q[i];
+        }
+        const float coef = warp_reduce_scatter32(pr);  // lane i: <x, Q_i>
+        float a0 = x, a1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < 32; i += 2) {
+            a0 = fmaf(-__shfl_sync(0xffffffffu, coef, i), q[i], a0);
+            a1 = fmaf(-__shfl_sync(0xffffffffu, coef, i + 1), q[i + 1], a1);
+        }
+        x = a0 + a1;
+    }
+    return x;
+}
+
+__device__ __forceinline__ float warp_total(float v)
+{
+    return __shfl_sync(0xffffffffu, warp_sum(v), 0);
+}
+
+// Golub-Kahan-Lanczos bidiagonalization with full reorthogonalization for an
+// m x n matrix with m, n <= 32 (column-major, leading dimension m) by one
+// warp: vectors hold one entry per lane, A v by broadcasting v's entries, A^T u
+// by a reduce-scatter of the lanes' products.  Runs min(m, n) steps (exact for
+// the top singular value in exact arithmetic) or stops at a breakdown; writes
+// the bidiagonal to ab and returns the number of steps.  U: 32 x 32, V: 33 x 32
+// floats of shared memory.
+__device__ int lanczos_warp32(const float* A, int m, int n, float* U, float* V, float* ab)
+{
+    const int lane = threadIdx.x & 31;
+    const int K = min(m, n);
+    float v = lane < n ? 1.f + 0.01f * (float)((lane * 37) % 11) : 0.f;  // fixed start vector
+    v *= rsqrtf(warp_total(v * v));
+    V[lane] = v;
+    float beta = 0.f, uprev = 0.f;
+    int steps = 0;
+    for (int k = 0; k < K; ++k) {
+        float u = 0.f;
+        for (int c = 0; c < n; ++c) {
+            const float vc = __shfl_sync(0xffffffffu, v, c);
+            u = lane < m ? fmaf(A[c * m + lane], vc, u) : 0.f;
+        }
+        u = lane < m ? fmaf(-beta, uprev, u) : 0.f;
+        __syncwarp();
+        u = warp_reorth32(u, U, k);
+        const float alpha = sqrtf(warp_total(u * u));
+        if (lane == 0)
+            ab[2 * k] = alpha;
+        if (!(alpha > 1e-30f))
+            break;
+        u *= 1.f / alpha;
+        U[k * 32 + lane] = u;
+        uprev = u;
+        steps = k + 1;
+        // A^T u: lane r holds u_r and row r of A; lane c receives column c's sum.
+        float pr[32];
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+            pr[c] = (c < n && lane < m) ? A[c * m + lane] * u : 0.f;
+        float vn = warp_reduce_scatter32(pr);
+        vn = lane < n ? fmaf(-alpha, v, vn) : 0.f;
+        __syncwarp();
+        vn = warp_reorth32(vn, V, k + 1);
+        beta = sqrtf(warp_total(vn * vn));
+        if (lane == 0)
+            ab[2 * k + 1] = beta;
+        if (!(beta > 1e-30f) || k + 1 == K)
+            break;
+        v = vn * (1.f / beta);
+        V[(k + 1) * 32 + lane] = v;
+        __syncwarp();
+    }
+    __syncwarp();
+    return steps;
+}
+
 struct LanczosWork {
     float* xs;    // n floats, shared
     float* ys;    // m floats, shared
@@ -805,7 +909,9 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     L.part = take((size_t)kColGroups * 256 * 4);
     const size_t u0 = o;
     L.a = take((size_t)(nn < kSmemAFloats ? nn : kSmemAFloats) * 4);
-    L.uv = take((size_t)(uv < kSmemUVFloats ? uv : kSmemUVFloats) * 4);
+    // At least 32 x 32 + 33 x 32 floats: the one-warp path for supports <= 32.
+    const long long uvf = uv < kSmemUVFloats ? uv : kSmemUVFloats;
+    L.uv = take((size_t)(uvf > 65 * 32 ? uvf : 65 * 32) * 4);
     const size_t u1 = o;
     L.blk = L.bpart = L.qv = L.tri = 0;
     if (N > 128) {
@@ -1041,6 +1147,16 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
         mcc = sym_lanczos_absmax(blk, N, reinterpret_cast<float*>(smem_raw + Lo.qv),
                                  reinterpret_cast<float*>(smem_raw + Lo.tri),
                                  reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop, s_msk);
+    } else if (nr >= 2 && nr <= 32 && nc <= 32 && a_smem) {
+        // Small supports: one warp runs the whole bidiagonalization.
+        float* U32 = reinterpret_cast<float*>(smem_raw + Lo.uv);
+        if (warp == 0) {
+            const int steps = lanczos_warp32(A, nr, nc, U32, U32 + 32 * 32, s_ab);
+            if (lane == 0)
+                s_stop = steps;
+        }
+        __syncthreads();
+        mcc = gk_sigma_max_block(s_ab, s_stop, s_msk);
     } else if (nr >= 2 && have_work) {
         LanczosWork w;
         w.xs = reinterpret_cast<float*>(smem_raw + Lo.xs);
