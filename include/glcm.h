@@ -210,7 +210,9 @@ int glcm_get_timing(glcm_ctx *ctx, double *vote_ms, long long *vote_launches,
  * of the private histogram copies per CTA (0..5; copy c serves lanes with
  * lane % copies == c), the shared-memory layout (0: one row of copies per
  * bin; 1: two offsets' rows interleaved per bin; 2: two offsets as 16-bit
- * halves of one word), and anchor rows per work item (0 = derived).  Offsets
+ * halves of one word; 3: one offset's partner levels j and j + ceil(N/2) as
+ * 16-bit halves of one word, so that N = 256 takes one pass per offset), and
+ * anchor rows per work item (0 = derived).  Offsets
  * that do not fit one CTA's shared memory together are split over several
  * passes, and a histogram whose one level row does not fit is rejected.
  * threads <= 0 removes the override.  Errors: GLCM_ERR_ARG. */

@@ -18,8 +18,8 @@ import os
 
 from . import binding as B
 
-DEFAULT_CANDIDATES = tuple([(512, r, lay) for r in (5, 4, 3, 2, 1, 0) for lay in (1, 0, 2)] +
-                           [(256, 5, 1), (1024, 5, 1)])
+DEFAULT_CANDIDATES = tuple([(512, r, lay) for r in (5, 4, 3, 2, 1, 0) for lay in (1, 0, 2, 3)] +
+                           [(256, 5, 1), (1024, 5, 1), (1024, 0, 3)])
 
 
 def class_key(levels: int, n_offsets: int, dtype: int) -> str:

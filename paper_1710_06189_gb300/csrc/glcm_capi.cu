@@ -217,9 +217,11 @@ int hist_budget_words(const glcm_ctx* ctx)
     return (ctx->smem_optin - 2 * kTileRows * vote_row_bytes() - 4096) / 4;
 }
 
-// Offsets per histogram group and words per bin row of a group.
-int group_offsets(int layout) { return layout == 0 ? 1 : 2; }
+// Offsets per histogram group, words per bin row of a group, and bin rows
+// per anchor level (layout 3 packs partner levels j and j + ceil(N/2)).
+int group_offsets(int layout) { return layout == 0 || layout == 3 ? 1 : 2; }
 long long group_row_words(int layout, int rshift) { return (layout == 1 ? 2ll : 1ll) << rshift; }
+long long level_rows(int layout, int levels) { return layout == 3 ? (levels + 1) / 2 : levels; }
 
 // How one image's offsets are split into jobs for a configuration: groups per
 // job, and anchor-level span per job (span < N splits the levels).
@@ -234,14 +236,15 @@ JobShape job_shape(const glcm_ctx* ctx, int levels, int n_off, int layout, int r
     const long long wrow = group_row_words(layout, rshift);
     const int opg = group_offsets(layout);
     const int groups = (n_off + opg - 1) / opg;
-    const long long per_group = (long long)levels * levels * wrow;
+    const long long per_level = level_rows(layout, levels) * wrow;
+    const long long per_group = (long long)levels * per_level;
     if (per_group <= budget) {
         s.groups_per_job = (int)std::min<long long>(groups, budget / per_group);
         s.span = levels;
         s.jobs = (groups + s.groups_per_job - 1) / s.groups_per_job;
     } else {
         s.groups_per_job = 1;
-        s.span = (int)(budget / ((long long)levels * wrow));
+        s.span = (int)(budget / per_level);
         if (s.span < 1)
             return JobShape{1, 0, 0};
         s.jobs = groups * ((levels + s.span - 1) / s.span);
@@ -252,20 +255,22 @@ JobShape job_shape(const glcm_ctx* ctx, int levels, int n_off, int layout, int r
 // Default vote configuration from a cost model in units of one conflict-free
 // shared-memory reduction per pixel: each offset costs the bank-conflict
 // factor of its copy count (measured: 32 interleaved copies never conflict,
-// a single copy costs ~3x on random bins), each pass over the image ~0.6.
+// a single copy costs ~3x on random bins), each pass over the image ~0.6,
+// packed halves (layout 3) ~0.15 per offset for the half select and spills.
 VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
 {
     static const double conflict[6] = {3.0, 3.0, 2.8, 2.5, 2.0, 1.0};  // by log2 copies
     VoteCfg best;
     double best_cost = 1e30;
     for (int r = 5; r >= 0; --r) {
-        for (int layout : {1, 0, 2}) {
+        for (int layout : {1, 0, 2, 3}) {
             if (layout == 2 && 65535ll * (1 << r) / (16ll * 512) < 64)
                 continue;  // 16-bit halves would force a merge every few rows
             const JobShape s = job_shape(ctx, levels, n_off, layout, r);
             if (s.jobs <= 0)
                 continue;
-            const double cost = n_off * conflict[r] + 0.6 * s.jobs + (layout == 2 ? 0.05 * n_off : 0.0);
+            const double cost = n_off * conflict[r] + 0.6 * s.jobs + (layout == 2 ? 0.05 * n_off : 0.0) +
+                                (layout == 3 ? 0.15 * n_off : 0.0);
             if (cost < best_cost - 1e-9) {
                 best_cost = cost;
                 best.rshift = r;
@@ -329,6 +334,12 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
             return fail(ctx, GLCM_ERR_ARG, "vote config cannot bound 16-bit counters");
         band = (int)std::min<long long>(band, max_rows_per_warp * nwarps);
     }
+    if (cfg.layout == 3) {
+        // An item must fit between two spills: 49152 votes per half, PX per
+        // anchor row of each lane sharing a copy.
+        const long long rows_spill = 49152ll * (1 << cfg.rshift) / (32ll * PX);
+        band = (int)std::min<long long>(band, rows_spill);
+    }
     band = std::max(1, band);
     // Superbands only when the image takes several passes.
     const int passes = ((s.n_off + per_job - 1) / per_job) * ((s.levels + shape.span - 1) / shape.span);
@@ -379,7 +390,8 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                                  ? 1
                                  : 0;
                 const int groups = (cnt + opg - 1) / opg;
-                j.hist_words = (int)((long long)groups * span * s.levels * group_row_words(cfg.layout, cfg.rshift));
+                j.hist_words = (int)((long long)groups * span * level_rows(cfg.layout, s.levels) *
+                                     group_row_words(cfg.layout, cfg.rshift));
                 j.item0 = plan.n_items;
                 j.n_job_items = n_strips * n_bands;
                 // Weight of an item: pixel loads plus expected votes (offsets x
@@ -451,6 +463,15 @@ int target_items(const glcm_ctx* ctx)
     return ctx->sm_count * 4;
 }
 
+// Whether a plan needs the vote kernel instance with packed halves (layout 3).
+bool plan_packed(const VotePlan& plan)
+{
+    for (const VoteJob& j : plan.jobs)
+        if (j.layout == 3)
+            return true;
+    return false;
+}
+
 size_t vote_smem(const VotePlan& plan)
 {
     return std::max<size_t>(16, 2 * (size_t)plan.tile_rows * vote_row_bytes() + (size_t)plan.max_hist_words * 4);
@@ -459,7 +480,7 @@ size_t vote_smem(const VotePlan& plan)
 int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 {
     const size_t smem = vote_smem(plan);
-    const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem));
+    const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem, plan_packed(plan)));
     int ctas = ctx->sm_count * per_sm;
     if (plan.max_ctas > 0)
         ctas = std::min(ctas, plan.max_ctas * per_sm);
@@ -601,7 +622,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         tp = take_pair(ctx);
         CK(cudaEventRecord(tp.a, st));
     }
-    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st));
+    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
     if (time_it) {
         CK(cudaEventRecord(tp.b, st));
         ctx->pending.push_back(tp);
@@ -1006,7 +1027,7 @@ extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, in
         return GLCM_OK;
     }
     if (threads % 32 || threads < 64 || threads > kMaxThreads || log2_copies < 0 || log2_copies > 5 ||
-        layout < 0 || layout > 2 || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1 || band_rows < 0)
+        layout < 0 || layout > 3 || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1 || band_rows < 0)
         return fail(ctx, GLCM_ERR_ARG, "invalid vote config");
     if (job_shape(ctx, levels, n_offsets, layout, log2_copies).jobs <= 0)
         return fail(ctx, GLCM_ERR_ARG, "one level row of the histograms does not fit shared memory");

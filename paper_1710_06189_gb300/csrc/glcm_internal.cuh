@@ -37,7 +37,9 @@ struct VoteJob {
     int off0;          // first entry in the offsets table
     int rshift;        // log2(copies): R = 1 << rshift private copies
     int layout;        // 0: R words per bin; 1: two offsets' R words interleaved
-                       // per bin; 2: two offsets as 16-bit halves of R words
+                       // per bin; 2: two offsets as 16-bit halves of R words;
+                       // 3: partner levels j and j + ceil(N/2) of one offset as
+                       // 16-bit halves of R words
     int bytecode;      // N <= 16 power of two, layout 1, R = 32, no level split
     int lv_lo, lv_span;  // anchor levels [lv_lo, lv_lo + lv_span) counted
     int hist_words;    // shared words this job uses
@@ -110,8 +112,9 @@ struct WindowParams {
 };
 
 // Launchers (defined in the .cu files).
+// packed: some job of the launch uses layout 3 (a separate kernel instance).
 cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem,
-                        cudaStream_t s);
+                        cudaStream_t s, bool packed = false);
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);
@@ -120,7 +123,7 @@ size_t features_smem_bytes(int max_levels);
 long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
 int vote_max_smem_optin();
-int vote_blocks_per_sm(int bpp, int threads, size_t smem);
+int vote_blocks_per_sm(int bpp, int threads, size_t smem, bool packed = false);
 int vote_row_bytes();
 // Host image rows to the device on `st` (a copy kernel for registered host
 // memory, else cudaMemcpy(2D)Async); defined in glcm_capi.cu.

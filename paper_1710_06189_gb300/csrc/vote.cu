@@ -29,7 +29,17 @@
 //    Layouts: (0) one R-word row per bin; (1) two offsets' rows interleaved
 //    per bin (R = 32: a bin is 256 bytes, so a byte code c addresses its bin
 //    as c << 8); (2) two offsets share each word as 16-bit halves -- the
-//    merge comes before any half can reach 65536.
+//    merge comes before any half can reach 65536; (3) one offset's N bins of
+//    anchor level i share H = ceil(N / 2) words as 16-bit halves, so the
+//    65536 bins of N = 256 fit one CTA (128 KB) and an image takes one pass
+//    per offset instead of one per offset and anchor-level part.  Partner
+//    level j goes to position k = (j - i + floor(H / 2)) mod N: the lower
+//    half of word k for k < H, the upper half of word k - H otherwise, so
+//    the bins near the diagonal (flat regions, where many lanes hit one
+//    word) take the constant increment 1.  Every few tiles a spill pass
+//    moves each half that reached 2^14 into the global counts, so no half
+//    can wrap in between.  Layout 3 is compiled into its own kernel
+//    instance (PACKED), so launches without it run the plain vote loop.
 //  * For N <= 16 (power of two) the 4 codes i*N + j of a word come from one
 //    shift and one OR; a vote is a byte permute, an add and a reduction.
 //  * The merge (Sec. II.A, last step) sums the copies and adds each non-zero
@@ -255,7 +265,8 @@ __device__ __forceinline__ void partner_words(int dx, const uint32_t (&B)[4 / BP
 }
 
 // Where offset o of a job votes: shared byte address of (bin 0, copy 0),
-// bytes between bins, and the increment (1 or 1 << 16).
+// bytes between bins (between words in layout 3), and the increment (1 or
+// 1 << 16; layout 3 picks it per vote).
 struct HistRef {
     uint32_t base;
     uint32_t stride;
@@ -275,6 +286,11 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
         h.base = hbase + 4u * ((uint32_t)(o >> 1) * NNs * R + (uint32_t)c);
         h.stride = 4u * R;
         h.inc = (o & 1) ? 0x10000u : 1u;
+    } else if (j.layout == 3) {
+        const uint32_t Hh = ((uint32_t)j.levels + 1u) >> 1;
+        h.base = hbase + 4u * ((uint32_t)o * (uint32_t)j.lv_span * Hh * R + (uint32_t)c);
+        h.stride = 4u * R;
+        h.inc = 0u;
     } else {
         h.base = hbase + 4u * ((uint32_t)o * NNs * R + (uint32_t)c);
         h.stride = 4u * R;
@@ -290,7 +306,8 @@ __device__ __forceinline__ HistRef hist_ref(const VoteJob& j, int o, uint32_t hb
 // INC1: the increment is the constant 1 (every layout but the upper halves of
 // layout 2), which lets lanes of a warp that hit the same word be combined
 // into one update instead of serializing.
-template <int BPP, bool BYTECODE, bool SPLIT, bool FULL, bool INC1>
+// PACK: layout 3 (P2: N is a power of two).
+template <int BPP, bool BYTECODE, bool SPLIT, bool FULL, bool INC1, bool PACK = false, bool P2 = false>
 __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)[4 / BPP],
                                            const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask)
 {
@@ -312,6 +329,34 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
         return;
     }
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
+    if (PACK) {
+        const uint32_t Hh = (N + 1u) >> 1, q = Hh >> 1;
+#pragma unroll
+        for (int m = 0; m < LW; ++m) {
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
+                const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
+                const uint32_t ii = SPLIT ? i - lo : i;
+                uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
+                if (SPLIT)
+                    on &= ii < span ? 1u : 0u;
+                const uint32_t t = jv + q - i;
+                uint32_t k;
+                if (P2) {
+                    k = t & (N - 1u);
+                } else {
+                    k = (int)t < 0 ? t + N : t;
+                    k = k >= N ? k - N : k;
+                }
+                const uint32_t up = k >= Hh ? 1u : 0u;
+                const uint32_t addr = h.base + (ii * Hh + (up ? k - Hh : k)) * h.stride;
+                red_shared_add_if(addr, 1u, on & (up ^ 1u));
+                red_shared_add_if(addr, 0x10000u, on & up);
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
 #pragma unroll
@@ -333,13 +378,35 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
     }
 }
 
-template <int BPP, bool INC1>
+template <int BPP, bool SPLIT, bool FULL>
+__device__ __forceinline__ void vote_words_packed(const VoteJob& j, const uint32_t (&A)[4 / BPP],
+                                                  const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask)
+{
+    if (j.log2n >= 0)
+        vote_words<BPP, false, SPLIT, FULL, false, true, true>(j, A, PW, h, mask);
+    else
+        vote_words<BPP, false, SPLIT, FULL, false, true, false>(j, A, PW, h, mask);
+}
+
+template <int BPP, bool INC1, bool PACKED>
 __device__ __forceinline__ void vote_words_inc(const VoteJob& j, const uint32_t (&A)[4 / BPP],
                                                const uint32_t (&PW)[4 / BPP], const HistRef& h, uint32_t mask,
                                                bool full)
 {
     const bool split = j.lv_span < j.levels;
-    if (j.bytecode) {
+    if (PACKED && j.layout == 3) {
+        if (split) {
+            if (full)
+                vote_words_packed<BPP, true, true>(j, A, PW, h, mask);
+            else
+                vote_words_packed<BPP, true, false>(j, A, PW, h, mask);
+        } else {
+            if (full)
+                vote_words_packed<BPP, false, true>(j, A, PW, h, mask);
+            else
+                vote_words_packed<BPP, false, false>(j, A, PW, h, mask);
+        }
+    } else if (j.bytecode) {
         if (full)
             vote_words<BPP, true, false, true, true>(j, A, PW, h, mask);
         else
@@ -357,15 +424,15 @@ __device__ __forceinline__ void vote_words_inc(const VoteJob& j, const uint32_t 
     }
 }
 
-template <int BPP>
+template <int BPP, bool PACKED>
 __device__ __forceinline__ void vote_words_dispatch(const VoteJob& j, const uint32_t (&A)[4 / BPP],
                                                     const uint32_t (&PW)[4 / BPP], const HistRef& h,
                                                     uint32_t mask, bool full)
 {
-    if (h.inc == 1u)
-        vote_words_inc<BPP, true>(j, A, PW, h, mask, full);
+    if (h.inc == 1u || (PACKED && j.layout == 3))
+        vote_words_inc<BPP, true, PACKED>(j, A, PW, h, mask, full);
     else
-        vote_words_inc<BPP, false>(j, A, PW, h, mask, full);
+        vote_words_inc<BPP, false, PACKED>(j, A, PW, h, mask, full);
 }
 
 // Per-pixel path with full checks (|dx| > 4, bad levels): reads the image.
@@ -393,7 +460,14 @@ __device__ __noinline__ void vote_slow(const VoteJob* __restrict__ jp, int dx, i
         const uint32_t ii = i - (uint32_t)j.lv_lo;
         if (ii >= (uint32_t)j.lv_span)
             continue;
-        red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
+        if (j.layout == 3) {
+            const uint32_t Hh = (N + 1u) >> 1;
+            const uint32_t k = (jv + N + (Hh >> 1) - i) % N;
+            const bool up = k >= Hh;
+            red_shared_add(h.base + (ii * Hh + (up ? k - Hh : k)) * h.stride, up ? 0x10000u : 1u);
+        } else {
+            red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
+        }
     }
 }
 
@@ -451,6 +525,127 @@ __device__ void flush_hist(const VoteJob& j, const VoteOffset* offs, uint32_t* h
             ++g;
         }
     }
+}
+
+// Partner level of position k in anchor level i's packed row (layout 3).
+__device__ __forceinline__ int packed_partner(int k, int i, int N, int Hh)
+{
+    int jv = k + i - (Hh >> 1);
+    jv = jv < 0 ? jv + N : jv;
+    return jv >= N ? jv - N : jv;
+}
+
+// Layout 3: the same for packed halves.  Row w of the job's words is word
+// (g * span + ii) * H + kk of offset g, anchor level lv_lo + ii: positions kk
+// (lower half) and kk + H (upper half).  Advanced incrementally, without a
+// division per row.
+__device__ void flush_hist_packed(const VoteJob& j, const VoteOffset* offs, uint32_t* hist)
+{
+    const int R = 1 << j.rshift;
+    const int N = j.levels, Hh = (N + 1) >> 1, span = j.lv_span;
+    const long long NN = (long long)N * N;
+    const int rows = j.hist_words >> j.rshift;
+    const int lane = threadIdx.x & 31;
+    const int T = (int)blockDim.x;
+    const int sq = T / Hh, sr = T - sq * Hh;
+    const int q0 = (int)threadIdx.x / Hh;
+    int kk = (int)threadIdx.x - q0 * Hh;
+    int g = q0 / span;
+    int ii = q0 - g * span;
+    int cur_g = -1;
+    uint32_t* dst = nullptr;
+    for (int w = threadIdx.x; w < rows; w += T) {
+        uint32_t lo = 0, hi = 0;
+        uint32_t* base = hist + (long long)w * R;
+        for (int r = 0; r < R; ++r) {
+            const int c = (r + lane) & (R - 1);
+            const uint32_t v = base[c];
+            base[c] = 0u;
+            lo += v & 0xFFFFu;
+            hi += v >> 16;
+        }
+        if (g != cur_g) {
+            cur_g = g;
+            dst = g < j.n_off ? j.out + (long long)offs[j.off0 + g].slot * NN + (long long)j.lv_lo * N : nullptr;
+        }
+        if (dst) {
+            const int lvl = j.lv_lo + ii;
+            if (lo)
+                red_global_add(dst + ii * N + packed_partner(kk, lvl, N, Hh), lo);
+            if (hi && kk + Hh < N)
+                red_global_add(dst + ii * N + packed_partner(kk + Hh, lvl, N, Hh), hi);
+        }
+        if (w + T < rows) {
+            kk += sr;
+            ii += sq;
+            if (kk >= Hh) {
+                kk -= Hh;
+                ++ii;
+            }
+            while (ii >= span) {
+                ii -= span;
+                ++g;
+            }
+        }
+    }
+}
+
+// Layout 3 spill threshold: a half at or above 2^14 is moved to the global
+// counts, so the halves left are below 2^14 and the next tiles may add up to
+// 65535 - 16383 = 49152 votes to a half before the next spill.
+constexpr uint32_t kSpillMask = 0xC000C000u;
+constexpr int kSpillVotes = 49152;
+
+__device__ void spill_word(const VoteJob& j, const VoteOffset* offs, uint32_t* hist, int w)
+{
+    const uint32_t v = hist[w];
+    if ((v & kSpillMask) == 0u)
+        return;
+    const int N = j.levels, Hh = (N + 1) >> 1;
+    const int row = w >> j.rshift;
+    const int q = row / Hh, kk = row - q * Hh;
+    const int g = q / j.lv_span, ii = q - g * j.lv_span;
+    if (g >= j.n_off)
+        return;
+    const int lvl = j.lv_lo + ii;
+    uint32_t* dst = j.out + (long long)offs[j.off0 + g].slot * ((long long)N * N) + (long long)lvl * N;
+    uint32_t keep = v;
+    if (v & (kSpillMask & 0xFFFFu)) {
+        red_global_add(dst + packed_partner(kk, lvl, N, Hh), v & 0xFFFFu);
+        keep &= 0xFFFF0000u;
+    }
+    if ((v & (kSpillMask & 0xFFFF0000u)) && kk + Hh < N) {
+        red_global_add(dst + packed_partner(kk + Hh, lvl, N, Hh), v >> 16);
+        keep &= 0xFFFFu;
+    }
+    hist[w] = keep;
+}
+
+// Layout 3: spill the halves at or above 2^14 (one 16-byte read per four
+// words; almost every word is below).  Called by the whole CTA between
+// __syncthreads().
+__device__ void spill_hist_packed(const VoteJob& j, const VoteOffset* offs, uint32_t* hist)
+{
+    const int words = j.hist_words;
+    const uint4* h4 = reinterpret_cast<const uint4*>(hist);
+    for (int q = threadIdx.x; q < (words >> 2); q += blockDim.x) {
+        const uint4 v = h4[q];
+        if (((v.x | v.y | v.z | v.w) & kSpillMask) == 0u)
+            continue;
+        for (int e = 0; e < 4; ++e)
+            spill_word(j, offs, hist, 4 * q + e);
+    }
+    for (int w = (words & ~3) + (int)threadIdx.x; w < words; w += blockDim.x)
+        spill_word(j, offs, hist, w);
+}
+
+template <bool PACKED>
+__device__ __forceinline__ void flush_any(const VoteJob& j, const VoteOffset* offs, uint32_t* hist)
+{
+    if (PACKED && j.layout == 3)
+        flush_hist_packed(j, offs, hist);
+    else
+        flush_hist(j, offs, hist);
 }
 
 // ---- tiles -------------------------------------------------------------------
@@ -514,7 +709,7 @@ __device__ void fill_tile_plain(const VoteJob& j, const Tile& t, uint8_t* buf)
 }
 
 // Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps, ...
-template <int BPP>
+template <int BPP, bool PACKED>
 __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
                                           const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
 {
@@ -564,7 +759,7 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
                     const int hi_k = min(min(PX, wrem), wrem - d.x);
                     mask = hi_k > lo_k ? (((1u << hi_k) - 1u) & ~((1u << lo_k) - 1u)) : 0u;
                 }
-                vote_words_dispatch<BPP>(j, A, PW, h, mask, full);
+                vote_words_dispatch<BPP, PACKED>(j, A, PW, h, mask, full);
             } else if (xl < j.W) {
                 vote_slow(jg, d.x, d.y, y, xl, PX, h, err);
             }
@@ -598,7 +793,7 @@ __device__ void vote_tile_unstaged(const VoteJob& j, const VoteJob* jg, const Ti
 // dynamically balances images whose contention makes items cost very
 // different times.  Dynamic shared memory: two tile buffers, then the
 // histograms.
-template <int BPP, int MAXT>
+template <int BPP, int MAXT, bool PACKED>
 __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
 {
     extern __shared__ __align__(128) uint8_t smem[];
@@ -622,6 +817,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
     uint32_t uses[2] = {0u, 0u};  // completed phases per tile buffer
     int cur = -1;                 // job whose partial histograms are in shared memory
     long long acc_rows = 0;       // rows per warp voted into 16-bit halves since the last merge
+    int spill_rows = 0;           // anchor rows voted into packed halves (layout 3) since the last spill
     // Chunk b goes to CTA b; later chunks are claimed from the counter.
     bool first = true;
     for (;;) {
@@ -646,7 +842,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
             j.layout == 2 ? 65535ll / ((16 / BPP) * (long long)(blockDim.x >> j.rshift)) : (1ll << 62);
         const long long chunk_rows = (long long)(ch.z - ch.y) * j.band_rows / nwarps + 1;
         if (cur >= 0 && (cur != ch.x || acc_rows + chunk_rows > rows_ok)) {
-            flush_hist(p.jobs[cur], p.offs, hist);
+            flush_any<PACKED>(p.jobs[cur], p.offs, hist);
             __syncthreads();
             cur = -1;
         }
@@ -659,7 +855,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
             __syncthreads();
             cur = ch.x;
             acc_rows = 0;
+            spill_rows = 0;
         }
+        // Layout 3: anchor rows between spills (votes per half per CTA row:
+        // PX anchors of each of the 32 / R lanes that share a copy).
+        const int rows_spill = kSpillVotes * (1 << j.rshift) / (32 * (16 / BPP));
         // Items per merge inside the chunk (16-bit halves only).
         int step = ch.z - ch.y;
         if (j.layout == 2)
@@ -677,6 +877,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
                 const int b = (kk - ka) & 1;
                 uint8_t* buf = tiles + b * p.tile_bytes;
                 const Tile t = tile_of(j, kk);
+                if (PACKED && j.layout == 3) {
+                    const int rows_t = t.y1 - t.y0;
+                    if (spill_rows + rows_t > rows_spill) {
+                        spill_hist_packed(j, p.offs, hist);
+                        __syncthreads();
+                        spill_rows = 0;
+                    }
+                    spill_rows += rows_t;
+                }
                 if (!j.staged) {
                     vote_tile_unstaged<BPP>(j, jg, t, s_off_h, s_off_d, p.err);
                     __syncthreads();
@@ -697,14 +906,14 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
                     __syncthreads();
                 }
                 if (s_ok)
-                    vote_tile<BPP>(j, jg, t, buf, s_off_h, s_off_d, p.err);
+                    vote_tile<BPP, PACKED>(j, jg, t, buf, s_off_h, s_off_d, p.err);
                 __syncthreads();
             }
         }
         acc_rows += chunk_rows;
     }
     if (cur >= 0)
-        flush_hist(p.jobs[cur], p.offs, hist);
+        flush_any<PACKED>(p.jobs[cur], p.offs, hist);
 }
 
 // Scheme 1 of the paper (Sec. I.B): one thread per anchor pixel, one global
@@ -741,14 +950,14 @@ __global__ void k_glcm_naive(const uint8_t* img, long long pitch, int W, int H, 
 
 // Raise the dynamic shared-memory limit only when a launch needs more than
 // before, so no attribute call happens while a stream is being captured.
-template <int BPP, int MAXT>
+template <int BPP, int MAXT, bool PACKED>
 cudaError_t vote_prepare(size_t smem)
 {
     static size_t set_to = 0;
     if (smem <= set_to)
         return cudaSuccess;
-    cudaError_t e =
-        cudaFuncSetAttribute(k_glcm_vote<BPP, MAXT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_glcm_vote<BPP, MAXT, PACKED>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         set_to = smem;
     return e;
@@ -756,24 +965,34 @@ cudaError_t vote_prepare(size_t smem)
 
 // Two register budgets: up to 1024 threads at 64 registers, or up to 512
 // threads at 128 registers.
-template <int BPP>
+template <int BPP, bool PACKED>
 cudaError_t vote_launch_t(const VoteParams& p, int grid, int threads, size_t smem, cudaStream_t s, int* occ)
 {
     cudaError_t e;
     if (threads > 512) {
-        if ((e = vote_prepare<BPP, 1024>(smem)) != cudaSuccess)
+        if ((e = vote_prepare<BPP, 1024, PACKED>(smem)) != cudaSuccess)
             return e;
         if (occ)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 1024>, threads, smem);
-        k_glcm_vote<BPP, 1024><<<grid, threads, smem, s>>>(p);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 1024, PACKED>, threads,
+                                                                 smem);
+        k_glcm_vote<BPP, 1024, PACKED><<<grid, threads, smem, s>>>(p);
     } else {
-        if ((e = vote_prepare<BPP, 512>(smem)) != cudaSuccess)
+        if ((e = vote_prepare<BPP, 512, PACKED>(smem)) != cudaSuccess)
             return e;
         if (occ)
-            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 512>, threads, smem);
-        k_glcm_vote<BPP, 512><<<grid, threads, smem, s>>>(p);
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_glcm_vote<BPP, 512, PACKED>, threads,
+                                                                 smem);
+        k_glcm_vote<BPP, 512, PACKED><<<grid, threads, smem, s>>>(p);
     }
     return cudaGetLastError();
+}
+
+template <bool PACKED>
+cudaError_t vote_launch_b(const VoteParams& p, int bpp, int grid, int threads, size_t smem, cudaStream_t s,
+                          int* occ)
+{
+    return bpp == 1 ? vote_launch_t<1, PACKED>(p, grid, threads, smem, s, occ)
+                    : vote_launch_t<2, PACKED>(p, grid, threads, smem, s, occ);
 }
 
 }  // namespace
@@ -788,18 +1007,19 @@ int vote_max_smem_optin()
 
 int vote_row_bytes() { return kRowBytes; }
 
-int vote_blocks_per_sm(int bpp, int threads, size_t smem)
+int vote_blocks_per_sm(int bpp, int threads, size_t smem, bool packed)
 {
     int n = 0;
-    cudaError_t e = bpp == 1 ? vote_launch_t<1>(VoteParams{}, 0, threads, smem, nullptr, &n)
-                             : vote_launch_t<2>(VoteParams{}, 0, threads, smem, nullptr, &n);
+    cudaError_t e = packed ? vote_launch_b<true>(VoteParams{}, bpp, 0, threads, smem, nullptr, &n)
+                           : vote_launch_b<false>(VoteParams{}, bpp, 0, threads, smem, nullptr, &n);
     return e == cudaSuccess ? n : 1;
 }
 
-cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem, cudaStream_t s)
+cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem, cudaStream_t s,
+                        bool packed)
 {
-    return bpp == 1 ? vote_launch_t<1>(p, grid, threads, smem, s, nullptr)
-                    : vote_launch_t<2>(p, grid, threads, smem, s, nullptr);
+    return packed ? vote_launch_b<true>(p, bpp, grid, threads, smem, s, nullptr)
+                  : vote_launch_b<false>(p, bpp, grid, threads, smem, s, nullptr);
 }
 
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels, int levels_mode,

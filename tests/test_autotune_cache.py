@@ -28,4 +28,4 @@ def test_cache_round_trip(tmp_path):
 def test_default_candidates_are_valid_shapes():
     for threads, r, layout in autotune.DEFAULT_CANDIDATES:
         assert threads % 32 == 0 and 64 <= threads <= 1024
-        assert 0 <= r <= 5 and layout in (0, 1, 2)
+        assert 0 <= r <= 5 and layout in (0, 1, 2, 3)

@@ -207,7 +207,7 @@ def test_every_vote_config_is_exact(gctx, n):
     tried = 0
     for threads in (1024, 256):
         for r in (5, 3, 0):
-            for layout in (0, 1, 2):
+            for layout in (0, 1, 2, 3):
                 try:
                     G.glcm_set_vote_config(gctx.ctx, n, len(offs), G.GLCM_U8, threads, r, layout, 64)
                 except G.GlcmError:
@@ -218,3 +218,28 @@ def test_every_vote_config_is_exact(gctx, n):
                 tried += 1
     G.glcm_set_vote_config(gctx.ctx, n, len(offs), G.GLCM_U8, 0, 0, 0, 0)
     assert tried >= 3
+
+
+@pytest.mark.parametrize("dtype", [np.uint8, np.uint16])
+@pytest.mark.parametrize("n", [256, 255, 8])
+def test_packed_halves_spill(gctx, n, dtype):
+    """Packed 16-bit halves (layout 3): images whose votes pile into one or
+    two bins, millions of votes each, in the lower and the upper half of the
+    packed words, for every thread count.  Any half that wrapped between two
+    spills would lose 65536 votes."""
+    h, w = 1536, 1400
+    top = np.iinfo(dtype).max
+    img = np.full((h, w), top // 5, dtype)         # a lower-half level
+    img[:, 700:] = top - top // 7                    # an upper-half level
+    img[::97, :] = top // 2                          # a few rows elsewhere
+    offs = C4 + [(3, 2)]
+    want = oracle.glcm(img, n, offs)
+    assert want.max() > 4 * 65536
+    d = dev(img)
+    dt = G.GLCM_U8 if dtype == np.uint8 else G.GLCM_U16
+    for threads in (1024, 512, 256):
+        G.glcm_set_vote_config(gctx.ctx, n, len(offs), dt, threads, 0, 3, 0)
+        c = gctx.compute(d, n, offs)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_u32(c), want), threads
+    G.glcm_set_vote_config(gctx.ctx, n, len(offs), dt, 0, 0, 0, 0)
