@@ -34,9 +34,12 @@
 //    65536 bins of N = 256 fit one CTA (128 KB) and an image takes one pass
 //    per offset instead of one per offset and anchor-level part.  Partner
 //    level j goes to position k = (j - i + floor(H / 2)) mod N: the lower
-//    half of word k for k < H, the upper half of word k - H otherwise, so
-//    the bins near the diagonal (flat regions, where many lanes hit one
-//    word) take the constant increment 1.  Every few tiles a spill pass
+//    half of column k for k < H, the upper half of column k - H otherwise,
+//    so the bins near the diagonal (flat regions, where many lanes hit one
+//    word) take the constant increment 1.  Column kk of anchor level i is
+//    word i * H + (kk + i) mod H: rotating each row spreads the lanes of a
+//    smooth region (same kk, different i) over the banks, and a merge still
+//    reads and writes along rows.  Every few tiles a spill pass
 //    moves each half that reached 2^14 into the global counts, so no half
 //    can wrap in between.  Layout 3 is compiled into its own kernel
 //    instance (PACKED), so launches without it run the plain vote loop.
@@ -330,7 +333,15 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
     }
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
     if (PACK) {
+        // Addresses and upper-half bits of the lane's votes first; a warp row
+        // with no upper-half vote (flat and smooth regions) reduces with the
+        // constant 1, so lanes that hit one word combine, the others with a
+        // per-vote increment.
         const uint32_t Hh = (N + 1u) >> 1, q = Hh >> 1;
+        const uint32_t lh = P2 ? (uint32_t)j.log2n - 1u : 0u;  // log2(H)
+        const uint32_t cq = q - lo;                              // mod H below (P2)
+        uint32_t addr[4 * LW];
+        uint32_t upm = 0u, onm = FULL ? 0xFFFFFFFFu : mask;
 #pragma unroll
         for (int m = 0; m < LW; ++m) {
 #pragma unroll
@@ -338,22 +349,39 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
                 const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
                 const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
                 const uint32_t ii = SPLIT ? i - lo : i;
-                uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
-                if (SPLIT)
-                    on &= ii < span ? 1u : 0u;
+                if (SPLIT && ii >= span)
+                    onm &= ~(1u << (4 * m + b));
                 const uint32_t t = jv + q - i;
-                uint32_t k;
+                uint32_t up, c;
                 if (P2) {
-                    k = t & (N - 1u);
+                    // H divides N: (k mod H + ii) mod H = (j + q - lo) mod H,
+                    // and the half is bit log2(H) of j - i + q.
+                    up = (t >> lh) & 1u;
+                    c = (jv + cq) & (Hh - 1u);
                 } else {
-                    k = (int)t < 0 ? t + N : t;
+                    uint32_t k = (int)t < 0 ? t + N : t;
                     k = k >= N ? k - N : k;
+                    up = k >= Hh ? 1u : 0u;
+                    c = (up ? k - Hh : k) + ii;
+                    c = c >= Hh ? c - Hh : c;
+                    c = c >= Hh ? c - Hh : c;
                 }
-                const uint32_t up = k >= Hh ? 1u : 0u;
-                const uint32_t addr = h.base + (ii * Hh + (up ? k - Hh : k)) * h.stride;
-                red_shared_add_if(addr, 1u, on & (up ^ 1u));
-                red_shared_add_if(addr, 0x10000u, on & up);
+                upm |= up << (4 * m + b);
+                addr[4 * m + b] = h.base + (ii * Hh + c) * h.stride;
             }
+        }
+        if (!__any_sync(0xffffffffu, (upm & onm) != 0u)) {
+#pragma unroll
+            for (int v = 0; v < 4 * LW; ++v) {
+                if (FULL && !SPLIT)
+                    red_shared_add(addr[v], 1u);
+                else
+                    red_shared_add_if(addr[v], 1u, (onm >> v) & 1u);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4 * LW; ++v)
+                red_shared_add_if(addr[v], ((upm >> v) & 1u) ? 0x10000u : 1u, (onm >> v) & 1u);
         }
         return;
     }
@@ -464,7 +492,8 @@ __device__ __noinline__ void vote_slow(const VoteJob* __restrict__ jp, int dx, i
             const uint32_t Hh = (N + 1u) >> 1;
             const uint32_t k = (jv + N + (Hh >> 1) - i) % N;
             const bool up = k >= Hh;
-            red_shared_add(h.base + (ii * Hh + (up ? k - Hh : k)) * h.stride, up ? 0x10000u : 1u);
+            const uint32_t c = ((up ? k - Hh : k) + ii) % Hh;
+            red_shared_add(h.base + (ii * Hh + c) * h.stride, up ? 0x10000u : 1u);
         } else {
             red_shared_add(h.base + (ii * N + jv) * h.stride, h.inc);
         }
@@ -536,9 +565,9 @@ __device__ __forceinline__ int packed_partner(int k, int i, int N, int Hh)
 }
 
 // Layout 3: the same for packed halves.  Row w of the job's words is word
-// (g * span + ii) * H + kk of offset g, anchor level lv_lo + ii: positions kk
-// (lower half) and kk + H (upper half).  Advanced incrementally, without a
-// division per row.
+// (g * span + ii) * H + c of offset g, anchor level lv_lo + ii: positions
+// kk = (c - ii) mod H (lower half) and kk + H (upper half).  Advanced
+// incrementally, without a division per row.
 __device__ void flush_hist_packed(const VoteJob& j, const VoteOffset* offs, uint32_t* hist)
 {
     const int R = 1 << j.rshift;
@@ -549,18 +578,19 @@ __device__ void flush_hist_packed(const VoteJob& j, const VoteOffset* offs, uint
     const int T = (int)blockDim.x;
     const int sq = T / Hh, sr = T - sq * Hh;
     const int q0 = (int)threadIdx.x / Hh;
-    int kk = (int)threadIdx.x - q0 * Hh;
+    int c = (int)threadIdx.x - q0 * Hh;
     int g = q0 / span;
     int ii = q0 - g * span;
+    const bool p2 = j.log2n >= 0;
     int cur_g = -1;
     uint32_t* dst = nullptr;
     for (int w = threadIdx.x; w < rows; w += T) {
         uint32_t lo = 0, hi = 0;
         uint32_t* base = hist + (long long)w * R;
         for (int r = 0; r < R; ++r) {
-            const int c = (r + lane) & (R - 1);
-            const uint32_t v = base[c];
-            base[c] = 0u;
+            const int cc = (r + lane) & (R - 1);  // rotate so lanes hit distinct banks
+            const uint32_t v = base[cc];
+            base[cc] = 0u;
             lo += v & 0xFFFFu;
             hi += v >> 16;
         }
@@ -568,18 +598,25 @@ __device__ void flush_hist_packed(const VoteJob& j, const VoteOffset* offs, uint
             cur_g = g;
             dst = g < j.n_off ? j.out + (long long)offs[j.off0 + g].slot * NN + (long long)j.lv_lo * N : nullptr;
         }
-        if (dst) {
+        if (dst && (lo | hi)) {
             const int lvl = j.lv_lo + ii;
+            int kk;
+            if (p2) {
+                kk = (c - ii) & (Hh - 1);
+            } else {
+                kk = c - ii % Hh;
+                kk += kk < 0 ? Hh : 0;
+            }
             if (lo)
                 red_global_add(dst + ii * N + packed_partner(kk, lvl, N, Hh), lo);
             if (hi && kk + Hh < N)
                 red_global_add(dst + ii * N + packed_partner(kk + Hh, lvl, N, Hh), hi);
         }
         if (w + T < rows) {
-            kk += sr;
+            c += sr;
             ii += sq;
-            if (kk >= Hh) {
-                kk -= Hh;
+            if (c >= Hh) {
+                c -= Hh;
                 ++ii;
             }
             while (ii >= span) {
@@ -603,8 +640,10 @@ __device__ void spill_word(const VoteJob& j, const VoteOffset* offs, uint32_t* h
         return;
     const int N = j.levels, Hh = (N + 1) >> 1;
     const int row = w >> j.rshift;
-    const int q = row / Hh, kk = row - q * Hh;
+    const int q = row / Hh, c = row - q * Hh;
     const int g = q / j.lv_span, ii = q - g * j.lv_span;
+    int kk = c - ii % Hh;
+    kk += kk < 0 ? Hh : 0;
     if (g >= j.n_off)
         return;
     const int lvl = j.lv_lo + ii;
