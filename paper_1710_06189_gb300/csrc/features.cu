@@ -12,8 +12,11 @@
 //  * Every other sum is float32 with Kahan compensation per thread and a
 //    two-sum (error-free) block reduction; no fused multiply-add contraction
 //    is allowed in those sums (__fadd_rn / __fmul_rn).
-//  * The means, variances and covariance behind correlation (f3) and sum of
-//    squares (f4) are float64 -- the one float64 step.
+//  * Correlation (f3) and sum of squares (f4) come from exact integer
+//    moments: T^2 var = T sum i^2 r_i - (sum i r_i)^2 and T^2 cov =
+//    T sum i j S(i, j) - (sum i r_i)(sum j c_j) in 128-bit integers, turned
+//    into float64 once by one thread (float64 is slow on this GPU, so no
+//    thread does float64 arithmetic per cell).
 //  * f12 and f13 are functions of the mutual information
 //    I = HX + HY - HXY (= HXY1 - HXY = HXY2 - HXY, since HXY1 = HXY2 =
 //    HX + HY).  I is summed as sum q * phi(x) with q = p_x p_y,
@@ -26,7 +29,10 @@
 //    A'(i,j) = (S*T - r*c) / (T sqrt(r c)), and the largest singular value
 //    of A' is found by Golub-Kahan-Lanczos bidiagonalization with full
 //    reorthogonalization in float32, stopped when its top Ritz value
-//    settles (exact after min(rows, cols) steps).
+//    settles (exact after min(rows, cols) steps).  Supports of at most 32
+//    levels instead square G = A'^T A' (or A' A'^T) repeatedly with the
+//    whole block and take a Rayleigh quotient: a few dozen barrier-separated
+//    steps instead of a serial chain of Lanczos steps in one warp.
 //  * Symmetric GLCMs with N > 128 (A' symmetric, too large for shared
 //    memory as a full matrix) keep A' as its upper 32 x 32 blocks in shared
 //    memory and find max |eigenvalue| of A' -- its largest singular value --
@@ -55,6 +61,12 @@ constexpr int kBigTiles = kBigNB * (kBigNB + 1) / 2;
 constexpr int kTileFloats = 32 * 33;
 constexpr int kMaxSymSteps = 384;
 constexpr int kMaxLevelsPerLane = 256 / 32;  // N <= 256
+// Repeated squaring for supports of at most 32 levels: row stride (16-byte
+// rows, conflict-free float4 reads), minimum and maximum squarings, floats.
+constexpr int kSqLD = 36;
+constexpr int kSqMin = 13;
+constexpr int kSqMax = 30;
+constexpr int kSqFloats = 96 * kSqLD + 64;
 
 struct DF {  // float value hi + lo (unevaluated sum)
     float hi, lo;
@@ -146,33 +158,13 @@ __device__ void block_reduce_df(DF (&v)[K], DF* scratch /* K * 32 */)
     __syncthreads();
 }
 
-template <int K>
-__device__ void block_reduce_d(double (&v)[K], double* scratch)
+// Signed 128-bit integer to double (the two 64-bit halves, rounded once each).
+__device__ __forceinline__ double i128_to_double(__int128 v)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        for (int o = 16; o > 0; o >>= 1)
-            v[k] += __shfl_down_sync(0xffffffffu, v[k], o);
-        if (lane == 0)
-            scratch[k * 32 + warp] = v[k];
-    }
-    __syncthreads();
-    if (warp == 0) {
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            double a = lane < nw ? scratch[k * 32 + lane] : 0.0;
-            for (int o = 16; o > 0; o >>= 1)
-                a += __shfl_down_sync(0xffffffffu, a, o);
-            if (lane == 0)
-                scratch[k * 32] = a;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k = 0; k < K; ++k)
-        v[k] = scratch[k * 32];
-    __syncthreads();
+    const bool neg = v < 0;
+    const unsigned __int128 u = neg ? (unsigned __int128)(-v) : (unsigned __int128)v;
+    const double d = (double)(unsigned long long)(u >> 64) * 18446744073709551616.0 + (double)(unsigned long long)u;
+    return neg ? -d : d;
 }
 
 __device__ __forceinline__ unsigned long long cell(const uint32_t* C, int N, int i, int j, int sym)
@@ -392,108 +384,132 @@ __device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk
     return block_multisect(below, L + 1, 0.f, hi, true, 0, nw < 16 ? nw : 16, 3, s_msk);
 }
 
-// Reduce-scatter over the lanes of a warp: on entry every lane holds 32
-// values p[0..31]; on exit p[0] of lane l is the sum over all lanes of their
-// p[l] (recursive halving: 31 shuffles for 32 sums).
-__device__ __forceinline__ float warp_reduce_scatter32(float (&p)[32])
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const bool hi = (lane & o) != 0;
-#pragma unroll
-        for (int j = 0; j < o; ++j) {
-            const float keep = hi ? p[j + o] : p[j];
-            const float send = hi ? p[j] : p[j + o];
-            p[j] = keep + __shfl_xor_sync(0xffffffffu, send, o);
-        }
-    }
-    return p[0];
-}
-
-// x -= sum_{i<k} <x, Q_i> Q_i, twice; x and the rows Q_i hold one entry per
-// lane (Q in shared memory, rows of 32).  One warp, no block barriers.
-__device__ __forceinline__ float warp_reorth32(float x, const float* Q, int k)
-{
-    const int lane = threadIdx.x & 31;
-    for (int pass = 0; pass < 2; ++pass) {
-        float q[32], pr[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) {
-            q[i] = i < k ? Q[i * 32 + lane] : 0.f;
-            pr[i] = x * q[i];
-        }
-        const float coef = warp_reduce_scatter32(pr);  // lane i: <x, Q_i>
-        float a0 = x, a1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < 32; i += 2) {
-            a0 = fmaf(-__shfl_sync(0xffffffffu, coef, i), q[i], a0);
-            a1 = fmaf(-__shfl_sync(0xffffffffu, coef, i + 1), q[i + 1], a1);
-        }
-        x = a0 + a1;
-    }
-    return x;
-}
-
 __device__ __forceinline__ float warp_total(float v)
 {
     return __shfl_sync(0xffffffffu, warp_sum(v), 0);
 }
 
-// Golub-Kahan-Lanczos bidiagonalization with full reorthogonalization for an
-// m x n matrix with m, n <= 32 (column-major, leading dimension m) by one
-// warp: vectors hold one entry per lane, A v by broadcasting v's entries, A^T u
-// by a reduce-scatter of the lanes' products.  Runs min(m, n) steps (exact for
-// the top singular value in exact arithmetic) or stops at a breakdown; writes
-// the bidiagonal to ab and returns the number of steps.  U: 32 x 32, V: 33 x 32
-// floats of shared memory.
-__device__ int lanczos_warp32(const float* A, int m, int n, float* U, float* V, float* ab)
+// Largest singular value of the m x n matrix A (column-major, leading
+// dimension m; 2 <= m, n <= 32) by the whole block, through repeated
+// squaring.  G = A^T A or A A^T (the smaller, order d) has sigma_max^2 as its
+// top eigenvalue.  X_0 = G / tr(G) and X_{s+1} = X_s^2 / tr(X_s)^2 keep every
+// entry of the positive semidefinite X_s within [0, 1] in magnitude and its
+// top eigenvalue at least 1/d^2, while each other eigenvector's weight
+// shrinks as (lambda_k / lambda_1)^(2^s) against the top one: X_s tends to
+// the projector onto G's top eigenvector(s).  The Rayleigh quotient of G at
+// X's column with the largest diagonal entry then gives lambda_1, with an
+// error second order in the residual weights.  Squaring stops after at
+// least kSqMin steps once tr(X) moved by less than 1e-6 of itself (float
+// rounding alone moves it by about 1e-7): the trace stays put only when the
+// residual weights are negligible or the gap lambda_1 - lambda_2 is below
+// about 3e-3 / 2^kSqMin of lambda_1 (the quotient lies between the two), so
+// the error stays within a few float roundings either way.
+// Buffers: three 32 x kSqLD matrices and two diagonals (kSqFloats floats,
+// 16-byte aligned).  Returns sigma_max in every thread.
+__device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, float* s_out)
 {
-    const int lane = threadIdx.x & 31;
-    const int K = min(m, n);
-    float v = lane < n ? 1.f + 0.01f * (float)((lane * 37) % 11) : 0.f;  // fixed start vector
-    v *= rsqrtf(warp_total(v * v));
-    V[lane] = v;
-    float beta = 0.f, uprev = 0.f;
-    int steps = 0;
-    for (int k = 0; k < K; ++k) {
-        float u = 0.f;
-        for (int c = 0; c < n; ++c) {
-            const float vc = __shfl_sync(0xffffffffu, v, c);
-            u = lane < m ? fmaf(A[c * m + lane], vc, u) : 0.f;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = min(m, n);
+    const bool ata = n <= m;
+    // G, then X in two buffers (X_s in buffer s & 1), then their diagonals.
+    float* G = buf;
+    auto Xb = [&](int c) { return buf + (32 + 32 * c) * kSqLD; };
+    auto Db = [&](int c) { return buf + 96 * kSqLD + 32 * c; };
+    // Everything is 32 x 32 with zero padding beyond d: fixed, unrolled loops.
+    for (int t = threadIdx.x; t < kSqFloats; t += blockDim.x)
+        buf[t] = 0.f;
+    __syncthreads();
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int a = t >> 5, b = t & 31;
+        if (a < d && b < d) {
+            float acc = 0.f;
+            if (ata) {
+                for (int r = 0; r < m; ++r)
+                    acc = fmaf(A[a * m + r], A[b * m + r], acc);
+            } else {
+                for (int c = 0; c < n; ++c)
+                    acc = fmaf(A[c * m + a], A[c * m + b], acc);
+            }
+            G[a * kSqLD + b] = acc;
         }
-        u = lane < m ? fmaf(-beta, uprev, u) : 0.f;
-        __syncwarp();
-        u = warp_reorth32(u, U, k);
-        const float alpha = sqrtf(warp_total(u * u));
-        if (lane == 0)
-            ab[2 * k] = alpha;
-        if (!(alpha > 1e-30f))
-            break;
-        u *= 1.f / alpha;
-        U[k * 32 + lane] = u;
-        uprev = u;
-        steps = k + 1;
-        // A^T u: lane r holds u_r and row r of A; lane c receives column c's sum.
-        float pr[32];
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-            pr[c] = (c < n && lane < m) ? A[c * m + lane] * u : 0.f;
-        float vn = warp_reduce_scatter32(pr);
-        vn = lane < n ? fmaf(-alpha, v, vn) : 0.f;
-        __syncwarp();
-        vn = warp_reorth32(vn, V, k + 1);
-        beta = sqrtf(warp_total(vn * vn));
-        if (lane == 0)
-            ab[2 * k + 1] = beta;
-        if (!(beta > 1e-30f) || k + 1 == K)
-            break;
-        v = vn * (1.f / beta);
-        V[(k + 1) * 32 + lane] = v;
-        __syncwarp();
     }
-    __syncwarp();
-    return steps;
+    __syncthreads();
+    // Traces are summed in the same fixed order by every thread, so every
+    // thread takes the same decisions.
+    auto trace32 = [](const float* v, int stride) {
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            p[k & 3] += v[k * stride];
+        return (p[0] + p[1]) + (p[2] + p[3]);
+    };
+    const float tr = trace32(G, kSqLD + 1);
+    if (!(tr > 0.f))
+        return 0.f;
+    const float inv = 1.f / tr;
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int a = t >> 5, b = t & 31;
+        const float v = G[a * kSqLD + b] * inv;
+        Xb(0)[a * kSqLD + b] = v;
+        if (a == b)
+            Db(0)[a] = v;
+    }
+    __syncthreads();
+    int cur = 0;
+    float prev = 2.f;
+    for (int step = 0; step < kSqMax; ++step) {
+        const float trc = trace32(Db(cur), 1);
+        if (step >= kSqMin && fabsf(trc - prev) <= 1e-6f * trc)
+            break;
+        prev = trc;
+        const float sc = 1.f / (trc * trc);
+        const float* Xc = Xb(cur);
+        float* Xn = Xb(cur ^ 1);
+        float* dn = Db(cur ^ 1);
+        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+            const int a = t >> 5, b = t & 31;
+            const float4* ra = reinterpret_cast<const float4*>(Xc + a * kSqLD);
+            const float4* rb = reinterpret_cast<const float4*>(Xc + b * kSqLD);
+            float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const float4 xa = ra[k], xb = rb[k];
+                p[0] = fmaf(xa.x, xb.x, p[0]);
+                p[1] = fmaf(xa.y, xb.y, p[1]);
+                p[2] = fmaf(xa.z, xb.z, p[2]);
+                p[3] = fmaf(xa.w, xb.w, p[3]);
+            }
+            const float v = ((p[0] + p[1]) + (p[2] + p[3])) * sc;
+            Xn[a * kSqLD + b] = v;
+            if (a == b)
+                dn[a] = v;
+        }
+        __syncthreads();
+        cur ^= 1;
+    }
+    if (warp == 0) {
+        float best = lane < d ? Db(cur)[lane] : -1.f;
+        int c = lane;
+        for (int o = 16; o > 0; o >>= 1) {
+            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
+            const int oc = __shfl_xor_sync(0xffffffffu, c, o);
+            if (ob > best || (ob == best && oc < c)) {
+                best = ob;
+                c = oc;
+            }
+        }
+        const float x = Xb(cur)[lane * kSqLD + c];  // zero beyond d
+        float p[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+        for (int k = 0; k < 32; ++k)
+            p[k & 3] = fmaf(G[lane * kSqLD + k], __shfl_sync(0xffffffffu, x, k), p[k & 3]);
+        const float y = (p[0] + p[1]) + (p[2] + p[3]);
+        const float xy = warp_total(x * y), xx = warp_total(x * x);
+        if (lane == 0)
+            *s_out = sqrtf(fmaxf(0.f, xy / xx));
+    }
+    __syncthreads();
+    return *s_out;
 }
 
 struct LanczosWork {
@@ -625,8 +641,8 @@ __device__ __forceinline__ int tile_index(int I, int J, int nb)
 // the normalized output, and A' written over each staged block.
 // Requires T < 2^32 so that every S entry fits 32 bits.
 __device__ void sym_cell_pass(const FeatJob& J, int N, unsigned long long T, const unsigned long long* rs,
-                              const unsigned long long* cs, double mux, double muy, float* blk, Kahan& k_asm,
-                              Kahan& k_ent, Kahan& k_mi, double& cov)
+                              const unsigned long long* cs, float* blk, Kahan& k_asm, Kahan& k_ent, Kahan& k_mi,
+                              unsigned long long& cij)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nb = (N + 31) >> 5;
@@ -681,10 +697,9 @@ __device__ void sym_cell_pass(const FeatJob& J, int N, unsigned long long T, con
                 }
                 if (sv) {
                     const float t1 = __fmul_rn(pv, pv), t2 = neg_plogp(pv);
-                    const double tc = ((double)i - mux) * ((double)jc - muy) * (double)sv;
                     k_asm.add(twice ? 2.f * t1 : t1);
                     k_ent.add(twice ? 2.f * t2 : t2);
-                    cov += twice ? 2.0 * tc : tc;
+                    cij += (twice ? 2ull : 1ull) * (unsigned long long)(i * jc) * sv;
                 }
                 const unsigned long long ri = rs[i], cj = cs[jc];
                 if (ri && cj) {
@@ -883,7 +898,7 @@ __device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* t
 
 // Dynamic shared memory layout for a launch whose largest N is `N`.
 struct FeatLayout {
-    size_t marg, maps, dscr, dd, xs, ys, part, a, uv, total;
+    size_t marg, maps, dscr, xs, ys, part, a, uv, total;
     // Blocked symmetric path (N > 128), overlapping a and uv.
     size_t blk, bpart, qv, tri;
 };
@@ -903,15 +918,14 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     L.marg = take((size_t)5 * N * 8);
     L.maps = take((size_t)2 * N * 4);
     L.dscr = take(10 * 32 * sizeof(DF));
-    L.dd = take(6 * 32 * 8);
     L.xs = take((size_t)N * 4);
     L.ys = take((size_t)N * 4);
     L.part = take((size_t)kColGroups * 256 * 4);
     const size_t u0 = o;
     L.a = take((size_t)(nn < kSmemAFloats ? nn : kSmemAFloats) * 4);
-    // At least 32 x 32 + 33 x 32 floats: the one-warp path for supports <= 32.
+    // At least kSqFloats: the squaring path for supports <= 32.
     const long long uvf = uv < kSmemUVFloats ? uv : kSmemUVFloats;
-    L.uv = take((size_t)(uvf > 65 * 32 ? uvf : 65 * 32) * 4);
+    L.uv = take((size_t)(uvf > kSqFloats ? uvf : kSqFloats) * 4);
     const size_t u1 = o;
     L.blk = L.bpart = L.qv = L.tri = 0;
     if (N > 128) {
@@ -927,7 +941,7 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     return L;
 }
 
-__global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int maxN)
+__global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int maxN)
 {
     const FeatJob J = p.jobs[blockIdx.x];
     const int N = J.levels;
@@ -945,14 +959,15 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     int* rmap = reinterpret_cast<int*>(smem_raw + Lo.maps);                             // N
     int* cmap = rmap + N;                                                               // N
     DF* dscr = reinterpret_cast<DF*>(smem_raw + Lo.dscr);
-    double* dd = reinterpret_cast<double*>(smem_raw + Lo.dd);
-    __shared__ unsigned long long s_T, s_m[6];
+    __shared__ unsigned long long s_T, s_m[7], s_cij;
     __shared__ int s_nr, s_nc, s_stop;
     __shared__ float s_red[32], s_coef[kMaxLanczos + 1], s_ab[2 * kMaxLanczos + 2], s_sig;
     __shared__ unsigned s_msk[2][32];
 
     for (int k = threadIdx.x; k < 5 * N; k += blockDim.x)
         rs[k] = 0ull;
+    if (threadIdx.x == 0)
+        s_cij = 0ull;
     __syncthreads();
     // Exact integer marginals of P.  Warp w takes rows w, w + nwarps, ...; the
     // row sum is a warp reduction, the other marginals shared atomics.  For
@@ -999,7 +1014,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
     }
     // Totals, integer moments and the support maps (warp 0).
     if (warp == 0) {
-        unsigned long long T = 0, m_i = 0, m_j = 0, c2 = 0, m_s = 0, m_d = 0;
+        unsigned long long T = 0, m_i = 0, m_j = 0, c2 = 0, m_s = 0, m_d = 0, q_i = 0, q_j = 0;
         int nr = 0, nc = 0;
         for (int k0 = 0; k0 < 2 * N; k0 += 32) {
             const int k = k0 + lane;
@@ -1010,6 +1025,8 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
             m_i += (unsigned long long)k * r;
             m_j += (unsigned long long)k * c;
             c2 += (unsigned long long)k * k * d;
+            q_i += (unsigned long long)k * k * r;
+            q_j += (unsigned long long)k * k * c;
             m_d += (unsigned long long)k * d;
             m_s += (unsigned long long)k * sv;
             const unsigned rb = __ballot_sync(0xffffffffu, r != 0ull);
@@ -1029,6 +1046,8 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
             c2 += __shfl_xor_sync(0xffffffffu, c2, o);
             m_s += __shfl_xor_sync(0xffffffffu, m_s, o);
             m_d += __shfl_xor_sync(0xffffffffu, m_d, o);
+            q_i += __shfl_xor_sync(0xffffffffu, q_i, o);
+            q_j += __shfl_xor_sync(0xffffffffu, q_j, o);
         }
         if (lane == 0) {
             s_T = T;
@@ -1037,6 +1056,8 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
             s_m[2] = c2;
             s_m[3] = m_s;
             s_m[4] = m_d;
+            s_m[5] = q_i;
+            s_m[6] = q_j;
             s_nr = nr;
             s_nc = nc;
         }
@@ -1060,8 +1081,6 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
         }
         return;
     }
-    const double Td = (double)T;
-    const double mux = (double)s_m[0] / Td, muy = (double)s_m[1] / Td;
     const int nr = s_nr, nc = s_nc;
     const int K = min(kMaxLanczos, min(nr, nc));
     // Symmetric GLCMs too large for a full A' in shared memory take the
@@ -1081,9 +1100,9 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
 
     // Cell pass: normalized output, f1, f9, MI terms, covariance, A'.
     Kahan k_asm, k_ent, k_mi;
-    double cov = 0.0;
+    unsigned long long cij = 0;  // sum of i j S(i, j), exact
     if (big_sym)
-        sym_cell_pass(J, N, T, rs, cs, mux, muy, blk, k_asm, k_ent, k_mi, cov);
+        sym_cell_pass(J, N, T, rs, cs, blk, k_asm, k_ent, k_mi, cij);
     for (int t = threadIdx.x; !big_sym && t < NN; t += blockDim.x) {
         const int i = t / N, j = t - (t / N) * N;
         const unsigned long long s = cell(C, N, i, j, sym);
@@ -1093,7 +1112,7 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
         if (s) {
             k_asm.add(__fmul_rn(pv, pv));
             k_ent.add(neg_plogp(pv));
-            cov += ((double)i - mux) * ((double)j - muy) * (double)s;
+            cij += (unsigned long long)(i * j) * s;
         }
         const unsigned long long r = rs[i], c = cs[j];
         if (r && c) {
@@ -1116,7 +1135,6 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
 
     // Marginal passes (length N or 2N-1).
     Kahan k_idm, k_svar, k_sent, k_dvar, k_dent, k_hx, k_hy;
-    double vx = 0.0, vy = 0.0;
     const float f6 = __fdiv_rn((float)s_m[3], Tf);
     const float mean_d = __fdiv_rn((float)s_m[4], Tf);
     for (int k = threadIdx.x; k < 2 * N - 1; k += blockDim.x) {
@@ -1132,15 +1150,15 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
             k_dent.add(neg_plogp(pd));
             k_hx.add(neg_plogp(__fdiv_rn((float)rs[k], Tf)));
             k_hy.add(neg_plogp(__fdiv_rn((float)cs[k], Tf)));
-            vx += ((double)k - mux) * ((double)k - mux) * (double)rs[k];
-            vy += ((double)k - muy) * ((double)k - muy) * (double)cs[k];
         }
     }
+    for (int o = 16; o > 0; o >>= 1)
+        cij += __shfl_xor_sync(0xffffffffu, cij, o);
+    if (lane == 0 && cij)
+        atomicAdd(&s_cij, cij);  // complete after the block reduction's barriers
     DF v[10] = {k_asm.df(), k_ent.df(), k_mi.df(), k_idm.df(), k_svar.df(),
                 k_sent.df(), k_dvar.df(), k_dent.df(), k_hx.df(), k_hy.df()};
     block_reduce_df<10>(v, dscr);
-    double dv[3] = {cov, vx, vy};
-    block_reduce_d<3>(dv, dd);
 
     float mcc = 0.f;
     if (big_sym && nr >= 2) {
@@ -1148,15 +1166,8 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
                                  reinterpret_cast<float*>(smem_raw + Lo.tri),
                                  reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop, s_msk);
     } else if (nr >= 2 && nr <= 32 && nc <= 32 && a_smem) {
-        // Small supports: one warp runs the whole bidiagonalization.
-        float* U32 = reinterpret_cast<float*>(smem_raw + Lo.uv);
-        if (warp == 0) {
-            const int steps = lanczos_warp32(A, nr, nc, U32, U32 + 32 * 32, s_ab);
-            if (lane == 0)
-                s_stop = steps;
-        }
-        __syncthreads();
-        mcc = gk_sigma_max_block(s_ab, s_stop, s_msk);
+        // Small supports: repeated squaring by the whole block.
+        mcc = sigma_max_squaring(A, nr, nc, reinterpret_cast<float*>(smem_raw + Lo.uv), &s_sig);
     } else if (nr >= 2 && have_work) {
         LanczosWork w;
         w.xs = reinterpret_cast<float*>(smem_raw + Lo.xs);
@@ -1176,14 +1187,21 @@ __global__ void __launch_bounds__(kFeatThreads) k_haralick(FeatParams p, int max
         atomicOr(p.err, kErrInternal);
 
     if (threadIdx.x == 0) {
-        const double varx = dv[1] / Td, vary = dv[2] / Td;
-        const double sdx = sqrt(varx), sdy = sqrt(vary);
+        // f3 and f4 from exact integer moments: T^2 var_x = T sum i^2 r_i -
+        // (sum i r_i)^2, T^2 cov = T sum i j S(i, j) - (sum i r_i)(sum j c_j).
+        const __int128 Ti = (__int128)T;
+        const __int128 vxn = Ti * (__int128)s_m[5] - (__int128)s_m[0] * (__int128)s_m[0];
+        const __int128 vyn = Ti * (__int128)s_m[6] - (__int128)s_m[1] * (__int128)s_m[1];
+        const __int128 cvn = Ti * (__int128)s_cij - (__int128)s_m[0] * (__int128)s_m[1];
+        const double Td = (double)T;
+        const double varx = i128_to_double(vxn) / (Td * Td);
+        const double vxy = i128_to_double(vxn) * i128_to_double(vyn);
         const float mi = fmaxf(0.f, v[2].hi + v[2].lo);
         const float hx = v[8].hi + v[8].lo, hy = v[9].hi + v[9].lo;
         const float hmax = fmaxf(hx, hy);
         feat[0] = v[0].hi + v[0].lo;
         feat[1] = (float)s_m[2] / Tf;
-        feat[2] = (sdx * sdy > 0.0) ? (float)((dv[0] / Td) / (sdx * sdy)) : 1.f;
+        feat[2] = vxy > 0.0 ? (float)(i128_to_double(cvn) / sqrt(vxy)) : 1.f;
         feat[3] = (float)varx;
         feat[4] = v[3].hi + v[3].lo;
         feat[5] = f6;

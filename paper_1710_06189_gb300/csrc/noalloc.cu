@@ -74,19 +74,24 @@ struct NaShape {
     int groups_per_job, span, jobs;
 };
 
+// Bin rows per anchor level: layout 3 packs two partner levels per word.
+long long na_level_rows(int layout, int levels) { return layout == 3 ? (levels + 1) / 2 : levels; }
+int na_group_offsets(int layout) { return layout == 0 || layout == 3 ? 1 : 2; }
+
 NaShape na_shape(long long budget, int levels, int n_off, int layout, int rshift)
 {
     const long long wrow = (layout == 1 ? 2ll : 1ll) << rshift;
-    const int opg = layout == 0 ? 1 : 2;
+    const int opg = na_group_offsets(layout);
     const int groups = (n_off + opg - 1) / opg;
-    const long long per_group = (long long)levels * levels * wrow;
+    const long long per_level = na_level_rows(layout, levels) * wrow;
+    const long long per_group = (long long)levels * per_level;
     NaShape s{1, 0, 0};
     if (per_group <= budget) {
         s.groups_per_job = (int)(budget / per_group < groups ? budget / per_group : groups);
         s.span = levels;
         s.jobs = (groups + s.groups_per_job - 1) / s.groups_per_job;
     } else {
-        s.span = (int)(budget / ((long long)levels * wrow));
+        s.span = (int)(budget / per_level);
         if (s.span < 1)
             return NaShape{1, 0, 0};
         s.jobs = groups * ((levels + s.span - 1) / s.span);
@@ -151,13 +156,14 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     int rshift = 0, layout = 0;
     double best = 1e30;
     for (int r = 5; r >= 0; --r)
-        for (int lay : {1, 0, 2}) {
+        for (int lay : {1, 0, 2, 3}) {
             if (lay == 2 && 65535ll * (1 << r) / (16ll * kNaThreads) < 64)
                 continue;
             const NaShape s = na_shape(budget, levels, n_offsets, lay, r);
             if (s.jobs <= 0)
                 continue;
-            const double cost = n_offsets * conflict[r] + 0.6 * s.jobs + (lay == 2 ? 0.05 * n_offsets : 0.0);
+            const double cost = n_offsets * conflict[r] + 0.6 * s.jobs + (lay == 2 ? 0.05 * n_offsets : 0.0) +
+                                (lay == 3 ? 0.15 * n_offsets : 0.0);
             if (cost < best - 1e-9) {
                 best = cost;
                 rshift = r;
@@ -181,7 +187,7 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     const int strip_px = 32 * PX;
     const int n_strips = (width + strip_px - 1) / strip_px;
     const int n_bands = (height + kNaBand - 1) / kNaBand;
-    const int opg = layout == 0 ? 1 : 2;
+    const int opg = na_group_offsets(layout);
     const int per_job = shape.groups_per_job * opg;
     const int log2n = ilog2_or(levels);
     const bool aligned = ((reinterpret_cast<uintptr_t>(image) | (uintptr_t)pitch_bytes) & 15) == 0;
@@ -228,7 +234,8 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
             j.lv_lo = lv;
             j.lv_span = span;
             j.bytecode = (layout == 1 && rshift == 5 && span == levels && log2n >= 0 && levels <= 16) ? 1 : 0;
-            j.hist_words = (int)((long long)((cnt + opg - 1) / opg) * span * levels * ((layout == 1 ? 2 : 1) << rshift));
+            j.hist_words = (int)((long long)((cnt + opg - 1) / opg) * span * na_level_rows(layout, levels) *
+                                 ((layout == 1 ? 2 : 1) << rshift));
             j.item0 = n_items;
             j.n_job_items = n_strips * n_bands;
             const double votes_per_item = (double)kNaBand * strip_px * cnt * span / levels;
@@ -308,12 +315,12 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     size_t smem = 2 * (size_t)tile_rows * vote_row_bytes() + (size_t)max_words * 4;
     if (smem < 16)
         smem = 16;
-    int per_sm = vote_blocks_per_sm(bpp, kNaThreads, smem);
+    int per_sm = vote_blocks_per_sm(bpp, kNaThreads, smem, layout == 3);
     per_sm = per_sm < 1 ? 1 : per_sm;
     int grid = sms * per_sm;
     grid = grid < n_chunks ? grid : n_chunks;
     grid = grid < 1 ? 1 : grid;
-    NA_CK(launch_vote(vp, bpp, grid, kNaThreads, smem, stream));
+    NA_CK(launch_vote(vp, bpp, grid, kNaThreads, smem, stream, layout == 3));
     unsigned err_bits = 0;
     NA_CK(cudaMemcpyAsync(&err_bits, &dscr->words[0], sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
     NA_CK(cudaStreamSynchronize(stream));

@@ -332,7 +332,7 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
         return;
     }
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
-    if (PACK) {
+    if constexpr (PACK) {
         // Addresses and upper-half bits of the lane's votes first; a warp row
         // with no upper-half vote (flat and smooth regions) reduces with the
         // constant 1, so lanes that hit one word combine, the others with a
@@ -384,23 +384,24 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
                 red_shared_add_if(addr[v], ((upm >> v) & 1u) ? 0x10000u : 1u, (onm >> v) & 1u);
         }
         return;
-    }
+    } else {
 #pragma unroll
-    for (int m = 0; m < LW; ++m) {
+        for (int m = 0; m < LW; ++m) {
 #pragma unroll
-        for (int b = 0; b < 4; ++b) {
-            const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
-            const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
-            const uint32_t ii = SPLIT ? i - lo : i;
-            const uint32_t addr = h.base + (ii * N + jv) * h.stride;
-            const uint32_t inc = INC1 ? 1u : h.inc;
-            if (FULL && !SPLIT) {
-                red_shared_add(addr, inc);
-            } else {
-                uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
-                if (SPLIT)
-                    on &= ii < span ? 1u : 0u;
-                red_shared_add_if(addr, inc, on);
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
+                const uint32_t jv = __byte_perm(PW[m], 0u, 0x4440u | (uint32_t)b);
+                const uint32_t ii = SPLIT ? i - lo : i;
+                const uint32_t addr = h.base + (ii * N + jv) * h.stride;
+                const uint32_t inc = INC1 ? 1u : h.inc;
+                if (FULL && !SPLIT) {
+                    red_shared_add(addr, inc);
+                } else {
+                    uint32_t on = FULL ? 1u : ((mask >> (4 * m + b)) & 1u);
+                    if (SPLIT)
+                        on &= ii < span ? 1u : 0u;
+                    red_shared_add_if(addr, inc, on);
+                }
             }
         }
     }

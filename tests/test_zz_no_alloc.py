@@ -13,6 +13,8 @@ CASES = [
     ("iid", np.uint8, 777, 1031, 32, [(1, 0), (1, -1), (0, -1), (-1, -1)], 0),
     ("smooth", np.uint16, 300, 513, 256, [(1, 0), (0, -2), (-3, 1)], 0),
     ("iid", np.uint8, 65, 200, 8, [(1, 0), (2, -2), (7, 0), (0, 20)], 0),
+    ("constant", np.uint8, 1200, 1100, 256, [(1, 0), (1, -1), (0, -1), (-1, -1)], 0),
+    ("iid", np.uint8, 900, 1300, 256, [(1, 0), (1, -1), (0, -1), (-1, -1)], 0),
 ]
 
 
