@@ -146,9 +146,27 @@ __device__ __forceinline__ uint32_t level_of(const VoteJob& j, uint32_t v)
     return (uint32_t)(((unsigned long long)v * (unsigned)j.levels) >> (8 * j.bpp));
 }
 
-// 4 uint8 pixels -> 4 level bytes.  `bad` gets set if levels mode sees v >= N.
-__device__ __forceinline__ uint32_t quant_u8x4(const VoteJob& j, uint32_t w, bool& bad)
+// Quantization of a job, set once per tile: N a power of two and pixels not
+// already levels -- a shift and a mask per packed word.
+struct Quant {
+    bool fast;
+    uint32_t shift, mask;
+};
+
+__device__ __forceinline__ Quant quant_of(const VoteJob& j)
 {
+    Quant q;
+    q.fast = !j.levels_mode && j.log2n >= 0;
+    q.shift = q.fast ? (uint32_t)(8 - j.log2n) : 0u;
+    q.mask = 0x01010101u * (0xFFu >> q.shift);
+    return q;
+}
+
+// 4 uint8 pixels -> 4 level bytes.  `bad` gets set if levels mode sees v >= N.
+__device__ __forceinline__ uint32_t quant_u8x4(const VoteJob& j, const Quant& q, uint32_t w, bool& bad)
+{
+    if (q.fast)
+        return (w >> q.shift) & q.mask;
     if (j.levels_mode) {
         if (j.levels < 256)
             bad |= __vcmpgeu4(w, 0x01010101u * (uint32_t)j.levels) != 0u;
@@ -168,8 +186,11 @@ __device__ __forceinline__ uint32_t quant_u8x4(const VoteJob& j, uint32_t w, boo
 }
 
 // 4 uint16 pixels (two words) -> 4 level bytes.
-__device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, uint32_t w0, uint32_t w1, bool& bad)
+__device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, const Quant& q, uint32_t w0, uint32_t w1,
+                                                bool& bad)
 {
+    if (q.fast)
+        return (__byte_perm(w0, w1, 0x7531) >> q.shift) & q.mask;
     if (j.levels_mode) {
         const uint32_t hi = __byte_perm(w0, w1, 0x7531);
         const uint32_t lo = __byte_perm(w0, w1, 0x6420);
@@ -196,75 +217,69 @@ __device__ __forceinline__ uint32_t quant_u16x4(const VoteJob& j, uint32_t w0, u
 // A staged row of the tile as this lane sees it: levels of its PX pixels
 // (LW words) with one 4-level halo word on each side.
 template <int BPP>
-__device__ __forceinline__ void row_levels(const VoteJob& j, const uint8_t* trow, int lane, uint32_t (&A)[4 / BPP],
-                                           uint32_t& left, uint32_t& right, bool& bad)
+__device__ __forceinline__ void row_levels(const VoteJob& j, const Quant& q, const uint8_t* trow, int lane,
+                                           uint32_t (&A)[4 / BPP], uint32_t& left, uint32_t& right, bool& bad)
 {
     const uint8_t* c = trow + kHaloBytes + 16 * lane;
     const uint4 v = *reinterpret_cast<const uint4*>(c);
     if (BPP == 1) {
-        A[0] = quant_u8x4(j, v.x, bad);
-        A[1 % (4 / BPP)] = quant_u8x4(j, v.y, bad);
-        A[2 % (4 / BPP)] = quant_u8x4(j, v.z, bad);
-        A[3 % (4 / BPP)] = quant_u8x4(j, v.w, bad);
-        left = quant_u8x4(j, *reinterpret_cast<const uint32_t*>(c - 4), bad);
-        right = quant_u8x4(j, *reinterpret_cast<const uint32_t*>(c + 16), bad);
+        A[0] = quant_u8x4(j, q, v.x, bad);
+        A[1 % (4 / BPP)] = quant_u8x4(j, q, v.y, bad);
+        A[2 % (4 / BPP)] = quant_u8x4(j, q, v.z, bad);
+        A[3 % (4 / BPP)] = quant_u8x4(j, q, v.w, bad);
+        left = quant_u8x4(j, q, *reinterpret_cast<const uint32_t*>(c - 4), bad);
+        right = quant_u8x4(j, q, *reinterpret_cast<const uint32_t*>(c + 16), bad);
     } else {
-        A[0] = quant_u16x4(j, v.x, v.y, bad);
-        A[1] = quant_u16x4(j, v.z, v.w, bad);
+        A[0] = quant_u16x4(j, q, v.x, v.y, bad);
+        A[1] = quant_u16x4(j, q, v.z, v.w, bad);
         const uint2 l = *reinterpret_cast<const uint2*>(c - 8);
         const uint2 r = *reinterpret_cast<const uint2*>(c + 16);
-        left = quant_u16x4(j, l.x, l.y, bad);
-        right = quant_u16x4(j, r.x, r.y, bad);
+        left = quant_u16x4(j, q, l.x, l.y, bad);
+        right = quant_u16x4(j, q, r.x, r.y, bad);
     }
 }
 
 // Anchor levels only (no halos needed).
 template <int BPP>
-__device__ __forceinline__ void anchor_levels(const VoteJob& j, const uint8_t* trow, int lane,
+__device__ __forceinline__ void anchor_levels(const VoteJob& j, const Quant& q, const uint8_t* trow, int lane,
                                               uint32_t (&A)[4 / BPP], bool& bad)
 {
     const uint4 v = *reinterpret_cast<const uint4*>(trow + kHaloBytes + 16 * lane);
     if (BPP == 1) {
-        A[0] = quant_u8x4(j, v.x, bad);
-        A[1 % (4 / BPP)] = quant_u8x4(j, v.y, bad);
-        A[2 % (4 / BPP)] = quant_u8x4(j, v.z, bad);
-        A[3 % (4 / BPP)] = quant_u8x4(j, v.w, bad);
+        A[0] = quant_u8x4(j, q, v.x, bad);
+        A[1 % (4 / BPP)] = quant_u8x4(j, q, v.y, bad);
+        A[2 % (4 / BPP)] = quant_u8x4(j, q, v.z, bad);
+        A[3 % (4 / BPP)] = quant_u8x4(j, q, v.w, bad);
     } else {
-        A[0] = quant_u16x4(j, v.x, v.y, bad);
-        A[1] = quant_u16x4(j, v.z, v.w, bad);
+        A[0] = quant_u16x4(j, q, v.x, v.y, bad);
+        A[1] = quant_u16x4(j, q, v.z, v.w, bad);
     }
 }
 
 // Partner level words aligned with the anchor words: PW[m] holds the levels
-// of the partners of anchors 4m .. 4m + 3 for horizontal offset dx.
+// of the partners of anchors 4m .. 4m + 3 for horizontal offset dx in
+// [-4, 4].  Byte t = 4m + dx + 4 of the extended row [left, B..., right] is
+// the partner of anchor byte 4m; with t0 = dx + 4 = 4 hi + sh (hi in {0, 1},
+// sh in [0, 4]) it is byte sh of the word pair (B[m + hi], B[m + hi + 1]),
+// so each word is one byte permute with selector 0x3210 + 0x1111 sh.  hi and
+// the selector are set once per offset.
+__device__ __forceinline__ int2 partner_sel(int dx)
+{
+    const int t0 = dx + 4;
+    const int hi = t0 >= 4 ? 1 : 0;
+    return make_int2(hi, 0x3210 + 0x1111 * (t0 - 4 * hi));
+}
+
 template <int BPP>
-__device__ __forceinline__ void partner_words(int dx, const uint32_t (&B)[4 / BPP + 2], uint32_t (&PW)[4 / BPP])
+__device__ __forceinline__ void partner_words(int2 ps, const uint32_t (&B)[4 / BPP + 2], uint32_t (&PW)[4 / BPP])
 {
     constexpr int LW = 4 / BPP;
-    // Byte t = 4m + dx + 4 of the extended row [left, B..., right].
-#define GLCM_PW(D)                                                                       \
-    case D:                                                                              \
-        _Pragma("unroll") for (int m = 0; m < LW; ++m)                                   \
-        {                                                                                \
-            constexpr int t0 = D + 4;                                                    \
-            const int t = 4 * m + t0;                                                    \
-            PW[m] = (t0 & 3) == 0 ? B[t >> 2] : __funnelshift_r(B[t >> 2], B[(t >> 2) + 1], 8 * (t0 & 3)); \
-        }                                                                                \
-        break;
-    switch (dx) {
-        GLCM_PW(-4)
-        GLCM_PW(-3)
-        GLCM_PW(-2)
-        GLCM_PW(-1)
-        GLCM_PW(0)
-        GLCM_PW(1)
-        GLCM_PW(2)
-        GLCM_PW(3)
-        GLCM_PW(4)
-        default:
-            break;
+#pragma unroll
+    for (int m = 0; m < LW; ++m) {
+        const uint32_t lo = ps.x ? B[m + 1] : B[m];
+        const uint32_t hi = ps.x ? B[m + 2] : B[m + 1];
+        PW[m] = __byte_perm(lo, hi, (uint32_t)ps.y);
     }
-#undef GLCM_PW
 }
 
 // Where offset o of a job votes: shared byte address of (bin 0, copy 0),
@@ -751,7 +766,7 @@ __device__ void fill_tile_plain(const VoteJob& j, const Tile& t, uint8_t* buf)
 // Votes of one staged tile: warp w takes anchor rows y0 + w, y0 + w + nwarps, ...
 template <int BPP, bool PACKED>
 __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, const Tile& t, const uint8_t* buf,
-                                          const HistRef* s_off_h, const int2* s_off_d, unsigned* err)
+                                          const HistRef* s_off_h, const int4* s_off_d, unsigned* err)
 {
     constexpr int PX = 16 / BPP;
     constexpr int LW = PX / 4;
@@ -761,15 +776,16 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
     const bool lane_interior = xl >= 4 && xl + PX + 4 <= j.W;
     const bool full = __all_sync(0xffffffffu, lane_interior);
     const int wrem = j.W - xl;
+    const Quant q = quant_of(j);
     for (int y = t.y0 + warp; y < t.y1; y += nwarps) {
         bool bad_a = false;
         uint32_t A[LW];
-        anchor_levels<BPP>(j, buf + (y - t.ty0) * kRowBytes, lane, A, bad_a);
+        anchor_levels<BPP>(j, q, buf + (y - t.ty0) * kRowBytes, lane, A, bad_a);
         int cur_dy = 0x7fffffff;
         uint32_t B[LW + 2];
         bool bad_b = false;
         for (int o = 0; o < j.n_off; ++o) {
-            const int2 d = s_off_d[o];
+            const int4 d = s_off_d[o];  // dx, dy, partner word pair, byte selector
             const int yp = y + d.y;
             if (yp < 0 || yp >= j.H)
                 continue;
@@ -778,7 +794,7 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
             if (d.y != cur_dy) {
                 bad_b = false;
                 uint32_t P[LW];
-                row_levels<BPP>(j, buf + (yp - t.ty0) * kRowBytes, lane, P, B[0], B[LW + 1], bad_b);
+                row_levels<BPP>(j, q, buf + (yp - t.ty0) * kRowBytes, lane, P, B[0], B[LW + 1], bad_b);
 #pragma unroll
                 for (int w = 0; w < LW; ++w)
                     B[w + 1] = P[w];
@@ -791,7 +807,7 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
             }
             if (fast) {
                 uint32_t PW[LW];
-                partner_words<BPP>(d.x, B, PW);
+                partner_words<BPP>(make_int2(d.z, d.w), B, PW);
                 uint32_t mask = 0xFFFFu;
                 if (!full) {
                     // Anchors k with xl + k < W and 0 <= xl + k + dx < W.
@@ -810,7 +826,7 @@ __device__ __forceinline__ void vote_tile(const VoteJob& j, const VoteJob* jg, c
 // Jobs whose offsets span too many rows to stage: per-pixel votes only.
 template <int BPP>
 __device__ void vote_tile_unstaged(const VoteJob& j, const VoteJob* jg, const Tile& t, const HistRef* s_off_h,
-                                   const int2* s_off_d, unsigned* err)
+                                   const int4* s_off_d, unsigned* err)
 {
     constexpr int PX = 16 / BPP;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
@@ -840,7 +856,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
     __shared__ __align__(8) uint64_t s_bar[2];
     __shared__ int s_chunk, s_ok;
     __shared__ HistRef s_off_h[kMaxJobOffsets];
-    __shared__ int2 s_off_d[kMaxJobOffsets];
+    __shared__ int4 s_off_d[kMaxJobOffsets];
     uint8_t* tiles = smem;
     uint32_t* hist = reinterpret_cast<uint32_t*>(smem + 2 * p.tile_bytes);
     for (int i = threadIdx.x; i < p.max_hist_words; i += blockDim.x)
@@ -890,7 +906,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_glcm_vote(VoteParams p)
             if (threadIdx.x < j.n_off) {
                 const VoteOffset vo = p.offs[j.off0 + threadIdx.x];
                 s_off_h[threadIdx.x] = hist_ref(j, threadIdx.x, hbase, 0);
-                s_off_d[threadIdx.x] = make_int2(vo.dx, vo.dy);
+                const int2 ps = partner_sel(vo.dx);  // used only for |dx| <= kFastMaxDx
+                s_off_d[threadIdx.x] = make_int4(vo.dx, vo.dy, ps.x, ps.y);
             }
             __syncthreads();
             cur = ch.x;
