@@ -185,6 +185,42 @@ def test_features_of_special_matrices(gctx):
     assert np.all(f[0] == 0)
 
 
+@pytest.mark.parametrize("n", [2, 5, 8, 16, 31, 32])
+def test_features_small_supports(gctx, n):
+    """Supports of at most 32 levels (f14 by repeated squaring of A'^T A'):
+    block-diagonal GLCMs whose top singular values of A' repeat (two and
+    three disconnected level groups give one and two extra singular values
+    of exactly 1), rectangular supports (anchor and partner level sets
+    differ), a total of 1, and random dense counts, plain and symmetric."""
+    rng = np.random.default_rng(700 + n)
+    mats = []
+    for groups in (2, 3):
+        m = np.zeros((n, n), dtype=np.uint32)
+        edges = np.linspace(0, n, groups + 1).astype(int)
+        for a, b in zip(edges[:-1], edges[1:]):
+            if b > a:
+                m[a:b, a:b] = rng.integers(1, 50, (b - a, b - a))
+        mats.append(m)
+    rect = np.zeros((n, n), dtype=np.uint32)
+    rect[: max(1, n // 2), n // 3:] = rng.integers(0, 9, (max(1, n // 2), n - n // 3))
+    mats.append(rect)
+    one = np.zeros((n, n), dtype=np.uint32)
+    one[n - 1, 0] = 1
+    mats.append(one)
+    mats.append(rng.integers(0, 1000, (n, n)).astype(np.uint32))
+    mats.append(rng.integers(0, 3, (n, n)).astype(np.uint32) * (rng.random((n, n)) < 0.3))
+    big = rng.integers(0, 1 << 22, (n, n)).astype(np.uint32)   # total near 2^32 / 4 at n = 32
+    mats.append(big)
+    mats = np.stack(mats).astype(np.uint32)
+    for sym in (False, True):
+        if sym and np.any(mats.astype(np.uint64).sum(axis=(1, 2)) * 2 >= (1 << 32)):
+            mats = mats.copy()
+            mats[-1] //= 4
+        c = torch.from_numpy(mats.view(np.int32)).cuda()
+        f = gctx.features(c, n, symmetric=sym).cpu().numpy()
+        assert_features(f, oracle.haralick_batch(mats, sym), n, what=f"n={n} sym={sym}")
+
+
 def test_naive_scheme1_matches(gctx):
     img = S.smooth(2, 300, 400, 4.0, np.uint8)
     c = torch.empty((8, 8), dtype=torch.int32, device="cuda")
