@@ -282,6 +282,18 @@ __device__ __forceinline__ void partner_words(int2 ps, const uint32_t (&B)[4 / B
     }
 }
 
+// Byte-wise arithmetic on four packed levels, no carry or borrow between
+// bytes: (x - y) mod 256, and (d + q) mod 256 for q < 128.
+__device__ __forceinline__ uint32_t bytes_sub(uint32_t x, uint32_t y)
+{
+    return ((x | 0x80808080u) - (y & 0x7F7F7F7Fu)) ^ ((x ^ ~y) & 0x80808080u);
+}
+
+__device__ __forceinline__ uint32_t bytes_add_small(uint32_t d, uint32_t qq)
+{
+    return ((d & 0x7F7F7F7Fu) + qq) ^ (d & 0x80808080u);
+}
+
 // Where offset o of a job votes: shared byte address of (bin 0, copy 0),
 // bytes between bins (between words in layout 3), and the increment (1 or
 // 1 << 16; layout 3 picks it per vote).
@@ -347,7 +359,50 @@ __device__ __forceinline__ void vote_words(const VoteJob& j, const uint32_t (&A)
         return;
     }
     const uint32_t N = (uint32_t)j.levels, lo = (uint32_t)j.lv_lo, span = (uint32_t)j.lv_span;
-    if constexpr (PACK) {
+    if constexpr (PACK && P2 && !SPLIT) {
+        // Power-of-two N, whole level range: the packed column (j + q) mod H
+        // and the half bit (bit log2(H) of (j - i + q) mod N) of four votes at
+        // a time, byte-wise (N divides 256, so byte arithmetic mod 256 keeps
+        // the low bits right).  A warp row with no upper-half vote among its
+        // active votes reduces with the constant 1, the others with a per-vote
+        // increment.
+        const uint32_t Hh = N >> 1, q = Hh >> 1, lh = (uint32_t)j.log2n - 1u;
+        const uint32_t Mh = (Hh - 1u) * 0x01010101u, qq = q * 0x01010101u;
+        uint32_t U4[LW], anyu = 0u, addr[4 * LW];
+#pragma unroll
+        for (int m = 0; m < LW; ++m) {
+            const uint32_t C4 = ((PW[m] & Mh) + qq) & Mh;
+            U4[m] = (bytes_add_small(bytes_sub(PW[m], A[m]), qq) >> lh) & 0x01010101u;
+            // Active votes of this word as bytes (the 4 mask bits spread to bits 0, 8, 16, 24).
+            const uint32_t act = FULL ? 0x01010101u : (((mask >> (4 * m)) & 0xFu) * 0x00204081u) & 0x01010101u;
+            anyu |= U4[m] & act;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const uint32_t i = __byte_perm(A[m], 0u, 0x4440u | (uint32_t)b);
+                const uint32_t c = __byte_perm(C4, 0u, 0x4440u | (uint32_t)b);
+                addr[4 * m + b] = h.base + (i * Hh + c) * h.stride;
+            }
+        }
+        // All addresses first, then the reductions back to back: lanes that
+        // share a word in a flat region combine best that way (measured).
+        if (!__any_sync(0xffffffffu, anyu != 0u)) {
+#pragma unroll
+            for (int v = 0; v < 4 * LW; ++v) {
+                if (FULL)
+                    red_shared_add(addr[v], 1u);
+                else
+                    red_shared_add_if(addr[v], 1u, (mask >> v) & 1u);
+            }
+        } else {
+#pragma unroll
+            for (int v = 0; v < 4 * LW; ++v) {
+                const uint32_t up = (U4[v >> 2] >> (8 * (v & 3))) & 1u;
+                const uint32_t on = FULL ? 1u : ((mask >> v) & 1u);
+                red_shared_add_if(addr[v], up ? 0x10000u : 1u, on);
+            }
+        }
+        return;
+    } else if constexpr (PACK) {
         // Addresses and upper-half bits of the lane's votes first; a warp row
         // with no upper-half vote (flat and smooth regions) reduces with the
         // constant 1, so lanes that hit one word combine, the others with a
