@@ -17,6 +17,7 @@ from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_INPUT_
                       glcm_set_timing, glcm_set_vote_config, glcm_synchronize, glcm_windows)
 
 __all__ = [
+    "PreparedBatch",
     "binding", "Context", "Server", "GlcmError", "GLCM_OK", "GLCM_ERR_BUSY", "GLCM_ERR_NOMEM", "GLCM_ERR_RANGE", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_U8",
     "GLCM_U16", "glcm_compute", "glcm_compute_batch", "glcm_compute_naive", "glcm_create", "glcm_destroy",
     "glcm_features", "glcm_get_timing", "glcm_last_error", "glcm_offset_from_angle", "glcm_set_timing",
@@ -48,6 +49,16 @@ def image_args(img):
         raise ValueError("image must be a 2-D array with unit column stride")
     dt = {np.dtype(np.uint8): GLCM_U8, np.dtype(np.uint16): GLCM_U16}[a.dtype]
     return a, a.shape[1], a.shape[0], a.strides[0], dt
+
+
+class PreparedBatch:
+    """Descriptors of a batch (a ctypes glcm_desc array), the output buffers,
+    and the offset arrays the descriptors point to (kept alive here)."""
+
+    def __init__(self, descs, outs, keep):
+        self.descs = descs
+        self.outs = outs
+        self._keep = keep
 
 
 class Context:
@@ -108,6 +119,14 @@ class Context:
     def batch(self, jobs):
         """jobs: list of dicts {image, levels, offsets, flags, counts, normalized, features};
         missing outputs are allocated (counts always; normalized / features when True)."""
+        prepared = self.prepare(jobs)
+        glcm_compute_batch(self.ctx, prepared.descs)
+        return prepared.outs
+
+    def prepare(self, jobs):
+        """The descriptors of a batch, built once: run(prepared) then repeats the
+        batch on the same buffers with a single call (no per-image Python work).
+        Outputs are allocated as in batch()."""
         torch = _torch()
         descs = []
         outs = []
@@ -128,8 +147,12 @@ class Context:
             ft = ft if ft is not False else None
             descs.append(binding.make_desc(src, w, h, pitch, dt, N, jb["offsets"], jb.get("flags", 0), c, nm, ft))
             outs.append((c, nm, ft))
-        glcm_compute_batch(self.ctx, descs)
-        return outs
+        return PreparedBatch(binding.desc_array(descs), outs, descs)
+
+    def run(self, prepared):
+        """Run a batch from prepare() again (same images and output buffers)."""
+        glcm_compute_batch(self.ctx, prepared.descs)
+        return prepared.outs
 
     def windows(self, img, levels: int, win: int, stride: int, offsets, flags: int = 0, counts: bool = True,
                 maps: bool = True):

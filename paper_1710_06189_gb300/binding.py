@@ -191,9 +191,15 @@ def make_desc(image, width, height, pitch_bytes, dtype, levels, offsets, flags, 
     return d, offs
 
 
+def desc_array(descs):
+    """A ctypes glcm_desc array of make_desc results, reusable across calls."""
+    return (glcm_desc * len(descs))(*[d[0] if isinstance(d, tuple) else d for d in descs])
+
+
 def glcm_compute_batch(ctx, descs):
-    arr = (glcm_desc * len(descs))(*[d[0] if isinstance(d, tuple) else d for d in descs])
-    return _check(ctx, load().glcm_compute_batch(ctx, arr, len(descs)))
+    """descs: make_desc results, or an array from desc_array (reused as is)."""
+    arr = descs if isinstance(descs, ctypes.Array) else desc_array(descs)
+    return _check(ctx, load().glcm_compute_batch(ctx, arr, len(arr)))
 
 
 def glcm_enqueue_batch(ctx, descs):

@@ -707,47 +707,75 @@ int collect_device_errors(glcm_ctx* ctx)
 }
 
 // Image rows from host memory to the device (see copy_rows_to_device).  The
-// destination rows are 16-byte aligned; thread k of a row writes destination
-// bytes [16k, 16k + 16) from two aligned 16-byte source blocks realigned by
-// funnel shifts.  Only blocks that hold at least one byte of the row are read,
-// so no read leaves the pages of the caller's rows; destination bytes past
-// row_bytes (up to the next 16) are don't-care padding.
+// destination rows are 16-byte aligned; unit k of a row is destination bytes
+// [16k, 16k + 16).  A row that starts on a 16-byte boundary is copied one
+// aligned 16-byte block per unit; otherwise a unit comes from two aligned
+// blocks realigned by funnel shifts.  Only blocks that hold at least one byte
+// of the row are read, so no read leaves the pages of the caller's rows;
+// destination bytes past row_bytes (up to the next 16) are don't-care padding.
+// Each thread keeps kCopyUnroll units in flight (the reads cross the
+// chip-to-chip link, so bytes in flight set the rate).
+constexpr int kCopyUnroll = 4;
+
+__device__ __forceinline__ uint4 load_row_unit(const uint8_t* src, size_t spitch, size_t row_bytes, long long r,
+                                               size_t u)
+{
+    const uintptr_t row = reinterpret_cast<uintptr_t>(src) + (uintptr_t)(r * (long long)spitch);
+    const uintptr_t first = row + 16 * u;
+    const unsigned off = (unsigned)(first & 15);
+    if (off == 0)
+        return *reinterpret_cast<const uint4*>(first);
+    const uintptr_t b0 = first & ~(uintptr_t)15;
+    const uintptr_t last_blk = (row + row_bytes - 1) & ~(uintptr_t)15;
+    const uint4 x = *reinterpret_cast<const uint4*>(b0);
+    const uint4 y = b0 + 16 <= last_blk ? *reinterpret_cast<const uint4*>(b0 + 16) : make_uint4(0, 0, 0, 0);
+    const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+    const unsigned q = off >> 2, sh = 8 * (off & 3);
+    uint32_t o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        // words q + i and q + i + 1 of the 8, selected without dynamic indexing
+        uint32_t lo = w[i], hi = w[i + 1];
+        if (q == 1) {
+            lo = w[i + 1];
+            hi = w[i + 2];
+        } else if (q == 2) {
+            lo = w[i + 2];
+            hi = w[i + 3];
+        } else if (q == 3) {
+            lo = w[i + 3];
+            hi = i + 4 < 8 ? w[i + 4] : 0u;
+        }
+        o[i] = __funnelshift_r(lo, hi, sh);
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
 __global__ void k_copy_rows(uint8_t* __restrict__ dst, size_t dpitch, const uint8_t* __restrict__ src, size_t spitch,
                             size_t row_bytes, int rows)
 {
     const size_t units = (row_bytes + 15) / 16;
     const long long total = (long long)units * rows;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const long long r = k / (long long)units;
-        const size_t u = (size_t)(k - r * (long long)units);
-        const uintptr_t row = reinterpret_cast<uintptr_t>(src) + (uintptr_t)(r * (long long)spitch);
-        const uintptr_t first = row + 16 * u;
-        const uintptr_t b0 = first & ~(uintptr_t)15;
-        const uintptr_t last_blk = (row + row_bytes - 1) & ~(uintptr_t)15;
-        const uint4 x = *reinterpret_cast<const uint4*>(b0);
-        const uint4 y = b0 + 16 <= last_blk ? *reinterpret_cast<const uint4*>(b0 + 16) : make_uint4(0, 0, 0, 0);
-        const uint32_t w[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
-        const unsigned off = (unsigned)(first & 15);
-        const unsigned q = off >> 2, sh = 8 * (off & 3);
-        uint32_t o[4];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k0 < total; k0 += kCopyUnroll * stride) {
+        uint4 v[kCopyUnroll];
+        long long at[kCopyUnroll];
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            // words q + i and q + i + 1 of the 8, selected without dynamic indexing
-            uint32_t lo = w[i], hi = w[i + 1];
-            if (q == 1) {
-                lo = w[i + 1];
-                hi = w[i + 2];
-            } else if (q == 2) {
-                lo = w[i + 2];
-                hi = w[i + 3];
-            } else if (q == 3) {
-                lo = w[i + 3];
-                hi = i + 4 < 8 ? w[i + 4] : 0u;
+        for (int e = 0; e < kCopyUnroll; ++e) {
+            const long long k = k0 + e * stride;
+            at[e] = -1;
+            if (k < total) {
+                const long long r = total <= 0xFFFFFFFFll ? (long long)((unsigned)k / (unsigned)units)
+                                                           : k / (long long)units;
+                const size_t u = (size_t)(k - r * (long long)units);
+                v[e] = load_row_unit(src, spitch, row_bytes, r, u);
+                at[e] = r * (long long)dpitch + 16 * (long long)u;
             }
-            o[i] = __funnelshift_r(lo, hi, sh);
         }
-        *reinterpret_cast<uint4*>(dst + r * (long long)dpitch + 16 * u) = make_uint4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+        for (int e = 0; e < kCopyUnroll; ++e)
+            if (at[e] >= 0)
+                *reinterpret_cast<uint4*>(dst + at[e]) = v[e];
     }
 }
 
@@ -1340,6 +1368,8 @@ int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, Sp
 // Images with expensive epilogues (features of N > 64) come first, and their
 // groups' epilogues run on the side stream on a few SMs reserved from the
 // votes.  Results come back to the host buffers once, at the end.
+constexpr int kCopySMs = 8;
+
 int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
 {
     std::vector<glcm_desc> descs;
@@ -1355,7 +1385,7 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
         }
     std::vector<glcm_desc> dd(descs);
     std::vector<size_t> img_off(n), dpitch(n);
-    std::vector<char> host_img(n), heavy(n);
+    std::vector<char> host_img(n);
     size_t ib = 0, ob = 0;
     auto r256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
     struct OutMap {
@@ -1365,7 +1395,6 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
     for (int i = 0; i < n; ++i) {
         const glcm_desc& d = descs[i];
         const int bpp = d.dtype == GLCM_U8 ? 1 : 2;
-        heavy[i] = d.features && d.levels > 64;
         host_img[i] = !is_device_ptr(d.image);
         dpitch[i] = (((size_t)d.width * bpp) + 15) & ~(size_t)15;
         img_off[i] = ib;
@@ -1402,18 +1431,49 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
         if (om[i].feat != (size_t)-1)
             dd[i].features = reinterpret_cast<float*>(go + om[i].feat);
     }
-    // Groups of consecutive images with about equal bytes.
-    const int G = std::min(n, 3);
+    // Groups of consecutive images, each voting as soon as its copies are in.
+    // Host-to-device copies run at about 210 GB/s whatever moves them, so the
+    // aim is to keep votes going while the rest copies in: the heavy images
+    // (epilogue at N > 64, first in the order) form the first group -- their
+    // votes cost several times their copy time -- and the light images follow
+    // in three groups (55 / 25 / 20 % of their bytes), the last short so that
+    // the exposed tail after the last copy stays small.  Without heavy images
+    // the cuts are at 1/4, 5/8 and 7/8 of the bytes.  (Measured against 3, 4
+    // and 6 groups of equal bytes, and 6 with small first groups.)
     std::vector<int> gend;
     {
-        const size_t total = std::max<size_t>(1, ib);
+        int n_heavy = 0;
+        size_t heavy_bytes = 0, total = 0;
+        for (int i = 0; i < n; ++i) {
+            const size_t b = host_img[i] ? r256(dpitch[i] * descs[i].height) : 0;
+            total += b;
+            if (descs[i].features && descs[i].levels > 64) {
+                ++n_heavy;
+                heavy_bytes += b;
+            }
+        }
+        std::vector<size_t> cuts;  // cumulative byte targets of the group ends but the last
+        if (n_heavy > 0 && n_heavy < n) {
+            cuts.push_back(heavy_bytes);
+            cuts.push_back(heavy_bytes + (total - heavy_bytes) * 55 / 100);
+            cuts.push_back(heavy_bytes + (total - heavy_bytes) * 80 / 100);
+        } else {
+            cuts.push_back(total / 4);
+            cuts.push_back(total * 5 / 8);
+            cuts.push_back(total * 7 / 8);
+        }
         size_t acc = 0;
-        int g = 1;
+        size_t c = 0;
         for (int i = 0; i < n; ++i) {
             acc += host_img[i] ? r256(dpitch[i] * descs[i].height) : 0;
-            if ((acc * G >= total * g && (int)gend.size() < G - 1) || i == n - 1) {
+            if (i == n - 1) {
                 gend.push_back(i + 1);
-                ++g;
+                break;
+            }
+            if (c < cuts.size() && acc >= cuts[c]) {
+                gend.push_back(i + 1);
+                while (c < cuts.size() && acc >= cuts[c])
+                    ++c;
             }
         }
     }
@@ -1424,19 +1484,7 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
     }
     if (ctx->hb_tab.size() < gend.size())
         ctx->hb_tab.resize(gend.size());
-    // Plans and tables of every group first: their uploads must not queue
-    // behind the image copies on a copy engine.
-    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
-    std::vector<SplitBatch> sbs(gend.size());
     int first = 0;
-    for (size_t g = 0; g < gend.size(); ++g) {
-        auto& tab = ctx->hb_tab[g];
-        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sbs[g], tab[0], tab[1], tab[2]));
-        if (reserve > 0)
-            sbs[g].p8.max_ctas = sbs[g].p16.max_ctas = ctx->sm_count - reserve;
-        first = gend[g];
-    }
-    first = 0;
     for (size_t g = 0; g < gend.size(); ++g) {
         for (int i = first; i < gend[g]; ++i) {
             if (!host_img[i])
@@ -1448,6 +1496,39 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
         CK(cudaEventRecord(ctx->stripe_events[g], ctx->copy_stream));
         first = gend[g];
     }
+    // Plans and tables of every group while the copies run (the copies go
+    // through a copy kernel for registered memory, so the tables' small
+    // uploads do not queue behind them on a copy engine).
+    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
+    std::vector<SplitBatch> sbs(gend.size());
+    first = 0;
+    for (size_t g = 0; g < gend.size(); ++g) {
+        auto& tab = ctx->hb_tab[g];
+        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sbs[g], tab[0], tab[1], tab[2]));
+        // While later groups' copies are in flight, kCopySMs SMs stay free for the
+        // copy kernel: a vote CTA fills its SM's register file, so without them
+        // the copies stall behind the votes (measured).
+        const int copy_sms = g + 1 < gend.size() ? kCopySMs : 0;
+        if (reserve + copy_sms > 0)
+            sbs[g].p8.max_ctas = sbs[g].p16.max_ctas = ctx->sm_count - reserve - copy_sms;
+        first = gend[g];
+    }
+    // Results of images [i0, i1) to the caller's host buffers on stream st.
+    auto read_back = [&](int i0, int i1, cudaStream_t st) -> int {
+        for (int i = i0; i < i1; ++i) {
+            const size_t nn = (size_t)descs[i].levels * descs[i].levels;
+            if (om[i].counts != (size_t)-1)
+                CK(cudaMemcpyAsync(descs[i].counts, dd[i].counts, descs[i].n_offsets * nn * 4,
+                                   cudaMemcpyDeviceToHost, st));
+            if (om[i].norm != (size_t)-1)
+                CK(cudaMemcpyAsync(descs[i].normalized, dd[i].normalized, descs[i].n_offsets * nn * 4,
+                                   cudaMemcpyDeviceToHost, st));
+            if (om[i].feat != (size_t)-1)
+                CK(cudaMemcpyAsync(descs[i].features, dd[i].features,
+                                   (size_t)descs[i].n_offsets * GLCM_N_FEATURES * 4, cudaMemcpyDeviceToHost, st));
+        }
+        return GLCM_OK;
+    };
     bool forked = false;
     first = 0;
     for (size_t g = 0; g < gend.size(); ++g) {
@@ -1458,35 +1539,19 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
             TRY(enqueue_vote(ctx, sb.p8, tab[0], tab[1], sb.c8, true, false, nullptr));
         if (!sb.p16.jobs.empty())
             TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, false, nullptr));
-        bool group_heavy = false;
-        for (int i = first; i < gend[g]; ++i)
-            group_heavy |= heavy[i] != 0;
-        if (group_heavy) {
-            CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-            CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
-            TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr, ctx->side_stream));
-            forked = true;
-        } else {
-            TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr));
-        }
+        // Every group's epilogue and read-back on the side stream, so the next
+        // group's vote does not wait behind them and only the last group's
+        // read-back is exposed.
+        CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+        CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
+        TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr, ctx->side_stream));
+        TRY(read_back(first, gend[g], ctx->side_stream));
+        forked = true;
         first = gend[g];
     }
     if (forked) {
         CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
         CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
-    }
-    for (int i = 0; i < n; ++i) {
-        const size_t nn = (size_t)descs[i].levels * descs[i].levels;
-        if (om[i].counts != (size_t)-1)
-            CK(cudaMemcpyAsync(descs[i].counts, dd[i].counts, descs[i].n_offsets * nn * 4, cudaMemcpyDeviceToHost,
-                               ctx->stream));
-        if (om[i].norm != (size_t)-1)
-            CK(cudaMemcpyAsync(descs[i].normalized, dd[i].normalized, descs[i].n_offsets * nn * 4,
-                               cudaMemcpyDeviceToHost, ctx->stream));
-        if (om[i].feat != (size_t)-1)
-            CK(cudaMemcpyAsync(descs[i].features, dd[i].features,
-                               (size_t)descs[i].n_offsets * GLCM_N_FEATURES * 4, cudaMemcpyDeviceToHost,
-                               ctx->stream));
     }
     return collect_device_errors(ctx);
 }

@@ -97,3 +97,33 @@ def test_host_buffer_batch(gctx, pinned):
             assert np.array_equal(h["counts"].numpy().view(np.uint32), P), (im.shape, n, rep)
             assert np.array_equal(h["features"].numpy(), ft.cpu().numpy())
             assert np.array_equal(h["normalized"].numpy(), nm.cpu().numpy())
+
+
+def test_prepared_batch_repeats(gctx):
+    """prepare() builds a batch's descriptors once; run() repeats it on the same
+    buffers: pinned host images and results in one batch, device ones in
+    another, each run equal to the oracle and to batch()."""
+    jobs = _jobs(6)
+    spec_h, spec_d = [], []
+    for im, n, o, f in jobs:
+        outs = [torch.empty((len(o), n, n), dtype=torch.int32).pin_memory(),
+                torch.empty((len(o), n, n), dtype=torch.float32).pin_memory(),
+                torch.empty((len(o), 14), dtype=torch.float32).pin_memory()]
+        spec_h.append(dict(image=torch.from_numpy(np.ascontiguousarray(im)).pin_memory(), levels=n, offsets=o,
+                           flags=f, counts=outs[0], normalized=outs[1], features=outs[2]))
+        spec_d.append(dict(image=torch.from_numpy(im).cuda(), levels=n, offsets=o, flags=f, normalized=True,
+                           features=True))
+    ph, pd = gctx.prepare(spec_h), gctx.prepare(spec_d)
+    want = gctx.batch([dict(s, normalized=True, features=True, counts=None) for s in spec_d])
+    torch.cuda.synchronize()
+    for rep in range(3):
+        gctx.run(ph)
+        dev = gctx.run(pd)
+        torch.cuda.synchronize()
+        for (im, n, o, f), h, (c, nm, ft), (wc, wn, wf) in zip(jobs, spec_h, dev, want):
+            P = oracle.glcm(im, n, o)
+            assert np.array_equal(h["counts"].numpy().view(np.uint32), P), (im.shape, n, rep)
+            assert np.array_equal(to_u32(c), P)
+            assert np.array_equal(h["features"].numpy(), wf.cpu().numpy())
+            assert np.array_equal(ft.cpu().numpy(), wf.cpu().numpy())
+            assert np.array_equal(h["normalized"].numpy(), wn.cpu().numpy())
