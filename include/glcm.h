@@ -274,10 +274,12 @@ int glcm_compute_noalloc(const void *image, int width, int height, size_t pitch_
  *   - admits queued requests in arrival order while their device footprint
  *     (pitched image + counts + normalized + features) fits in the free
  *     arena, and enqueues their image copies on the copy stream;
- *   - gives every admitted request not yet launched to the next idle lane as
- *     one batch (at most max_batch requests): the lane waits for those
- *     copies, runs the batch's votes and epilogue, and copies the results to
- *     the requests' host buffers;
+ *   - gives the admitted requests not yet launched to the next idle lane as
+ *     one batch (at most max_batch requests and, past its first request, at
+ *     most 256 MiB of images, so that a burst votes batch by batch while the
+ *     later batches still copy): the lane waits for those copies, runs the
+ *     batch's votes and epilogue, and copies the results to the requests'
+ *     host buffers;
  *   - retires finished batches, frees their arena space and wakes waiters.
  * So requests that arrive while others are on the GPU join the next batch as
  * lanes and memory free up, and copies overlap earlier batches' kernels.

@@ -73,6 +73,7 @@ struct glcm_ctx {
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
+    int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
     unsigned* d_words = nullptr;  // [0] error bits, [1] work-item counter
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
     DevBuf hb_img, hb_out;        // host-buffer batches: staged images, device results
@@ -254,14 +255,19 @@ JobShape job_shape(const glcm_ctx* ctx, int levels, int n_off, int layout, int r
     return s;
 }
 
-// Default vote configuration from a cost model in units of one conflict-free
-// shared-memory reduction per pixel: each offset costs the bank-conflict
-// factor of its copy count (measured: 32 interleaved copies never conflict,
-// a single copy costs ~3x on random bins), each pass over the image ~0.6,
-// packed halves (layout 3) ~0.15 per offset for the half select and spills.
+// Default vote configuration (used when the autotuner has not set one for a
+// class) from a cost model in units of one conflict-free shared-memory
+// reduction per pixel, calibrated on timing probes of the kernel: every pass
+// over the image costs ~2 (tile staging and anchor levels); every offset voted
+// in a pass ~1.5 (partner words and dispatch) plus the bank-conflict factor of
+// the copy count (32 interleaved copies never conflict; a single copy costs
+// ~2x over the benchmark's image mix) plus ~1.5 for packed halves (layout 3, more arithmetic
+// per vote) or ~2 for two offsets in 16-bit halves (layout 2: merges every
+// few rows, no constant increment for the upper halves).  A level-split job
+// votes all its offsets in every part.
 VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
 {
-    static const double conflict[6] = {3.0, 3.0, 2.8, 2.5, 2.0, 1.0};  // by log2 copies
+    static const double conflict[6] = {2.2, 2.0, 1.8, 1.6, 1.4, 1.0};  // by log2 copies
     VoteCfg best;
     double best_cost = 1e30;
     for (int r = 5; r >= 0; --r) {
@@ -271,8 +277,9 @@ VoteCfg default_cfg(const glcm_ctx* ctx, int levels, int n_off)
             const JobShape s = job_shape(ctx, levels, n_off, layout, r);
             if (s.jobs <= 0)
                 continue;
-            const double cost = n_off * conflict[r] + 0.6 * s.jobs + (layout == 2 ? 0.05 * n_off : 0.0) +
-                                (layout == 3 ? 0.15 * n_off : 0.0);
+            const int parts = (levels + s.span - 1) / s.span;
+            const double per_off = 1.5 + conflict[r] + (layout == 3 ? 1.5 : 0.0) + (layout == 2 ? 2.0 : 0.0);
+            const double cost = 2.0 * s.jobs + (double)n_off * parts * per_off;
             if (cost < best_cost - 1e-9) {
                 best_cost = cost;
                 best.rshift = r;
@@ -487,7 +494,7 @@ int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 {
     const size_t smem = vote_smem(plan);
     const int per_sm = std::max(1, vote_blocks_per_sm(plan.bpp, plan.threads, smem, plan_packed(plan)));
-    int ctas = ctx->sm_count * per_sm;
+    int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve) * per_sm;
     if (plan.max_ctas > 0)
         ctas = std::min(ctas, plan.max_ctas * per_sm);
     return std::max(1, std::min((int)plan.chunks.size(), ctas));
@@ -786,11 +793,10 @@ __global__ void k_copy_rows(uint8_t* __restrict__ dst, size_t dpitch, const uint
 // aligned reads, realigned on the device): on GB300
 // (host memory behind the chip-to-chip link) copy-engine transfers from host
 // memory held back the kernels of other streams until every queued transfer
-// had finished, while a copy kernel overlaps them.  Other host memory takes
+// had finished, while a copy kernel overlaps them (the vote launches that
+// run beside it leave it a few SMs).  Other host memory takes
 // cudaMemcpyAsync (one flat copy when both sides have the same pitch) or
-// cudaMemcpy2DAsync, as does every copy when allow_kernel is false (the
-// serving loop: its lanes' vote launches fill every SM, and copy CTAs waiting
-// for SMs cost more there than the copy engine's hold-back; measured).
+// cudaMemcpy2DAsync, as does every copy when allow_kernel is false.
 cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes,
                                       int rows, cudaStream_t st, bool allow_kernel)
 {
@@ -814,6 +820,12 @@ cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src,
     if (dpitch == spitch)
         return cudaMemcpyAsync(dst, src, spitch * (size_t)(rows - 1) + row_bytes, cudaMemcpyHostToDevice, st);
     return cudaMemcpy2DAsync(dst, dpitch, src, spitch, row_bytes, rows, cudaMemcpyHostToDevice, st);
+}
+
+void glcm::set_vote_sm_reserve(glcm_ctx* ctx, int sms)
+{
+    if (ctx)
+        ctx->sm_reserve = std::max(0, std::min(sms, ctx->sm_count - 1));
 }
 
 namespace {

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+struct glcm_ctx;  // the context (glcm_capi.cu; opaque in the public header)
+
 namespace glcm {
 
 // Fast-path horizontal reach: a lane holds its own pixels plus one word of
@@ -129,5 +131,8 @@ int vote_row_bytes();
 // memory, else cudaMemcpy(2D)Async); defined in glcm_capi.cu.
 cudaError_t copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
                                 cudaStream_t st, bool allow_kernel = true);
+// Every vote launch of `ctx` leaves `sms` SMs free (for a concurrent copy
+// kernel; a vote CTA fills its SM's register file); defined in glcm_capi.cu.
+void set_vote_sm_reserve(::glcm_ctx* ctx, int sms);
 
 }  // namespace glcm

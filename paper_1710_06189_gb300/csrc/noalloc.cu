@@ -152,7 +152,10 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const long long budget = (optin - 2 * kNaTileRows * vote_row_bytes() - 4096) / 4;
-    static const double conflict[6] = {3.0, 3.0, 2.8, 2.5, 2.0, 1.0};
+    // The context planner's cost model (default_cfg): ~2 per pass over the
+    // image, per offset voted in a pass ~1.5 plus the copy count's conflict
+    // factor, plus ~1.5 for packed halves or ~2 for two offsets in halves.
+    static const double conflict[6] = {2.2, 2.0, 1.8, 1.6, 1.4, 1.0};
     int rshift = 0, layout = 0;
     double best = 1e30;
     for (int r = 5; r >= 0; --r)
@@ -162,8 +165,9 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
             const NaShape s = na_shape(budget, levels, n_offsets, lay, r);
             if (s.jobs <= 0)
                 continue;
-            const double cost = n_offsets * conflict[r] + 0.6 * s.jobs + (lay == 2 ? 0.05 * n_offsets : 0.0) +
-                                (lay == 3 ? 0.15 * n_offsets : 0.0);
+            const int parts = (levels + s.span - 1) / s.span;
+            const double per_off = 1.5 + conflict[r] + (lay == 3 ? 1.5 : 0.0) + (lay == 2 ? 2.0 : 0.0);
+            const double cost = 2.0 * s.jobs + (double)n_offsets * parts * per_off;
             if (cost < best - 1e-9) {
                 best = cost;
                 rshift = r;

@@ -7,8 +7,9 @@
 // stream, and launches whatever has been admitted as one batch on the next
 // idle lane (a context with its own stream), so copies of new requests run
 // under the kernels of earlier batches and several batches can be on the GPU
-// at once.  Only the public context API is used for the compute itself
-// (glcm_enqueue_batch, glcm_synchronize, glcm_get_timing).
+// at once.  The compute itself goes through the public context API
+// (glcm_enqueue_batch, glcm_synchronize, glcm_get_timing); each lane context
+// also leaves a few SMs to the image copy kernel.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -57,6 +58,15 @@ struct Batch {
 };
 
 size_t r256(size_t b) { return glcm_arena::Arena::round_up(b); }
+
+// Image bytes in one batch, at most (a batch always takes at least one
+// request): a batch waits for all its copies before it votes, so a burst cut
+// into batches of about 1 ms of copying at 210 GB/s votes batch by batch
+// while the next batches still copy, instead of copying everything first.
+constexpr size_t kBatchImageBytes = 256ull << 20;
+
+// SMs every lane's vote launches leave to the image copy kernel.
+constexpr int kServerCopySMs = 8;
 
 std::string g_server_create_error;
 
@@ -180,7 +190,7 @@ bool admit(glcm_server* s)
     for (Req* r : take) {
         const int bpp = r->d.dtype == GLCM_U8 ? 1 : 2;
         cudaError_t e = glcm::copy_rows_to_device(s->base + r->off, r->dpitch, r->d.image, r->d.pitch_bytes,
-                                                  (size_t)r->d.width * bpp, r->d.height, s->copy, false);
+                                                  (size_t)r->d.width * bpp, r->d.height, s->copy);
         r->copied = take_event(s);
         if (e == cudaSuccess && r->copied)
             e = cudaEventRecord(r->copied, s->copy);
@@ -214,12 +224,15 @@ bool launch(glcm_server* s)
         // The batch: staged requests in admission order; a levels-mode
         // request runs alone so that a range error is its own.
         std::vector<Req*> b;
-        size_t k = 0;
+        size_t k = 0, bytes = 0;
         for (; k < s->staged.size() && (int)b.size() < s->max_batch; ++k) {
             Req* r = s->staged[k];
             const bool alone = (r->d.flags & GLCM_INPUT_LEVELS) != 0;
             if (alone && !b.empty())
                 break;
+            if (!b.empty() && bytes + r->img_bytes > kBatchImageBytes)
+                break;
+            bytes += r->img_bytes;
             b.push_back(r);
             if (alone) {
                 ++k;
@@ -392,6 +405,10 @@ extern "C" int glcm_server_create(glcm_server** out, int device, size_t hbm_budg
             cudaStreamDestroy(ln.stream);
             break;
         }
+        // Image copies go through the copy kernel (copy-engine transfers from
+        // host memory held back the lanes' kernels until every queued transfer
+        // was done); the lanes' votes leave it kServerCopySMs SMs.
+        glcm::set_vote_sm_reserve(ln.ctx, kServerCopySMs);
         s->lanes.push_back(ln);
     }
     if (rc != GLCM_OK) {
