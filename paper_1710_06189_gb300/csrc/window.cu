@@ -10,6 +10,8 @@
 // quantized to levels, in shared memory once; each warp then owns one window
 // and keeps its histograms in shared memory with 8- or 16-bit counters
 // packed into words (a window of 15 x 15 has at most 225 pairs per offset).
+// The counter width is a template parameter and power-of-two N takes shifts,
+// so no vote, count or map bin needs an integer division.
 #include "glcm_internal.cuh"
 
 namespace glcm {
@@ -27,8 +29,24 @@ __device__ __forceinline__ uint32_t px_at(const WindowParams& p, int x, int y)
     return (uint32_t)__ldg(row + 2 * x) | ((uint32_t)__ldg(row + 2 * x + 1) << 8);
 }
 
-__global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int cbits, int hist_words)
+// Row and column of bin b of an N x N GLCM (l2 = log2 N, or -1).
+__device__ __forceinline__ void bin_ij(int b, int N, int l2, int& i, int& j)
 {
+    if (l2 >= 0) {
+        i = b >> l2;
+        j = b & (N - 1);
+    } else {
+        i = b / N;
+        j = b - i * N;
+    }
+}
+
+template <int CB>
+__global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int hist_words)
+{
+    constexpr int kPwLog = CB == 8 ? 2 : (CB == 16 ? 1 : 0);  // log2(counters per word)
+    constexpr uint32_t kPwMask = (1u << kPwLog) - 1u;
+    constexpr uint32_t cmask = CB == 32 ? 0xFFFFFFFFu : ((1u << CB) - 1u);
     extern __shared__ __align__(16) uint32_t sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int S = p.stride, Wn = p.win, N = p.levels, NN = N * N;
@@ -60,11 +78,13 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
         hist[k] = 0u;
     __syncwarp();
     const int lx0 = wxl * S, ly0 = wyl * S;
-    const int per_word = 32 / cbits;
+    const int l2 = (N & (N - 1)) == 0 ? __ffs(N) - 1 : -1;
     const uint32_t hist_base = static_cast<uint32_t>(__cvta_generic_to_shared(hist));
     bool bad = false;
+    // Anchor t = lane + 32k of the window as (ay, ax), stepped without divisions.
+    const int q32 = 32 / Wn, r32 = 32 - q32 * Wn;
+    int ay = lane / Wn, ax = lane - ay * Wn;
     for (int t = lane; t < Wn * Wn; t += 32) {
-        const int ay = t / Wn, ax = t - ay * Wn;
         const uint32_t i = lv[(ly0 + ay) * RW + lx0 + ax];
         for (int o = 0; o < p.n_off; ++o) {
             const int bx = ax + p.dx[o], by = ay + p.dy[o];
@@ -76,9 +96,15 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
                 continue;
             }
             const uint32_t idx = (uint32_t)(o * NN) + i * (uint32_t)N + jv;
-            const uint32_t word = idx / per_word;
-            const uint32_t sh = (idx - word * per_word) * cbits;
+            const uint32_t word = idx >> kPwLog;
+            const uint32_t sh = (idx & kPwMask) * CB;
             asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(hist_base + 4u * word), "r"(1u << sh));
+        }
+        ax += r32;
+        ay += q32;
+        if (ax >= Wn) {
+            ax -= Wn;
+            ++ay;
         }
     }
     if (bad)
@@ -86,13 +112,12 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
     __syncwarp();
 
     const long long win_id = (long long)wy * p.nwx + wx;
-    const uint32_t cmask = cbits == 32 ? 0xFFFFFFFFu : ((1u << cbits) - 1u);
+    auto count_of = [&](uint32_t idx) { return (hist[idx >> kPwLog] >> ((idx & kPwMask) * CB)) & cmask; };
     for (int o = 0; o < p.n_off; ++o) {
         // Counts out and the window's total for this offset.
         unsigned long long tot = 0;
         for (int b = lane; b < NN; b += 32) {
-            const uint32_t idx = (uint32_t)(o * NN + b);
-            const uint32_t c = (hist[idx / per_word] >> ((idx % per_word) * cbits)) & cmask;
+            const uint32_t c = count_of((uint32_t)(o * NN + b));
             tot += c;
             if (p.counts)
                 p.counts[(win_id * p.n_off + o) * NN + b] = c;
@@ -105,13 +130,11 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
         float con = 0.f, asmv = 0.f, idm = 0.f, ent = 0.f;
         if (tot > 0) {
             for (int b = lane; b < NN; b += 32) {
-                const int i = b / N, j = b - (b / N) * N;
-                const uint32_t idx = (uint32_t)(o * NN + b);
-                uint32_t c = (hist[idx / per_word] >> ((idx % per_word) * cbits)) & cmask;
-                if (p.symmetric) {
-                    const uint32_t idt = (uint32_t)(o * NN + j * N + i);
-                    c += (hist[idt / per_word] >> ((idt % per_word) * cbits)) & cmask;
-                }
+                int i, j;
+                bin_ij(b, N, l2, i, j);
+                uint32_t c = count_of((uint32_t)(o * NN + b));
+                if (p.symmetric)
+                    c += count_of((uint32_t)(o * NN + j * N + i));
                 if (!c)
                     continue;
                 const float pv = __fdiv_rn((float)c, Tf);
@@ -152,15 +175,23 @@ cudaError_t launch_windows(const WindowParams& p, cudaStream_t s)
     const size_t smem = (size_t)((RW * RH + 1) / 2) * 4 + (size_t)hist_words * 4 * kWX * kWY;
     if (smem > (size_t)vote_max_smem_optin())
         return cudaErrorInvalidConfiguration;
-    static size_t set_to = 0;
-    if (smem > set_to) {
-        cudaError_t e = cudaFuncSetAttribute(k_window_glcm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static size_t set_to[3] = {0, 0, 0};
+    const int ci = cbits == 8 ? 0 : (cbits == 16 ? 1 : 2);
+    if (smem > set_to[ci]) {
+        const void* fn = cbits == 8 ? (const void*)k_window_glcm<8>
+                                    : (cbits == 16 ? (const void*)k_window_glcm<16> : (const void*)k_window_glcm<32>);
+        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess)
             return e;
-        set_to = smem;
+        set_to[ci] = smem;
     }
     dim3 grid((p.nwx + kWX - 1) / kWX, (p.nwy + kWY - 1) / kWY);
-    k_window_glcm<<<grid, kWinThreads, smem, s>>>(p, cbits, hist_words);
+    if (cbits == 8)
+        k_window_glcm<8><<<grid, kWinThreads, smem, s>>>(p, hist_words);
+    else if (cbits == 16)
+        k_window_glcm<16><<<grid, kWinThreads, smem, s>>>(p, hist_words);
+    else
+        k_window_glcm<32><<<grid, kWinThreads, smem, s>>>(p, hist_words);
     return cudaGetLastError();
 }
 
