@@ -169,6 +169,38 @@ def oracle_sample(jobs, seconds: float):
     return done_pairs / el / 1e9, f"{k} whole 4096^2 images of the sweep (counts + features), {el:.1f} s, 1 thread"
 
 
+def oracle_sample_all_cores(jobs, seconds: float):
+    """The same oracle on every host core: one thread per core, each taking whole
+    images of the workload in turn until `seconds` have passed (the oracle's C
+    counting loop runs outside the GIL); returns (Gpairs/s, threads, desc)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import oracle
+    oracle.build()
+    threads = max(1, len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1))
+    t0 = time.perf_counter()
+    stop = t0 + seconds
+
+    def worker(w):
+        done, n, k = 0, 0, w
+        while time.perf_counter() < stop:
+            j = jobs[k % len(jobs)]
+            img = j["image"]
+            P = oracle.glcm(img, j["levels"], j["offsets"])
+            oracle.haralick_batch(P, True)
+            done += pairs_of(img.shape[1], img.shape[0], j["offsets"])
+            n += 1
+            k += threads
+        return done, n
+
+    with ThreadPoolExecutor(threads) as ex:
+        res = list(ex.map(worker, range(threads)))
+    el = time.perf_counter() - t0
+    pairs = sum(r[0] for r in res)
+    images = sum(r[1] for r in res)
+    return pairs / el / 1e9, threads, f"{images} whole 4096^2 images of the sweep on {threads} threads, {el:.1f} s"
+
+
 def run_reference(args):
     import numpy as np  # noqa: F401
 
@@ -400,6 +432,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-all-seconds", type=float, default=6.0,
+                    help="seconds of the all-core oracle run beside the 1-thread one (0: skip)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
     ap.add_argument("--no-tune", action="store_true", help="use the planner's default vote configurations")
@@ -551,6 +585,9 @@ def main():
     if not args.no_cpu_baseline and world == 1:
         v, desc = oracle_sample(jobs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+        if args.cpu_all_seconds > 0:
+            va, nt, da = oracle_sample_all_cores(jobs, args.cpu_all_seconds)
+            line["cpu_baseline"]["all_cores"] = {"value": va, "unit": UNIT, "cores": nt, "sample": da}
     print(json.dumps(line))
     ctx.close()
     if dist is not None:
