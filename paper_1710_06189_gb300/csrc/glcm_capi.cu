@@ -70,7 +70,8 @@ struct glcm_ctx {
     bool own_stream = false;
     cudaStream_t copy_stream = nullptr;
     cudaStream_t side_stream = nullptr;  // epilogues overlapped with votes in split batches
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaStream_t epi_stream = nullptr;   // light groups' epilogues in host-buffer batches
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
     int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
@@ -147,6 +148,8 @@ int ensure(glcm_ctx* ctx, DevBuf& b, size_t bytes)
         cudaStreamSynchronize(ctx->stream);
         if (ctx->side_stream)
             cudaStreamSynchronize(ctx->side_stream);
+        if (ctx->epi_stream)
+            cudaStreamSynchronize(ctx->epi_stream);
         cudaFree(b.p);
         ctx->used -= b.cap;
         b.p = nullptr;
@@ -948,8 +951,10 @@ extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, 
     }
     if (cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&ctx->epi_stream, cudaStreamNonBlocking) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
         glcm_destroy(ctx);
         return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
@@ -977,6 +982,8 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaStreamSynchronize(ctx->copy_stream);
     if (ctx->side_stream)
         cudaStreamSynchronize(ctx->side_stream);
+    if (ctx->epi_stream)
+        cudaStreamSynchronize(ctx->epi_stream);
     for (auto& kv : ctx->graphs)
         destroy_graph(kv.second);
     for (DevBuf* b : {&ctx->jobs, &ctx->offs, &ctx->feat, &ctx->work, &ctx->img, &ctx->counts, &ctx->norm,
@@ -1007,6 +1014,10 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaStreamDestroy(ctx->copy_stream);
     if (ctx->side_stream)
         cudaStreamDestroy(ctx->side_stream);
+    if (ctx->epi_stream)
+        cudaStreamDestroy(ctx->epi_stream);
+    if (ctx->ev_join2)
+        cudaEventDestroy(ctx->ev_join2);
     if (ctx->ev_fork)
         cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join)
@@ -1551,19 +1562,27 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
             TRY(enqueue_vote(ctx, sb.p8, tab[0], tab[1], sb.c8, true, false, nullptr));
         if (!sb.p16.jobs.empty())
             TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, false, nullptr));
-        // Every group's epilogue and read-back on the side stream, so the next
+        // Every group's epilogue and read-back off the vote stream, so the next
         // group's vote does not wait behind them and only the last group's
-        // read-back is exposed.
+        // read-back is exposed: heavy groups on the side stream, light ones on
+        // their own stream, so a light epilogue does not queue behind a heavy
+        // one (their tables are per group; light epilogues use no global scratch).
+        bool group_heavy = false;
+        for (int i = first; i < gend[g]; ++i)
+            group_heavy |= descs[i].features && descs[i].levels > 64;
+        cudaStream_t es = group_heavy ? ctx->side_stream : ctx->epi_stream;
         CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
-        CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
-        TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr, ctx->side_stream));
-        TRY(read_back(first, gend[g], ctx->side_stream));
+        CK(cudaStreamWaitEvent(es, ctx->ev_fork, 0));
+        TRY(enqueue_features(ctx, sb.feats, tab[2], sb.max_levels, false, nullptr, es));
+        TRY(read_back(first, gend[g], es));
         forked = true;
         first = gend[g];
     }
     if (forked) {
         CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
+        CK(cudaEventRecord(ctx->ev_join2, ctx->epi_stream));
         CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join2, 0));
     }
     return collect_device_errors(ctx);
 }
