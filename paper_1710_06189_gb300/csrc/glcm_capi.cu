@@ -504,11 +504,12 @@ int grid_for(const glcm_ctx* ctx, const VotePlan& plan)
 }
 
 // Split every job of a plan into chunks of chunk_items consecutive items,
-// capped so that the launch has at least ~3 chunks per CTA to balance.
+// capped so that the launch has at least ~4 chunks per CTA to balance
+// (measured against 1, 2, 3 and 6).
 void build_chunks(VotePlan& plan, int ctas)
 {
     plan.chunks.clear();
-    const int cap = std::max(1, plan.n_items / std::max(1, 3 * ctas));
+    const int cap = std::max(1, plan.n_items / std::max(1, 4 * ctas));
     for (int jb = 0; jb < (int)plan.jobs.size(); ++jb) {
         const VoteJob& j = plan.jobs[jb];
         const int cs = std::max(1, std::min(j.chunk_items, cap));
