@@ -34,3 +34,23 @@ def test_windows_levels_and_u16(gctx):
     torch.cuda.synchronize()
     want = oracle.window_glcm(img, 32, offs, 9, 3)
     assert np.array_equal(to_u32(c).reshape(want.shape), want)
+
+
+@pytest.mark.parametrize("win, stride, n, sym", [(21, 5, 12, True), (260, 1, 4, False)])
+def test_windows_wide_counters(gctx, win, stride, n, sym):
+    """Windows with more than 255 pairs per offset (16-bit counters: 21 x 21)
+    and more than 65535 (32-bit counters: 260 x 260), a level count that is not
+    a power of two, counts and maps against the oracle."""
+    side = win + 10 * stride
+    img = S.smooth(40 + win, side, side, 3.0, np.uint8)
+    offs = [(1, 0), (1, -1)] if win < 100 else [(1, 0)]
+    c, m = gctx.windows(torch.from_numpy(img).cuda(), n, win, stride, offs, flags=1 if sym else 0)
+    torch.cuda.synchronize()
+    want = oracle.window_glcm(img, n, offs, win, stride)
+    nw = (side - win) // stride + 1
+    got = to_u32(c).reshape(nw * nw, len(offs), n, n)
+    assert np.array_equal(got, want)
+    maps = oracle.window_maps(want, symmetric=sym)
+    g = m.cpu().numpy().reshape(4, len(offs), nw * nw).transpose(0, 2, 1).astype(np.float64)
+    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / (n * n), 1.0, 1.0])[:, None, None])
+    assert (np.abs(g - maps) / scale).max() <= 1e-5
