@@ -127,6 +127,7 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
         if (!p.maps)
             continue;
         const float Tf = p.symmetric ? 2.f * (float)tot : (float)tot;
+        const float invT = tot > 0 ? __frcp_rn(Tf) : 0.f;  // p = c / T as c * (1 / T): within 1.5 ulp
         float con = 0.f, asmv = 0.f, idm = 0.f, ent = 0.f;
         if (tot > 0) {
             for (int b = lane; b < NN; b += 32) {
@@ -137,11 +138,11 @@ __global__ void __launch_bounds__(kWinThreads) k_window_glcm(WindowParams p, int
                     c += count_of((uint32_t)(o * NN + j * N + i));
                 if (!c)
                     continue;
-                const float pv = __fdiv_rn((float)c, Tf);
+                const float pv = __fmul_rn((float)c, invT);
                 const float d2 = (float)((i - j) * (i - j));
                 con = __fadd_rn(con, __fmul_rn(d2, pv));
                 asmv = __fadd_rn(asmv, __fmul_rn(pv, pv));
-                idm = __fadd_rn(idm, __fdiv_rn(pv, __fadd_rn(1.f, d2)));
+                idm = __fadd_rn(idm, __fmul_rn(pv, __frcp_rn(__fadd_rn(1.f, d2))));
                 ent = __fsub_rn(ent, __fmul_rn(pv, logf(pv)));
             }
         }
