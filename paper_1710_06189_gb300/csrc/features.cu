@@ -384,11 +384,6 @@ __device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk
     return block_multisect(below, L + 1, 0.f, hi, true, 0, nw < 16 ? nw : 16, 3, s_msk);
 }
 
-__device__ __forceinline__ float warp_total(float v)
-{
-    return __shfl_sync(0xffffffffu, warp_sum(v), 0);
-}
-
 // Largest singular value of the m x n matrix A (column-major, leading
 // dimension m; 2 <= m, n <= 32) by the whole block, through repeated
 // squaring.  G = A^T A or A A^T (the smaller, order d) has sigma_max^2 as its
@@ -419,13 +414,28 @@ __device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, fl
     for (int t = threadIdx.x; t < kSqFloats; t += blockDim.x)
         buf[t] = 0.f;
     __syncthreads();
+    // For A^T A the lanes read columns of A m floats apart, one bank when m is
+    // a multiple of 32: the columns are first copied 33 floats apart into the
+    // second X buffer (unused until the first squaring rewrites it whole).
+    const float* Ac = A;
+    int lda = m;
+    if (ata) {
+        float* Ap = Xb(1);
+        for (int t = threadIdx.x; t < n * m; t += blockDim.x) {
+            const int c = t / m, r = t - c * m;
+            Ap[c * 33 + r] = A[t];
+        }
+        __syncthreads();
+        Ac = Ap;
+        lda = 33;
+    }
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int a = t >> 5, b = t & 31;
         if (a < d && b < d) {
             float acc = 0.f;
             if (ata) {
                 for (int r = 0; r < m; ++r)
-                    acc = fmaf(A[a * m + r], A[b * m + r], acc);
+                    acc = fmaf(Ac[a * lda + r], Ac[b * lda + r], acc);
             } else {
                 for (int c = 0; c < n; ++c)
                     acc = fmaf(A[c * m + a], A[c * m + b], acc);
@@ -487,26 +497,40 @@ __device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, fl
         __syncthreads();
         cur ^= 1;
     }
-    if (warp == 0) {
-        float best = lane < d ? Db(cur)[lane] : -1.f;
-        int c = lane;
-        for (int o = 16; o > 0; o >>= 1) {
-            const float ob = __shfl_xor_sync(0xffffffffu, best, o);
-            const int oc = __shfl_xor_sync(0xffffffffu, c, o);
-            if (ob > best || (ob == best && oc < c)) {
-                best = ob;
-                c = oc;
-            }
+    // Column c of X with the largest diagonal entry (every thread, same
+    // order), then x^T G x and x^T x for x = column c (X is symmetric) over the
+    // whole block: product (a, k) by thread a * 32 + k, fixed-order sums.
+    const float* dgc = Db(cur);
+    int c = 0;
+    for (int k = 1; k < d; ++k)
+        c = dgc[k] > dgc[c] ? k : c;
+    const float* Xf = Xb(cur);
+    float gx = 0.f, xx = 0.f;
+    for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
+        const int a = t >> 5, k = t & 31;
+        const float xa = Xf[a * kSqLD + c], xk = Xf[k * kSqLD + c];
+        gx = fmaf(G[a * kSqLD + k] * xa, xk, gx);
+        if (k == 0)
+            xx = fmaf(xa, xa, xx);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        gx += __shfl_xor_sync(0xffffffffu, gx, o);
+        xx += __shfl_xor_sync(0xffffffffu, xx, o);
+    }
+    float* part = Db(cur ^ 1);  // 32 floats free here
+    if (lane == 0 && warp < 16) {
+        part[2 * warp] = gx;
+        part[2 * warp + 1] = xx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float sg = 0.f, sx = 0.f;
+        const int nw = min((int)(blockDim.x >> 5), 16);
+        for (int w = 0; w < nw; ++w) {
+            sg += part[2 * w];
+            sx += part[2 * w + 1];
         }
-        const float x = Xb(cur)[lane * kSqLD + c];  // zero beyond d
-        float p[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-        for (int k = 0; k < 32; ++k)
-            p[k & 3] = fmaf(G[lane * kSqLD + k], __shfl_sync(0xffffffffu, x, k), p[k & 3]);
-        const float y = (p[0] + p[1]) + (p[2] + p[3]);
-        const float xy = warp_total(x * y), xx = warp_total(x * x);
-        if (lane == 0)
-            *s_out = sqrtf(fmaxf(0.f, xy / xx));
+        *s_out = sqrtf(fmaxf(0.f, sg / sx));
     }
     __syncthreads();
     return *s_out;
