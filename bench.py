@@ -83,18 +83,29 @@ def load_peaks():
 
 def profiled_traffic(name: str):
     """DRAM bytes of a step's vote launches from the committed ncu summary,
-    valid only while the kernel source is unchanged since the capture."""
+    valid only while the kernel's code is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
     text = open(path).read()
     m = re.search(r"traffic_bytes_per_step:\s*([0-9.eE+]+)", text)
-    s = re.search(r"vote_source_sha256:\s*([0-9a-f]{64})", text)
+    s = re.search(r"vote_code_sha256:\s*([0-9a-f]{64})", text)
     if not m or not s:
         return None
     src = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc", "vote.cu")
-    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    return float(m.group(1)) if sha == s.group(1) else None
+    return float(m.group(1)) if code_sha256(open(src).read()) == s.group(1) else None
+
+
+def code_sha256(text: str) -> str:
+    """SHA-256 of a source file's code: each line without its // comment and
+    surrounding blanks, empty lines dropped (a comment edit keeps the hash)."""
+    lines = []
+    for ln in text.splitlines():
+        i = ln.find("//")
+        ln = (ln[:i] if i >= 0 else ln).strip()
+        if ln:
+            lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
 class ClockSampler:

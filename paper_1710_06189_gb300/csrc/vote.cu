@@ -7,10 +7,12 @@
 //
 // How (the paper's Scheme 2 copy strategy, Sec. II.A, and its image
 // partitioning with halo, Sec. III, redone for sm_103a):
-//  * Work items are tiles: a strip of 512 bytes of a row range of one job
-//    (one image x one group of offsets x one anchor-level range).  Persistent
-//    CTAs (one per SM) each take a contiguous, weight-balanced range of
-//    items, so a CTA spans few jobs and merges each once.
+//  * Work items are tiles: a strip of 512 bytes of a band of anchor rows of
+//    one job (one image x one group of offsets x one anchor-level range).
+//    Items are grouped host-side into chunks of consecutive items of one job;
+//    persistent CTAs (one per SM) take chunk b first and then claim chunks
+//    from a global counter, merging their histograms only when the job
+//    changes.
 //  * A tile is staged into shared memory by TMA bulk copies
 //    (cp.async.bulk, one per row: 16 halo bytes + 512 + 16 halo bytes, plus
 //    the halo rows the offsets' dy need), double-buffered and completed on
@@ -19,8 +21,9 @@
 //    staged by plain loads into the same layout.
 //  * Each lane reads its 16 bytes of a row (16 uint8 or 8 uint16 pixels) and
 //    the 4 pixels on each side from shared memory and quantizes them in
-//    registers to packed level bytes; the partner words of an offset are
-//    funnel shifts of the partner row's words.
+//    registers to packed level bytes (a shift and a mask per word for
+//    power-of-two N); the partner words of an offset are one byte permute
+//    each of the partner row's words.
 //  * Votes go into R private copies of the job's histograms in shared
 //    memory, interleaved so that copy c of a bin is word c of the bin's
 //    R-word row and lane l uses copy l mod R: with R = 32 every lane of a
@@ -39,7 +42,9 @@
 //    word) take the constant increment 1.  Column kk of anchor level i is
 //    word i * H + (kk + i) mod H: rotating each row spreads the lanes of a
 //    smooth region (same kk, different i) over the banks, and a merge still
-//    reads and writes along rows.  Every few tiles a spill pass
+//    reads and writes along rows.  For power-of-two N the columns and half
+//    bits of four votes come from byte-wise arithmetic on the packed level
+//    words.  Every few tiles a spill pass
 //    moves each half that reached 2^14 into the global counts, so no half
 //    can wrap in between.  Layout 3 is compiled into its own kernel
 //    instance (PACKED), so launches without it run the plain vote loop.
