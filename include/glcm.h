@@ -159,10 +159,15 @@ int glcm_features(glcm_ctx *ctx, const uint32_t *counts, int levels, int n_glcm,
  * non-NULL (GLCM_NORMALIZE implied), features if non-NULL.  Each desc's
  * results equal those of a glcm_compute + glcm_features on that image alone.
  * Host images (and host results) may be mixed with device ones: host images
- * are copied once into device staging on a side stream in groups of about
- * equal bytes, each group's votes starting as soon as its copies are in
- * (Sec. III's overlap of copies with earlier votes); the call then returns
- * after the host results are written.
+ * are copied once into device staging on a side stream in up to four groups
+ * of consecutive images, each group's votes starting as soon as its copies
+ * are in (Sec. III's overlap of copies with earlier votes).  Images whose
+ * features are asked for at N > 64 come first, as one group, and their
+ * epilogue overlaps the votes of the rest.  Registered (pinned) host images
+ * are read by a copy kernel on a few SMs, which the vote launches leave free
+ * while later groups are still copying; other host memory goes through
+ * cudaMemcpyAsync / cudaMemcpy2DAsync.  The call returns after the host
+ * results are written.  Results do not depend on the grouping.
  * Errors: as glcm_compute, per the first failing desc. */
 int glcm_compute_batch(glcm_ctx *ctx, const glcm_desc *descs, int n);
 
