@@ -109,12 +109,18 @@ def code_sha256(text: str) -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling during the timed region."""
+    """nvidia-smi clock / throttle sampling (every 100 ms) over a loaded window.
+
+    The window is the timed region plus LOAD_SECONDS of the same step before and
+    after it, so that a timed region shorter than the sampling period still has
+    samples taken under its load; `mark` brackets the timed region itself and
+    `samples_timed` counts the samples that arrived inside it."""
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.lines = []
+        self.t_start = self.t_end = None
 
     def __enter__(self):
         q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
@@ -126,13 +132,22 @@ class ClockSampler:
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.01)
         except (OSError, FileNotFoundError):
             self.proc = None
         return self
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark(self, start: bool):
+        if start:
+            self.t_start = time.perf_counter()
+        else:
+            self.t_end = time.perf_counter()
 
     def __exit__(self, *exc):
         if self.proc:
@@ -143,9 +158,9 @@ class ClockSampler:
                 self.proc.kill()
 
     def summary(self):
-        sm, mx, reasons = [], None, set()
+        sm, mx, reasons, timed = [], None, set(), 0
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for t, ln in self.lines:
             parts = [p.strip() for p in ln.split(",")]
             if len(parts) < 7:
                 continue
@@ -154,11 +169,32 @@ class ClockSampler:
                 mx = float(parts[1])
             except ValueError:
                 continue
+            if self.t_start is not None and self.t_end is not None and self.t_start <= t <= self.t_end:
+                timed += 1
             for k, nm in enumerate(names):
                 if parts[3 + k].lower().startswith("active"):
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples": len(sm), "samples_timed": timed,
+                "window": f"timed region plus {LOAD_SECONDS:g} s of the same step before and after"}
+
+
+LOAD_SECONDS = 0.5
+
+
+def keep_loaded(step, seconds: float):
+    """Run `step` untimed for about `seconds` of wall time, synchronizing every
+    32 steps so the host never runs far ahead of the device."""
+    import torch
+
+    t0 = time.perf_counter()
+    n = 0
+    while time.perf_counter() - t0 < seconds:
+        step()
+        n += 1
+        if n % 32 == 0:
+            torch.cuda.synchronize()
+    torch.cuda.synchronize()
 
 
 def oracle_sample(jobs, seconds: float):
@@ -501,23 +537,27 @@ def main():
         for _ in range(max(3, args.warmup)):
             ctx.run(step_batch)
     stream.synchronize()
-    G.glcm_get_timing(ctx.ctx, reset=True)
 
     barrier, max_over_ranks = rank_helpers(dist)
 
     # --- device-resident, batched (the headline value) ---
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    barrier()
-    torch.cuda.synchronize()
     with ClockSampler(local) as clk:
+        keep_loaded(lambda: ctx.run(step_batch), LOAD_SECONDS)
+        G.glcm_get_timing(ctx.ctx, reset=True)
+        barrier()
+        torch.cuda.synchronize()
+        clk.mark(True)
         e0.record(stream)
         for _ in range(args.steps):
             ctx.run(step_batch)
         e1.record(stream)
         torch.cuda.synchronize()
+        clk.mark(False)
+        vote_ms, vote_n, launches = G.glcm_get_timing(ctx.ctx, reset=True)
+        keep_loaded(lambda: ctx.run(step_batch), LOAD_SECONDS)
     barrier()
     ms = max_over_ranks(e0.elapsed_time(e1))
-    vote_ms, vote_n, launches = G.glcm_get_timing(ctx.ctx, reset=True)
     value = whole_job_value(world, pairs_step, args.steps, ms * 1e-3)
 
     # --- plain: one image at a time, sync per image ---
