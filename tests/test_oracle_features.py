@@ -162,3 +162,38 @@ def test_window_maps_match_full_features():
     assert np.allclose(maps[1], feats[..., 0], rtol=1e-14)
     assert np.allclose(maps[2], feats[..., 4], rtol=1e-14)
     assert np.allclose(maps[3], feats[..., 8], rtol=1e-14)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_moment_identities(seed):
+    """Features of the sum / difference distributions and the correlation
+    checked through moments of the joint distribution of (i, j):
+    f6 = E[i + j], f7 = Var(i) + Var(j) + 2 Cov(i, j), f2 = E[(i - j)^2],
+    f10 = E[(i - j)^2] - E[|i - j|]^2, f3 = Cov / (sd_i sd_j) from np.cov with
+    the cells' probabilities as weights, and f8 / f11 the entropies of the
+    distributions of i + j and |i - j| formed by bincount."""
+    rng = np.random.default_rng(300 + seed)
+    n = int(rng.integers(3, 21))
+    p = rng.random((n, n)) ** 2
+    p[rng.random((n, n)) < 0.3] = 0.0
+    p[rng.integers(n), rng.integers(n)] += 0.5
+    p /= p.sum()
+    f = haralick(p)
+    ii, jj = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    w = p.ravel()
+    i, j = ii.ravel().astype(float), jj.ravel().astype(float)
+    cov = np.cov(np.stack([i, j]), aweights=w, ddof=0)
+    ei, ej = float((w * i).sum()), float((w * j).sum())
+    assert f[5] == pytest.approx(ei + ej, rel=1e-12)
+    assert f[6] == pytest.approx(cov[0, 0] + cov[1, 1] + 2 * cov[0, 1], rel=1e-10)
+    e2 = float((w * (i - j) ** 2).sum())
+    assert f[1] == pytest.approx(e2, rel=1e-12)
+    assert f[9] == pytest.approx(e2 - float((w * np.abs(i - j)).sum()) ** 2, rel=1e-9, abs=1e-12)
+    assert f[2] == pytest.approx(cov[0, 1] / math.sqrt(cov[0, 0] * cov[1, 1]), abs=1e-10)
+
+    def ent(q):
+        q = q[q > 0]
+        return -float((q * np.log(q)).sum())
+
+    assert f[7] == pytest.approx(ent(np.bincount((i + j).astype(int), weights=w)), rel=1e-12)
+    assert f[10] == pytest.approx(ent(np.bincount(np.abs(i - j).astype(int), weights=w)), rel=1e-12)
