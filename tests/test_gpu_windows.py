@@ -54,3 +54,23 @@ def test_windows_wide_counters(gctx, win, stride, n, sym):
     g = m.cpu().numpy().reshape(4, len(offs), nw * nw).transpose(0, 2, 1).astype(np.float64)
     scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / (n * n), 1.0, 1.0])[:, None, None])
     assert (np.abs(g - maps) / scale).max() <= 1e-5
+
+
+def test_windows_maps_only(gctx):
+    """Maps without counts (the per-window GLCMs never leave shared memory):
+    bit-identical to the maps written beside the counts, and within the
+    feature tolerance of the oracle."""
+    img = S.smooth(11, 96, 131, 2.0, np.uint8)
+    offs = S.CONTENTION_OFFSETS
+    t = torch.from_numpy(img).cuda()
+    c, m_both = gctx.windows(t, 16, 15, 4, offs, flags=1)
+    none, m_only = gctx.windows(t, 16, 15, 4, offs, flags=1, counts=False)
+    torch.cuda.synchronize()
+    assert none is None
+    assert torch.equal(m_only, m_both)
+    want = oracle.window_glcm(img, 16, offs, 15, 4)
+    nwy, nwx = (96 - 15) // 4 + 1, (131 - 15) // 4 + 1
+    maps = oracle.window_maps(want, symmetric=True)
+    g = m_only.cpu().numpy().reshape(4, 4, nwy * nwx).transpose(0, 2, 1).astype(np.float64)
+    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / 256, 1.0, 1.0])[:, None, None])
+    assert (np.abs(g - maps) / scale).max() <= 1e-5
