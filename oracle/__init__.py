@@ -15,6 +15,8 @@ Functions
     the row).
 ``window_glcm(img, levels, offsets, win, stride, windows)``
     local GLCMs of win x win windows (pairs with both pixels inside).
+``histogram(img, levels, levels_mode=False)``
+    uint32 pixels per level, shape (N,) (the one-pixel statistic, Sec. I).
 ``symmetrize_normalize`` / ``haralick`` / ``window_maps``
     float64 epilogue and features, see ``haralick.py``.
 """
@@ -63,6 +65,8 @@ def _load():
             lib.oracle_glcm_multi.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, vp, vp]
             lib.oracle_window_glcm.restype = i64
             lib.oracle_window_glcm.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, ci, ci, vp, ci, vp, vp, vp]
+            lib.oracle_histogram.restype = i64
+            lib.oracle_histogram.argtypes = [vp, ci, ci, sz, ci, ci, ci, vp]
             _lib = lib
     return _lib
 
@@ -115,6 +119,17 @@ def window_glcm(img: np.ndarray, levels: int, offsets, win: int, stride: int, wi
     if s < 0:
         raise ValueError("oracle_window_glcm: bad arguments or window outside the image")
     return out
+
+
+def histogram(img: np.ndarray, levels: int, levels_mode: bool = False, return_skipped: bool = False):
+    """Pixels per level over the whole image: (N,) uint32."""
+    lib = _load()
+    img, w, h, pitch, bpp = _img_args(img)
+    out = np.zeros(levels, dtype=np.uint32)
+    s = lib.oracle_histogram(img.ctypes.data, w, h, pitch, bpp, levels, int(levels_mode), out.ctypes.data)
+    if s < 0:
+        raise ValueError("oracle_histogram: bad arguments")
+    return (out, int(s)) if return_skipped else out
 
 
 def pair_count(w: int, h: int, dx: int, dy: int) -> int:

@@ -141,3 +141,29 @@ long long oracle_window_glcm(const void *image, int W, int H, size_t pitch, int 
     }
     return total;
 }
+
+/* Gray-level histogram of the whole image: h[q] counts the pixels whose level
+ * is q (the one-pixel statistic whose voting the paper's contention analysis
+ * also covers, Sec. I, contribution 2).  h has N entries.  A pixel >= N in
+ * levels mode is not counted; returns how many were skipped, or -1 on bad
+ * arguments. */
+long long oracle_histogram(const void *image, int W, int H, size_t pitch, int bpp,
+                           int n_levels, int levels_mode, uint32_t *h)
+{
+    if (!image || !h || W < 0 || H < 0 || (bpp != 1 && bpp != 2) || n_levels < 1)
+        return -1;
+    const unsigned char *img = (const unsigned char *)image;
+    long long skipped = 0;
+    memset(h, 0, sizeof(uint32_t) * (size_t)n_levels);
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            unsigned q = level_of(read_pixel(img, pitch, bpp, x, y), bpp, n_levels, levels_mode);
+            if (q >= (unsigned)n_levels) {
+                ++skipped;
+                continue;
+            }
+            h[q] += 1u;
+        }
+    }
+    return skipped;
+}

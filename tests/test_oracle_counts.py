@@ -6,7 +6,8 @@ enumeration of all pixel pairs, exhaustive tiny images, the closed-form pair
 total, the transpose identity for the opposite direction (theta + 180 deg),
 constant images, marginals equal to 1-D histograms, a numpy bincount
 formulation, and the stripe decomposition with halo rows of Scheme 3
-(Eqs. 7-9)."""
+(Eqs. 7-9).  The gray-level histogram is pinned by hand counts, by the GLCM
+marginals plus the pixels that anchor no pair, and by enumeration."""
 import itertools
 import json
 import os
@@ -194,3 +195,65 @@ def test_window_glcm_equals_crop(oracle_lib):
         assert np.array_equal(W[idx], oracle.glcm(crop, 16, offs))
     for k, (dx, dy) in enumerate(offs):
         assert int(W[0, k].sum()) == (win - abs(dx)) * (win - abs(dy))
+
+
+# ---- the gray-level histogram (one-pixel statistic, Sec. I) ----------------
+
+def test_histogram_hand_counted(oracle_lib):
+    with open(GOLDEN) as f:
+        cases = json.load(f)["cases"]
+    n_checked = 0
+    for c in cases:
+        if "histogram" not in c:
+            continue
+        img = np.array(c["image"], dtype=np.dtype(c["dtype"]))
+        got = oracle.histogram(img, c["levels"], levels_mode=c["levels_mode"])
+        assert np.array_equal(got, np.array(c["histogram"])), c["name"]
+        n_checked += 1
+    assert n_checked == 3
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_histogram_is_glcm_marginal_plus_last_column(oracle_lib, seed):
+    """Every pixel but those of the last column is the anchor of exactly one
+    (1, 0) pair, so the histogram is the row sums of P(1, 0) plus the levels
+    of the last column; likewise the column sums of P(0, 1) plus the first
+    row's levels."""
+    rng = np.random.default_rng(400 + seed)
+    h, w = int(rng.integers(1, 30)), int(rng.integers(2, 40))
+    dt = np.uint8 if seed % 2 == 0 else np.uint16
+    img = rng.integers(0, np.iinfo(dt).max + 1, size=(h, w)).astype(dt)
+    n = [2, 7, 16, 256][seed]
+    bits = 8 * img.itemsize
+    hist = oracle.histogram(img, n)
+    last = [(int(v) * n) >> bits for v in img[:, -1]]
+    want = oracle.glcm(img, n, [(1, 0)])[0].sum(axis=1).astype(np.int64)
+    for q in last:
+        want[q] += 1
+    assert np.array_equal(hist, want)
+    first_row = [(int(v) * n) >> bits for v in img[0, :]]
+    want2 = oracle.glcm(img, n, [(0, 1)])[0].sum(axis=0).astype(np.int64)
+    for q in first_row:
+        want2[q] += 1
+    assert np.array_equal(hist, want2)
+    assert int(hist.sum()) == h * w
+
+
+def test_histogram_brute_force_and_levels_mode(oracle_lib):
+    rng = np.random.default_rng(7)
+    img = rng.integers(0, 12, size=(9, 11)).astype(np.uint8)
+    n = 10
+    want = np.zeros(n, dtype=np.int64)
+    skipped = 0
+    for y in range(img.shape[0]):
+        for x in range(img.shape[1]):
+            v = int(img[y, x])
+            if v >= n:
+                skipped += 1
+            else:
+                want[v] += 1
+    got, s = oracle.histogram(img, n, levels_mode=True, return_skipped=True)
+    assert np.array_equal(got, want) and s == skipped and skipped > 0
+    const = np.full((5, 6), 200, dtype=np.uint8)
+    hc = oracle.histogram(const, 8)
+    assert hc[(200 * 8) >> 8] == 30 and hc.sum() == 30
