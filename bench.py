@@ -420,7 +420,8 @@ def other_workloads(G, S, torch, local: int):
     the same public calls a user makes, inputs already in HBM):
     plain 512^2 N=8 levels-mode single offset; 8 bands of 8192^2 uint16 x 12
     offsets with symmetric normalized GLCMs and features in one batch; the
-    2048^2 sliding-window texture maps (259,081 windows x 4 offsets); 1000
+    2048^2 sliding-window texture maps (259,081 windows x 4 offsets), also
+    without counts; the gray-level histogram of a 16384^2 uint8 image; 1000
     uneven uint8 images (64..2048) in one batch."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
@@ -457,6 +458,16 @@ def other_workloads(G, S, torch, local: int):
                                                     G.GLCM_SYMMETRIC, cw, mw))
         wp = nw * sum((15 - abs(dx)) * (15 - abs(dy)) for dx, dy in offs)
         out["windows_2048_15x15_s4"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3), "gpairs_s": wp / (ms * 1e-3) / 1e9}
+        # Gray-level histogram of a 16384^2 uint8 image (268 MB, above L2), N = 256.
+        himg = torch.from_numpy(S.iid(S.BASE_SEED + 900, 16384, 16384, np.uint8)).cuda(local)
+        hh = torch.empty(256, dtype=torch.int32, device=f"cuda:{local}")
+        hsrc, hw, hhgt, hpitch, hdt = G.image_args(himg)
+        ms = _timed(stream, lambda: G.glcm_histogram(ctx.ctx, hsrc, hw, hhgt, hpitch, hdt, 256, 0, hh))
+        hpeak, hkind = load_peaks()
+        gbs = 16384 * 16384 / (ms * 1e-3) / 1e9
+        out["histogram_16384_u8_n256"] = {"ms": ms, "gpixels_s": gbs, "hbm_read_gbs": gbs,
+                                          "frac_of_hbm": gbs / hpeak, "peak_kind": f"{hkind} hbm_gbs (copy)"}
+        del himg, hh
         # The same maps without the per-window counts (1.06 GB not written).
         ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
                                                     G.GLCM_SYMMETRIC, None, mw))

@@ -196,6 +196,21 @@ int glcm_windows(glcm_ctx *ctx, const void *image, int width, int height, size_t
                  int dtype, int levels, int win, int stride, const glcm_offset *offsets,
                  int n_offsets, int flags, uint32_t *counts, float *maps);
 
+/* Gray-level histogram of one image: hist[q] = the number of pixels whose
+ * level (quantized as for glcm_compute) is q.  The one-pixel statistic to
+ * which the paper's analysis of vote collisions also applies (Sec. I,
+ * contribution 2).
+ *   image, width, height, pitch_bytes, dtype, levels   as for glcm_compute
+ *   flags   GLCM_INPUT_LEVELS (others ignored)
+ *   hist    out: levels uint32 (host or device pointer), overwritten
+ * In GLCM_INPUT_LEVELS mode a pixel >= levels is not counted and the call
+ * returns GLCM_ERR_RANGE (after the kernel, or at glcm_synchronize for device
+ * buffers on a caller's stream).
+ * Errors: GLCM_ERR_ARG (also more than 2^32 - 1 pixels), GLCM_ERR_UNSUPPORTED
+ * (levels > 256), GLCM_ERR_RANGE, GLCM_ERR_NOMEM, GLCM_ERR_CUDA. */
+int glcm_histogram(glcm_ctx *ctx, const void *image, int width, int height, size_t pitch_bytes,
+                   int dtype, int levels, int flags, uint32_t *hist);
+
 /* Wait for the context's stream; report device-detected errors of the work
  * enqueued since the last check (GLCM_ERR_RANGE, GLCM_ERR_TIMEOUT) and
  * clear them. */

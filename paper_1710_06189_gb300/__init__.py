@@ -14,14 +14,14 @@ from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_INPUT_
                       GLCM_SYMMETRIC, GLCM_U8, GLCM_U16, GlcmError,
                       glcm_compute, glcm_compute_batch, glcm_compute_naive, glcm_create, glcm_destroy,
                       glcm_features, glcm_get_timing, glcm_last_error, glcm_offset_from_angle,
-                      glcm_set_timing, glcm_set_vote_config, glcm_synchronize, glcm_windows)
+                      glcm_histogram, glcm_set_timing, glcm_set_vote_config, glcm_synchronize, glcm_windows)
 
 __all__ = [
     "PreparedBatch",
     "binding", "Context", "Server", "GlcmError", "GLCM_OK", "GLCM_ERR_BUSY", "GLCM_ERR_NOMEM", "GLCM_ERR_RANGE", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_U8",
     "GLCM_U16", "glcm_compute", "glcm_compute_batch", "glcm_compute_naive", "glcm_create", "glcm_destroy",
     "glcm_features", "glcm_get_timing", "glcm_last_error", "glcm_offset_from_angle", "glcm_set_timing",
-    "glcm_set_vote_config", "glcm_synchronize", "glcm_windows",
+    "glcm_set_vote_config", "glcm_synchronize", "glcm_windows", "glcm_histogram",
 ]
 
 
@@ -165,6 +165,15 @@ class Context:
         m = self._empty((4, n, nwy, nwx), torch.float32, dev) if maps else None
         glcm_windows(self.ctx, src, w, h, pitch, dt, levels, win, stride, offsets, flags, c, m)
         return c, m
+
+    def histogram(self, img, levels: int, flags: int = 0, out=None):
+        """glcm_histogram: pixels per level, int32 view of uint32 [levels]."""
+        torch = _torch()
+        src, w, h, pitch, dt = image_args(img)
+        on_dev = isinstance(img, torch.Tensor) and img.is_cuda
+        hist = out if out is not None else self._empty((levels,), torch.int32, on_dev)
+        glcm_histogram(self.ctx, src, w, h, pitch, dt, levels, flags, hist)
+        return hist
 
     def enqueue_batch(self, jobs):
         """glcm_enqueue_batch: the batch launched directly, no graph, no sync;

@@ -74,6 +74,7 @@ _PROTOS = {
     "glcm_server_destroy": (c_int, [c_void_p]),
     "glcm_windows": (c_int, [c_void_p, c_void_p, c_int, c_int, c_size_t, c_int, c_int, c_int, c_int,
                              ctypes.POINTER(glcm_offset), c_int, c_int, c_void_p, c_void_p]),
+    "glcm_histogram": (c_int, [c_void_p, c_void_p, c_int, c_int, c_size_t, c_int, c_int, c_int, c_void_p]),
     "glcm_synchronize": (c_int, [c_void_p]),
     "glcm_set_timing": (c_int, [c_void_p, c_int]),
     "glcm_get_timing": (c_int, [c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_longlong),
@@ -261,6 +262,11 @@ def glcm_windows(ctx, image, width, height, pitch_bytes, dtype, levels, win, str
     return _check(ctx, load().glcm_windows(ctx, _ptr(image), int(width), int(height), int(pitch_bytes),
                                            int(dtype), int(levels), int(win), int(stride), offs, len(offsets),
                                            int(flags), _ptr(counts), _ptr(maps)))
+
+
+def glcm_histogram(ctx, image, width, height, pitch_bytes, dtype, levels, flags, hist):
+    return _check(ctx, load().glcm_histogram(ctx, _ptr(image), int(width), int(height), int(pitch_bytes),
+                                             int(dtype), int(levels), int(flags), _ptr(hist)))
 
 
 def glcm_synchronize(ctx):

@@ -1748,6 +1748,58 @@ extern "C" int glcm_enqueue_batch(glcm_ctx* ctx, const glcm_desc* descs, int n)
     return enqueue_batch(ctx, sb, ctx->jobs, ctx->offs, ctx->feat, false, nullptr);
 }
 
+extern "C" int glcm_histogram(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes,
+                              int dtype, int levels, int flags, uint32_t* hist)
+{
+    if (!ctx)
+        return GLCM_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    const glcm_offset unit{1, 0};
+    TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, &unit, 1));
+    if (!hist)
+        return fail(ctx, GLCM_ERR_ARG, "hist is NULL");
+    if ((long long)width * height > 0xFFFFFFFFll)
+        return fail(ctx, GLCM_ERR_ARG, "more than 2^32 - 1 pixels (uint32 counts)");
+    const int bpp = dtype == GLCM_U8 ? 1 : 2;
+    const bool dev_img = is_device_ptr(image);
+    const bool dev_h = is_device_ptr(hist);
+    const uint8_t* d_img = static_cast<const uint8_t*>(image);
+    size_t dpitch = pitch_bytes;
+    if (!dev_img) {
+        std::vector<int> cut{height};
+        TRY(stage_host_image(ctx, image, width, height, pitch_bytes, bpp, ctx->img, dpitch, cut));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[0], 0));
+        d_img = static_cast<const uint8_t*>(ctx->img.p);
+    }
+    uint32_t* d_h = hist;
+    if (!dev_h) {
+        TRY(ensure(ctx, ctx->counts, (size_t)levels * 4));
+        d_h = static_cast<uint32_t*>(ctx->counts.p);
+    }
+    CK(cudaMemsetAsync(d_h, 0, (size_t)levels * 4, ctx->stream));
+    const long long row_bytes = (long long)width * bpp;
+    HistParams hp{};
+    hp.img = d_img;
+    hp.pitch = (long long)dpitch;
+    hp.flat = (dpitch == (size_t)row_bytes || height == 1) ? 1 : 0;
+    hp.row_bytes = hp.flat ? row_bytes * height : row_bytes;
+    hp.seg_bytes = histogram_seg_bytes();
+    hp.segs = (row_bytes + hp.seg_bytes - 1) / hp.seg_bytes;
+    hp.units = hp.segs * height;
+    hp.bpp = bpp;
+    hp.levels = levels;
+    hp.levels_mode = (flags & GLCM_INPUT_LEVELS) ? 1 : 0;
+    hp.hist = d_h;
+    hp.err = ctx->d_words;
+    CK(launch_histogram(hp, ctx->sm_count, ctx->stream));
+    ctx->kernel_launches += 1;
+    if (!dev_h)
+        CK(cudaMemcpyAsync(hist, d_h, (size_t)levels * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ctx->own_stream || !dev_img || !dev_h)
+        return collect_device_errors(ctx);
+    return GLCM_OK;
+}
+
 extern "C" int glcm_windows(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch_bytes, int dtype,
                             int levels, int win, int stride, const glcm_offset* offsets, int n_offsets, int flags,
                             uint32_t* counts, float* maps)

@@ -113,6 +113,20 @@ struct WindowParams {
     unsigned* err;
 };
 
+// Gray-level histogram of one image (histogram.cu).
+struct HistParams {
+    const uint8_t* img;
+    long long pitch;      // bytes between rows (pitched mode)
+    long long row_bytes;  // bytes of one row, or of the whole image when flat
+    long long seg_bytes;  // row segment a warp takes (pitched mode; multiple of 16)
+    long long segs;       // segments per row (pitched mode)
+    long long units;      // rows * segs (pitched mode)
+    int flat;             // the image is one contiguous span of row_bytes
+    int bpp, levels, levels_mode;
+    uint32_t* hist;       // levels counts, zeroed before the launch and added into
+    unsigned* err;
+};
+
 // Launchers (defined in the .cu files).
 // packed: some job of the launch uses layout 3 (a separate kernel instance).
 cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem,
@@ -124,6 +138,8 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
 size_t features_smem_bytes(int max_levels);
 long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
+cudaError_t launch_histogram(const HistParams& p, int sm_count, cudaStream_t s);
+long long histogram_seg_bytes();
 int vote_max_smem_optin();
 int vote_blocks_per_sm(int bpp, int threads, size_t smem, bool packed = false);
 int vote_row_bytes();
