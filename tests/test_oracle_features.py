@@ -197,3 +197,37 @@ def test_moment_identities(seed):
 
     assert f[7] == pytest.approx(ent(np.bincount((i + j).astype(int), weights=w)), rel=1e-12)
     assert f[10] == pytest.approx(ent(np.bincount(np.abs(i - j).astype(int), weights=w)), rel=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_library_routines_on_count_tables(seed):
+    """Features of integer count tables against library routines that compute
+    the same quantities by their own code: scikit-learn's mutual information
+    of a contingency table (f12, f13), scipy's entropy (f8, f9, f11), scipy's
+    Pearson correlation of the expanded (i, j) samples (f3), and numpy's
+    variance of the expanded samples (f4, f7)."""
+    pytest.importorskip("sklearn")
+    from scipy import stats
+    from sklearn.metrics import mutual_info_score
+
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(3, 17))
+    C = rng.integers(0, 9, size=(n, n))
+    C[rng.random((n, n)) < 0.35] = 0
+    C[0, n - 1] += 3
+    C[n - 1, 0] += 2
+    p = C / C.sum()
+    f = haralick(p)
+    ii, jj = np.nonzero(C)
+    reps = C[ii, jj]
+    si, sj = np.repeat(ii, reps).astype(float), np.repeat(jj, reps).astype(float)
+    mi = mutual_info_score(None, None, contingency=C)
+    hx, hy = stats.entropy(C.sum(1)), stats.entropy(C.sum(0))
+    assert f[11] == pytest.approx(-mi / max(hx, hy), abs=1e-10)
+    assert f[12] == pytest.approx(math.sqrt(max(0.0, 1 - math.exp(-2 * mi))), abs=1e-8)
+    assert f[8] == pytest.approx(stats.entropy(C.ravel()), rel=1e-12)
+    assert f[7] == pytest.approx(stats.entropy(np.bincount((si + sj).astype(int))), rel=1e-12)
+    assert f[10] == pytest.approx(stats.entropy(np.bincount(np.abs(si - sj).astype(int))), rel=1e-12)
+    assert f[2] == pytest.approx(stats.pearsonr(si, sj).statistic, abs=1e-10)
+    assert f[3] == pytest.approx(np.var(si), rel=1e-12)
+    assert f[6] == pytest.approx(np.var(si + sj), rel=1e-10)
