@@ -17,7 +17,9 @@
 // copies of every bin with a warp reduction and adds the sum into the global
 // histogram, which the host has zeroed.
 //
-// HBM-bound: W * H * bytes-per-pixel read once, N * 4 bytes added per CTA.
+// Algorithmic traffic: W * H * bytes-per-pixel read once, N * 4 bytes added
+// per CTA; the roofline is the HBM read (the shared reductions, one per
+// pixel, and the instructions that form their addresses run beside it).
 #include "glcm_internal.cuh"
 
 namespace glcm {
