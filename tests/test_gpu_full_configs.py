@@ -20,6 +20,7 @@ import glcm_synth as S
 import oracle
 import paper_1710_06189_gb300 as G
 from conftest import to_u32
+import featcheck
 from featcheck import FEATURE_TOL, assert_normalized, feature_errors, relative_errors
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -92,7 +93,7 @@ def test_windows_2048_full(gctx):
     assert np.array_equal(got, want)
     maps = oracle.window_maps(want, symmetric=True)  # (4 maps, n_win, n_off)
     g = m.cpu().numpy().reshape(4, 4, nwy * nwx)[:, :, idx].transpose(0, 2, 1).astype(np.float64)
-    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / (n * n), 1.0, 1.0])[:, None, None])
+    scale = np.maximum(np.abs(maps), featcheck.map_scale(n)[:, None, None])
     assert (np.abs(g - maps) / scale).max() <= 1e-5
 
 

@@ -6,6 +6,7 @@ import torch
 import glcm_synth as S
 import oracle
 from conftest import to_u32
+import featcheck
 
 pytestmark = pytest.mark.gpu
 
@@ -22,7 +23,7 @@ def test_windows_counts_and_maps(gctx, sym):
     assert np.array_equal(got, want)
     maps = oracle.window_maps(want, symmetric=sym)  # (4, n_win, n_off)
     g = m.cpu().numpy().reshape(4, 4, nwy * nwx).transpose(0, 2, 1).astype(np.float64)
-    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / 256, 1.0, 1.0])[:, None, None])
+    scale = np.maximum(np.abs(maps), featcheck.map_scale(16)[:, None, None])
     err = np.abs(g - maps) / scale
     assert err.max() <= 1e-5, err.max()
 
@@ -52,7 +53,7 @@ def test_windows_wide_counters(gctx, win, stride, n, sym):
     assert np.array_equal(got, want)
     maps = oracle.window_maps(want, symmetric=sym)
     g = m.cpu().numpy().reshape(4, len(offs), nw * nw).transpose(0, 2, 1).astype(np.float64)
-    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / (n * n), 1.0, 1.0])[:, None, None])
+    scale = np.maximum(np.abs(maps), featcheck.map_scale(n)[:, None, None])
     assert (np.abs(g - maps) / scale).max() <= 1e-5
 
 
@@ -72,5 +73,5 @@ def test_windows_maps_only(gctx):
     nwy, nwx = (96 - 15) // 4 + 1, (131 - 15) // 4 + 1
     maps = oracle.window_maps(want, symmetric=True)
     g = m_only.cpu().numpy().reshape(4, 4, nwy * nwx).transpose(0, 2, 1).astype(np.float64)
-    scale = np.maximum(np.abs(maps), np.array([1.0, 1.0 / 256, 1.0, 1.0])[:, None, None])
+    scale = np.maximum(np.abs(maps), featcheck.map_scale(16)[:, None, None])
     assert (np.abs(g - maps) / scale).max() <= 1e-5

@@ -45,6 +45,27 @@ def test_one_hot(a):
     assert f[13] == 0.0  # only one row in the support
 
 
+def _idm_uniform(n):
+    """Inverse difference moment of the uniform n x n distribution, counted by
+    diagonals: n cells have |i - j| = 0 and 2 (n - k) cells have |i - j| = k."""
+    return (n + sum(2.0 * (n - k) / (1.0 + k * k) for k in range(1, n))) / (n * n)
+
+
+@pytest.mark.parametrize("n", [3, 4, 8, 32])
+def test_idm_uniform_by_diagonals(n):
+    p = np.full((n, n), 1.0 / (n * n))
+    assert haralick(p)[4] == pytest.approx(_idm_uniform(n), rel=TOL)
+
+
+def test_idm_hand_worked_3x3():
+    # Half the mass at (0, 2) (|i - j| = 2, weight 1/5), a quarter at (1, 1)
+    # (weight 1) and a quarter at (2, 1) (|i - j| = 1, weight 1/2):
+    # 0.5 / 5 + 0.25 + 0.25 / 2 = 0.475.
+    p = np.zeros((3, 3))
+    p[0, 2], p[1, 1], p[2, 1] = 0.5, 0.25, 0.25
+    assert haralick(p)[4] == pytest.approx(0.475, rel=TOL)
+
+
 @pytest.mark.parametrize("n", [2, 5, 16])
 def test_diagonal(n):
     p = np.eye(n) / n
@@ -164,6 +185,28 @@ def test_window_maps_match_full_features():
     assert np.allclose(maps[3], feats[..., 8], rtol=1e-14)
 
 
+@pytest.mark.parametrize("n", [3, 16])
+def test_window_maps_closed_forms(n):
+    """Window maps of constructed count tables: uniform counts (contrast
+    (n^2 - 1) / 6, ASM 1 / n^2, IDM counted by diagonals, entropy 2 ln n), a
+    single bin (0, 0, 1, 0), and the hand-worked 3 x 3 table of
+    test_idm_hand_worked_3x3 scaled to counts 2 : 1 : 1."""
+    C = np.zeros((3, 1, n, n), dtype=np.uint32)
+    C[0, 0] = 7
+    C[1, 0, n - 1, n - 1] = 5
+    C[2, 0, 0, 2], C[2, 0, 1, 1], C[2, 0, 2, 1] = 2, 1, 1
+    m = oracle.window_maps(C)
+    assert m[0, 0, 0] == pytest.approx((n * n - 1) / 6.0, rel=TOL)
+    assert m[1, 0, 0] == pytest.approx(1.0 / (n * n), rel=TOL)
+    assert m[2, 0, 0] == pytest.approx(_idm_uniform(n), rel=TOL)
+    assert m[3, 0, 0] == pytest.approx(2 * math.log(n), rel=TOL)
+    assert (m[0, 1, 0], m[1, 1, 0], m[2, 1, 0], m[3, 1, 0]) == (0.0, 1.0, 1.0, 0.0)
+    assert m[0, 2, 0] == pytest.approx(0.5 * 4 + 0.25 * 1, rel=TOL)
+    assert m[1, 2, 0] == pytest.approx(0.25 + 0.0625 + 0.0625, rel=TOL)
+    assert m[2, 2, 0] == pytest.approx(0.475, rel=TOL)
+    assert m[3, 2, 0] == pytest.approx(-(0.5 * math.log(0.5) + 0.5 * math.log(0.25)), rel=TOL)
+
+
 @pytest.mark.parametrize("seed", range(8))
 def test_moment_identities(seed):
     """Features of the sum / difference distributions and the correlation
@@ -197,6 +240,8 @@ def test_moment_identities(seed):
 
     assert f[7] == pytest.approx(ent(np.bincount((i + j).astype(int), weights=w)), rel=1e-12)
     assert f[10] == pytest.approx(ent(np.bincount(np.abs(i - j).astype(int), weights=w)), rel=1e-12)
+    pd = np.bincount(np.abs(i - j).astype(int), weights=w)
+    assert f[4] == pytest.approx(float((pd / (1.0 + np.arange(len(pd)) ** 2)).sum()), rel=1e-12)
 
 
 @pytest.mark.parametrize("seed", range(5))
@@ -231,3 +276,4 @@ def test_library_routines_on_count_tables(seed):
     assert f[2] == pytest.approx(stats.pearsonr(si, sj).statistic, abs=1e-10)
     assert f[3] == pytest.approx(np.var(si), rel=1e-12)
     assert f[6] == pytest.approx(np.var(si + sj), rel=1e-10)
+    assert f[4] == pytest.approx(float(np.mean(1.0 / (1.0 + (si - sj) ** 2))), rel=1e-12)
