@@ -258,9 +258,10 @@ int glcm_compute_naive(glcm_ctx *ctx, const void *image, int width, int height,
  *
  * The vote kernel's scratch (job, offset and chunk tables, the chunk counter,
  * the error word; about 113 KB) is one fixed static device array present on
- * every device that loads the library until the process exits.  The first call
- * on a device, with that device current, looks up the array's device address
- * (cudaGetSymbolAddress) and keeps it; make that first call before any stream
+ * every device that loads the library until the process exits.  Every call
+ * looks up the array's device address in the current context
+ * (cudaGetSymbolAddress, which allocates nothing); the first call on a device
+ * also loads the library's device code there, so make it before any stream
  * capture.  Every call reuses the array and clears the counter and error word
  * it needs.  Calls are serialized by a process-wide mutex and each waits for
  * its own work, but calls that overlap on the GPU through the same array (for

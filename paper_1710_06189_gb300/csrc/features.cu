@@ -1260,13 +1260,10 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
     if (p.n_jobs <= 0)
         return cudaSuccess;
     const size_t smem = features_smem_bytes(max_levels);
-    static size_t set_to = 0;
-    if (smem > set_to) {
-        cudaError_t e = cudaFuncSetAttribute(k_haralick, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess)
-            return e;
-        set_to = smem;
-    }
+    static SmemLimit lim;
+    const cudaError_t e = lim.raise((const void*)k_haralick, smem);
+    if (e != cudaSuccess)
+        return e;
     k_haralick<<<p.n_jobs, kFeatThreads, smem, s>>>(p, max_levels);
     return cudaGetLastError();
 }

@@ -2,6 +2,8 @@
 // kernels.  Not part of the public ABI (include/glcm.h is).
 #pragma once
 #include <cstdint>
+#include <mutex>
+
 #include <cuda_runtime.h>
 
 struct glcm_ctx;  // the context (glcm_capi.cu; opaque in the public header)
@@ -125,6 +127,36 @@ struct HistParams {
     int bpp, levels, levels_mode;
     uint32_t* hist;       // levels counts, zeroed before the launch and added into
     unsigned* err;
+};
+
+// The dynamic shared-memory limit of one kernel, raised per device
+// (cudaFuncSetAttribute applies to the current device's context): the
+// attribute is set only when a launch needs more than was set on the current
+// device before, so once an uncaptured launch of a size has run, no attribute
+// call happens inside a later stream capture.  Thread-safe.
+class SmemLimit {
+public:
+    static constexpr int kMaxDevices = 64;
+    cudaError_t raise(const void* fn, size_t smem)
+    {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess)
+            return e;
+        if (dev < 0 || dev >= kMaxDevices)
+            return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        std::lock_guard<std::mutex> g(m_);
+        if (smem <= set_[dev])
+            return cudaSuccess;
+        e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+            set_[dev] = smem;
+        return e;
+    }
+
+private:
+    std::mutex m_;
+    size_t set_[kMaxDevices] = {};
 };
 
 // Launchers (defined in the .cu files).

@@ -12,11 +12,14 @@
 // chunk counter and the error word -- lives in one file-scope
 // `static __device__` array of fixed size (kScratchBytes, about 113 KB),
 // present on every device that loads the library until the process exits.
-// Host code cannot use that array's name as a device address, so the first
-// call on each device (with that device current) looks the address up with
-// cudaGetSymbolAddress and keeps it; that first call should therefore come
-// before any stream capture.  Planning uses fixed host arrays, never the
-// heap.  Every call reuses the array, so the counter and error word are
+// Host code cannot use that array's name as a device address, so every call
+// looks the address up with cudaGetSymbolAddress in the current device's
+// context (a lookup: it allocates nothing).  The address is not kept between
+// calls, because it belongs to one context: after cudaDeviceReset, or under
+// another context on the same device, a kept address would point at memory
+// that no longer holds the array.  The first call on a device also loads the
+// library's device code into that context (set-up), so it should come before
+// any stream capture.  Planning uses fixed host arrays, never the heap.  Every call reuses the array, so the counter and error word are
 // cleared on each call; a process-wide mutex serializes calls and each call
 // waits for its own work, but two callers sharing the array from different
 // processes or library copies would race.
@@ -36,7 +39,6 @@ constexpr int kNaMaxChunks = GLCM_NOALLOC_MAX_CHUNKS;
 constexpr int kNaThreads = 512;
 constexpr int kNaBand = 32;
 constexpr int kNaTileRows = 48;
-constexpr int kMaxDevices = 64;
 
 struct NaScratch {
     VoteJob jobs[kNaMaxJobs];
@@ -49,8 +51,7 @@ constexpr size_t kScratchBytes = sizeof(NaScratch);
 static __device__ __align__(256) unsigned char g_na_scratch[kScratchBytes];
 
 std::mutex g_na_mutex;
-void* g_na_ptr[kMaxDevices];  // device address of g_na_scratch per device
-NaScratch g_na_host;          // host-side plan, copied into the device array
+NaScratch g_na_host;  // host-side plan, copied into the device array
 
 int na_fail(char* errbuf, size_t len, int code, const char* msg)
 {
@@ -114,7 +115,9 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     const int bpp = dtype == GLCM_U8 ? 1 : 2;
     if (pitch_bytes < (size_t)width * bpp)
         return na_fail(errbuf, errbuf_len, GLCM_ERR_ARG, "pitch_bytes < width * bytes per pixel");
-    if (levels < 2 || levels > GLCM_MAX_LEVELS)
+    if (levels > GLCM_MAX_LEVELS)
+        return na_fail(errbuf, errbuf_len, GLCM_ERR_UNSUPPORTED, "levels > 256");
+    if (levels < 2)
         return na_fail(errbuf, errbuf_len, GLCM_ERR_ARG, "levels must be in 2..256");
     if (n_offsets < 1 || n_offsets > GLCM_MAX_OFFSETS)
         return na_fail(errbuf, errbuf_len, GLCM_ERR_ARG, "need 1..64 offsets");
@@ -122,7 +125,7 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
         if (offsets[k].dx <= -65536 || offsets[k].dx >= 65536 || offsets[k].dy <= -65536 || offsets[k].dy >= 65536)
             return na_fail(errbuf, errbuf_len, GLCM_ERR_ARG, "offset out of range");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
         return na_fail(errbuf, errbuf_len, GLCM_ERR_CUDA, "no current CUDA device");
     for (const void* ptr : {image, static_cast<const void*>(counts)}) {
         cudaPointerAttributes a;
@@ -134,17 +137,17 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
         }
     }
     std::lock_guard<std::mutex> guard(g_na_mutex);
-    // Set-up, once per device: the device address of the static scratch.
-    if (!g_na_ptr[dev]) {
+    // The device address of the static scratch in the current context.
+    NaScratch* dscr = nullptr;
+    {
         void* p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_na_scratch);
         if (e != cudaSuccess || !p) {
             cudaGetLastError();
             return na_fail(errbuf, errbuf_len, GLCM_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed");
         }
-        g_na_ptr[dev] = p;
+        dscr = static_cast<NaScratch*>(p);
     }
-    NaScratch* dscr = static_cast<NaScratch*>(g_na_ptr[dev]);
     cudaStream_t stream = static_cast<cudaStream_t>(cuda_stream);
 
     // Plan into fixed host arrays (the same rules as the context planner).
@@ -270,10 +273,21 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
             if (h.jobs[jb].chunk_items > cap)
                 h.jobs[jb].chunk_items = cap;
     }
-    long long want_chunks = 0;
-    for (int jb = 0; jb < n_jobs; ++jb)
-        want_chunks += (h.jobs[jb].n_job_items + h.jobs[jb].chunk_items - 1) / h.jobs[jb].chunk_items;
-    const long long scale = (want_chunks + kNaMaxChunks - 1) / kNaMaxChunks;
+    // Coarser chunks (items per chunk times `scale`, at most a whole job)
+    // until the chunks fit; every job needs at least one, and the jobs fit.
+    auto chunks_at = [&](long long scale) {
+        long long n = 0;
+        for (int jb = 0; jb < n_jobs; ++jb) {
+            const long long ci = h.jobs[jb].chunk_items * scale < h.jobs[jb].n_job_items
+                                     ? h.jobs[jb].chunk_items * scale
+                                     : h.jobs[jb].n_job_items;
+            n += (h.jobs[jb].n_job_items + ci - 1) / ci;
+        }
+        return n;
+    };
+    long long scale = 1;
+    while (chunks_at(scale) > kNaMaxChunks)
+        scale *= 2;
     int n_chunks = 0;
     for (int jb = 0; jb < n_jobs; ++jb) {
         VoteJob& j = h.jobs[jb];

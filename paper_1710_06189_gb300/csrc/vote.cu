@@ -1065,19 +1065,13 @@ __global__ void k_glcm_naive(const uint8_t* img, long long pitch, int W, int H, 
     }
 }
 
-// Raise the dynamic shared-memory limit only when a launch needs more than
-// before, so no attribute call happens while a stream is being captured.
+// Raise the dynamic shared-memory limit on the current device only when a
+// launch needs more than before (see SmemLimit).
 template <int BPP, int MAXT, bool PACKED>
 cudaError_t vote_prepare(size_t smem)
 {
-    static size_t set_to = 0;
-    if (smem <= set_to)
-        return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(k_glcm_vote<BPP, MAXT, PACKED>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-        set_to = smem;
-    return e;
+    static SmemLimit lim;
+    return lim.raise((const void*)k_glcm_vote<BPP, MAXT, PACKED>, smem);
 }
 
 // Two register budgets: up to 1024 threads at 64 registers, or up to 512

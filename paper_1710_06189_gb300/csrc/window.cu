@@ -176,15 +176,14 @@ cudaError_t launch_windows(const WindowParams& p, cudaStream_t s)
     const size_t smem = (size_t)((RW * RH + 1) / 2) * 4 + (size_t)hist_words * 4 * kWX * kWY;
     if (smem > (size_t)vote_max_smem_optin())
         return cudaErrorInvalidConfiguration;
-    static size_t set_to[3] = {0, 0, 0};
+    static SmemLimit lim[3];
     const int ci = cbits == 8 ? 0 : (cbits == 16 ? 1 : 2);
-    if (smem > set_to[ci]) {
+    {
         const void* fn = cbits == 8 ? (const void*)k_window_glcm<8>
                                     : (cbits == 16 ? (const void*)k_window_glcm<16> : (const void*)k_window_glcm<32>);
-        cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const cudaError_t e = lim[ci].raise(fn, smem);
         if (e != cudaSuccess)
             return e;
-        set_to[ci] = smem;
     }
     dim3 grid((p.nwx + kWX - 1) / kWX, (p.nwy + kWY - 1) / kWY);
     if (cbits == 8)
