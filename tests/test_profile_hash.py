@@ -16,5 +16,23 @@ def test_code_hash_ignores_comments_only():
     assert bench.code_sha256(src) != bench.code_sha256("int a = 1;\nint b = 3;\n")
 
 
-def test_committed_profile_matches_vote_source():
-    assert bench.profiled_traffic("vote_contention_4096.md") is not None
+def test_traffic_reported_only_for_the_captured_code(tmp_path, monkeypatch):
+    """profiled_traffic() gives the summary's figure when its hash is the
+    current source's, and None (traffic unknown) once the code has changed."""
+    src = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc", "vote.cu")
+    good = bench.code_sha256(open(src).read())
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "cur.md").write_text(f"traffic_bytes_per_step: 1234\nvote_code_sha256: {good}\n")
+    (prof / "old.md").write_text("traffic_bytes_per_step: 1234\nvote_code_sha256: " + "0" * 64 + "\n")
+    real_join = os.path.join
+
+    def join(*parts):
+        if len(parts) >= 2 and parts[0] == bench.ROOT and parts[1] == "profiles":
+            return real_join(str(prof), *parts[2:])
+        return real_join(*parts)
+
+    monkeypatch.setattr(bench.os.path, "join", join)
+    assert bench.profiled_traffic("cur.md") == 1234.0
+    assert bench.profiled_traffic("old.md") is None
+    assert bench.profiled_traffic("missing.md") is None
