@@ -231,11 +231,15 @@ int glcm_get_timing(glcm_ctx *ctx, double *vote_ms, long long *vote_launches,
  * lane % copies == c), the shared-memory layout (0: one row of copies per
  * bin; 1: two offsets' rows interleaved per bin; 2: two offsets as 16-bit
  * halves of one word; 3: one offset's partner levels j and j + ceil(N/2) as
- * 16-bit halves of one word, so that N = 256 takes one pass per offset), and
- * anchor rows per work item (0 = derived).  Offsets
- * that do not fit one CTA's shared memory together are split over several
- * passes, and a histogram whose one level row does not fit is rejected.
- * threads <= 0 removes the override.  Errors: GLCM_ERR_ARG. */
+ * 16-bit halves of one word, so that N = 256 takes one pass per offset; 4:
+ * the column-walk kernel, which every offset at chessboard distance 1 of an
+ * image with N a power of two up to 32 takes by default -- threads and
+ * copies are then fixed), and anchor rows per work item (0 = derived).
+ * Offsets that do not fit one CTA's shared memory together are split over
+ * several passes, and a histogram whose one level row does not fit is
+ * rejected.  A layout of 0..3 sends the class's distance-1 offsets to the
+ * general kernel too.  threads <= 0 removes the override.
+ * Errors: GLCM_ERR_ARG. */
 int glcm_set_vote_config(glcm_ctx *ctx, int levels, int n_offsets, int dtype, int threads,
                          int log2_copies, int layout, int band_rows);
 

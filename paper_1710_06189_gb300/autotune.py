@@ -2,11 +2,13 @@
 
 For one (levels, offsets, pixel type) class it times every feasible vote
 configuration -- threads per CTA, log2 of the private histogram copies and
-the shared-memory layout (see glcm_set_vote_config) -- on the caller's own
-images.  The paper picks block size and copy count from Eqs. 4-6 and by
-experiment (Sec. II.B); here the experiment is automated.  The best
-configuration is applied to the context and kept in a JSON cache keyed by
-GPU name and class, so later runs can apply it without timing.
+the shared-memory layout, including the column-walk kernel (layout 4; see
+glcm_set_vote_config) -- on the caller's own images, then the tile shape
+(anchor rows per work item) of the winner.  The paper picks block size and
+copy count from Eqs. 4-6 and by experiment (Sec. II.B); here the experiment
+is automated.  The best configuration is applied to the context and kept in
+a JSON cache keyed by GPU name and class, so later runs can apply it without
+timing.
 
 All timing is of the vote kernel alone, with CUDA events on the context's
 stream (glcm_set_timing / glcm_get_timing).
@@ -18,8 +20,11 @@ import os
 
 from . import binding as B
 
-DEFAULT_CANDIDATES = tuple([(512, r, lay) for r in (5, 4, 3, 2, 1, 0) for lay in (1, 0, 2, 3)] +
+DEFAULT_CANDIDATES = tuple([(512, 5, 4)] + [(512, r, lay) for r in (5, 4, 3, 2, 1, 0) for lay in (1, 0, 2, 3)] +
                            [(256, 5, 1), (1024, 5, 1), (1024, 0, 3)])
+# Anchor rows per work item tried for the winning configuration (0: the
+# planner's choice); the general kernel's tiles hold at most 64.
+BAND_CANDIDATES = {4: (0, 8, 16, 32, 64, 128), "general": (0, 16, 32, 64)}
 
 
 def class_key(levels: int, n_offsets: int, dtype: int) -> str:
@@ -57,13 +62,26 @@ def tune(ctx, images, levels: int, offsets, flags: int = 0, reps: int = 3, candi
         except B.GlcmError:
             continue  # histograms do not fit this configuration
         ms = _time_config(ctx, images, levels, offsets, flags, reps)
-        tried.append({"threads": threads, "log2_copies": r, "layout": layout, "ms": ms})
+        tried.append({"threads": threads, "log2_copies": r, "layout": layout, "band_rows": 0, "ms": ms})
         if best is None or ms < best["ms"]:
             best = tried[-1]
     if best is None:
         B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, 0, 0, 0, 0)
         return None
-    B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"], best["layout"], 0)
+    # Tile shape of the winner.
+    for band in BAND_CANDIDATES[4 if best["layout"] == 4 else "general"][1:]:
+        try:
+            B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"],
+                                   best["layout"], band)
+        except B.GlcmError:
+            continue
+        ms = _time_config(ctx, images, levels, offsets, flags, reps)
+        tried.append({"threads": best["threads"], "log2_copies": best["log2_copies"], "layout": best["layout"],
+                      "band_rows": band, "ms": ms})
+        if ms < best["ms"]:
+            best = tried[-1]
+    B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"], best["layout"],
+                           best["band_rows"])
     return dict(best, tried=tried)
 
 
@@ -81,7 +99,8 @@ class TuneCache:
         return self.data.get(gpu, {}).get(key)
 
     def put(self, gpu: str, key: str, cfg: dict):
-        self.data.setdefault(gpu, {})[key] = {k: cfg[k] for k in ("threads", "log2_copies", "layout", "ms")}
+        self.data.setdefault(gpu, {})[key] = {k: cfg.get(k, 0) for k in ("threads", "log2_copies", "layout",
+                                                                           "band_rows", "ms")}
 
     def save(self):
         tmp = self.path + ".tmp"
@@ -94,7 +113,7 @@ class TuneCache:
         if not cfg:
             return False
         B.glcm_set_vote_config(ctx.ctx, levels, n_offsets, dtype, cfg["threads"], cfg["log2_copies"],
-                               cfg["layout"], 0)
+                               cfg["layout"], cfg.get("band_rows", 0))
         return True
 
 
@@ -111,7 +130,7 @@ def tune_classes(ctx, groups, flags: int = 0, cache: TuneCache | None = None, gp
             continue
         res = tune(ctx, images, levels, list(offsets), flags, reps)
         if res is not None:
-            chosen[key] = {k: res[k] for k in ("threads", "log2_copies", "layout", "ms")}
+            chosen[key] = {k: res[k] for k in ("threads", "log2_copies", "layout", "band_rows", "ms")}
             if cache is not None:
                 cache.put(gpu, key, res)
     if cache is not None:

@@ -29,7 +29,7 @@ struct DevBuf {
 struct VoteCfg {
     int threads = 512;
     int rshift = 5;     // log2 private copies
-    int layout = 1;     // see VoteJob::layout
+    int layout = 1;     // see VoteJob::layout; 4: the column-walk kernel for offsets at distance 1
     int band_rows = 0;  // 0: derived from the launch size
 };
 
@@ -48,6 +48,16 @@ struct GraphEntry {
     int n_kernels = 0;
 };
 
+// Jobs of the column-walk kernel for one (pixel type, N): one launch.
+struct FastClass {
+    int bpp = 1, log2n = 1;
+    std::vector<FastJob> jobs;
+    std::vector<int3> chunks;  // (class-local job, first item, end item)
+    int n_items = 0;
+    int max_hist_words = 0;
+    size_t jobs_off = 0, chunks_off = 0;  // byte offsets in the uploaded jobs buffer
+};
+
 // Host-side plan of one vote launch.
 struct VotePlan {
     std::vector<VoteJob> jobs;
@@ -60,7 +70,10 @@ struct VotePlan {
     int threads = 0;    // max over the plan's jobs
     int bpp = 1;
     int max_ctas = 0;   // grid cap (0: every SM), leaves SMs to a concurrent kernel
+    std::vector<FastClass> fast;  // column-walk launches (offsets at distance 1)
 };
+
+bool plan_empty(const VotePlan& p) { return p.jobs.empty() && p.fast.empty(); }
 
 }  // namespace
 
@@ -314,21 +327,24 @@ struct ImageSpec {
 // Append the jobs of one image to a plan.  Jobs run in the order
 // (superband, offset group, level part): when an image needs several passes
 // each pass re-reads at most one superband (<= 24 MB), which stays in L2.
-int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
+int plan_image_general(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, const std::vector<int>& idx)
 {
-    const VoteCfg cfg = get_cfg(ctx, s.levels, s.n_off, s.bpp);
+    const int n_gen = (int)idx.size();
+    if (n_gen == 0)
+        return GLCM_OK;
+    VoteCfg cfg = get_cfg(ctx, s.levels, s.n_off, s.bpp);
+    if (cfg.layout == 4)
+        cfg = default_cfg(ctx, s.levels, n_gen);
     const int T = std::max(plan.threads, cfg.threads);
     plan.threads = T;
     plan.bpp = s.bpp;
     const int nwarps = T / 32;
     const int PX = 16 / s.bpp;
-    const JobShape shape = job_shape(ctx, s.levels, s.n_off, cfg.layout, cfg.rshift);
+    const JobShape shape = job_shape(ctx, s.levels, n_gen, cfg.layout, cfg.rshift);
     if (shape.jobs <= 0)
         return fail(ctx, GLCM_ERR_ARG, "vote config cannot hold one level row of the histogram");
     // Offsets sorted by dy so a partner row is loaded once per distinct dy.
-    std::vector<int> order(s.n_off);
-    for (int k = 0; k < s.n_off; ++k)
-        order[k] = k;
+    std::vector<int> order(idx);
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return s.offsets[a].dy < s.offsets[b].dy; });
     const int opg = group_offsets(cfg.layout);
@@ -336,7 +352,6 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     const int rows = s.y_end - s.y_begin;
     const int strip_px = 32 * PX;
     const int n_strips = std::max(1, (s.W + strip_px - 1) / strip_px);
-    (void)target_items;
     // Default band: 64 anchor rows, or 32 when that leaves a small image fewer
     // than 16 items (a 512 x 512 image would run on 8 CTAs).
     int band = cfg.band_rows > 0 ? cfg.band_rows : kDefaultBand;
@@ -358,7 +373,7 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     }
     band = std::max(1, band);
     // Superbands only when the image takes several passes.
-    const int passes = ((s.n_off + per_job - 1) / per_job) * ((s.levels + shape.span - 1) / shape.span);
+    const int passes = ((n_gen + per_job - 1) / per_job) * ((s.levels + shape.span - 1) / shape.span);
     int sb_rows = rows;
     if (passes > 1) {
         const long long row_bytes = (long long)s.W * s.bpp;
@@ -368,13 +383,13 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     for (int sb0 = s.y_begin; sb0 < s.y_end; sb0 += sb_rows) {
         const int sb1 = std::min(s.y_end, sb0 + sb_rows);
         const int n_bands = (sb1 - sb0 + band - 1) / band;
-        for (int o0 = 0; o0 < s.n_off;) {
+        for (int o0 = 0; o0 < n_gen;) {
             // Up to per_job consecutive offsets (sorted by dy) whose dy range,
             // with 0, spans at most kMaxDySpan rows; a lone wider offset is
             // voted unstaged.
             int cnt = 1;
             int dmin = std::min(0, s.offsets[order[o0]].dy), dmax = std::max(0, s.offsets[order[o0]].dy);
-            while (o0 + cnt < s.n_off && cnt < per_job) {
+            while (o0 + cnt < n_gen && cnt < per_job) {
                 const int d = s.offsets[order[o0 + cnt]].dy;
                 const int nmin = std::min(dmin, d), nmax = std::max(dmax, d);
                 if (nmax - nmin > kMaxDySpan && dmax - dmin <= kMaxDySpan)
@@ -448,6 +463,152 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
         }
     }
     return GLCM_OK;
+}
+
+
+// Canonical offset (0: (1, 0), 1: (1, -1), 2: (0, -1), 3: (-1, -1)) of an
+// offset at chessboard distance 1 and whether it is the opposite one (its
+// counts are the canonical counts transposed); -1 for any other offset.
+int canonical_d1(int dx, int dy, bool& transposed)
+{
+    transposed = false;
+    if (std::max(std::abs(dx), std::abs(dy)) != 1)
+        return -1;
+    if (dy > 0 || (dy == 0 && dx < 0)) {
+        dx = -dx;
+        dy = -dy;
+        transposed = true;
+    }
+    if (dy == 0)
+        return 0;
+    return dx == 1 ? 1 : (dx == 0 ? 2 : 3);
+}
+
+FastClass& fast_class(VotePlan& plan, int bpp, int log2n)
+{
+    for (FastClass& c : plan.fast)
+        if (c.bpp == bpp && c.log2n == log2n)
+            return c;
+    plan.fast.emplace_back();
+    plan.fast.back().bpp = bpp;
+    plan.fast.back().log2n = log2n;
+    return plan.fast.back();
+}
+
+// Items per chunk of the column-walk kernel: one per warp of a CTA.
+constexpr int kFastChunkItems = 16;
+
+// Column-walk jobs of one image for the canonical offsets in `present`
+// (slot / slot_t: the output GLCMs of each canonical offset as counted and
+// transposed).  Bands of 64 anchor rows, halved down to 8 while the image
+// has fewer items than its share of the launch (about two chunks per CTA).
+void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int present, const int (&slot)[4],
+                     const int (&slot_t)[4], int target_items)
+{
+    int band_override = 0;
+    {
+        auto it = ctx->overrides.find(cfg_key(s.levels, s.n_off, s.bpp));
+        if (it != ctx->overrides.end() && it->second.layout == 4)
+            band_override = it->second.band_rows;
+    }
+    const int log2n = ilog2_exact(s.levels);
+    FastClass& fc = fast_class(plan, s.bpp, log2n);
+    const int PX = 16 / s.bpp;
+    const int n_strips = (s.W + 32 * PX - 1) / (32 * PX);
+    const int rows = s.y_end - s.y_begin;
+    if (rows <= 0 || n_strips <= 0)
+        return;
+    int band = 64;
+    while (band > 8 && (long long)n_strips * ((rows + band - 1) / band) < target_items)
+        band /= 2;
+    if (band_override > 0)
+        band = std::min(band_override, 1024);
+    const int n_bands = (rows + band - 1) / band;
+    struct Group {
+        int mode, present, half_hi;
+    };
+    std::vector<Group> groups;
+    if (log2n <= 3 && present == 15) {
+        groups.push_back({kFastJoint, 15, -1});
+    } else if (log2n <= 4) {
+        groups.push_back({kFastPair, present, -1});
+    } else {
+        int pending = -1;
+        for (int k = 0; k < 4; ++k) {
+            if (!((present >> k) & 1))
+                continue;
+            if (pending < 0) {
+                pending = k;
+            } else {
+                groups.push_back({kFastHalf, (1 << pending) | (1 << k), k});
+                pending = -1;
+            }
+        }
+        if (pending >= 0)
+            groups.push_back({kFastHalf, 1 << pending, -1});
+    }
+    for (const Group& g : groups) {
+        FastJob j{};
+        j.img = s.img;
+        j.pitch = s.pitch;
+        j.W = s.W;
+        j.H = s.H;
+        j.bpp = s.bpp;
+        j.log2n = log2n;
+        j.mode = g.mode;
+        j.present = g.present;
+        j.half_hi = g.half_hi;
+        for (int k = 0; k < 4; ++k) {
+            const bool in = (g.present >> k) & 1;
+            j.slot[k] = in ? slot[k] : -1;
+            j.slot_t[k] = in ? slot_t[k] : -1;
+        }
+        j.hist_words = vote_fast_hist_words(log2n, g.mode);
+        j.item0 = fc.n_items;
+        j.n_items = n_strips * n_bands;
+        j.n_strips = n_strips;
+        j.band = band;
+        j.y_begin = s.y_begin;
+        j.y_end = s.y_end;
+        j.out = s.out;
+        const int jb = (int)fc.jobs.size();
+        for (int k = 0; k < j.n_items; k += kFastChunkItems)
+            fc.chunks.push_back(make_int3(jb, j.item0 + k, j.item0 + std::min(j.n_items, k + kFastChunkItems)));
+        fc.n_items += j.n_items;
+        fc.max_hist_words = std::max(fc.max_hist_words, j.hist_words);
+        fc.jobs.push_back(j);
+    }
+}
+
+// Append the jobs of one image to a plan: offsets at chessboard distance 1 of
+// a uint8/uint16 image with N a power of two up to 32 (aligned rows, levels
+// quantized here) go to the column-walk kernel unless the autotuner chose a
+// general layout for the class; the others to the general vote kernel.
+int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
+{
+    const int log2n = ilog2_exact(s.levels);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
+    auto it = ctx->overrides.find(cfg_key(s.levels, s.n_off, s.bpp));
+    const bool tuned_general = it != ctx->overrides.end() && it->second.layout != 4;
+    const bool eligible = !tuned_general && log2n >= 1 && log2n <= 5 && aligned &&
+                          !s.levels_mode && s.y_end > s.y_begin;
+    std::vector<int> gen;
+    int present = 0;
+    int slot[4] = {-1, -1, -1, -1}, slot_t[4] = {-1, -1, -1, -1};
+    for (int k = 0; k < s.n_off; ++k) {
+        bool tr = false;
+        const int c = eligible ? canonical_d1(s.offsets[k].dx, s.offsets[k].dy, tr) : -1;
+        int* dst = c < 0 ? nullptr : (tr ? &slot_t[c] : &slot[c]);
+        if (dst && *dst < 0) {
+            *dst = k;
+            present |= 1 << c;
+        } else {
+            gen.push_back(k);  // any other offset, or a repeat of one already placed
+        }
+    }
+    if (present)
+        plan_image_fast(ctx, s, plan, present, slot, slot_t, 2 * target_items);
+    return plan_image_general(ctx, s, plan, gen);
 }
 
 int check_image_args(glcm_ctx* ctx, const void* image, int width, int height, size_t pitch, int dtype,
@@ -524,7 +685,19 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
                   DevBuf& doffs, DevBuf& dfeat)
 {
     const size_t bj0 = (plan.jobs.size() * sizeof(VoteJob) + 15) & ~(size_t)15;
-    const size_t bj = bj0 + plan.chunks.size() * sizeof(int3);
+    // Column-walk tables after the general chunks: every class's jobs back to
+    // back (one array over all classes, which the zeroing kernel walks), then
+    // every class's chunks.
+    size_t bj = (bj0 + plan.chunks.size() * sizeof(int3) + 15) & ~(size_t)15;
+    for (const FastClass& c : plan.fast) {
+        const_cast<FastClass&>(c).jobs_off = bj;
+        bj += c.jobs.size() * sizeof(FastJob);
+    }
+    bj = (bj + 15) & ~(size_t)15;
+    for (const FastClass& c : plan.fast) {
+        const_cast<FastClass&>(c).chunks_off = bj;
+        bj += c.chunks.size() * sizeof(int3);
+    }
     const size_t bo = plan.offs.size() * sizeof(VoteOffset);
     const size_t bf = feats.size() * sizeof(FeatJob);
     TRY(ensure(ctx, djobs, bj));
@@ -541,6 +714,12 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
     if (!plan.chunks.empty())
         memcpy(h + bj0, plan.chunks.data(), plan.chunks.size() * sizeof(int3));
     const_cast<VotePlan&>(plan).chunk_off = bj0;
+    for (const FastClass& c : plan.fast) {
+        if (!c.jobs.empty())
+            memcpy(h + c.jobs_off, c.jobs.data(), c.jobs.size() * sizeof(FastJob));
+        if (!c.chunks.empty())
+            memcpy(h + c.chunks_off, c.chunks.data(), c.chunks.size() * sizeof(int3));
+    }
     if (bo)
         memcpy(h + oo, plan.offs.data(), bo);
     if (bf)
@@ -576,17 +755,46 @@ int zero_words(glcm_ctx* ctx, uint32_t* p, long long n, cudaStream_t st)
     return GLCM_OK;
 }
 
-__global__ void k_zero_job_outputs(const VoteJob* jobs, const VoteOffset* offs, unsigned* counter)
+// Chunk counters in the context's device words: [1] the general vote kernel,
+// [2 + c] column-walk class c.
+constexpr int kCounterWords = 12;
+constexpr int kMaxFastClasses = kCounterWords - 2;
+
+// Blocks [0, n_gen) zero general job b's outputs, blocks [n_gen, n_gen +
+// n_fast) the outputs of column-walk job b - n_gen; block 0 also clears the
+// chunk counters.
+__global__ void k_zero_job_outputs(const VoteJob* jobs, int n_gen, const VoteOffset* offs, const FastJob* fjobs,
+                                   unsigned* counters)
 {
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-        *counter = 0u;
-    const VoteJob j = jobs[blockIdx.x];
-    const long long NN = (long long)j.levels * j.levels;
-    for (int o = 0; o < j.n_off; ++o) {
-        uint32_t* dst = j.out + offs[j.off0 + o].slot * NN;
-        for (long long k = threadIdx.x; k < NN; k += blockDim.x)
-            dst[k] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < kCounterWords - 1)
+        counters[threadIdx.x] = 0u;
+    if ((int)blockIdx.x < n_gen) {
+        const VoteJob j = jobs[blockIdx.x];
+        const long long NN = (long long)j.levels * j.levels;
+        for (int o = 0; o < j.n_off; ++o) {
+            uint32_t* dst = j.out + offs[j.off0 + o].slot * NN;
+            for (long long k = threadIdx.x; k < NN; k += blockDim.x)
+                dst[k] = 0u;
+        }
+        return;
     }
+    const FastJob& f = fjobs[blockIdx.x - n_gen];
+    const long long NN = 1ll << (2 * f.log2n);
+    for (int k = 0; k < kFastOffsets; ++k)
+        for (int t = 0; t < 2; ++t) {
+            const int sl = t ? f.slot_t[k] : f.slot[k];
+            if (sl < 0)
+                continue;
+            uint32_t* dst = f.out + sl * NN;
+            for (long long e = threadIdx.x; e < NN; e += blockDim.x)
+                dst[e] = 0u;
+        }
+}
+
+__global__ void k_clear_counters(unsigned* counters)
+{
+    if (threadIdx.x < kCounterWords - 1)
+        counters[threadIdx.x] = 0u;
 }
 
 TimedPair take_pair(glcm_ctx* ctx)
@@ -606,15 +814,24 @@ TimedPair take_pair(glcm_ctx* ctx)
 int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, const int3* dchunks,
                  bool zero, bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
 {
-    if (plan.jobs.empty())
+    if (plan_empty(plan))
         return GLCM_OK;
     if (!st)
         st = ctx->stream;
+    if ((int)plan.fast.size() > kMaxFastClasses)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "more column-walk classes than chunk counters");
+    int n_fast_jobs = 0;
+    for (const FastClass& c : plan.fast)
+        n_fast_jobs += (int)c.jobs.size();
+    const FastJob* fjobs0 =
+        plan.fast.empty() ? nullptr
+                          : reinterpret_cast<const FastJob*>(static_cast<uint8_t*>(djobs.p) + plan.fast[0].jobs_off);
     if (zero) {
-        k_zero_job_outputs<<<(int)plan.jobs.size(), 256, 0, st>>>(
-            static_cast<const VoteJob*>(djobs.p), static_cast<const VoteOffset*>(doffs.p), ctx->d_words + 1);
+        k_zero_job_outputs<<<(int)plan.jobs.size() + n_fast_jobs, 256, 0, st>>>(
+            static_cast<const VoteJob*>(djobs.p), (int)plan.jobs.size(), static_cast<const VoteOffset*>(doffs.p),
+            fjobs0, ctx->d_words + 1);
     } else {
-        k_clear_word<<<1, 1, 0, st>>>(ctx->d_words + 1);
+        k_clear_counters<<<1, 32, 0, st>>>(ctx->d_words + 1);
     }
     CK(cudaGetLastError());
     ctx->kernel_launches += capturing ? 0 : 1;
@@ -632,25 +849,47 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     vp.item_counter = ctx->d_words + 1;
     vp.err = ctx->d_words;
     const size_t smem = vote_smem(plan);
-    const int grid = grid_for(ctx, plan);
+    const int grid = plan.jobs.empty() ? 1 : grid_for(ctx, plan);
     TimedPair tp{};
     const bool time_it = ctx->timing && !capturing;
     if (time_it) {
         tp = take_pair(ctx);
         CK(cudaEventRecord(tp.a, st));
     }
-    CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
+    int n_launch = 0;
+    for (size_t ci = 0; ci < plan.fast.size(); ++ci) {
+        const FastClass& c = plan.fast[ci];
+        if (c.chunks.empty())
+            continue;
+        FastParams fp{};
+        fp.jobs = reinterpret_cast<const FastJob*>(static_cast<uint8_t*>(djobs.p) + c.jobs_off);
+        fp.chunks = reinterpret_cast<const int3*>(static_cast<uint8_t*>(djobs.p) + c.chunks_off);
+        fp.n_chunks = (int)c.chunks.size();
+        fp.max_hist_words = c.max_hist_words;
+        fp.chunk_counter = ctx->d_words + 2 + ci;
+        fp.err = ctx->d_words;
+        const size_t fsmem = vote_fast_smem_bytes(c.max_hist_words);
+        int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve);
+        if (plan.max_ctas > 0)
+            ctas = std::min(ctas, plan.max_ctas);
+        CK(launch_vote_fast(fp, c.bpp, c.log2n, std::max(1, std::min(fp.n_chunks, ctas)), fsmem, st));
+        ++n_launch;
+    }
+    if (!plan.jobs.empty()) {
+        CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
+        ++n_launch;
+    }
     if (time_it) {
         CK(cudaEventRecord(tp.b, st));
         ctx->pending.push_back(tp);
     }
     if (!capturing) {
-        ctx->kernel_launches += 1;
-        ctx->vote_launches += 1;
+        ctx->kernel_launches += n_launch;
+        ctx->vote_launches += n_launch;
     }
     if (ge) {
-        ge->n_kernels++;
-        ge->n_vote_kernels++;
+        ge->n_kernels += n_launch;
+        ge->n_vote_kernels += n_launch;
     }
     return GLCM_OK;
 }
@@ -1085,8 +1324,22 @@ extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, in
         return GLCM_OK;
     }
     if (threads % 32 || threads < 64 || threads > kMaxThreads || log2_copies < 0 || log2_copies > 5 ||
-        layout < 0 || layout > 3 || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1 || band_rows < 0)
+        layout < 0 || layout > 4 || levels < 2 || levels > GLCM_MAX_LEVELS || n_offsets < 1 || band_rows < 0)
         return fail(ctx, GLCM_ERR_ARG, "invalid vote config");
+    if (layout == 4) {
+        // The column-walk kernel: N a power of two up to 32; threads and
+        // copies are fixed by the kernel, band_rows (0 = derived) is its item height.
+        const int l2 = ilog2_exact(levels);
+        if (l2 < 1 || l2 > 5)
+            return fail(ctx, GLCM_ERR_ARG, "the column-walk kernel needs N a power of two up to 32");
+        VoteCfg c;
+        c.threads = 512;
+        c.rshift = 5;
+        c.layout = 4;
+        c.band_rows = band_rows;
+        ctx->overrides[key] = c;
+        return GLCM_OK;
+    }
     if (job_shape(ctx, levels, n_offsets, layout, log2_copies).jobs <= 0)
         return fail(ctx, GLCM_ERR_ARG, "one level row of the histograms does not fit shared memory");
     if (layout == 2 && 65535ll * (1 << log2_copies) / ((16 / bpp) * (long long)threads) < 1)
@@ -1162,7 +1415,7 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         VotePlan plan;
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
                     offsets, n_offsets, d_counts, r0, r1};
-        TRY(plan_image(ctx, s, plan, target_items(ctx)));
+        TRY(plan_image(ctx, s, plan, 4 * target_items(ctx) / n_stripes));
         build_chunks(plan, ctx->sm_count);
         std::vector<FeatJob> none;
         TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
@@ -1320,7 +1573,10 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
             dst.jobs.push_back(c);
         }
     }
+    // The column-walk classes (either pixel type) launch with the uint8 part.
+    sb.p8.fast = plan.fast;
     VotePlan all;
+    all.fast = plan.fast;
     all.jobs = sb.p8.jobs;
     all.jobs.insert(all.jobs.end(), sb.p16.jobs.begin(), sb.p16.jobs.end());
     for (size_t k = sb.p8.jobs.size(); k < all.jobs.size(); ++k)
@@ -1332,6 +1588,10 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
     all.chunks = sb.p8.chunks;
     all.chunks.insert(all.chunks.end(), sb.p16.chunks.begin(), sb.p16.chunks.end());
     TRY(upload_tables(ctx, all, sb.feats, djobs, doffs, dfeat));
+    for (size_t c = 0; c < all.fast.size(); ++c) {
+        sb.p8.fast[c].jobs_off = all.fast[c].jobs_off;
+        sb.p8.fast[c].chunks_off = all.fast[c].chunks_off;
+    }
     sb.j16.p = static_cast<VoteJob*>(djobs.p) + sb.p8.jobs.size();
     sb.o16.p = doffs.p;  // p16's off0 are already shifted past p8's offsets
     sb.c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(djobs.p) + all.chunk_off);
@@ -1345,9 +1605,9 @@ int enqueue_batch(glcm_ctx* ctx, const SplitBatch& sb, const DevBuf& djobs, cons
 {
     if (capturing)
         TRY(capture_mark(ctx, ge, true));
-    if (!sb.p8.jobs.empty())
+    if (!plan_empty(sb.p8))
         TRY(enqueue_vote(ctx, sb.p8, djobs, doffs, sb.c8, true, capturing, ge));
-    if (!sb.p16.jobs.empty())
+    if (!plan_empty(sb.p16))
         TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, capturing, ge));
     if (capturing)
         TRY(capture_mark(ctx, ge, false));
@@ -1363,18 +1623,18 @@ int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, Sp
 {
     if (capturing)
         TRY(capture_mark(ctx, ge, true));
-    if (!h.p8.jobs.empty())
+    if (!plan_empty(h.p8))
         TRY(enqueue_vote(ctx, h.p8, th[0], th[1], h.c8, true, capturing, ge));
-    if (!h.p16.jobs.empty())
+    if (!plan_empty(h.p16))
         TRY(enqueue_vote(ctx, h.p16, h.j16, h.o16, h.c16, true, capturing, ge));
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
     TRY(enqueue_features(ctx, h.feats, th[2], h.max_levels, capturing, ge, ctx->side_stream));
     const int reserve = std::min((int)h.feats.size(), ctx->sm_count / 4);
     r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - reserve);
-    if (!r.p8.jobs.empty())
+    if (!plan_empty(r.p8))
         TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge));
-    if (!r.p16.jobs.empty())
+    if (!plan_empty(r.p16))
         TRY(enqueue_vote(ctx, r.p16, r.j16, r.o16, r.c16, true, capturing, ge));
     if (capturing)
         TRY(capture_mark(ctx, ge, false));
@@ -1559,9 +1819,9 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
         CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[g], 0));
         auto& tab = ctx->hb_tab[g];
         SplitBatch& sb = sbs[g];
-        if (!sb.p8.jobs.empty())
+        if (!plan_empty(sb.p8))
             TRY(enqueue_vote(ctx, sb.p8, tab[0], tab[1], sb.c8, true, false, nullptr));
-        if (!sb.p16.jobs.empty())
+        if (!plan_empty(sb.p16))
             TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, false, nullptr));
         // Every group's epilogue and read-back off the vote stream, so the next
         // group's vote does not wait behind them and only the last group's

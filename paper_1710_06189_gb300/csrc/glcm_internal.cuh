@@ -84,6 +84,47 @@ struct VoteParams {
     unsigned* err;           // error bits (kErr*)
 };
 
+// Column-walk vote kernel (vote_fast.cu) for offsets at chessboard distance 1.
+// The canonical offsets are k = 0: (1, 0), 1: (1, -1), 2: (0, -1), 3: (-1, -1)
+// (partner to the right or in the row above); every offset at distance 1 is
+// one of them or its opposite, whose GLCM is the transpose (an anchor of one
+// is the partner of the other).
+constexpr int kFastOffsets = 4;
+enum : int {
+    kFastJoint = 0,  // N <= 8, all four offsets: two joint votes per anchor
+    kFastPair = 1,   // N <= 16: one vote per anchor and offset, two offsets per bin row
+    kFastHalf = 2,   // N = 32: up to two offsets as 16-bit halves of one word
+};
+
+struct FastJob {
+    const uint8_t* img;
+    long long pitch;   // bytes between rows (base and pitch 16-byte aligned)
+    int W, H;
+    int bpp;           // 1 or 2
+    int log2n;         // N = 2^log2n, 1..5
+    int mode;          // kFast*
+    int present;       // bit k: canonical offset k is voted by this job
+    int half_hi;       // kFastHalf: the offset (k) counted in the upper halves, or -1
+    int slot[kFastOffsets];    // output GLCM of canonical offset k, or -1
+    int slot_t[kFastOffsets];  // output GLCM that receives its transpose, or -1
+    int hist_words;    // shared words of the job's histograms
+    int item0;         // first item of this job in the launch
+    int n_items;       // items: n_strips column strips x bands of band rows
+    int n_strips;
+    int band;
+    int y_begin, y_end;  // anchor rows voted by this job
+    uint32_t* out;     // counts: GLCM s at out + s*N*N
+};
+
+struct FastParams {
+    const FastJob* jobs;
+    const int3* chunks;       // (job, first item, end item), job-major order
+    int n_chunks;
+    int max_hist_words;
+    unsigned* chunk_counter;  // zeroed before each launch
+    unsigned* err;
+};
+
 // Epilogue: symmetrize / normalize / Haralick features for one GLCM.
 struct FeatJob {
     const uint32_t* counts;  // N*N
@@ -163,6 +204,12 @@ private:
 // packed: some job of the launch uses layout 3 (a separate kernel instance).
 cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, size_t smem,
                         cudaStream_t s, bool packed = false);
+// Column-walk votes: one launch per pixel type and N (every job of the launch
+// has them).
+cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, int grid, size_t smem, cudaStream_t s);
+size_t vote_fast_smem_bytes(int max_hist_words);
+int vote_fast_hist_words(int log2n, int mode);
+int vote_fast_blocks_per_sm(int bpp, int log2n, size_t smem);
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);

@@ -16,10 +16,11 @@ def test_cache_round_trip(tmp_path):
     path = str(tmp_path / "tune.json")
     cache = autotune.TuneCache(path)
     assert cache.get("gpu", "k") is None
-    cache.put("gpu", "k", {"threads": 512, "log2_copies": 5, "layout": 1, "ms": 0.25, "tried": [1, 2]})
+    cache.put("gpu", "k", {"threads": 512, "log2_copies": 5, "layout": 1, "band_rows": 32, "ms": 0.25,
+                           "tried": [1, 2]})
     cache.save()
     again = autotune.TuneCache(path)
-    assert again.get("gpu", "k") == {"threads": 512, "log2_copies": 5, "layout": 1, "ms": 0.25}
+    assert again.get("gpu", "k") == {"threads": 512, "log2_copies": 5, "layout": 1, "band_rows": 32, "ms": 0.25}
     assert again.get("other", "k") is None
     with open(path) as f:
         assert "tried" not in json.load(f)["gpu"]["k"]
@@ -28,4 +29,9 @@ def test_cache_round_trip(tmp_path):
 def test_default_candidates_are_valid_shapes():
     for threads, r, layout in autotune.DEFAULT_CANDIDATES:
         assert threads % 32 == 0 and 64 <= threads <= 1024
-        assert 0 <= r <= 5 and layout in (0, 1, 2, 3)
+        assert 0 <= r <= 5 and layout in (0, 1, 2, 3, 4)
+    assert autotune.DEFAULT_CANDIDATES[0][2] == 4  # the column-walk kernel is tried first
+    for layout, bands in autotune.BAND_CANDIDATES.items():
+        assert bands[0] == 0 and all(b > 0 for b in bands[1:])
+        if layout != 4:
+            assert max(bands) <= 64  # the general kernel's tiles hold 64 anchor rows
