@@ -15,10 +15,14 @@ Printed (one JSON line, rank 0): value = pairs per second over all ranks
 with inputs resident in HBM; e2e = the same through the C ABI with pinned
 host buffers (host->device image copies and device->host results inside the
 timed region); plain = one image at a time with a sync per image; roofline
-of the vote kernel from CUDA events on its stream; serving = the served
-stream (continuous batching vs a one-at-a-time loop, p50/p99 latency);
-cpu_baseline = the CPU oracle on a bounded sample.  ``--impl reference``
-times the oracle alone.
+of the vote kernels from CUDA events on their stream; ceilings = measured
+shared-reduction and HBM-read rates (glcm_measure_ceilings); classes = each
+kind and N of the sweep as one image per launch (the vote kernel's own
+roofline line per class); serving = the served stream (continuous batching
+vs a one-at-a-time loop, p50/p99 latency); parity = the timed batch's own
+counts, normalized GLCMs and features against the CPU oracle (a mismatch
+makes the run fail); cpu_baseline = the CPU oracle on a bounded sample.
+``--impl reference`` times the oracle alone.
 """
 from __future__ import annotations
 
@@ -41,6 +45,14 @@ UNIT = "Gpairs/s"
 WORKLOAD = ("contention sweep: 12 x 4096^2 uint8 images (iid, smooth sigma=8, constant 128) x N in "
             "{8,16,32,256}, offsets d=1 at 0/45/90/135 deg, plain uint32 counts + symmetric normalized GLCMs "
             "+ 14 Haralick features, one batched graph launch per step")
+
+
+def workload_config():
+    """The workload both arms measure (the same dict in both JSON lines)."""
+    return {"workload": WORKLOAD, "images": 12, "side": 4096, "levels": [8, 16, 32, 256],
+            "kinds": ["iid", "smooth", "constant"], "offsets": [[1, 0], [1, -1], [0, -1], [-1, -1]],
+            "pairs_per_step": 12 * 67084290, "image_bytes_per_step": 12 * 4096 * 4096,
+            "l2": "inputs 201 MB > 129 MB L2 per step, no flush"}
 
 
 def rank_helpers(dist):
@@ -109,7 +121,7 @@ def code_sha256(text: str) -> str:
 
 
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling (every 100 ms) over a loaded window.
+    """nvidia-smi clock / throttle sampling (every 50 ms) over a loaded window.
 
     The window is the timed region plus LOAD_SECONDS of the same step before and
     after it, so that a timed region shorter than the sampling period still has
@@ -128,7 +140,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -271,8 +283,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / max(1, args.steps),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": "each step: whole images of the sweep for ~%.0f s" % per_step},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": descs[-1]},
+            "config": workload_config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "each step: whole images of the sweep for ~%.0f s; last: %s" % (per_step, descs[-1])},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -491,10 +504,96 @@ def other_workloads(G, S, torch, local: int):
     return out
 
 
+def ceilings_leg(G, local: int):
+    """Measured ceilings of the vote kernels on this GPU (glcm_measure_ceilings):
+    shared-memory reductions per second for interleaved copies, one word per
+    warp and random words of one copy, and a streaming HBM read rate."""
+    c = G.binding.glcm_measure_ceilings(local)
+    c["kind"] = "measured by microbenchmark kernels in csrc/ceilings.cu (glcm_measure_ceilings)"
+    return c
+
+
+CLASS_POOL = 8  # distinct 4096^2 images per class (134 MB, above the 129 MB L2)
+
+
+def class_lines(G, torch, ctx, imgs, jobs, local: int, peak: float, ceil_red: float | None, stream, reps: int = 5):
+    """Per-class vote-kernel lines: each 4096^2 uint8 image timed alone (one
+    glcm_compute per image, the context's CUDA events around its vote launch),
+    for every kind and N of the sweep.  A class rotates over 8 distinct images:
+    the sweep's four images of that kind and four circular shifts of them
+    (the smooth generator is circular, so shifts keep its statistics).  Runs
+    on the benchmark's context, so each class has the vote configuration the
+    batch was timed with."""
+    out = {}
+    offs = jobs[0]["offsets"]
+    pairs = pairs_of(4096, 4096, offs)
+    by_kind = {}
+    for im, j in zip(imgs, jobs):
+        by_kind.setdefault(j["kind"], []).append(im)
+    G.glcm_get_timing(ctx.ctx, reset=True)
+    for kind, base in by_kind.items():
+        with torch.cuda.stream(stream):
+            pool = list(base) + [torch.roll(b, shifts=977 * (k + 1), dims=1) for k, b in enumerate(base)]
+            pool = pool[:CLASS_POOL]
+        for n in sorted({j["levels"] for j in jobs}):
+            res = torch.empty((len(offs), n, n), dtype=torch.int32, device=f"cuda:{local}")
+            with torch.cuda.stream(stream):
+                for im in pool:
+                    ctx.compute(im, n, offs, out=res)
+                stream.synchronize()
+                G.glcm_get_timing(ctx.ctx, reset=True)
+                for _ in range(reps):
+                    for im in pool:
+                        ctx.compute(im, n, offs, out=res)
+                ms, nl, _ = G.glcm_get_timing(ctx.ctx, reset=True)
+            us = ms * 1e3 / (reps * len(pool))
+            gbs = 4096 * 4096 / (us * 1e-6) / 1e9
+            line = {"us_per_image": us, "hbm_read_gbs": gbs, "frac_of_hbm": gbs / peak,
+                    "tvotes_s": pairs / (us * 1e-6) / 1e12, "vote_launches_per_image": nl / (reps * len(pool))}
+            if ceil_red:
+                line["frac_of_red_ceiling"] = pairs / (us * 1e-6) / ceil_red
+            out[f"{kind}_N{n}"] = line
+        del pool
+    return out
+
+
+def parity_leg(outs, jobs):
+    """The timed batch's own results against the CPU oracle: counts bit for bit
+    for every GLCM, symmetric normalized GLCMs within 4e-7 relative, features
+    within 1e-5 scaled error (floor 1 for correlation and the three
+    correlation measures, 1/N^2 for the rest).  Part of the CPU-baseline leg."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    worst, worst_norm, bad = 0.0, 0.0, []
+    for (c, nm, ft), j in zip(outs, jobs):
+        P = oracle.glcm(j["image"], j["levels"], j["offsets"])
+        got = c.cpu().numpy().view(np.uint32)
+        if not np.array_equal(got, P):
+            bad.append(f"{j['kind']} N={j['levels']}: counts differ at {int((got != P).sum())} bins")
+            continue
+        S_ = oracle.symmetrize(P)
+        pw = oracle.normalize(S_)
+        g = nm.cpu().numpy().astype(np.float64)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            rn = np.where(pw > 0, np.abs(g - pw) / pw, np.abs(g - pw))
+        worst_norm = max(worst_norm, float(rn.max()))
+        fw = oracle.haralick_batch(P, True)
+        floor = np.full(14, 1.0 / (j["levels"] ** 2))
+        floor[[2, 11, 12, 13]] = 1.0
+        err = np.abs(ft.cpu().numpy().astype(np.float64) - fw) / np.maximum(np.abs(fw), floor)
+        worst = max(worst, float(err.max()))
+    ok = not bad and worst <= 1e-5 and worst_norm <= 4e-7
+    return {"counts": "bit_exact" if not bad else "MISMATCH", "glcms": sum(len(j["offsets"]) for j in jobs),
+            "max_scaled_feature_error": worst, "max_normalized_rel_error": worst_norm, "ok": ok,
+            "failures": bad}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=600)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -504,6 +603,8 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
     ap.add_argument("--no-tune", action="store_true", help="use the planner's default vote configurations")
+    ap.add_argument("--no-classes", action="store_true", help="skip the per-class single-image lines")
+    ap.add_argument("--no-ceilings", action="store_true", help="skip the shared-reduction / HBM ceilings")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -524,6 +625,7 @@ def main():
     torch.cuda.set_device(local)
     G.binding.load()
 
+    ceilings = None if args.no_ceilings else ceilings_leg(G, local)
     jobs = S.contention_jobs(4096)
     pairs_step = sum(pairs_of(4096, 4096, j["offsets"]) for j in jobs)
     bytes_step = sum(j["image"].nbytes for j in jobs)
@@ -619,12 +721,17 @@ def main():
     e2e_value = world * pairs_step * e2e_steps / e2e_s / 1e9
     d2h = sum(o[0].numel() * 4 + o[1].numel() * 4 + o[2].numel() * 4 for o in h_outs)
 
+    peak, peak_kind = load_peaks()
+    classes = None
+    if not args.no_classes:
+        classes = class_lines(G, torch, ctx, imgs, jobs, local, peak,
+                              ceilings["red_interleaved_per_s"] if ceilings else None, stream)
+
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    peak, peak_kind = load_peaks()
     # One CUDA-event pair brackets all vote launches of a step (one launch, or
     # two when the batch is split so that expensive epilogues overlap votes).
     avg_vote_ms = vote_ms / max(1, args.steps)
@@ -634,14 +741,12 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "images": len(jobs), "side": 4096, "levels": [8, 16, 32, 256],
-                   "kinds": ["iid", "smooth", "constant"], "offsets": S.CONTENTION_OFFSETS,
-                   "pairs_per_step": pairs_step, "image_bytes_per_step": bytes_step,
-                   "l2": "inputs 201 MB > 129 MB L2 per step, no flush",
-                   "vote_configs": tuned or "planner defaults"},
+        "config": workload_config(),
+        "vote_configs": tuned or "planner defaults",
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-                     "kernel": "k_glcm_vote", "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                     "kernel": "vote kernels (k_glcm_vote_d1 column walk, k_glcm_vote general)",
+                     "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                      "vote_ms_per_step": avg_vote_ms, "vote_launches_per_step": vote_n / max(1, args.steps),
                      "algorithmic_bytes_per_step": bytes_step},
         "plain": {"value": plain_value, "unit": UNIT, "batched_over_plain": value / plain_value},
@@ -649,20 +754,37 @@ def main():
         "gpu_launches": launches,
         "clocks": clk.summary(),
     }
+    if ceilings:
+        line["ceilings"] = ceilings
+        line["roofline"]["red_ceiling_per_s"] = ceilings["red_interleaved_per_s"]
+        line["roofline"]["tvotes_s"] = pairs_step / (avg_vote_ms * 1e-3) / 1e12 if avg_vote_ms > 0 else None
+    if classes:
+        line["classes"] = {"workload": "one 4096^2 uint8 image per launch, 4 offsets at d = 1, vote kernel only "
+                                       "(CUDA events), 8 distinct images per class (134 MB > L2)",
+                           "peak_kind": f"{peak_kind} hbm_gbs (copy)", "lines": classes}
     if not args.no_serving:
         line["serving"] = serving_leg(G, S, torch, local)
     if not args.no_extra:
         line["other_workloads"] = other_workloads(G, S, torch, local)
+    parity = None
     if not args.no_cpu_baseline and world == 1:
+        # The oracle, first on the timed batch's own results (untimed), then timed.
+        parity = parity_leg(step_batch.outs, jobs)
+        line["parity"] = parity
         v, desc = oracle_sample(jobs, args.cpu_seconds)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
         if args.cpu_all_seconds > 0:
             va, nt, da = oracle_sample_all_cores(jobs, args.cpu_all_seconds)
             line["cpu_baseline"]["all_cores"] = {"value": va, "unit": UNIT, "cores": nt, "sample": da}
+    else:
+        line["parity"] = "not checked (no CPU-baseline leg)"
     print(json.dumps(line))
     ctx.close()
     if dist is not None:
         dist.destroy_process_group()
+    if parity is not None and not parity["ok"]:
+        print(f"parity check failed: {parity}", file=sys.stderr)
+        return 1
     return 0
 
 

@@ -289,6 +289,30 @@ int glcm_compute_noalloc(const void *image, int width, int height, size_t pitch_
                          int levels, const glcm_offset *offsets, int n_offsets, int flags,
                          uint32_t *counts, void *cuda_stream, char *errbuf, size_t errbuf_len);
 
+/* ---- Measured ceilings ---------------------------------------------------
+ *
+ * The rates the vote kernels are held against, measured on `device` by
+ * microbenchmarks (the paper weighs its copy strategy by the serialization of
+ * colliding votes, Sec. I.B and Sec. II.A; these are that serialization's
+ * limits on this GPU).  Shared-memory reductions (red.shared.add.u32, one
+ * per vote) per second over the whole GPU, one 512-thread CTA per SM, for
+ *   red_interleaved_per_s      lane l of every warp on bank l (the
+ *                              lane-interleaved private copies: no conflict)
+ *   red_same_word_per_s        every lane of a warp on one word, increment 1
+ *   red_random_one_copy_per_s  each lane on a random word of one 128 KB copy
+ * and hbm_read_gbs, the best of five streaming 16-byte-load reads of a 1 GiB
+ * buffer (GB/s, 1e9 bytes).  Allocates 1 GiB for the duration of the call.
+ * Errors: GLCM_ERR_ARG (bad device, out NULL), GLCM_ERR_NOMEM, GLCM_ERR_CUDA. */
+typedef struct {
+    int sm_count;
+    double red_interleaved_per_s;
+    double red_same_word_per_s;
+    double red_random_one_copy_per_s;
+    double hbm_read_gbs;
+} glcm_ceilings;
+
+int glcm_measure_ceilings(int device, glcm_ceilings *out);
+
 /* ---- Serving: continuous batching of host requests ----------------------
  *
  * A server owns a device-memory arena of hbm_budget_bytes, `lanes` contexts

@@ -50,6 +50,11 @@ class glcm_server_stats_t(ctypes.Structure):
                 ("queue_peak", c_longlong), ("arena_bytes", c_size_t), ("arena_peak", c_size_t)]
 
 
+class glcm_ceilings_t(ctypes.Structure):
+    _fields_ = [("sm_count", c_int), ("red_interleaved_per_s", c_double), ("red_same_word_per_s", c_double),
+                ("red_random_one_copy_per_s", c_double), ("hbm_read_gbs", c_double)]
+
+
 class GlcmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"glcm status {status}: {message}")
@@ -84,6 +89,7 @@ _PROTOS = {
                                    c_int, c_void_p]),
     "glcm_compute_noalloc": (c_int, [c_void_p, c_int, c_int, c_size_t, c_int, c_int, ctypes.POINTER(glcm_offset),
                                      c_int, c_int, c_void_p, c_void_p, ctypes.c_char_p, c_size_t]),
+    "glcm_measure_ceilings": (c_int, [c_int, ctypes.POINTER(glcm_ceilings_t)]),
 }
 
 _lib = None
@@ -304,3 +310,12 @@ def glcm_compute_noalloc(image, width, height, pitch_bytes, dtype, levels, offse
     if st != GLCM_OK:
         raise GlcmError(st, buf.value.decode())
     return st
+
+
+def glcm_measure_ceilings(device: int = 0) -> dict:
+    """Measured shared-reduction and HBM-read ceilings of a device (see glcm.h)."""
+    out = glcm_ceilings_t()
+    st = load().glcm_measure_ceilings(int(device), ctypes.byref(out))
+    if st != GLCM_OK:
+        raise GlcmError(st, "glcm_measure_ceilings failed")
+    return {k: getattr(out, k) for k, _ in glcm_ceilings_t._fields_}

@@ -500,30 +500,23 @@ constexpr int kFastChunkItems = 16;
 
 // Column-walk jobs of one image for the canonical offsets in `present`
 // (slot / slot_t: the output GLCMs of each canonical offset as counted and
-// transposed).  Bands of 64 anchor rows, halved down to 8 while the image
-// has fewer items than its share of the launch (about two chunks per CTA).
+// transposed).  Items and chunks are made by finalize_fast; a band height
+// configured for the class (the autotuner's tile shape) is kept.
 void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int present, const int (&slot)[4],
-                     const int (&slot_t)[4], int target_items)
+                     const int (&slot_t)[4])
 {
     int band_override = 0;
     {
         auto it = ctx->overrides.find(cfg_key(s.levels, s.n_off, s.bpp));
         if (it != ctx->overrides.end() && it->second.layout == 4)
-            band_override = it->second.band_rows;
+            band_override = std::min(it->second.band_rows, 1024);
     }
     const int log2n = ilog2_exact(s.levels);
     FastClass& fc = fast_class(plan, s.bpp, log2n);
     const int PX = 16 / s.bpp;
     const int n_strips = (s.W + 32 * PX - 1) / (32 * PX);
-    const int rows = s.y_end - s.y_begin;
-    if (rows <= 0 || n_strips <= 0)
+    if (s.y_end <= s.y_begin || n_strips <= 0)
         return;
-    int band = 64;
-    while (band > 8 && (long long)n_strips * ((rows + band - 1) / band) < target_items)
-        band /= 2;
-    if (band_override > 0)
-        band = std::min(band_override, 1024);
-    const int n_bands = (rows + band - 1) / band;
     struct Group {
         int mode, present, half_hi;
     };
@@ -564,19 +557,44 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
             j.slot_t[k] = in ? slot_t[k] : -1;
         }
         j.hist_words = vote_fast_hist_words(log2n, g.mode);
-        j.item0 = fc.n_items;
-        j.n_items = n_strips * n_bands;
         j.n_strips = n_strips;
-        j.band = band;
+        j.band = band_override;  // 0: set by finalize_fast
         j.y_begin = s.y_begin;
         j.y_end = s.y_end;
         j.out = s.out;
-        const int jb = (int)fc.jobs.size();
-        for (int k = 0; k < j.n_items; k += kFastChunkItems)
-            fc.chunks.push_back(make_int3(jb, j.item0 + k, j.item0 + std::min(j.n_items, k + kFastChunkItems)));
-        fc.n_items += j.n_items;
         fc.max_hist_words = std::max(fc.max_hist_words, j.hist_words);
         fc.jobs.push_back(j);
+    }
+}
+
+// Bands, items and chunks of every column-walk class of a plan.  One band
+// height per class, chosen so that the class's items come to whole chunks of
+// kFastChunkItems (one item per warp of a CTA) spread evenly over `ctas`
+// CTAs: one chunk per CTA while a warp's share of the class is at most 64
+// rows, else the fewest chunks per CTA that keep bands at most 64 rows (at
+// least 4 rows: the row above a band is loaded too).
+void finalize_fast(VotePlan& plan, int ctas)
+{
+    for (FastClass& fc : plan.fast) {
+        long long strip_rows = 0;
+        for (const FastJob& j : fc.jobs)
+            strip_rows += (long long)j.n_strips * (j.y_end - j.y_begin);
+        const long long warps = (long long)kFastChunkItems * std::max(1, ctas);
+        const long long per_warp = std::max(1ll, (strip_rows + warps - 1) / warps);
+        const long long k = std::max(1ll, (per_warp + 63) / 64);
+        const int band = (int)std::max(4ll, std::min(64ll, (per_warp + k - 1) / k));
+        fc.n_items = 0;
+        fc.chunks.clear();
+        for (int jb = 0; jb < (int)fc.jobs.size(); ++jb) {
+            FastJob& j = fc.jobs[jb];
+            if (j.band <= 0)
+                j.band = band;
+            j.item0 = fc.n_items;
+            j.n_items = j.n_strips * ((j.y_end - j.y_begin + j.band - 1) / j.band);
+            for (int i = 0; i < j.n_items; i += kFastChunkItems)
+                fc.chunks.push_back(make_int3(jb, j.item0 + i, j.item0 + std::min(j.n_items, i + kFastChunkItems)));
+            fc.n_items += j.n_items;
+        }
     }
 }
 
@@ -606,8 +624,9 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
             gen.push_back(k);  // any other offset, or a repeat of one already placed
         }
     }
+    (void)target_items;
     if (present)
-        plan_image_fast(ctx, s, plan, present, slot, slot_t, 2 * target_items);
+        plan_image_fast(ctx, s, plan, present, slot, slot_t);
     return plan_image_general(ctx, s, plan, gen);
 }
 
@@ -1415,7 +1434,8 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         VotePlan plan;
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
                     offsets, n_offsets, d_counts, r0, r1};
-        TRY(plan_image(ctx, s, plan, 4 * target_items(ctx) / n_stripes));
+        TRY(plan_image(ctx, s, plan, target_items(ctx)));
+        finalize_fast(plan, ctx->sm_count);
         build_chunks(plan, ctx->sm_count);
         std::vector<FeatJob> none;
         TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
@@ -1533,6 +1553,7 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
                                         (d.flags & GLCM_SYMMETRIC) ? 1 : 0});
         }
     }
+    finalize_fast(plan, ctx->sm_count);
     return GLCM_OK;
 }
 

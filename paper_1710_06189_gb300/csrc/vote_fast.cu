@@ -32,7 +32,10 @@
 //    into two, of the joint codes (a, j0, j1) and (a, j2, j3) (M^3 bins each,
 //    interleaved); the merge marginalizes them.  Half the reductions, which
 //    bound this kernel.
-//  * N = 16: one vote per offset; two offsets interleaved per bin row.
+//  * N = 16: one vote per offset with the byte code a * 16 + j; two offsets
+//    interleaved per bin row.  Here every byte value is a bin, so there is
+//    no outside level: the warps of the first and last strip of a row vote
+//    under per-pixel masks, the top row skips the offsets into the row above.
 //  * N = 32: a job holds up to two offsets as the 16-bit halves of each word
 //    (increment 1 or 65536), so 32 copies still fit; the merge comes before
 //    any half can reach 65536.
@@ -55,6 +58,15 @@ constexpr unsigned kHalfRows = 4000;
 __device__ __forceinline__ void red1(uint32_t a)
 {
     asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(a));
+}
+
+// Reduction if bit `bit` of a lane's anchor mask is set (edge strips of N = 16).
+__device__ __forceinline__ void red1_if(uint32_t a, uint32_t mask, uint32_t bit)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %1, %2;\n\tsetp.ne.u32 p, t, 0;\n\t"
+        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
+        "r"(mask), "r"(bit));
 }
 
 __device__ __forceinline__ void red_hi(uint32_t a)
@@ -157,23 +169,36 @@ __device__ __forceinline__ void votes_one8(const uint32_t (&A9)[LW], const uint3
     }
 }
 
-// One offset K, N = 16: 16-bit codes a*17 + j (<= 288), same layout.
-template <int K, int LW>
-__device__ __forceinline__ void votes_one16(const uint32_t (&Alo)[LW], const uint32_t (&Ahi)[LW],
-                                            const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                            uint32_t PL, uint32_t PR, uint32_t hb, uint32_t l4)
+// One offset K, N = 16: byte codes a*16 + j in region K >> 1 (256 bin rows of
+// 64 words, 64 KB), offset K & 1 at words 32 (K & 1) .. + 31.  EDGE: only the
+// anchors whose bit is set in `mask` vote (bit 4m + b: byte b of word m).
+template <int K, int LW, bool EDGE>
+__device__ __forceinline__ void votes_one16(const uint32_t (&A16)[LW], const uint32_t (&C)[LW], uint32_t CR,
+                                            const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                            uint32_t l4, uint32_t mask)
 {
-    constexpr uint32_t M = 17u;
-    const uint32_t base = hb + (uint32_t)(K >> 1) * (M * M * 256u);
+    const uint32_t base = hb + (uint32_t)(K >> 1) * 65536u;
     const uint32_t lq = l4 + (uint32_t)(K & 1) * 128u;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
-        const uint32_t w = partner<K>(m, C, CR, P, PL, PR);
-        const uint32_t c0 = Alo[m] + spread_lo(w), c1 = Ahi[m] + spread_hi(w);
-        red1(base + __byte_perm(c0, lq, 0x5104));
-        red1(base + __byte_perm(c0, lq, 0x5324));
-        red1(base + __byte_perm(c1, lq, 0x5104));
-        red1(base + __byte_perm(c1, lq, 0x5324));
+        const uint32_t code = A16[m] | partner<K>(m, C, CR, P, PL, PR);
+        const uint32_t a0 = base + __byte_perm(code, lq, 0x5504);
+        const uint32_t a1 = base + __byte_perm(code, lq, 0x5514);
+        const uint32_t a2 = base + __byte_perm(code, lq, 0x5524);
+        const uint32_t a3 = base + __byte_perm(code, lq, 0x5534);
+        // In an edge strip only a few words have a masked-out anchor: the
+        // others take the unmasked votes, decided for the whole warp.
+        if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
+            red1_if(a0, mask, 1u << (4 * m));
+            red1_if(a1, mask, 1u << (4 * m + 1));
+            red1_if(a2, mask, 1u << (4 * m + 2));
+            red1_if(a3, mask, 1u << (4 * m + 3));
+        } else {
+            red1(a0);
+            red1(a1);
+            red1(a2);
+            red1(a3);
+        }
     }
 }
 
@@ -218,10 +243,17 @@ __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[L
         votes_one32<K, LW, false>(Alo, Ahi, C, CR, P, PL, PR, hb, l8);
 }
 
-template <int LW, int LOG2N>
+// Masks of an edge strip's anchors for N = 16 (bit 4m + b: pixel 4m + b of
+// the lane): anchors inside the image, with a partner to the right inside
+// it, with a partner to the left inside it.
+struct EdgeMasks {
+    uint32_t in, right, left;
+};
+
+template <int LW, int LOG2N, bool EDGE>
 __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[LW], uint32_t CR,
                                          const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
-                                         uint32_t l4)
+                                         uint32_t l4, bool top, const EdgeMasks& em)
 {
     const int pr = j.present;
     if constexpr (LOG2N <= 3) {
@@ -242,6 +274,21 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
             votes_one8<2, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
         if (pr & 8)
             votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+    } else if constexpr (LOG2N == 4) {
+        uint32_t A16[LW];
+#pragma unroll
+        for (int m = 0; m < LW; ++m)
+            A16[m] = C[m] << 4;  // packed bytes a*16 <= 240
+        if (pr & 1)
+            votes_one16<0, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.right);
+        if (top)
+            return;  // no row above the image's first row
+        if (pr & 2)
+            votes_one16<1, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.right);
+        if (pr & 4)
+            votes_one16<2, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.in);
+        if (pr & 8)
+            votes_one16<3, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.left);
     } else {
         constexpr uint32_t M = (1u << LOG2N) + 1u;
         uint32_t Alo[LW], Ahi[LW];
@@ -250,53 +297,47 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
             Alo[m] = spread_lo(C[m]) * M;
             Ahi[m] = spread_hi(C[m]) * M;
         }
-        if constexpr (LOG2N == 4) {
-            if (pr & 1)
-                votes_one16<0, LW>(Alo, Ahi, C, CR, P, PL, PR, hb, l4);
-            if (pr & 2)
-                votes_one16<1, LW>(Alo, Ahi, C, CR, P, PL, PR, hb, l4);
-            if (pr & 4)
-                votes_one16<2, LW>(Alo, Ahi, C, CR, P, PL, PR, hb, l4);
-            if (pr & 8)
-                votes_one16<3, LW>(Alo, Ahi, C, CR, P, PL, PR, hb, l4);
-        } else {
-            const uint32_t l8 = 2u * l4;
-            const int hk = j.half_hi;
-            if (pr & 1)
-                votes_one32_sel<0, LW>(hk == 0, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
-            if (pr & 2)
-                votes_one32_sel<1, LW>(hk == 1, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
-            if (pr & 4)
-                votes_one32_sel<2, LW>(hk == 2, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
-            if (pr & 8)
-                votes_one32_sel<3, LW>(hk == 3, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
-        }
+        const uint32_t l8 = 2u * l4;
+        const int hk = j.half_hi;
+        if (pr & 1)
+            votes_one32_sel<0, LW>(hk == 0, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+        if (pr & 2)
+            votes_one32_sel<1, LW>(hk == 1, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+        if (pr & 4)
+            votes_one32_sel<2, LW>(hk == 2, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+        if (pr & 8)
+            votes_one32_sel<3, LW>(hk == 3, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
     }
 }
 
 // ---- one work item: a warp walks down its strip ------------------------------
 
-template <int BPP, int LOG2N>
-__device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t hb)
+// EDGE: the strip holds the image's first or last column (pixels outside
+// the image get the outside level N, or for N = 16 the anchors are masked);
+// interior strips need neither.
+template <int BPP, int LOG2N, bool EDGE>
+__device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int y1, uint32_t hb)
 {
     constexpr int PX = 16 / BPP, LW = 4 / BPP;
     constexpr uint32_t N = 1u << LOG2N;
-    constexpr uint32_t D4 = N * 0x01010101u;  // four pixels outside the image
+    constexpr bool OUTLEVEL = LOG2N != 4;     // the outside level N exists
+    constexpr uint32_t D4 = (N & 0xFFu) * 0x01010101u;  // four pixels outside the image
     const int lane = threadIdx.x & 31;
-    const int local = item - j.item0;
-    const int band = local / j.n_strips;
-    const int strip = local - band * j.n_strips;
-    const int x0 = strip * 32 * PX, xl = x0 + lane * PX, xe = x0 + 32 * PX;
-    const int y0 = j.y_begin + band * j.band;
-    const int y1 = min(j.y_end, y0 + j.band);
-    if (y0 >= y1)
-        return;
+    const int xl = x0 + lane * PX, xe = x0 + 32 * PX;
     const bool on = xl < j.W;
     uint32_t om[LW];
 #pragma unroll
     for (int m = 0; m < LW; ++m)
-        om[m] = outside_mask(j.W - (xl + 4 * m));
-    const uint32_t omr = outside_mask(j.W - xe);
+        om[m] = EDGE ? outside_mask(j.W - (xl + 4 * m)) : 0u;
+    const uint32_t omr = EDGE ? outside_mask(j.W - xe) : 0u;
+    EdgeMasks em{0xFFFFu, 0xFFFFu, 0xFFFFu};
+    if (EDGE && LOG2N == 4) {
+        const int nin = max(0, min(PX, j.W - xl));           // pixels of the lane inside the image
+        const int nright = max(0, min(PX, j.W - 1 - xl));    // ... with a partner to the right
+        em.in = (1u << nin) - 1u;
+        em.right = (1u << nright) - 1u;
+        em.left = em.in & (xl == 0 ? ~1u : ~0u);
+    }
     const bool has_l = lane == 0 && x0 > 0;
     const bool has_r = lane == 31 && xe < j.W;
     const bool has_h = has_l || has_r;
@@ -332,14 +373,18 @@ __device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t h
             L[0] = qword<2, LOG2N>(v.x, v.y);
             L[1] = qword<2, LOG2N>(v.z, v.w);
         }
+        if constexpr (EDGE && OUTLEVEL) {
 #pragma unroll
-        for (int m = 0; m < LW; ++m)
-            L[m] = (L[m] & ~om[m]) | (D4 & om[m]);
-        const uint32_t hq = qword<BPP, LOG2N>(h.x, h.y);
+            for (int m = 0; m < LW; ++m)
+                L[m] = (L[m] & ~om[m]) | (D4 & om[m]);
+        }
+        uint32_t hq = qword<BPP, LOG2N>(h.x, h.y);
+        if constexpr (EDGE && OUTLEVEL)
+            hq = lane == 31 ? ((hq & ~omr) | (D4 & omr)) : hq;
         const uint32_t up = __shfl_up_sync(0xffffffffu, L[LW - 1], 1);
         const uint32_t dn = __shfl_down_sync(0xffffffffu, L[0], 1);
         ll = lane == 0 ? (has_l ? hq : D4) : up;
-        lr = lane == 31 ? (has_r ? ((hq & ~omr) | (D4 & omr)) : D4) : dn;
+        lr = lane == 31 ? (has_r ? hq : D4) : dn;
     };
 
     uint32_t P[LW], PL = D4, PR = D4;
@@ -363,8 +408,11 @@ __device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t h
                 load_row(y + kPF, qv[k], qh[k]);
             uint32_t C[LW], CL, CR;
             levels(v, h, C, CL, CR);
-            if (y >= y0 && on)
-                vote_row<LW, LOG2N>(j, C, CR, P, PL, PR, hb, l4);
+            // (N = 16 edge strips vote with all lanes -- lanes outside the
+            // image have empty masks -- since their word masks are decided
+            // warp-wide.)
+            if (y >= y0 && (on || (EDGE && LOG2N == 4)))
+                vote_row<LW, LOG2N, EDGE>(j, C, CR, P, PL, PR, hb, l4, y == 0, em);
 #pragma unroll
             for (int m = 0; m < LW; ++m)
                 P[m] = C[m];
@@ -374,20 +422,54 @@ __device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t h
     }
 }
 
+// Items of a job: first the interior strips (1 .. n_strips - 2) of every
+// band, then the edge strips (the first and the last), so that a chunk's
+// items, one per warp, cost about the same and no warp waits long at the
+// chunk's barrier for an edge strip.
+template <int BPP, int LOG2N>
+__device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t hb)
+{
+    constexpr int PX = 16 / BPP;
+    const int n_int = max(0, j.n_strips - 2);
+    const int n_bands = (j.y_end - j.y_begin + j.band - 1) / j.band;
+    int local = item - j.item0;
+    int band, strip;
+    if (local < n_int * n_bands) {
+        band = local / n_int;
+        strip = 1 + (local - band * n_int);
+    } else {
+        local -= n_int * n_bands;
+        const int n_edge = min(2, j.n_strips);
+        band = local / n_edge;
+        strip = (local - band * n_edge) == 0 ? 0 : j.n_strips - 1;
+    }
+    const int x0 = strip * 32 * PX;
+    const int y0 = j.y_begin + band * j.band;
+    const int y1 = min(j.y_end, y0 + j.band);
+    if (y0 >= y1)
+        return;
+    if (strip == 0 || strip == j.n_strips - 1)
+        walk_strip<BPP, LOG2N, true>(j, x0, y0, y1, hb);
+    else
+        walk_strip<BPP, LOG2N, false>(j, x0, y0, y1, hb);
+}
+
 // ---- merge -------------------------------------------------------------------
 
-// Sum of the 32 copies of bin row `row` (32 words), cleared; the rotation by
-// lane keeps the reads of consecutive rows by consecutive lanes conflict-free.
+// Sum of the 32 copies of bin row `row` (32 words), cleared: eight 16-byte
+// reads, rotated by lane so the rows of consecutive lanes spread over all
+// banks (four wavefronts per warp read, the least for 512 bytes).
 __device__ __forceinline__ uint32_t take_row(uint32_t* h, int row)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t* b = h + row * 32;
+    uint4* b = reinterpret_cast<uint4*>(h + row * 32);
     uint32_t s = 0;
-#pragma unroll 8
-    for (int c = 0; c < 32; ++c) {
-        const int w = (c + lane) & 31;
-        s += b[w];
-        b[w] = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int w = (c + lane) & 7;
+        const uint4 v = b[w];
+        s += (v.x + v.y) + (v.z + v.w);
+        b[w] = make_uint4(0u, 0u, 0u, 0u);
     }
     return s;
 }
@@ -395,15 +477,15 @@ __device__ __forceinline__ uint32_t take_row(uint32_t* h, int row)
 __device__ __forceinline__ void take_row_halves(uint32_t* h, int row, uint32_t& lo, uint32_t& hi)
 {
     const int lane = threadIdx.x & 31;
-    uint32_t* b = h + row * 32;
+    uint4* b = reinterpret_cast<uint4*>(h + row * 32);
     lo = hi = 0u;
-#pragma unroll 8
-    for (int c = 0; c < 32; ++c) {
-        const int w = (c + lane) & 31;
-        const uint32_t v = b[w];
-        lo += v & 0xFFFFu;
-        hi += v >> 16;
-        b[w] = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const int w = (c + lane) & 7;
+        const uint4 v = b[w];
+        lo += (v.x & 0xFFFFu) + (v.y & 0xFFFFu) + (v.z & 0xFFFFu) + (v.w & 0xFFFFu);
+        hi += (v.x >> 16) + (v.y >> 16) + (v.z >> 16) + (v.w >> 16);
+        b[w] = make_uint4(0u, 0u, 0u, 0u);
     }
 }
 
@@ -449,15 +531,18 @@ __device__ void flush_t(const FastJob& j, uint32_t* hist, uint32_t* marg)
             }
         }
     } else if (LOG2N <= 4) {
-        constexpr int rows = 4 * (int)M2;  // region, code, offset of the pair
+        // Region K >> 1 of MB^2 bin rows of 64 words (N = 16: codes a*16 + j,
+        // no outside level), each as two rows of 32: row = 2 (region MB^2 + code) + (K & 1).
+        constexpr uint32_t MB = LOG2N == 4 ? N : M, MB2 = MB * MB;
+        constexpr int rows = 4 * (int)MB2;
         for (int r = tid; r < rows; r += kFT) {
-            const int k = 2 * (r / (2 * (int)M2)) + (r & 1);
+            const int k = 2 * (r / (2 * (int)MB2)) + (r & 1);
             if (!((j.present >> k) & 1))
                 continue;
             const uint32_t s = take_row(hist, r);
             if (s) {
-                const uint32_t code = (uint32_t)(r % (2 * (int)M2)) >> 1;
-                const uint32_t a = code / M, b = code - a * M;
+                const uint32_t code = (uint32_t)(r % (2 * (int)MB2)) >> 1;
+                const uint32_t a = code / MB, b = code - a * MB;
                 if (a < N && b < N)
                     emit(j, k, a, b, s);
             }
@@ -487,17 +572,20 @@ __device__ void flush_t(const FastJob& j, uint32_t* hist, uint32_t* marg)
 }
 
 // Persistent CTAs: chunk b to CTA b first, then chunks from the counter.
-// One kernel instance per pixel type and N (every job of a launch has them);
-// dynamic shared memory: the histograms (max_hist_words), then the joint
-// merge's marginals.
+// One kernel instance per pixel type and N (every job of a launch has them).
+// Dynamic shared memory: the histograms (max_hist_words), the joint merge's
+// marginals, then the chunk index.
 template <int BPP, int LOG2N>
 __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
 {
     extern __shared__ __align__(16) uint32_t sh[];
-    __shared__ int s_chunk;
     uint32_t* marg = sh + p.max_hist_words;
-    for (int i = threadIdx.x; i < p.max_hist_words + kMargWords; i += kFT)
-        sh[i] = 0u;
+    int* s_chunk = reinterpret_cast<int*>(marg + kMargWords);
+    {
+        uint4* z = reinterpret_cast<uint4*>(sh);
+        for (int i = threadIdx.x; i < (p.max_hist_words + kMargWords) / 4; i += kFT)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
     const uint32_t hb = (uint32_t)__cvta_generic_to_shared(sh);
     const int warp = threadIdx.x >> 5;
@@ -506,10 +594,10 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
     bool first = true;
     for (;;) {
         if (threadIdx.x == 0)
-            s_chunk = first ? (int)blockIdx.x : (int)gridDim.x + (int)atomicAdd(p.chunk_counter, 1u);
+            *s_chunk = first ? (int)blockIdx.x : (int)gridDim.x + (int)atomicAdd(p.chunk_counter, 1u);
         first = false;
         __syncthreads();
-        const int c = s_chunk;
+        const int c = *s_chunk;
         if (c >= p.n_chunks)
             break;
         const int3 ch = p.chunks[c];
@@ -562,7 +650,7 @@ int vote_fast_hist_words(int log2n, int mode)
     if (mode == kFastJoint)
         return M * M * M * 64;
     if (mode == kFastPair)
-        return 2 * M * M * 64;
+        return log2n == 4 ? 2 * 256 * 64 : 2 * M * M * 64;  // N = 16: byte codes, no outside level
     return M * M * 32;
 }
 
@@ -570,7 +658,7 @@ int vote_fast_hist_words(int log2n, int mode)
 // max_hist_words words (the joint merge's marginals follow it).
 size_t vote_fast_smem_bytes(int max_hist_words)
 {
-    return (size_t)(max_hist_words + kMargWords) * 4;
+    return (size_t)(max_hist_words + kMargWords) * 4 + 16;  // + the chunk index
 }
 
 int vote_fast_blocks_per_sm(int bpp, int log2n, size_t smem)

@@ -66,3 +66,15 @@ def test_full_admission_queue_is_busy_and_recovers():
         st, _, (c, _, _) = srv.wait(srv.submit(imgs[0], 16, offs))
         assert st == G.GLCM_OK
         assert np.array_equal(c.numpy().view(np.uint32), oracle.glcm(imgs[0].numpy(), 16, offs))
+
+
+def test_measured_ceilings_are_ordered():
+    """glcm_measure_ceilings: interleaved copies never conflict, so they are
+    at least as fast as random words of one copy; the streaming read rate is
+    a plausible HBM rate."""
+    c = G.binding.glcm_measure_ceilings(0)
+    assert c["sm_count"] > 0
+    assert c["red_interleaved_per_s"] > 1e11
+    assert c["red_interleaved_per_s"] >= 0.9 * c["red_random_one_copy_per_s"]
+    assert c["red_same_word_per_s"] > 1e11
+    assert 100.0 < c["hbm_read_gbs"] < 20000.0
