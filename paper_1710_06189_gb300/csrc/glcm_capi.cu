@@ -88,7 +88,7 @@ struct glcm_ctx {
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
     int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
-    unsigned* d_words = nullptr;  // [0] error bits, [1] work-item counter
+    unsigned* d_words = nullptr;  // [0] error bits, [1] general vote chunk counter, [2..15] column-walk counters
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
     DevBuf hb_img, hb_out;        // host-buffer batches: staged images, device results
     std::vector<std::array<DevBuf, 3>> hb_tab;  // host-buffer batches: tables per group
@@ -518,13 +518,22 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
     if (s.y_end <= s.y_begin || n_strips <= 0)
         return;
     struct Group {
-        int mode, present, half_hi;
+        int mode, present, half_hi, row_half, transposed, slot;
     };
     std::vector<Group> groups;
-    if (log2n <= 3 && present == 15) {
-        groups.push_back({kFastJoint, 15, -1});
+    if (log2n == 8) {
+        // N = 256: one job per offset, orientation and half of the GLCM's rows.
+        for (int k = 0; k < 4; ++k)
+            for (int t = 0; t < 2; ++t) {
+                const int sl = t ? slot_t[k] : slot[k];
+                if (sl >= 0)
+                    for (int h = 0; h < 2; ++h)
+                        groups.push_back({kFastWide, 1 << k, -1, h, t, sl});
+            }
+    } else if (log2n <= 3 && present == 15) {
+        groups.push_back({kFastJoint, 15, -1, 0, 0, -1});
     } else if (log2n <= 4) {
-        groups.push_back({kFastPair, present, -1});
+        groups.push_back({kFastPair, present, -1, 0, 0, -1});
     } else {
         int pending = -1;
         for (int k = 0; k < 4; ++k) {
@@ -533,12 +542,12 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
             if (pending < 0) {
                 pending = k;
             } else {
-                groups.push_back({kFastHalf, (1 << pending) | (1 << k), k});
+                groups.push_back({kFastHalf, (1 << pending) | (1 << k), k, 0, 0, -1});
                 pending = -1;
             }
         }
         if (pending >= 0)
-            groups.push_back({kFastHalf, 1 << pending, -1});
+            groups.push_back({kFastHalf, 1 << pending, -1, 0, 0, -1});
     }
     for (const Group& g : groups) {
         FastJob j{};
@@ -551,10 +560,12 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
         j.mode = g.mode;
         j.present = g.present;
         j.half_hi = g.half_hi;
+        j.row_half = g.row_half;
+        j.transposed = g.transposed;
         for (int k = 0; k < 4; ++k) {
             const bool in = (g.present >> k) & 1;
-            j.slot[k] = in ? slot[k] : -1;
-            j.slot_t[k] = in ? slot_t[k] : -1;
+            j.slot[k] = in ? (g.mode == kFastWide ? g.slot : slot[k]) : -1;
+            j.slot_t[k] = in && g.mode != kFastWide ? slot_t[k] : -1;
         }
         j.hist_words = vote_fast_hist_words(log2n, g.mode);
         j.n_strips = n_strips;
@@ -608,8 +619,10 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     const bool aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
     auto it = ctx->overrides.find(cfg_key(s.levels, s.n_off, s.bpp));
     const bool tuned_general = it != ctx->overrides.end() && it->second.layout != 4;
-    const bool eligible = !tuned_general && log2n >= 1 && log2n <= 5 && aligned &&
-                          !s.levels_mode && s.y_end > s.y_begin;
+    // N = 256 merges by bulk reductions into the output rows: 16-byte aligned counts.
+    const bool out_aligned = (reinterpret_cast<uintptr_t>(s.out) & 15) == 0;
+    const bool eligible = !tuned_general && ((log2n >= 1 && log2n <= 5) || (log2n == 8 && out_aligned)) &&
+                          aligned && !s.levels_mode && s.y_end > s.y_begin;
     std::vector<int> gen;
     int present = 0;
     int slot[4] = {-1, -1, -1, -1}, slot_t[4] = {-1, -1, -1, -1};
@@ -776,7 +789,7 @@ int zero_words(glcm_ctx* ctx, uint32_t* p, long long n, cudaStream_t st)
 
 // Chunk counters in the context's device words: [1] the general vote kernel,
 // [2 + c] column-walk class c.
-constexpr int kCounterWords = 12;
+constexpr int kCounterWords = 16;
 constexpr int kMaxFastClasses = kCounterWords - 2;
 
 // Blocks [0, n_gen) zero general job b's outputs, blocks [n_gen, n_gen +
@@ -1218,13 +1231,13 @@ extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, 
         glcm_destroy(ctx);
         return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
     }
-    if (fault_injected("alloc") || cudaMalloc(&ctx->d_words, 64) != cudaSuccess) {
+    if (fault_injected("alloc") || cudaMalloc(&ctx->d_words, 128) != cudaSuccess) {
         cudaGetLastError();
         ctx->d_words = nullptr;
         glcm_destroy(ctx);
         return fail(nullptr, GLCM_ERR_NOMEM, "could not allocate the context's device words");
     }
-    cudaMemset(ctx->d_words, 0, 64);
+    cudaMemset(ctx->d_words, 0, 128);
     cudaDeviceSynchronize();
     *out = ctx;
     return GLCM_OK;
@@ -1349,8 +1362,8 @@ extern "C" int glcm_set_vote_config(glcm_ctx* ctx, int levels, int n_offsets, in
         // The column-walk kernel: N a power of two up to 32; threads and
         // copies are fixed by the kernel, band_rows (0 = derived) is its item height.
         const int l2 = ilog2_exact(levels);
-        if (l2 < 1 || l2 > 5)
-            return fail(ctx, GLCM_ERR_ARG, "the column-walk kernel needs N a power of two up to 32");
+        if (l2 < 1 || (l2 > 5 && l2 != 8))
+            return fail(ctx, GLCM_ERR_ARG, "the column-walk kernel needs N in {2, 4, 8, 16, 32, 256}");
         VoteCfg c;
         c.threads = 512;
         c.rshift = 5;

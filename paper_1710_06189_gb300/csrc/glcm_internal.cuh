@@ -94,6 +94,7 @@ enum : int {
     kFastJoint = 0,  // N <= 8, all four offsets: two joint votes per anchor
     kFastPair = 1,   // N <= 16: one vote per anchor and offset, two offsets per bin row
     kFastHalf = 2,   // N = 32: up to two offsets as 16-bit halves of one word
+    kFastWide = 3,   // N = 256: one offset, 128 rows of the GLCM as 32-bit counters
 };
 
 struct FastJob {
@@ -101,10 +102,12 @@ struct FastJob {
     long long pitch;   // bytes between rows (base and pitch 16-byte aligned)
     int W, H;
     int bpp;           // 1 or 2
-    int log2n;         // N = 2^log2n, 1..5
+    int log2n;         // N = 2^log2n: 1..5, or 8
     int mode;          // kFast*
     int present;       // bit k: canonical offset k is voted by this job
     int half_hi;       // kFastHalf: the offset (k) counted in the upper halves, or -1
+    int row_half;      // kFastWide: GLCM rows [128 row_half, 128 row_half + 128) are counted
+    int transposed;    // kFastWide: count the transpose (rows are partner levels)
     int slot[kFastOffsets];    // output GLCM of canonical offset k, or -1
     int slot_t[kFastOffsets];  // output GLCM that receives its transpose, or -1
     int hist_words;    // shared words of the job's histograms

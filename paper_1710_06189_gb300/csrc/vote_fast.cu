@@ -39,6 +39,14 @@
 //  * N = 32: a job holds up to two offsets as the 16-bit halves of each word
 //    (increment 1 or 65536), so 32 copies still fit; the merge comes before
 //    any half can reach 65536.
+//  * N = 256: a job counts one offset's GLCM rows [128 h, 128 h + 128) (anchor
+//    levels, or partner levels for a transposed offset) in one copy of 32768
+//    32-bit counters (128 KB), laid out as those rows of the output.  A vote
+//    is one byte permute for row * 256 + column, one multiply-add for the
+//    address and one reduction predicated on the row half; four offsets take
+//    eight jobs.  The merge is a single bulk reduction of the 128 KB into the
+//    output rows (cp.reduce.async.bulk ... add.u32, done at L2), not one
+//    global atomic per bin.
 //  * Persistent CTAs (one per SM, 16 warps) pull chunks of consecutive items
 //    of one job from a counter and merge their histograms into the global
 //    counts only when their job changes (Sec. II.A's final merge).
@@ -67,6 +75,24 @@ __device__ __forceinline__ void red1_if(uint32_t a, uint32_t mask, uint32_t bit)
         "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %1, %2;\n\tsetp.ne.u32 p, t, 0;\n\t"
         "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
         "r"(mask), "r"(bit));
+}
+
+// N = 256: reduction if the code's row half (bit 15) is this job's.
+__device__ __forceinline__ void red_row(uint32_t a, uint32_t x, uint32_t hbit)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %1, 32768;\n\tsetp.eq.u32 p, t, %2;\n\t"
+        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
+        "r"(x), "r"(hbit));
+}
+
+// ... and if bit `bit` of the lane's anchor mask is set (edge strips).
+__device__ __forceinline__ void red_row_if(uint32_t a, uint32_t x, uint32_t hbit, uint32_t mask, uint32_t bit)
+{
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t.reg .b32 t, u;\n\tand.b32 t, %1, 32768;\n\tsetp.eq.u32 p, t, %2;\n\t"
+        "and.b32 u, %3, %4;\n\tsetp.ne.and.u32 q, u, 0, p;\n\t@q red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
+        "r"(x), "r"(hbit), "r"(mask), "r"(bit));
 }
 
 __device__ __forceinline__ void red_hi(uint32_t a)
@@ -243,6 +269,50 @@ __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[L
         votes_one32<K, LW, false>(Alo, Ahi, C, CR, P, PL, PR, hb, l8);
 }
 
+// One offset K, N = 256: code row * 256 + column with row the anchor level
+// (TR: the partner level) -- one byte permute of the column word and the
+// row's 16-bit spread ([r0, 0, r1, 0]) -- at byte hb + 4 (code - 32768 h).
+template <int K, int LW, bool EDGE, bool TR>
+__device__ __forceinline__ void votes_wide(const uint32_t (&Slo)[LW], const uint32_t (&Shi)[LW],
+                                           const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
+                                           uint32_t PL, uint32_t PR, uint32_t base, uint32_t hbit, uint32_t mask)
+{
+#pragma unroll
+    for (int m = 0; m < LW; ++m) {
+        const uint32_t w = partner<K>(m, C, CR, P, PL, PR);
+        const uint32_t col = TR ? C[m] : w;
+        const uint32_t slo = TR ? spread_lo(w) : Slo[m];
+        const uint32_t shi = TR ? spread_hi(w) : Shi[m];
+        const uint32_t x0 = __byte_perm(col, slo, 0x5540);
+        const uint32_t x1 = __byte_perm(col, slo, 0x5561);
+        const uint32_t x2 = __byte_perm(col, shi, 0x5542);
+        const uint32_t x3 = __byte_perm(col, shi, 0x5563);
+        if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
+            red_row_if(base + 4u * x0, x0, hbit, mask, 1u << (4 * m));
+            red_row_if(base + 4u * x1, x1, hbit, mask, 1u << (4 * m + 1));
+            red_row_if(base + 4u * x2, x2, hbit, mask, 1u << (4 * m + 2));
+            red_row_if(base + 4u * x3, x3, hbit, mask, 1u << (4 * m + 3));
+        } else {
+            red_row(base + 4u * x0, x0, hbit);
+            red_row(base + 4u * x1, x1, hbit);
+            red_row(base + 4u * x2, x2, hbit);
+            red_row(base + 4u * x3, x3, hbit);
+        }
+    }
+}
+
+template <int K, int LW, bool EDGE>
+__device__ __forceinline__ void votes_wide_sel(bool tr, const uint32_t (&Slo)[LW], const uint32_t (&Shi)[LW],
+                                               const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
+                                               uint32_t PL, uint32_t PR, uint32_t base, uint32_t hbit,
+                                               uint32_t mask)
+{
+    if (tr)
+        votes_wide<K, LW, EDGE, true>(Slo, Shi, C, CR, P, PL, PR, base, hbit, mask);
+    else
+        votes_wide<K, LW, EDGE, false>(Slo, Shi, C, CR, P, PL, PR, base, hbit, mask);
+}
+
 // Masks of an edge strip's anchors for N = 16 (bit 4m + b: pixel 4m + b of
 // the lane): anchors inside the image, with a partner to the right inside
 // it, with a partner to the left inside it.
@@ -274,6 +344,28 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
             votes_one8<2, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
         if (pr & 8)
             votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+    } else if constexpr (LOG2N == 8) {
+        uint32_t Slo[LW], Shi[LW];
+#pragma unroll
+        for (int m = 0; m < LW; ++m) {
+            Slo[m] = spread_lo(C[m]);
+            Shi[m] = spread_hi(C[m]);
+        }
+        const uint32_t hbit = (uint32_t)j.row_half << 15;
+        const uint32_t base = hb - 4u * hbit;
+        const bool tr = j.transposed != 0;
+        if (pr & 1) {
+            votes_wide_sel<0, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.right);
+            return;
+        }
+        if (top)
+            return;  // no row above the image's first row
+        if (pr & 2)
+            votes_wide_sel<1, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.right);
+        else if (pr & 4)
+            votes_wide_sel<2, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.in);
+        else if (pr & 8)
+            votes_wide_sel<3, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.left);
     } else if constexpr (LOG2N == 4) {
         uint32_t A16[LW];
 #pragma unroll
@@ -320,7 +412,8 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
 {
     constexpr int PX = 16 / BPP, LW = 4 / BPP;
     constexpr uint32_t N = 1u << LOG2N;
-    constexpr bool OUTLEVEL = LOG2N != 4;     // the outside level N exists
+    constexpr bool OUTLEVEL = LOG2N <= 3 || LOG2N == 5;  // the outside level N exists
+    constexpr bool MASKED = !OUTLEVEL;                      // edge strips vote under masks
     constexpr uint32_t D4 = (N & 0xFFu) * 0x01010101u;  // four pixels outside the image
     const int lane = threadIdx.x & 31;
     const int xl = x0 + lane * PX, xe = x0 + 32 * PX;
@@ -331,7 +424,7 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
         om[m] = EDGE ? outside_mask(j.W - (xl + 4 * m)) : 0u;
     const uint32_t omr = EDGE ? outside_mask(j.W - xe) : 0u;
     EdgeMasks em{0xFFFFu, 0xFFFFu, 0xFFFFu};
-    if (EDGE && LOG2N == 4) {
+    if (EDGE && MASKED) {
         const int nin = max(0, min(PX, j.W - xl));           // pixels of the lane inside the image
         const int nright = max(0, min(PX, j.W - 1 - xl));    // ... with a partner to the right
         em.in = (1u << nin) - 1u;
@@ -408,10 +501,10 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
                 load_row(y + kPF, qv[k], qh[k]);
             uint32_t C[LW], CL, CR;
             levels(v, h, C, CL, CR);
-            // (N = 16 edge strips vote with all lanes -- lanes outside the
+            // (masked edge strips vote with all lanes -- lanes outside the
             // image have empty masks -- since their word masks are decided
             // warp-wide.)
-            if (y >= y0 && (on || (EDGE && LOG2N == 4)))
+            if (y >= y0 && (on || (EDGE && MASKED)))
                 vote_row<LW, LOG2N, EDGE>(j, C, CR, P, PL, PR, hb, l4, y == 0, em);
 #pragma unroll
             for (int m = 0; m < LW; ++m)
@@ -505,6 +598,28 @@ __device__ void flush_t(const FastJob& j, uint32_t* hist, uint32_t* marg)
 {
     constexpr uint32_t N = 1u << LOG2N, M = N + 1u, M2 = M * M;
     const int tid = threadIdx.x;
+    if constexpr (LOG2N == 8) {
+        // Every thread's reductions visible to the bulk-copy (async) proxy,
+        // then one bulk reduction of the 128 counted rows into the output.
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            int k = 0;
+            while (k < kFastOffsets - 1 && !((j.present >> k) & 1))
+                ++k;
+            uint32_t* dst = j.out + (long long)j.slot[k] * 65536 + (long long)j.row_half * 32768;
+            asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.u32 [%0], [%1], %2;" ::"l"(dst),
+                         "r"((uint32_t)__cvta_generic_to_shared(hist)), "r"(131072u)
+                         : "memory");
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+            asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+        }
+        __syncthreads();
+        uint4* z = reinterpret_cast<uint4*>(hist);
+        for (int i = tid; i < 32768 / 4; i += kFT)
+            z[i] = make_uint4(0u, 0u, 0u, 0u);
+        return;
+    }
     if (LOG2N <= 3 && j.mode == kFastJoint) {
         constexpr int rows = 2 * (int)(M * M2);
         for (int r = tid; r < rows; r += kFT) {
@@ -625,6 +740,8 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
     }
     if (cur >= 0)
         flush_t<LOG2N>(p.jobs[cur], sh, marg);
+    if (LOG2N == 8 && threadIdx.x == 0)
+        asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the bulk reductions have landed
 }
 
 template <int BPP>
@@ -635,17 +752,20 @@ const void* fast_kernel(int log2n)
         case 2: return (const void*)k_glcm_vote_d1<BPP, 2>;
         case 3: return (const void*)k_glcm_vote_d1<BPP, 3>;
         case 4: return (const void*)k_glcm_vote_d1<BPP, 4>;
-        default: return (const void*)k_glcm_vote_d1<BPP, 5>;
+        case 5: return (const void*)k_glcm_vote_d1<BPP, 5>;
+        default: return (const void*)k_glcm_vote_d1<BPP, 8>;
     }
 }
 
-SmemLimit g_fast_lim[2][6];
+SmemLimit g_fast_lim[2][9];
 
 }  // namespace
 
 // Shared words of one job's histograms.
 int vote_fast_hist_words(int log2n, int mode)
 {
+    if (mode == kFastWide)
+        return 32768;
     const int M = (1 << log2n) + 1;
     if (mode == kFastJoint)
         return M * M * M * 64;
@@ -676,7 +796,7 @@ cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, int grid, 
 {
     if (p.n_chunks <= 0)
         return cudaSuccess;
-    if (bpp < 1 || bpp > 2 || log2n < 1 || log2n > 5)
+    if (bpp < 1 || bpp > 2 || log2n < 1 || (log2n > 5 && log2n != 8))
         return cudaErrorInvalidValue;
     const void* fn = bpp == 1 ? fast_kernel<1>(log2n) : fast_kernel<2>(log2n);
     const cudaError_t e = g_fast_lim[bpp - 1][log2n].raise(fn, smem);

@@ -41,13 +41,13 @@ def _img(kind, seed, h, w, dt):
 
 @pytest.mark.parametrize("dt", [np.uint8, np.uint16])
 @pytest.mark.parametrize("kind", ["iid", "smooth", "constant"])
-@pytest.mark.parametrize("n", [2, 4, 8, 16, 32])
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 256])
 def test_every_level_count_and_kind(gctx, n, kind, dt):
     img = _img(kind, 100 + n, 300, 1100, dt)
     assert np.array_equal(run(gctx, img, n, C4), oracle.glcm(img, n, C4))
 
 
-@pytest.mark.parametrize("n", [4, 8, 16, 32])
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 256])
 @pytest.mark.parametrize("offs", [
     [(1, 0)],
     [(0, -1), (1, -1)],
@@ -67,7 +67,7 @@ def test_offset_sets(gctx, n, offs):
 
 @pytest.mark.parametrize("h,w", [(1, 1), (1, 17), (2, 1), (3, 5), (17, 16), (64, 511), (65, 512), (66, 513),
                                  (9, 1024), (33, 1537), (200, 4097)])
-@pytest.mark.parametrize("n", [8, 32])
+@pytest.mark.parametrize("n", [8, 32, 256])
 def test_shapes_around_strips(gctx, h, w, n):
     for dt in (np.uint8, np.uint16):
         img = _img("iid", h * 7919 + w, h, w, dt)
@@ -87,7 +87,7 @@ def test_pitched_views(gctx):
 def test_host_image_in_stripes(gctx):
     img = _img("smooth", 41, 3000, 2000, np.uint8)
     img[1500:] = _img("iid", 42, 1500, 2000, np.uint8)
-    for n in (8, 32):
+    for n in (8, 32, 256):
         c = gctx.compute(img, n, C4 + OPPOSITE[:1])
         assert np.array_equal(to_u32(c), oracle.glcm(img, n, C4 + OPPOSITE[:1])), n
 
@@ -110,6 +110,26 @@ def test_batch_mixing_both_kernels(gctx):
         torch.cuda.synchronize()
         for im, (_, _, _, _, n, offs), (c, _, _) in zip(imgs, specs, res):
             assert np.array_equal(to_u32(c), oracle.glcm(im, n, offs)), (n, offs, rep)
+
+
+def test_n256_counts_at_a_misaligned_address_take_the_general_kernel(gctx):
+    """N = 256 merges by 16-byte bulk reductions into the output rows; counts
+    that do not start on 16 bytes must still come out exact (general kernel)."""
+    img = _img("iid", 51, 300, 1000, np.uint8)
+    flat = torch.empty(4 * 256 * 256 + 1, dtype=torch.int32, device="cuda")
+    out = flat[1:].view(4, 256, 256)
+    gctx.compute(dev(img), 256, C4, out=out)
+    torch.cuda.synchronize()
+    assert np.array_equal(to_u32(out), oracle.glcm(img, 256, C4))
+
+
+def test_n256_all_in_one_bin_and_both_halves():
+    """A constant image (every vote of an offset in one bin, 16.7 M of them in
+    one half's counter), and a two-level image whose rows fall in both halves."""
+    with G.Context(0, hbm_budget_bytes=1 << 30) as ctx:
+        for img in (np.full((4096, 4096), 200, np.uint8),
+                    np.where(_img("smooth", 52, 1024, 2048, np.uint8) > 128, 250, 3).astype(np.uint8)):
+            assert np.array_equal(run(ctx, img, 256, C4 + OPPOSITE), oracle.glcm(img, 256, C4 + OPPOSITE))
 
 
 @pytest.mark.parametrize("band", [8, 100, 1024])
