@@ -77,22 +77,23 @@ __device__ __forceinline__ void red1_if(uint32_t a, uint32_t mask, uint32_t bit)
         "r"(mask), "r"(bit));
 }
 
-// N = 256: reduction if the code's row half (bit 15) is this job's.
-__device__ __forceinline__ void red_row(uint32_t a, uint32_t x, uint32_t hbit)
+// N = 256: reduction at hb + rel if rel, the byte offset of the code within
+// the job's 128 rows, lies inside them (unsigned: codes of the other half
+// fall below or above).
+__device__ __forceinline__ void red_row(uint32_t hb, uint32_t rel)
 {
     asm volatile(
-        "{\n\t.reg .pred p;\n\t.reg .b32 t;\n\tand.b32 t, %1, 32768;\n\tsetp.eq.u32 p, t, %2;\n\t"
-        "@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
-        "r"(x), "r"(hbit));
+        "{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, 131072;\n\t@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(hb + rel),
+        "r"(rel));
 }
 
 // ... and if bit `bit` of the lane's anchor mask is set (edge strips).
-__device__ __forceinline__ void red_row_if(uint32_t a, uint32_t x, uint32_t hbit, uint32_t mask, uint32_t bit)
+__device__ __forceinline__ void red_row_if(uint32_t hb, uint32_t rel, uint32_t mask, uint32_t bit)
 {
     asm volatile(
-        "{\n\t.reg .pred p, q;\n\t.reg .b32 t, u;\n\tand.b32 t, %1, 32768;\n\tsetp.eq.u32 p, t, %2;\n\t"
-        "and.b32 u, %3, %4;\n\tsetp.ne.and.u32 q, u, 0, p;\n\t@q red.shared.add.u32 [%0], 1;\n\t}" ::"r"(a),
-        "r"(x), "r"(hbit), "r"(mask), "r"(bit));
+        "{\n\t.reg .pred p, q;\n\t.reg .b32 u;\n\tsetp.lt.u32 p, %1, 131072;\n\t"
+        "and.b32 u, %2, %3;\n\tsetp.ne.and.u32 q, u, 0, p;\n\t@q red.shared.add.u32 [%0], 1;\n\t}" ::"r"(hb + rel),
+        "r"(rel), "r"(mask), "r"(bit));
 }
 
 __device__ __forceinline__ void red_hi(uint32_t a)
@@ -269,48 +270,43 @@ __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[L
         votes_one32<K, LW, false>(Alo, Ahi, C, CR, P, PL, PR, hb, l8);
 }
 
-// One offset K, N = 256: code row * 256 + column with row the anchor level
-// (TR: the partner level) -- one byte permute of the column word and the
-// row's 16-bit spread ([r0, 0, r1, 0]) -- at byte hb + 4 (code - 32768 h).
-template <int K, int LW, bool EDGE, bool TR>
-__device__ __forceinline__ void votes_wide(const uint32_t (&Slo)[LW], const uint32_t (&Shi)[LW],
-                                           const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                           uint32_t PL, uint32_t PR, uint32_t base, uint32_t hbit, uint32_t mask)
+// One offset k, N = 256: code x = row * 256 + column with row the anchor
+// level (tr: the partner level) -- one byte permute of the column word and
+// the row's 16-bit spread ([r0, 0, r1, 0]) -- counted at byte 4 x - 4 * 32768 h
+// of the job's rows (rbase = -4 * 32768 h).  The job's offset is a run-time
+// value: its partner word is one byte permute of operands and selector
+// chosen per offset (warp-uniform selects, no branch per row).
+template <int LW, bool EDGE>
+__device__ __forceinline__ void votes_wide(int k, bool tr, const uint32_t (&C)[LW], uint32_t CR,
+                                           const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                           uint32_t rbase, uint32_t mask)
 {
+    const uint32_t sel = k == 3 ? 0x6543u : (k == 2 ? 0x3210u : 0x4321u);
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
-        const uint32_t w = partner<K>(m, C, CR, P, PL, PR);
-        const uint32_t col = TR ? C[m] : w;
-        const uint32_t slo = TR ? spread_lo(w) : Slo[m];
-        const uint32_t shi = TR ? spread_hi(w) : Shi[m];
-        const uint32_t x0 = __byte_perm(col, slo, 0x5540);
-        const uint32_t x1 = __byte_perm(col, slo, 0x5561);
-        const uint32_t x2 = __byte_perm(col, shi, 0x5542);
-        const uint32_t x3 = __byte_perm(col, shi, 0x5563);
+        const uint32_t cur = k == 0 ? C[m] : P[m];
+        const uint32_t nxt = k == 0 ? (m + 1 < LW ? C[m + 1] : CR) : (m + 1 < LW ? P[m + 1] : PR);
+        const uint32_t prv = m > 0 ? P[m - 1] : PL;
+        const uint32_t w = __byte_perm(k == 3 ? prv : cur, k == 3 ? P[m] : nxt, sel);
+        const uint32_t col = tr ? C[m] : w;
+        const uint32_t rw = tr ? w : C[m];
+        const uint32_t slo = spread_lo(rw), shi = spread_hi(rw);
+        const uint32_t r0 = 4u * __byte_perm(col, slo, 0x5540) + rbase;
+        const uint32_t r1 = 4u * __byte_perm(col, slo, 0x5561) + rbase;
+        const uint32_t r2 = 4u * __byte_perm(col, shi, 0x5542) + rbase;
+        const uint32_t r3 = 4u * __byte_perm(col, shi, 0x5563) + rbase;
         if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
-            red_row_if(base + 4u * x0, x0, hbit, mask, 1u << (4 * m));
-            red_row_if(base + 4u * x1, x1, hbit, mask, 1u << (4 * m + 1));
-            red_row_if(base + 4u * x2, x2, hbit, mask, 1u << (4 * m + 2));
-            red_row_if(base + 4u * x3, x3, hbit, mask, 1u << (4 * m + 3));
+            red_row_if(hb, r0, mask, 1u << (4 * m));
+            red_row_if(hb, r1, mask, 1u << (4 * m + 1));
+            red_row_if(hb, r2, mask, 1u << (4 * m + 2));
+            red_row_if(hb, r3, mask, 1u << (4 * m + 3));
         } else {
-            red_row(base + 4u * x0, x0, hbit);
-            red_row(base + 4u * x1, x1, hbit);
-            red_row(base + 4u * x2, x2, hbit);
-            red_row(base + 4u * x3, x3, hbit);
+            red_row(hb, r0);
+            red_row(hb, r1);
+            red_row(hb, r2);
+            red_row(hb, r3);
         }
     }
-}
-
-template <int K, int LW, bool EDGE>
-__device__ __forceinline__ void votes_wide_sel(bool tr, const uint32_t (&Slo)[LW], const uint32_t (&Shi)[LW],
-                                               const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                               uint32_t PL, uint32_t PR, uint32_t base, uint32_t hbit,
-                                               uint32_t mask)
-{
-    if (tr)
-        votes_wide<K, LW, EDGE, true>(Slo, Shi, C, CR, P, PL, PR, base, hbit, mask);
-    else
-        votes_wide<K, LW, EDGE, false>(Slo, Shi, C, CR, P, PL, PR, base, hbit, mask);
 }
 
 // Masks of an edge strip's anchors for N = 16 (bit 4m + b: pixel 4m + b of
@@ -345,27 +341,13 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         if (pr & 8)
             votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
     } else if constexpr (LOG2N == 8) {
-        uint32_t Slo[LW], Shi[LW];
-#pragma unroll
-        for (int m = 0; m < LW; ++m) {
-            Slo[m] = spread_lo(C[m]);
-            Shi[m] = spread_hi(C[m]);
-        }
-        const uint32_t hbit = (uint32_t)j.row_half << 15;
-        const uint32_t base = hb - 4u * hbit;
-        const bool tr = j.transposed != 0;
-        if (pr & 1) {
-            votes_wide_sel<0, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.right);
-            return;
-        }
-        if (top)
+        // One offset and orientation per job, fixed for this loop instance.
+        const uint32_t rbase = 0u - 4u * 32768u * (uint32_t)j.row_half;
+        const int k = (pr & 1) ? 0 : ((pr & 2) ? 1 : ((pr & 4) ? 2 : 3));
+        if (top && k != 0)
             return;  // no row above the image's first row
-        if (pr & 2)
-            votes_wide_sel<1, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.right);
-        else if (pr & 4)
-            votes_wide_sel<2, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.in);
-        else if (pr & 8)
-            votes_wide_sel<3, LW, EDGE>(tr, Slo, Shi, C, CR, P, PL, PR, base, hbit, em.left);
+        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase,
+                             k == 2 ? em.in : (k == 3 ? em.left : em.right));
     } else if constexpr (LOG2N == 4) {
         uint32_t A16[LW];
 #pragma unroll
