@@ -13,6 +13,10 @@ Functions
     uint32 counts, shape (n_offsets, N, N), row-major [i][j] with i the
     anchor level (Eq. 1, partner by Eq. 2, bin by Eq. 3 with the anchor as
     the row).
+``glcm_flat(img, levels, offsets, levels_mode=False)``
+    the same counts with Eq. 2 read literally on the row-major buffer: pixel
+    p = y W + x pairs with p + dy W + dx whenever that index is in [0, W H),
+    so pairs may run across row ends (the flat-wrap mode).
 ``window_glcm(img, levels, offsets, win, stride, windows)``
     local GLCMs of win x win windows (pairs with both pixels inside).
 ``histogram(img, levels, levels_mode=False)``
@@ -63,6 +67,8 @@ def _load():
             lib.oracle_glcm.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, ci, vp]
             lib.oracle_glcm_multi.restype = i64
             lib.oracle_glcm_multi.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, vp, vp]
+            lib.oracle_glcm_flat_multi.restype = i64
+            lib.oracle_glcm_flat_multi.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, vp, vp]
             lib.oracle_window_glcm.restype = i64
             lib.oracle_window_glcm.argtypes = [vp, ci, ci, sz, ci, ci, ci, ci, ci, ci, vp, ci, vp, vp, vp]
             lib.oracle_histogram.restype = i64
@@ -90,6 +96,20 @@ def glcm(img: np.ndarray, levels: int, offsets, levels_mode: bool = False, retur
                               len(offs), dxy.ctypes.data, out.ctypes.data)
     if s < 0:
         raise ValueError("oracle_glcm_multi: bad arguments")
+    return (out, int(s)) if return_skipped else out
+
+
+def glcm_flat(img: np.ndarray, levels: int, offsets, levels_mode: bool = False, return_skipped: bool = False):
+    """Flat-wrap counts (Eq. 2 on the row-major buffer): (n_off, N, N) uint32."""
+    lib = _load()
+    img, w, h, pitch, bpp = _img_args(img)
+    offs = np.asarray(offsets, dtype=np.int32).reshape(-1, 2)
+    out = np.zeros((len(offs), levels, levels), dtype=np.uint32)
+    dxy = np.ascontiguousarray(offs.reshape(-1))
+    s = lib.oracle_glcm_flat_multi(img.ctypes.data, w, h, pitch, bpp, levels, int(levels_mode),
+                                   len(offs), dxy.ctypes.data, out.ctypes.data)
+    if s < 0:
+        raise ValueError("oracle_glcm_flat_multi: bad arguments")
     return (out, int(s)) if return_skipped else out
 
 

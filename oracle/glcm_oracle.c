@@ -167,3 +167,51 @@ long long oracle_histogram(const void *image, int W, int H, size_t pitch, int bp
     }
     return skipped;
 }
+
+/* Flat-wrap GLCM of one offset: Eq. 2 taken literally on the image as one
+ * row-major buffer of W * H pixels (the paper addresses the partner of pixel
+ * p as p + d for 0 degrees and p + d (N - 1), p + d N, p + d (N + 1) for the
+ * others, with N the image width, Sec. I.A, and pads stripes the same way,
+ * Eq. 9).  Pixel p = y W + x pairs with p + dy W + dx whenever that index
+ * lies in [0, W H), so a pair may run from the end of one row into another.
+ * Returns the skipped count (levels mode) or -1 on bad arguments. */
+long long oracle_glcm_flat(const void *image, int W, int H, size_t pitch, int bpp,
+                           int n_levels, int levels_mode, int dx, int dy, uint32_t *P)
+{
+    if (!image || !P || W < 1 || H < 1 || (bpp != 1 && bpp != 2) || n_levels < 1)
+        return -1;
+    const unsigned char *img = (const unsigned char *)image;
+    long long skipped = 0;
+    const long long n = (long long)W * H;
+    const long long off = (long long)dy * W + dx;
+    memset(P, 0, sizeof(uint32_t) * (size_t)n_levels * (size_t)n_levels);
+    for (long long p = 0; p < n; ++p) {
+        const long long q = p + off;
+        if (q < 0 || q >= n)
+            continue;
+        unsigned i = level_of(read_pixel(img, pitch, bpp, (int)(p % W), (int)(p / W)), bpp, n_levels, levels_mode);
+        unsigned j = level_of(read_pixel(img, pitch, bpp, (int)(q % W), (int)(q / W)), bpp, n_levels, levels_mode);
+        if (i >= (unsigned)n_levels || j >= (unsigned)n_levels) {
+            ++skipped;
+            continue;
+        }
+        P[(size_t)i * n_levels + j] += 1u;
+    }
+    return skipped;
+}
+
+long long oracle_glcm_flat_multi(const void *image, int W, int H, size_t pitch, int bpp,
+                                 int n_levels, int levels_mode, int n_off, const int *dxy,
+                                 uint32_t *P)
+{
+    long long total = 0;
+    for (int o = 0; o < n_off; ++o) {
+        long long s = oracle_glcm_flat(image, W, H, pitch, bpp, n_levels, levels_mode,
+                                       dxy[2 * o], dxy[2 * o + 1],
+                                       P + (size_t)o * n_levels * n_levels);
+        if (s < 0)
+            return -1;
+        total += s;
+    }
+    return total;
+}

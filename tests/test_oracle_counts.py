@@ -257,3 +257,90 @@ def test_histogram_brute_force_and_levels_mode(oracle_lib):
     const = np.full((5, 6), 200, dtype=np.uint8)
     hc = oracle.histogram(const, 8)
     assert hc[(200 * 8) >> 8] == 30 and hc.sum() == 30
+
+
+# ---- flat-wrap mode (Eq. 2 read literally on the row-major buffer) ----------
+
+def _flat_brute(img, n, dx, dy):
+    """Pure-Python enumeration of the flat buffer: pixel p pairs with p + dy W + dx."""
+    h, w = img.shape
+    flat = [int(v) for v in img.reshape(-1)]
+    P = np.zeros((n, n), dtype=np.uint32)
+    off = dy * w + dx
+    for p in range(h * w):
+        q = p + off
+        if 0 <= q < h * w:
+            P[flat[p], flat[q]] += 1
+    return P
+
+
+def test_flat_hand_worked_3x4():
+    # Pixels 0..11 row-major in a 4-wide image, levels as given.  Offset (1, 0)
+    # pairs p with p + 1: eleven pairs, two of them across row ends (3 -> 4 and
+    # 7 -> 8), which the no-wrap counts leave out.  Offset (1, -1) (45 deg)
+    # pairs p with p - 3: nine pairs, p = 3..11; (3 -> 0), (7 -> 4) and
+    # (11 -> 8) wrap (their partner is the first pixel of the same row).
+    img = np.arange(12, dtype=np.uint8).reshape(3, 4)
+    P = oracle.glcm_flat(img, 12, [(1, 0), (1, -1)], levels_mode=True)
+    want0 = np.zeros((12, 12), np.uint32)
+    for p in range(11):
+        want0[p, p + 1] = 1
+    want1 = np.zeros((12, 12), np.uint32)
+    for p in range(3, 12):
+        want1[p, p - 3] = 1
+    assert np.array_equal(P[0], want0) and np.array_equal(P[1], want1)
+    nowrap = oracle.glcm(img, 12, [(1, 0), (1, -1)], levels_mode=True)
+    assert int(nowrap[0].sum()) == 9 and int(nowrap[1].sum()) == 6
+    assert P[0][3, 4] == 1 and nowrap[0][3, 4] == 0
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_flat_matches_brute_force(seed):
+    rng = np.random.default_rng(900 + seed)
+    h, w, n = int(rng.integers(1, 7)), int(rng.integers(1, 7)), int(rng.integers(2, 6))
+    img = rng.integers(0, n, size=(h, w)).astype(np.uint8)
+    offs = [(int(rng.integers(-8, 9)), int(rng.integers(-3, 4))) for _ in range(6)] + [(1, 0), (-1, -1), (w, 0)]
+    P = oracle.glcm_flat(img, n, offs, levels_mode=True)
+    for k, (dx, dy) in enumerate(offs):
+        assert np.array_equal(P[k], _flat_brute(img, n, dx, dy)), (h, w, dx, dy)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_flat_is_the_lagged_pair_histogram_of_the_raveled_image(seed):
+    """The flat GLCM is the joint histogram of (s[t], s[t + L]) over the raveled
+    levels s at lag L = dy W + dx, formed here by numpy bincount; its total is
+    W H - |L|, and lag -L gives the transpose."""
+    rng = np.random.default_rng(950 + seed)
+    h, w, n = int(rng.integers(2, 40)), int(rng.integers(2, 40)), 16
+    img = rng.integers(0, 256, size=(h, w)).astype(np.uint8)
+    s = (img.astype(np.int64) * n) >> 8
+    s = s.reshape(-1)
+    for dx, dy in [(1, 0), (1, -1), (0, -1), (-1, -1), (3, 2), (w + 2, -1)]:
+        L = dy * w + dx
+        if abs(L) >= h * w:
+            continue
+        a, b = (s[:-L], s[L:]) if L > 0 else ((s[-L:], s[:L]) if L < 0 else (s, s))
+        want = np.bincount(a * n + b, minlength=n * n).reshape(n, n)
+        P = oracle.glcm_flat(img, n, [(dx, dy), (-dx, -dy)])
+        assert np.array_equal(P[0], want.astype(np.uint32)), (dx, dy)
+        assert int(P[0].sum()) == h * w - abs(L)
+        assert np.array_equal(P[1], P[0].T)
+
+
+def test_flat_equals_no_wrap_plus_row_seams():
+    """Flat counts = the in-bounds (no-wrap) counts + the pairs whose partner
+    column x + dx leaves [0, W) (enumerated here from the seam columns only)."""
+    rng = np.random.default_rng(77)
+    img = rng.integers(0, 256, size=(33, 29)).astype(np.uint8)
+    h, w, n = img.shape[0], img.shape[1], 8
+    q = (img.astype(np.int64) * n) >> 8
+    for dx, dy in [(1, 0), (2, -1), (-3, -2), (4, 1)]:
+        seam = np.zeros((n, n), np.int64)
+        xs = range(w - dx, w) if dx > 0 else range(0, -dx)
+        for y in range(h):
+            for x in xs:
+                p2 = (y + dy) * w + x + dx
+                if 0 <= p2 < h * w:
+                    seam[q[y, x], q[p2 // w, p2 % w]] += 1
+        nowrap = oracle.glcm(img, n, [(dx, dy)])[0].astype(np.int64)
+        assert np.array_equal(oracle.glcm_flat(img, n, [(dx, dy)])[0].astype(np.int64), nowrap + seam), (dx, dy)
