@@ -66,8 +66,19 @@ enum { GLCM_U8 = 0, GLCM_U16 = 1 };
 enum {
     GLCM_SYMMETRIC = 1,    /* normalized / features use S = P + P^T           */
     GLCM_NORMALIZE = 2,    /* write p = S / sum(S) as float32                 */
-    GLCM_INPUT_LEVELS = 4  /* pixels are levels already (must be < N)         */
+    GLCM_INPUT_LEVELS = 4, /* pixels are levels already (must be < N)         */
+    GLCM_FLAT_WRAP = 8     /* pair along the flat row-major buffer (below)    */
 };
+
+/* GLCM_FLAT_WRAP: Eq. 2 read literally on the image as one row-major buffer
+ * of width * height pixels (the paper addresses partners by adding d, d (N-1),
+ * d N or d (N+1) to a pixel's index, N the image width, Sec. I.A, and pads
+ * its stripes the same way, Eq. 9).  Pixel p = y * width + x pairs with
+ * p + dy * width + dx whenever that index lies in [0, width * height), so
+ * pairs also run from the end of a row into another row; the default (no
+ * flag) counts only partners inside the image rectangle.  The extra pairs are
+ * exactly those whose partner column x + dx leaves [0, width).  Accepted by
+ * glcm_compute, glcm_compute_batch, glcm_enqueue_batch and the server. */
 
 #define GLCM_MAX_LEVELS 256
 #define GLCM_MAX_OFFSETS 64
@@ -88,7 +99,7 @@ typedef struct {
     int levels;                 /* N, 2..256                                       */
     const glcm_offset *offsets; /* n_offsets entries (host memory)                 */
     int n_offsets;              /* 1..GLCM_MAX_OFFSETS                             */
-    int flags;                  /* GLCM_SYMMETRIC | GLCM_INPUT_LEVELS              */
+    int flags;                  /* GLCM_SYMMETRIC | GLCM_INPUT_LEVELS | GLCM_FLAT_WRAP */
     uint32_t *counts;           /* n_offsets x N x N, required                     */
     float *normalized;          /* n_offsets x N x N or NULL                       */
     float *features;            /* n_offsets x 14 or NULL                          */
@@ -120,7 +131,7 @@ int glcm_offset_from_angle(int d, int theta_deg, glcm_offset *out);
  *   image       height rows of pitch_bytes; pitch_bytes >= width * bytes per pixel
  *   levels      N in 2..256
  *   offsets     host array of n_offsets (1..64) offsets, |dx| < 65536, |dy| < 65536
- *   flags       GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS
+ *   flags       GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS, GLCM_FLAT_WRAP
  *   counts      out: n_offsets x N x N uint32, row-major [offset][i][j]; always
  *               the plain (non-symmetric) counts P
  *   normalized  out (or NULL): n_offsets x N x N float32, p = S / sum(S) with
@@ -273,7 +284,8 @@ int glcm_compute_naive(glcm_ctx *ctx, const void *image, int width, int height,
  *
  *   image      device pointer of the current device, height rows of pitch_bytes
  *   offsets    host array of n_offsets (1..64) offsets
- *   flags      GLCM_INPUT_LEVELS only (counts are always the plain P)
+ *   flags      GLCM_INPUT_LEVELS only (counts are always the plain P;
+ *              GLCM_FLAT_WRAP returns GLCM_ERR_UNSUPPORTED)
  *   counts     device pointer, out: n_offsets x N x N uint32 (as glcm_compute)
  *   cuda_stream  stream to run on (NULL: the legacy default stream); the call
  *              returns after the counts are complete

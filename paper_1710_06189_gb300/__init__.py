@@ -10,7 +10,8 @@ up to 46340^2).
 from __future__ import annotations
 
 from . import binding
-from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_INPUT_LEVELS, GLCM_NORMALIZE, GLCM_OK,
+from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_FLAT_WRAP, GLCM_INPUT_LEVELS, GLCM_NORMALIZE,
+                      GLCM_OK,
                       GLCM_SYMMETRIC, GLCM_U8, GLCM_U16, GlcmError,
                       glcm_compute, glcm_compute_batch, glcm_compute_naive, glcm_create, glcm_destroy,
                       glcm_features, glcm_get_timing, glcm_last_error, glcm_offset_from_angle,
@@ -18,7 +19,7 @@ from .binding import (GLCM_ERR_BUSY, GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_INPUT_
 
 __all__ = [
     "PreparedBatch",
-    "binding", "Context", "Server", "GlcmError", "GLCM_OK", "GLCM_ERR_BUSY", "GLCM_ERR_NOMEM", "GLCM_ERR_RANGE", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_U8",
+    "binding", "Context", "Server", "GlcmError", "GLCM_OK", "GLCM_ERR_BUSY", "GLCM_ERR_NOMEM", "GLCM_ERR_RANGE", "GLCM_SYMMETRIC", "GLCM_NORMALIZE", "GLCM_INPUT_LEVELS", "GLCM_FLAT_WRAP", "GLCM_U8",
     "GLCM_U16", "glcm_compute", "glcm_compute_batch", "glcm_compute_naive", "glcm_create", "glcm_destroy",
     "glcm_features", "glcm_get_timing", "glcm_last_error", "glcm_offset_from_angle", "glcm_set_timing",
     "glcm_set_vote_config", "glcm_synchronize", "glcm_windows", "glcm_histogram",

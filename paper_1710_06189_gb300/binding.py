@@ -26,7 +26,7 @@ GLCM_ERR_CUDA = -5
 GLCM_ERR_TIMEOUT = -6
 GLCM_ERR_BUSY = -7
 GLCM_U8, GLCM_U16 = 0, 1
-GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS = 1, 2, 4
+GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS, GLCM_FLAT_WRAP = 1, 2, 4, 8
 GLCM_N_FEATURES = 14
 GLCM_N_WINDOW_MAPS = 4
 

@@ -71,6 +71,8 @@ struct VotePlan {
     int bpp = 1;
     int max_ctas = 0;   // grid cap (0: every SM), leaves SMs to a concurrent kernel
     std::vector<FastClass> fast;  // column-walk launches (offsets at distance 1)
+    std::vector<SeamJob> seams;   // flat-wrap pairs across row ends (GLCM_FLAT_WRAP)
+    size_t seams_off = 0;         // byte offset of the seam table in the jobs buffer
 };
 
 bool plan_empty(const VotePlan& p) { return p.jobs.empty() && p.fast.empty(); }
@@ -322,6 +324,7 @@ struct ImageSpec {
     int n_off;
     uint32_t* out;       // device counts, n_off*N*N
     int y_begin, y_end;  // anchor rows of this launch
+    int flat = 0;        // GLCM_FLAT_WRAP: also the pairs across row ends
 };
 
 // Append the jobs of one image to a plan.  Jobs run in the order
@@ -640,6 +643,15 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     (void)target_items;
     if (present)
         plan_image_fast(ctx, s, plan, present, slot, slot_t);
+    if (s.flat) {
+        // Flat-wrap: the pairs whose partner column leaves [0, W), added after the votes.
+        const long long nn = (long long)s.levels * s.levels;
+        for (int k = 0; k < s.n_off; ++k)
+            if (s.offsets[k].dx != 0)
+                plan.seams.push_back(SeamJob{s.img, s.pitch, s.W, s.H, s.bpp, s.levels, s.levels_mode,
+                                             s.offsets[k].dx, s.offsets[k].dy, s.y_begin, s.y_end,
+                                             s.out + k * nn});
+    }
     return plan_image_general(ctx, s, plan, gen);
 }
 
@@ -730,6 +742,9 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
         const_cast<FastClass&>(c).chunks_off = bj;
         bj += c.chunks.size() * sizeof(int3);
     }
+    bj = (bj + 15) & ~(size_t)15;
+    const_cast<VotePlan&>(plan).seams_off = bj;
+    bj += plan.seams.size() * sizeof(SeamJob);
     const size_t bo = plan.offs.size() * sizeof(VoteOffset);
     const size_t bf = feats.size() * sizeof(FeatJob);
     TRY(ensure(ctx, djobs, bj));
@@ -752,6 +767,8 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
         if (!c.chunks.empty())
             memcpy(h + c.chunks_off, c.chunks.data(), c.chunks.size() * sizeof(int3));
     }
+    if (!plan.seams.empty())
+        memcpy(h + plan.seams_off, plan.seams.data(), plan.seams.size() * sizeof(SeamJob));
     if (bo)
         memcpy(h + oo, plan.offs.data(), bo);
     if (bf)
@@ -910,6 +927,19 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     if (!plan.jobs.empty()) {
         CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
         ++n_launch;
+    }
+    if (!plan.seams.empty()) {
+        long long most = 1;
+        for (const SeamJob& sj : plan.seams)
+            most = std::max<long long>(most, (long long)std::min(std::abs(sj.dx), sj.W) * (sj.y_end - sj.y_begin));
+        const int bpj = (int)std::max<long long>(1, std::min<long long>(ctx->sm_count, (most + 4095) / 4096));
+        const SeamJob* sjobs =
+            reinterpret_cast<const SeamJob*>(static_cast<uint8_t*>(djobs.p) + plan.seams_off);
+        CK(launch_seams(sjobs, (int)plan.seams.size(), bpj, ctx->d_words, st));
+        if (!capturing)
+            ctx->kernel_launches += 1;
+        if (ge)
+            ge->n_kernels++;
     }
     if (time_it) {
         CK(cudaEventRecord(tp.b, st));
@@ -1412,10 +1442,16 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         d_norm = static_cast<float*>(ctx->norm.p);
     }
     int dymin = 0, dymax = 0;
+    bool wide_wrap = false;  // a flat-wrap offset reaching a whole row or more sideways
     for (int k = 0; k < n_offsets; ++k) {
         dymin = std::min(dymin, offsets[k].dy);
         dymax = std::max(dymax, offsets[k].dy);
+        wide_wrap |= std::abs(offsets[k].dx) >= width;
     }
+    const bool flat = (flags & GLCM_FLAT_WRAP) != 0;
+    // A flat-wrap pair that leaves a row to the right lands one row further down.
+    if (flat)
+        dymax += 1;
 
     // Stripes (Sec. III): anchor rows [r_k, r_{k+1}); stripe k's copy ends at
     // r_{k+1} + max(dy, 0) so its partner rows are on the device.
@@ -1425,6 +1461,8 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         const long long bytes = (long long)height * width * bpp;
         n_stripes = (int)std::max<long long>(1, std::min<long long>(8, bytes / (4ll << 20)));
         n_stripes = std::min(n_stripes, height);
+        if (flat && wide_wrap)
+            n_stripes = 1;
     }
     for (int k = 1; k <= n_stripes; ++k)
         anchors_cut.push_back((int)((long long)height * k / n_stripes));
@@ -1446,7 +1484,7 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
             CK(cudaStreamWaitEvent(ctx->stream, ctx->stripe_events[k], 0));
         VotePlan plan;
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
-                    offsets, n_offsets, d_counts, r0, r1};
+                    offsets, n_offsets, d_counts, r0, r1, flat ? 1 : 0};
         TRY(plan_image(ctx, s, plan, target_items(ctx)));
         finalize_fast(plan, ctx->sm_count);
         build_chunks(plan, ctx->sm_count);
@@ -1555,7 +1593,7 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
                                                         std::max<long long>(1, total_rows_strips));
         ImageSpec s{static_cast<const uint8_t*>(d.image), (long long)d.pitch_bytes, d.width, d.height, bpp,
                     d.levels, (d.flags & GLCM_INPUT_LEVELS) ? 1 : 0, d.offsets, d.n_offsets, d.counts, 0,
-                    d.height};
+                    d.height, (d.flags & GLCM_FLAT_WRAP) ? 1 : 0};
         TRY(plan_image(ctx, s, plan, tgt));
         max_levels = std::max(max_levels, d.levels);
         const size_t nn = (size_t)d.levels * d.levels;
@@ -1607,10 +1645,13 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
             dst.jobs.push_back(c);
         }
     }
-    // The column-walk classes (either pixel type) launch with the uint8 part.
+    // The column-walk classes and the flat-wrap seams (either pixel type)
+    // launch with the uint8 part.
     sb.p8.fast = plan.fast;
+    sb.p8.seams = plan.seams;
     VotePlan all;
     all.fast = plan.fast;
+    all.seams = plan.seams;
     all.jobs = sb.p8.jobs;
     all.jobs.insert(all.jobs.end(), sb.p16.jobs.begin(), sb.p16.jobs.end());
     for (size_t k = sb.p8.jobs.size(); k < all.jobs.size(); ++k)
@@ -1626,6 +1667,7 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
         sb.p8.fast[c].jobs_off = all.fast[c].jobs_off;
         sb.p8.fast[c].chunks_off = all.fast[c].chunks_off;
     }
+    sb.p8.seams_off = all.seams_off;
     sb.j16.p = static_cast<VoteJob*>(djobs.p) + sb.p8.jobs.size();
     sb.o16.p = doffs.p;  // p16's off0 are already shifted past p8's offsets
     sb.c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(djobs.p) + all.chunk_off);

@@ -128,6 +128,18 @@ struct FastParams {
     unsigned* err;
 };
 
+// Flat-wrap pairs of one offset (GLCM_FLAT_WRAP): the anchors of rows
+// [y_begin, y_end) whose partner column x + dx leaves [0, W), paired along the
+// row-major buffer (seam.cu).
+struct SeamJob {
+    const uint8_t* img;
+    long long pitch;
+    int W, H, bpp, levels, levels_mode;
+    int dx, dy;
+    int y_begin, y_end;
+    uint32_t* out;  // this offset's N x N counts
+};
+
 // Epilogue: symmetrize / normalize / Haralick features for one GLCM.
 struct FeatJob {
     const uint32_t* counts;  // N*N
@@ -213,6 +225,7 @@ cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, int grid, 
 size_t vote_fast_smem_bytes(int max_hist_words);
 int vote_fast_hist_words(int log2n, int mode);
 int vote_fast_blocks_per_sm(int bpp, int log2n, size_t smem);
+cudaError_t launch_seams(const SeamJob* jobs, int n_jobs, int blocks_per_job, unsigned* err, cudaStream_t s);
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);

@@ -124,6 +124,8 @@ extern "C" int glcm_compute_noalloc(const void* image, int width, int height, si
     for (int k = 0; k < n_offsets; ++k)
         if (offsets[k].dx <= -65536 || offsets[k].dx >= 65536 || offsets[k].dy <= -65536 || offsets[k].dy >= 65536)
             return na_fail(errbuf, errbuf_len, GLCM_ERR_ARG, "offset out of range");
+    if (flags & GLCM_FLAT_WRAP)
+        return na_fail(errbuf, errbuf_len, GLCM_ERR_UNSUPPORTED, "GLCM_FLAT_WRAP is not supported here");
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0)
         return na_fail(errbuf, errbuf_len, GLCM_ERR_CUDA, "no current CUDA device");
