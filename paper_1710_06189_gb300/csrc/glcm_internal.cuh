@@ -233,6 +233,9 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
 size_t features_smem_bytes(int max_levels);
 long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);
+// The incremental window kernel (window_slide.cu); cudaErrorNotSupported when
+// the windows do not fit it.
+cudaError_t launch_windows_slide(const WindowParams& p, cudaStream_t s);
 cudaError_t launch_histogram(const HistParams& p, int sm_count, cudaStream_t s);
 long long histogram_seg_bytes();
 int vote_max_smem_optin();

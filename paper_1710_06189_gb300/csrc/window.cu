@@ -168,6 +168,10 @@ cudaError_t launch_windows(const WindowParams& p, cudaStream_t s)
 {
     if (p.nwx <= 0 || p.nwy <= 0)
         return cudaSuccess;
+    // Windows that fit the incremental kernel slide (window_slide.cu).
+    const cudaError_t es = launch_windows_slide(p, s);
+    if (es != cudaErrorNotSupported)
+        return es;
     long long maxpairs = (long long)p.win * p.win;
     const int cbits = maxpairs <= 255 ? 8 : (maxpairs <= 65535 ? 16 : 32);
     const long long bins = (long long)p.n_off * p.levels * p.levels;
