@@ -92,6 +92,8 @@ struct glcm_ctx {
     int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
     unsigned* d_words = nullptr;  // [0] error bits, [1] general vote chunk counter, [2..15] column-walk counters
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
+    DevBuf slide_tab;             // fixed-point tables of the incremental window kernel
+    bool slide_tab_ready = false;
     DevBuf hb_img, hb_out;        // host-buffer batches: staged images, device results
     std::vector<std::array<DevBuf, 3>> hb_tab;  // host-buffer batches: tables per group
     void* h_stage = nullptr;      // pinned table staging
@@ -1289,7 +1291,7 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
     for (auto& kv : ctx->graphs)
         destroy_graph(kv.second);
     for (DevBuf* b : {&ctx->jobs, &ctx->offs, &ctx->feat, &ctx->work, &ctx->img, &ctx->counts, &ctx->norm,
-                      &ctx->featout, &ctx->maps, &ctx->hb_img, &ctx->hb_out})
+                      &ctx->featout, &ctx->maps, &ctx->hb_img, &ctx->hb_out, &ctx->slide_tab})
         if (b->p)
             cudaFree(b->p);
     for (auto& t : ctx->hb_tab)
@@ -2200,6 +2202,14 @@ extern "C" int glcm_windows(glcm_ctx* ctx, const void* image, int width, int hei
     wp.counts = d_c;
     wp.maps = d_m;
     wp.err = ctx->d_words;
+    if (!ctx->slide_tab_ready) {
+        std::vector<long long> tab(kSlideTableWords);
+        window_slide_tables(tab.data());
+        TRY(ensure(ctx, ctx->slide_tab, tab.size() * sizeof(long long)));
+        CK(cudaMemcpy(ctx->slide_tab.p, tab.data(), tab.size() * sizeof(long long), cudaMemcpyHostToDevice));
+        ctx->slide_tab_ready = true;
+    }
+    wp.slide_tables = static_cast<const long long*>(ctx->slide_tab.p);
     cudaError_t e = launch_windows(wp, ctx->stream);
     if (e == cudaErrorInvalidConfiguration) {
         cudaGetLastError();

@@ -169,7 +169,15 @@ struct WindowParams {
     uint32_t* counts;   // nwy*nwx*n_off*N*N or null
     float* maps;        // 4*n_off*nwy*nwx or null  [map][offset][wy][wx]
     unsigned* err;
+    const long long* slide_tables;  // kSlideTableWords fixed-point terms (incremental kernel) or null
 };
+
+// Fixed-point tables of the incremental window kernel (scale 2^40), made on
+// the host in float64: g(c) = (c + 1) ln(c + 1) - c ln c for c < 512, its
+// prefix sums t ln t for t <= 512, and 1 / (1 + d^2) for d < 32.
+constexpr int kSlideG = 512;
+constexpr int kSlideTableWords = kSlideG + (kSlideG + 1) + 32;
+void window_slide_tables(long long* out);
 
 // Gray-level histogram of one image (histogram.cu).
 struct HistParams {

@@ -19,12 +19,16 @@
 // so each window's maps cost O(1) -- contrast C / T, ASM A / T^2, IDM I / T,
 // entropy ln T - E / T -- and never a scan of its N^2 bins.  Adding one to a
 // bin of count c changes sum S ln S by g(c) = (c + 1) ln(c + 1) - c ln c,
-// read from a table computed in float64 and rounded to 2^-40 once per CTA:
-// the sums are exact sums of rounded terms, within 2^-33 of the true ones.
+// read from a table made once on the host in float64 and rounded to 2^-40:
+// the sums are exact sums of rounded terms.  T ln T is the prefix sum of the
+// same terms, so T * entropy = T ln T - sum S ln S is an exact integer
+// difference (0 for a constant window) and the maps need no float64 on the
+// device (float64 is slow on this GPU): each is one float32 division.
 //
 // One CTA covers `tasks` consecutive window rows and `seg` windows of each;
 // it stages the levels of the pixels they span in shared memory once.
 #include <cmath>
+#include <type_traits>
 
 #include "glcm_internal.cuh"
 
@@ -33,7 +37,7 @@ namespace {
 
 constexpr int kSlideWarps = 8;
 constexpr int kSlideThreads = 32 * kSlideWarps;
-constexpr int kGTab = 512;          // g(c) for c < 512 (S <= 2 * 255 + 1)
+constexpr int kGTab = kSlideG;      // g(c) for c < 512 (S <= 2 * 255 + 1)
 constexpr double kFix = 1099511627776.0;  // 2^40
 constexpr uint8_t kBad = 0xFF;      // a pixel >= N (levels mode)
 
@@ -58,20 +62,16 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
     constexpr int TPW = 32 / LPW;  // tasks per warp
     extern __shared__ __align__(16) unsigned char sm[];
     long long* Gt = reinterpret_cast<long long*>(sm);
-    long long* Ht = Gt + kGTab;
+    long long* PGt = Gt + kGTab;       // t ln t, t <= 512
+    long long* Ht = PGt + kGTab + 1;
     uint8_t* tile = reinterpret_cast<uint8_t*>(Ht + 32);
     uint32_t* hist = reinterpret_cast<uint32_t*>(tile + (((size_t)RH * RWp + 15) & ~(size_t)15));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int S = p.stride, N = p.levels, NN = N * N;
     const int tasks = kSlideWarps * TPW;
 
-    for (int c = tid; c < kGTab; c += kSlideThreads) {
-        const double cd = (double)c;
-        const double g = (cd + 1.0) * log(cd + 1.0) - (c > 0 ? cd * log(cd) : 0.0);
-        Gt[c] = llrint(g * kFix);
-    }
-    if (tid < 32)
-        Ht[tid] = llrint(kFix / (1.0 + (double)tid * tid));
+    for (int c = tid; c < kSlideTableWords; c += kSlideThreads)
+        Gt[c] = p.slide_tables[c];
     const int wx0 = blockIdx.x * seg, wy0 = blockIdx.y * tasks;
     const int px0 = wx0 * S, py0 = wy0 * S;
     for (int t = tid; t < RH * RW; t += kSlideThreads) {
@@ -104,9 +104,15 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
     SlideSums s{0, 0, 0, 0ll, 0ll};
     bool bad = false;
 
-    // One vote of the pair at tile index a (anchor), with sign +1 or -1.
-    auto vote = [&](int a, int sg) {
-        const uint32_t i = tile[a], j = tile[a + tstep];
+    // One vote of the pair at tile index a (anchor), added (SG = +1) or removed
+    // (SG = -1).  Branch-free, so the lanes of a warp never split on i == j:
+    // with S the symmetric count before the vote (c + c^T; 2c on the
+    // diagonal) the pair moves two unit steps -- S(i, j) and S(j, i), or S(i, i)
+    // twice -- so sum S^2 changes by 2 (2 S + 1) + 2 [i == j] when added and
+    // by 2 (1 - 2 S) + 2 [i == j] when removed, and sum S ln S by
+    // g(S) + g(S + [i == j]), or -(g(S - 1) + g(S - 1 - [i == j])).
+    auto vote = [&](uint32_t i, uint32_t j, auto sg_tag) {
+        constexpr int SG = decltype(sg_tag)::value;
         if (i == kBad || j == kBad) {
             bad = true;
             return;
@@ -117,46 +123,50 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
         const uint32_t word = *w;
         const int c = (int)((word >> sh) & 0xFFu);
         const int d = (int)i - (int)j;
-        const int d2 = d * d;
         const long long h = Ht[d < 0 ? -d : d];
-        if (!sym) {
-            if (sg > 0) {
-                s.A += 2 * c + 1;
-                s.E += Gt[c];
-            } else {
-                s.A += 1 - 2 * c;
-                s.E -= Gt[c - 1];
-            }
-            s.T += sg;
-            s.C += sg * d2;
-            s.I += sg > 0 ? h : -h;
-        } else if (i != j) {
+        if (sym) {
             const uint32_t bt = j * (uint32_t)N + i;
             const int ct = (int)((hl[(bt >> 2) * 32] >> ((bt & 3u) * 8u)) & 0xFFu);
-            const int Sv = c + ct;  // S(i, j) = S(j, i) before the vote
-            if (sg > 0) {
-                s.A += 2 * (2 * Sv + 1);
-                s.E += 2 * Gt[Sv];
+            const int Sv = c + ct;
+            const int dg = i == j ? 1 : 0;
+            if (SG > 0) {
+                s.A += 2 * (2 * Sv + 1) + 2 * dg;
+                s.E += Gt[Sv] + Gt[Sv + dg];
             } else {
-                s.A += 2 * (1 - 2 * Sv);
-                s.E -= 2 * Gt[Sv - 1];
+                s.A += 2 * (1 - 2 * Sv) + 2 * dg;
+                s.E -= Gt[Sv - 1] + Gt[Sv - 1 - dg];
             }
-            s.T += 2 * sg;
-            s.C += 2 * sg * d2;
-            s.I += sg > 0 ? 2 * h : -2 * h;
+            s.T += 2 * SG;
+            s.C += 2 * SG * d * d;
+            s.I += 2 * SG * h;
         } else {
-            const int Sv = 2 * c;  // S(i, i) before the vote, changes by 2
-            if (sg > 0) {
-                s.A += 4 * Sv + 4;
-                s.E += Gt[Sv] + Gt[Sv + 1];
-            } else {
-                s.A += 4 - 4 * Sv;
-                s.E -= Gt[Sv - 1] + Gt[Sv - 2];
-            }
-            s.T += 2 * sg;
-            s.I += sg > 0 ? 2 * h : -2 * h;
+            s.A += 2 * SG * c + 1;
+            s.E += SG > 0 ? Gt[c] : -Gt[c - 1];
+            s.T += SG;
+            s.C += SG * d * d;
+            s.I += SG * h;
         }
-        *w = word + (sg > 0 ? (1u << sh) : (0u - (1u << sh)));
+        *w = word + (SG > 0 ? (1u << sh) : (0u - (1u << sh)));
+    };
+    using Add = std::integral_constant<int, 1>;
+    using Rem = std::integral_constant<int, -1>;
+    // Votes of n anchors in a row from tile index a0: the levels of four
+    // anchors and their partners are read before their votes, so those reads
+    // overlap instead of waiting behind each vote's counter update.
+    auto vote_run = [&](int a0, int n, auto sg_tag) {
+        for (int k0 = 0; k0 < n; k0 += 4) {
+            uint32_t ii[4], jj[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int a = a0 + k0 + (k0 + q < n ? q : 0);
+                ii[q] = tile[a];
+                jj[q] = tile[a + tstep];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (k0 + q < n)
+                    vote(ii[q], jj[q], sg_tag);
+        }
     };
     const long long plane = (long long)p.nwy * p.nwx;
     auto emit = [&](int wx) {
@@ -177,11 +187,14 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
         if (p.maps) {
             float con = 0.f, asmv = 0.f, idm = 0.f, ent = 0.f;
             if (s.T > 0) {
-                const double T = (double)s.T;
-                con = (float)((double)s.C / T);
-                asmv = (float)((double)s.A / (T * T));
-                idm = (float)((double)s.I / kFix / T);
-                ent = (float)(log(T) - (double)s.E / kFix / T);
+                // Exact integers (C, A, T^2 < 2^24) or exact fixed-point sums
+                // scaled by a power of two: one rounding each, then a division.
+                const float T = (float)s.T;
+                const float inv_fix = 1.0f / (float)kFix;
+                con = __fdiv_rn((float)s.C, T);
+                asmv = __fdiv_rn((float)s.A, __fmul_rn(T, T));
+                idm = __fdiv_rn(__fmul_rn(__ll2float_rn(s.I), inv_fix), T);
+                ent = __fdiv_rn(__fmul_rn(__ll2float_rn(PGt[s.T] - s.E), inv_fix), T);
             }
             p.maps[(0ll * p.n_off + o) * plane + win_id] = con;
             p.maps[(1ll * p.n_off + o) * plane + win_id] = asmv;
@@ -193,8 +206,7 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
     const int Y0 = task * S;  // the window's top row in the tile
     // First window of the row: every pair.
     for (int y = aylo; y < ayhi; ++y)
-        for (int x = axlo; x < axhi; ++x)
-            vote((Y0 + y) * RWp + x, 1);
+        vote_run((Y0 + y) * RWp + axlo, axhi - axlo, Add{});
     emit(wx0);
     // Slides: the anchor columns [X0 + axlo, X0 + axhi) become [X1 + axlo, X1 + axhi).
     for (int k = 1; k < n_w; ++k) {
@@ -203,10 +215,8 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
         const int a_beg = max(X0 + axhi, X1 + axlo);
         for (int y = aylo; y < ayhi; ++y) {
             const int row = (Y0 + y) * RWp;
-            for (int x = X0 + axlo; x < r_end; ++x)
-                vote(row + x, -1);
-            for (int x = a_beg; x < X1 + axhi; ++x)
-                vote(row + x, 1);
+            vote_run(row + X0 + axlo, r_end - (X0 + axlo), Rem{});
+            vote_run(row + a_beg, X1 + axhi - a_beg, Add{});
         }
         emit(wx0 + k);
     }
@@ -216,6 +226,22 @@ __global__ void __launch_bounds__(kSlideThreads) k_window_slide(WindowParams p, 
 
 }  // namespace
 
+void window_slide_tables(long long* out)
+{
+    long long* G = out;
+    long long* PG = out + kSlideG;
+    long long* H = PG + kSlideG + 1;
+    PG[0] = 0;
+    for (int c = 0; c < kSlideG; ++c) {
+        const double cd = (double)c;
+        const double g = (cd + 1.0) * std::log(cd + 1.0) - (c > 0 ? cd * std::log(cd) : 0.0);
+        G[c] = std::llrint(g * kFix);
+        PG[c + 1] = PG[c] + G[c];
+    }
+    for (int d = 0; d < 32; ++d)
+        H[d] = std::llrint(kFix / (1.0 + (double)d * d));
+}
+
 // The incremental kernel, when the windows fit it: N <= 16, at most 8
 // offsets, at most 255 pairs per window and offset (8-bit counters) and a
 // staged tile that fits shared memory.  Returns cudaErrorNotSupported
@@ -224,7 +250,7 @@ cudaError_t launch_windows_slide(const WindowParams& p, cudaStream_t s)
 {
     if (p.nwx <= 0 || p.nwy <= 0)
         return cudaSuccess;
-    if (p.levels > 16 || p.n_off < 1 || p.n_off > 8)
+    if (p.levels > 16 || p.n_off < 1 || p.n_off > 8 || !p.slide_tables)
         return cudaErrorNotSupported;
     for (int o = 0; o < p.n_off; ++o)
         if ((long long)(p.win - abs(p.dx[o])) * (p.win - abs(p.dy[o])) > 255)
@@ -234,7 +260,7 @@ cudaError_t launch_windows_slide(const WindowParams& p, cudaStream_t s)
     const int NN = p.levels * p.levels;
     const int hw = (NN + 3) / 4;
     const size_t hist_bytes = (size_t)kSlideWarps * hw * 32 * 4;
-    const size_t fixed = (size_t)(kGTab + 32) * 8 + hist_bytes;
+    const size_t fixed = (size_t)kSlideTableWords * 8 + hist_bytes;
     const int RH = (tasks - 1) * p.stride + p.win;
     // Windows per task: as many as keep the tile within 96 KB (a slide costs
     // what a first window costs once per task), at least one, and enough
