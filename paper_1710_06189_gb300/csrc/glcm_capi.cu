@@ -567,6 +567,7 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
         j.half_hi = g.half_hi;
         j.row_half = g.row_half;
         j.transposed = g.transposed;
+        j.aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0 ? 1 : 0;
         for (int k = 0; k < 4; ++k) {
             const bool in = (g.present >> k) & 1;
             j.slot[k] = in ? (g.mode == kFastWide ? g.slot : slot[k]) : -1;
@@ -615,8 +616,8 @@ void finalize_fast(VotePlan& plan, int ctas)
 }
 
 // Append the jobs of one image to a plan: offsets at chessboard distance 1 of
-// a uint8/uint16 image with N a power of two up to 32 (aligned rows, levels
-// quantized here) go to the column-walk kernel unless the autotuner chose a
+// a uint8/uint16 image with N in {2, 4, 8, 16, 32, 256} (levels quantized
+// here, not given) go to the column-walk kernel unless the autotuner chose a
 // general layout for the class; the others to the general vote kernel.
 int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
 {
@@ -627,7 +628,8 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
     // N = 256 merges by bulk reductions into the output rows: 16-byte aligned counts.
     const bool out_aligned = (reinterpret_cast<uintptr_t>(s.out) & 15) == 0;
     const bool eligible = !tuned_general && ((log2n >= 1 && log2n <= 5) || (log2n == 8 && out_aligned)) &&
-                          aligned && !s.levels_mode && s.y_end > s.y_begin;
+                          !s.levels_mode && s.y_end > s.y_begin;
+    (void)aligned;  // rows at any byte address are realigned by the kernel
     std::vector<int> gen;
     int present = 0;
     int slot[4] = {-1, -1, -1, -1}, slot_t[4] = {-1, -1, -1, -1};

@@ -99,13 +99,14 @@ enum : int {
 
 struct FastJob {
     const uint8_t* img;
-    long long pitch;   // bytes between rows (base and pitch 16-byte aligned)
+    long long pitch;   // bytes between rows
     int W, H;
     int bpp;           // 1 or 2
     int log2n;         // N = 2^log2n: 1..5, or 8
     int mode;          // kFast*
     int present;       // bit k: canonical offset k is voted by this job
     int half_hi;       // kFastHalf: the offset (k) counted in the upper halves, or -1
+    int aligned;       // base and pitch 16-byte aligned (one 16-byte load per lane and row)
     int row_half;      // kFastWide: GLCM rows [128 row_half, 128 row_half + 128) are counted
     int transposed;    // kFastWide: count the transpose (rows are partner levels)
     int slot[kFastOffsets];    // output GLCM of canonical offset k, or -1

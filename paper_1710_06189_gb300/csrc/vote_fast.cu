@@ -113,6 +113,33 @@ __device__ __forceinline__ uint32_t outside_mask(int rem)
     return rem >= 4 ? 0u : (rem <= 0 ? 0xFFFFFFFFu : (0xFFFFFFFFu << (8 * rem)));
 }
 
+// 16 bytes from any address p, of which the first `need` (1..16) belong to
+// the row: the aligned 16-byte block holding p and, only when a needed byte
+// lies in it, the next one, shifted into place.  A block read always holds a
+// byte of the row, so it lies within the row's allocation (an aligned block
+// never crosses a page).
+__device__ __forceinline__ uint4 load16_any(const uint8_t* p, int need)
+{
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t off = (uint32_t)(a & 15u);
+    const uint4* b = reinterpret_cast<const uint4*>(a - off);
+    const uint4 x = __ldg(b);
+    if (off == 0)
+        return x;
+    uint4 y = make_uint4(0u, 0u, 0u, 0u);
+    if ((int)off + need > 16)
+        y = __ldg(b + 1);
+    const uint32_t q = off >> 2, sh = 8u * (off & 3u);
+    // Words q .. q + 4 of (x, y), chosen without dynamic indexing.
+    const uint32_t w0 = q == 0 ? x.x : (q == 1 ? x.y : (q == 2 ? x.z : x.w));
+    const uint32_t w1 = q == 0 ? x.y : (q == 1 ? x.z : (q == 2 ? x.w : y.x));
+    const uint32_t w2 = q == 0 ? x.z : (q == 1 ? x.w : (q == 2 ? y.x : y.y));
+    const uint32_t w3 = q == 0 ? x.w : (q == 1 ? y.x : (q == 2 ? y.y : y.z));
+    const uint32_t w4 = q == 0 ? y.x : (q == 1 ? y.y : (q == 2 ? y.z : y.w));
+    return make_uint4(__funnelshift_r(w0, w1, sh), __funnelshift_r(w1, w2, sh), __funnelshift_r(w2, w3, sh),
+                      __funnelshift_r(w3, w4, sh));
+}
+
 // 16-bit lanes of a packed word: bytes 0, 1 (lo) or 2, 3 (hi).
 __device__ __forceinline__ uint32_t spread_lo(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }
 __device__ __forceinline__ uint32_t spread_hi(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }
@@ -425,17 +452,31 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
 
     uint4 qv[kPF];
     uint2 qh[kPF];
+    // Bytes of the row from the lane's first pixel, and from the halo's first pixel.
+    const int need = min(16, (j.W - (on ? xl : 0)) * BPP);
+    const int hneed = has_l ? 4 * BPP : min(4, j.W - xe) * BPP;
+    const bool aligned = j.aligned != 0;
     auto load_row = [&](int y, uint4& v, uint2& h) {
         const long long ro = (long long)y * j.pitch;
         v = make_uint4(0u, 0u, 0u, 0u);
         h = make_uint2(0u, 0u);
-        if (on)
-            v = __ldg(reinterpret_cast<const uint4*>(col + ro));
-        if (has_h) {
-            if constexpr (BPP == 1)
-                h.x = __ldg(reinterpret_cast<const uint32_t*>(hcol + ro));
-            else
-                h = __ldg(reinterpret_cast<const uint2*>(hcol + ro));
+        if (aligned) {
+            if (on)
+                v = __ldg(reinterpret_cast<const uint4*>(col + ro));
+            if (has_h) {
+                if constexpr (BPP == 1)
+                    h.x = __ldg(reinterpret_cast<const uint32_t*>(hcol + ro));
+                else
+                    h = __ldg(reinterpret_cast<const uint2*>(hcol + ro));
+            }
+        } else {
+            // Rows at any byte address: realigned loads.
+            if (on)
+                v = load16_any(col + ro, need);
+            if (has_h) {
+                const uint4 t = load16_any(hcol + ro, hneed);
+                h = make_uint2(t.x, t.y);
+            }
         }
     };
     auto levels = [&](const uint4& v, const uint2& h, uint32_t (&L)[LW], uint32_t& ll, uint32_t& lr) {

@@ -143,3 +143,20 @@ def test_configured_tile_height_and_general_agree(band):
         assert np.array_equal(run(ctx, img, n, offs), want)
         G.glcm_set_vote_config(ctx.ctx, n, len(offs), G.GLCM_U8, 512, 3, 1, 0)  # the general kernel
         assert np.array_equal(run(ctx, img, n, offs), want)
+
+
+@pytest.mark.parametrize("n", [4, 8, 16, 32, 256])
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+def test_rows_at_any_byte_address(gctx, n, dt):
+    """Contiguous images of odd widths (every row at a different alignment, the
+    last row ending short of a 16-byte block) and views starting at odd
+    columns: the column walk realigns its 16-byte loads."""
+    for h, w in [(70, 17), (33, 513), (41, 1001), (9, 777)]:
+        img = _img("iid", h * 131 + w, h, w, dt)
+        assert np.array_equal(run(gctx, img, n, C4 + OPPOSITE[:2]), oracle.glcm(img, n, C4 + OPPOSITE[:2])), (h, w)
+    base = _img("smooth", 97, 120, 1200, dt)
+    t = torch.from_numpy(base).cuda()
+    for x0, x1 in [(1, 600), (3, 1197), (7, 520)]:
+        c = gctx.compute(t[:, x0:x1], n, C4)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_u32(c), oracle.glcm(np.ascontiguousarray(base[:, x0:x1]), n, C4)), (x0, x1)
