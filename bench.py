@@ -499,6 +499,16 @@ def other_workloads(G, S, torch, local: int):
         ms = _timed(stream, lambda: ctx.run(prepared))
         pairs = sum(pairs_of(r["side"], r["side"], r["offsets"]) for r in recipe)
         out["uneven_1000"] = {"ms_per_batch": ms, "gpairs_s": pairs / (ms * 1e-3) / 1e9}
+        del prepared
+        # The whole of config 4 in one CUDA-graph launch: the 2048^2 window
+        # counts and maps, then the 1000 images (glcm_compute_batch_windows).
+        wjobs = [dict(image=wimg, levels=16, win=15, stride=4, offsets=S.CONTENTION_OFFSETS,
+                      flags=G.GLCM_SYMMETRIC, counts=True, maps=True)]
+        pw = ctx.prepare_batch_windows(spec, wjobs)
+        ms = _timed(stream, lambda: ctx.run_batch_windows(pw))
+        out["config4_one_graph"] = {"ms_per_launch": ms, "gpairs_s": (pairs + wp) / (ms * 1e-3) / 1e9,
+                                    "windows": nw, "images": len(recipe), "graph_launches_per_call": 1}
+        del pw
     stream.synchronize()
     ctx.close()
     return out

@@ -207,6 +207,35 @@ int glcm_windows(glcm_ctx *ctx, const void *image, int width, int height, size_t
                  int dtype, int levels, int win, int stride, const glcm_offset *offsets,
                  int n_offsets, int flags, uint32_t *counts, float *maps);
 
+/* One sliding-window job of a batch (glcm_compute_batch_windows): the
+ * arguments of glcm_windows, all buffers device memory. */
+typedef struct {
+    const void *image;          /* height rows of pitch_bytes (device)            */
+    int width, height;
+    size_t pitch_bytes;
+    int dtype;                  /* GLCM_U8 or GLCM_U16                             */
+    int levels;                 /* N, 2..256                                       */
+    int win, stride;            /* window side and step (glcm_windows)             */
+    const glcm_offset *offsets; /* 1..GLCM_MAX_WINDOW_OFFSETS (host memory)        */
+    int n_offsets;
+    int flags;                  /* GLCM_SYMMETRIC | GLCM_INPUT_LEVELS              */
+    uint32_t *counts;           /* nwy x nwx x n_offsets x N x N or NULL (device)  */
+    float *maps;                /* 4 x n_offsets x nwy x nwx or NULL (device)      */
+} glcm_window_desc;
+
+/* A batch of images (as glcm_compute_batch, device buffers only) and of
+ * sliding-window jobs (as glcm_windows) in one CUDA-graph launch: the first
+ * call runs them directly and captures the graph -- the window kernels, then
+ * the batch's persistent vote launches and epilogue -- and later calls with
+ * the same descriptors (pointers, sizes, flags) replay it, so a whole
+ * workload of many images and window maps costs one launch (the paper's
+ * launch-shape rules, Eqs. 4-6, give way to one captured schedule).  Results
+ * equal those of glcm_compute_batch and glcm_windows.  n or n_win may be 0.
+ * Errors: GLCM_ERR_ARG (host buffers, bad descs), GLCM_ERR_UNSUPPORTED,
+ * GLCM_ERR_NOMEM, GLCM_ERR_RANGE, GLCM_ERR_CUDA. */
+int glcm_compute_batch_windows(glcm_ctx *ctx, const glcm_desc *descs, int n, const glcm_window_desc *wins,
+                               int n_win);
+
 /* Gray-level histogram of one image: hist[q] = the number of pixels whose
  * level (quantized as for glcm_compute) is q.  The one-pixel statistic to
  * which the paper's analysis of vote collisions also applies (Sec. I,

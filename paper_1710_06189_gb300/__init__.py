@@ -155,6 +155,34 @@ class Context:
         glcm_compute_batch(self.ctx, prepared.descs)
         return prepared.outs
 
+    def prepare_batch_windows(self, jobs, windows):
+        """A batch of images (as prepare()) plus sliding-window jobs -- dicts
+        {image, levels, win, stride, offsets, flags, counts, maps} with counts /
+        maps True (allocated here), False or a device tensor -- for
+        run_batch_windows: one CUDA-graph launch per call.  Device buffers only."""
+        torch = _torch()
+        prepared = self.prepare(jobs)
+        wdescs, wouts = [], []
+        for w in windows:
+            src, wd, ht, pitch, dt = image_args(w["image"])
+            n_off, N = len(w["offsets"]), w["levels"]
+            nwx, nwy = (wd - w["win"]) // w["stride"] + 1, (ht - w["win"]) // w["stride"] + 1
+            c = w.get("counts", False)
+            c = self._empty((nwy, nwx, n_off, N, N), torch.int32) if c is True else (c if c is not False else None)
+            m = w.get("maps", True)
+            m = self._empty((4, n_off, nwy, nwx), torch.float32) if m is True else (m if m is not False else None)
+            wdescs.append(binding.make_window_desc(src, wd, ht, pitch, dt, N, w["win"], w["stride"], w["offsets"],
+                                                   w.get("flags", 0), c, m))
+            wouts.append((c, m))
+        return PreparedBatch(prepared.descs, (prepared.outs, wouts), (prepared, wdescs))
+
+    def run_batch_windows(self, prepared):
+        """Run (first call: run and capture; then replay) a prepare_batch_windows batch:
+        returns (image outputs, window outputs)."""
+        _, wdescs = prepared._keep
+        binding.glcm_compute_batch_windows(self.ctx, prepared.descs, wdescs)
+        return prepared.outs
+
     def windows(self, img, levels: int, win: int, stride: int, offsets, flags: int = 0, counts: bool = True,
                 maps: bool = True):
         torch = _torch()

@@ -44,6 +44,13 @@ class glcm_desc(ctypes.Structure):
                 ("features", c_void_p)]
 
 
+class glcm_window_desc(ctypes.Structure):
+    _fields_ = [("image", c_void_p), ("width", c_int), ("height", c_int), ("pitch_bytes", c_size_t),
+                ("dtype", c_int), ("levels", c_int), ("win", c_int), ("stride", c_int),
+                ("offsets", ctypes.POINTER(glcm_offset)), ("n_offsets", c_int), ("flags", c_int),
+                ("counts", c_void_p), ("maps", c_void_p)]
+
+
 class glcm_server_stats_t(ctypes.Structure):
     _fields_ = [("submitted", c_longlong), ("completed", c_longlong), ("failed", c_longlong),
                 ("batches", c_longlong), ("max_batch", c_longlong), ("kernel_launches", c_longlong),
@@ -90,6 +97,8 @@ _PROTOS = {
     "glcm_compute_noalloc": (c_int, [c_void_p, c_int, c_int, c_size_t, c_int, c_int, ctypes.POINTER(glcm_offset),
                                      c_int, c_int, c_void_p, c_void_p, ctypes.c_char_p, c_size_t]),
     "glcm_measure_ceilings": (c_int, [c_int, ctypes.POINTER(glcm_ceilings_t)]),
+    "glcm_compute_batch_windows": (c_int, [c_void_p, ctypes.POINTER(glcm_desc), c_int,
+                                           ctypes.POINTER(glcm_window_desc), c_int]),
 }
 
 _lib = None
@@ -319,3 +328,27 @@ def glcm_measure_ceilings(device: int = 0) -> dict:
     if st != GLCM_OK:
         raise GlcmError(st, "glcm_measure_ceilings failed")
     return {k: getattr(out, k) for k, _ in glcm_ceilings_t._fields_}
+
+
+def make_window_desc(image, width, height, pitch_bytes, dtype, levels, win, stride, offsets, flags, counts, maps):
+    """A glcm_window_desc (keeps its offsets array alive on the struct)."""
+    d = glcm_window_desc()
+    offs = _offsets(offsets)
+    d.image, d.width, d.height, d.pitch_bytes = _ptr(image), int(width), int(height), int(pitch_bytes)
+    d.dtype, d.levels, d.win, d.stride = int(dtype), int(levels), int(win), int(stride)
+    d.offsets, d.n_offsets, d.flags = offs, len(offsets), int(flags)
+    d.counts, d.maps = _ptr(counts), _ptr(maps)
+    d._keep = offs
+    return d
+
+
+def glcm_compute_batch_windows(ctx, descs, wins):
+    """One graph launch of a batch of images (make_desc results or a desc_array)
+    and sliding-window jobs (make_window_desc results), device buffers only."""
+    if isinstance(descs, ctypes.Array):
+        da, n = descs, len(descs)
+    else:
+        n = len(descs)
+        da = desc_array(descs) if n else (glcm_desc * 1)()
+    wa = (glcm_window_desc * max(1, len(wins)))(*wins) if wins else (glcm_window_desc * 1)()
+    return _check(ctx, load().glcm_compute_batch_windows(ctx, da, n, wa, len(wins)))
