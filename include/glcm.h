@@ -80,7 +80,8 @@ enum {
  * exactly those whose partner column x + dx leaves [0, width).  Accepted by
  * glcm_compute, glcm_compute_batch, glcm_enqueue_batch and the server. */
 
-#define GLCM_MAX_LEVELS 256
+#define GLCM_MAX_LEVELS 256        /* normalized GLCMs, features, windows, histograms */
+#define GLCM_MAX_COUNT_LEVELS 4096 /* counts alone (glcm_compute, batches, server)    */
 #define GLCM_MAX_OFFSETS 64
 #define GLCM_N_FEATURES 14
 #define GLCM_N_WINDOW_MAPS 4
@@ -96,7 +97,7 @@ typedef struct {
     int width, height;
     size_t pitch_bytes;
     int dtype;                  /* GLCM_U8 or GLCM_U16                             */
-    int levels;                 /* N, 2..256                                       */
+    int levels;                 /* N, 2..256 (..4096 without normalized/features)  */
     const glcm_offset *offsets; /* n_offsets entries (host memory)                 */
     int n_offsets;              /* 1..GLCM_MAX_OFFSETS                             */
     int flags;                  /* GLCM_SYMMETRIC | GLCM_INPUT_LEVELS | GLCM_FLAT_WRAP */
@@ -129,7 +130,11 @@ int glcm_offset_from_angle(int d, int theta_deg, glcm_offset *out);
 /* GLCMs of one image for n_offsets offsets (Eq. 1, all offsets fused in
  * one pass over the image).
  *   image       height rows of pitch_bytes; pitch_bytes >= width * bytes per pixel
- *   levels      N in 2..256
+ *   levels      N in 2..256; up to GLCM_MAX_COUNT_LEVELS (4096, e.g. 1024 for
+ *               full-range uint16) for counts alone -- those GLCMs vote straight
+ *               into the output counts in L2 (warp-aggregated global
+ *               reductions; N^2 bins do not fit shared memory) and GLCM_NORMALIZE
+ *               returns GLCM_ERR_UNSUPPORTED
  *   offsets     host array of n_offsets (1..64) offsets, |dx| < 65536, |dy| < 65536
  *   flags       GLCM_SYMMETRIC, GLCM_NORMALIZE, GLCM_INPUT_LEVELS, GLCM_FLAT_WRAP
  *   counts      out: n_offsets x N x N uint32, row-major [offset][i][j]; always

@@ -73,9 +73,11 @@ struct VotePlan {
     std::vector<FastClass> fast;  // column-walk launches (offsets at distance 1)
     std::vector<SeamJob> seams;   // flat-wrap pairs across row ends (GLCM_FLAT_WRAP)
     size_t seams_off = 0;         // byte offset of the seam table in the jobs buffer
+    std::vector<SeamJob> globals; // N > 256: every pair of one offset voted into global counts
+    size_t globals_off = 0;
 };
 
-bool plan_empty(const VotePlan& p) { return p.jobs.empty() && p.fast.empty(); }
+bool plan_empty(const VotePlan& p) { return p.jobs.empty() && p.fast.empty() && p.globals.empty(); }
 
 }  // namespace
 
@@ -621,6 +623,18 @@ void finalize_fast(VotePlan& plan, int ctas)
 // general layout for the class; the others to the general vote kernel.
 int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_items)
 {
+    if (s.levels > GLCM_MAX_LEVELS) {
+        // N > 256: every offset votes into global counts (vote_global.cu).
+        const long long nn = (long long)s.levels * s.levels;
+        for (int k = 0; k < s.n_off; ++k) {
+            const SeamJob g{s.img, s.pitch, s.W, s.H, s.bpp, s.levels, s.levels_mode,
+                            s.offsets[k].dx, s.offsets[k].dy, s.y_begin, s.y_end, s.out + k * nn};
+            plan.globals.push_back(g);
+            if (s.flat && s.offsets[k].dx != 0)
+                plan.seams.push_back(g);
+        }
+        return GLCM_OK;
+    }
     const int log2n = ilog2_exact(s.levels);
     const bool aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
     auto it = ctx->overrides.find(cfg_key(s.levels, s.n_off, s.bpp));
@@ -671,8 +685,8 @@ int check_image_args(glcm_ctx* ctx, const void* image, int width, int height, si
     const int bpp = dtype == GLCM_U8 ? 1 : 2;
     if (pitch < (size_t)width * bpp)
         return fail(ctx, GLCM_ERR_ARG, "pitch_bytes %zu < width * %d", pitch, bpp);
-    if (levels > GLCM_MAX_LEVELS)
-        return fail(ctx, GLCM_ERR_UNSUPPORTED, "levels %d > %d", levels, GLCM_MAX_LEVELS);
+    if (levels > GLCM_MAX_COUNT_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "levels %d > %d", levels, GLCM_MAX_COUNT_LEVELS);
     if (levels < 2)
         return fail(ctx, GLCM_ERR_ARG, "levels must be in 2..256 (got %d)", levels);
     if (!offsets || n_offsets < 1 || n_offsets > GLCM_MAX_OFFSETS)
@@ -749,6 +763,9 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
     bj = (bj + 15) & ~(size_t)15;
     const_cast<VotePlan&>(plan).seams_off = bj;
     bj += plan.seams.size() * sizeof(SeamJob);
+    bj = (bj + 15) & ~(size_t)15;
+    const_cast<VotePlan&>(plan).globals_off = bj;
+    bj += plan.globals.size() * sizeof(SeamJob);
     const size_t bo = plan.offs.size() * sizeof(VoteOffset);
     const size_t bf = feats.size() * sizeof(FeatJob);
     TRY(ensure(ctx, djobs, bj));
@@ -773,6 +790,8 @@ int upload_tables(glcm_ctx* ctx, const VotePlan& plan, const std::vector<FeatJob
     }
     if (!plan.seams.empty())
         memcpy(h + plan.seams_off, plan.seams.data(), plan.seams.size() * sizeof(SeamJob));
+    if (!plan.globals.empty())
+        memcpy(h + plan.globals_off, plan.globals.data(), plan.globals.size() * sizeof(SeamJob));
     if (bo)
         memcpy(h + oo, plan.offs.data(), bo);
     if (bf)
@@ -844,6 +863,15 @@ __global__ void k_zero_job_outputs(const VoteJob* jobs, int n_gen, const VoteOff
         }
 }
 
+// Zero the N x N counts of every N > 256 job (blockIdx.y: the job).
+__global__ void k_zero_global_outputs(const SeamJob* jobs)
+{
+    const SeamJob j = jobs[blockIdx.y];
+    const long long nn = (long long)j.levels * j.levels;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < nn; e += (long long)gridDim.x * blockDim.x)
+        j.out[e] = 0u;
+}
+
 __global__ void k_clear_counters(unsigned* counters)
 {
     if (threadIdx.x < kCounterWords - 1)
@@ -879,7 +907,22 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     const FastJob* fjobs0 =
         plan.fast.empty() ? nullptr
                           : reinterpret_cast<const FastJob*>(static_cast<uint8_t*>(djobs.p) + plan.fast[0].jobs_off);
-    if (zero) {
+    const SeamJob* gjobs =
+        plan.globals.empty() ? nullptr
+                             : reinterpret_cast<const SeamJob*>(static_cast<uint8_t*>(djobs.p) + plan.globals_off);
+    if (zero && !plan.globals.empty()) {
+        for (size_t g0 = 0; g0 < plan.globals.size(); g0 += 65535) {
+            const int ng = (int)std::min<size_t>(65535, plan.globals.size() - g0);
+            k_zero_global_outputs<<<dim3(64, ng), 256, 0, st>>>(gjobs + g0);
+            CK(cudaGetLastError());
+            ctx->kernel_launches += capturing ? 0 : 1;
+            if (ge)
+                ge->n_kernels++;
+        }
+    }
+    if (zero && plan.jobs.empty() && plan.fast.empty()) {
+        k_clear_counters<<<1, 32, 0, st>>>(ctx->d_words + 1);
+    } else if (zero) {
         k_zero_job_outputs<<<(int)plan.jobs.size() + n_fast_jobs, 256, 0, st>>>(
             static_cast<const VoteJob*>(djobs.p), (int)plan.jobs.size(), static_cast<const VoteOffset*>(doffs.p),
             fjobs0, ctx->d_words + 1);
@@ -930,6 +973,14 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     }
     if (!plan.jobs.empty()) {
         CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
+        ++n_launch;
+    }
+    if (!plan.globals.empty()) {
+        long long most = 1;
+        for (const SeamJob& gj : plan.globals)
+            most = std::max<long long>(most, (long long)gj.W * (gj.y_end - gj.y_begin));
+        const int bpj = (int)std::max<long long>(1, std::min<long long>(4ll * ctx->sm_count, (most + 8191) / 8192));
+        CK(launch_vote_global(gjobs, (int)plan.globals.size(), bpj, ctx->d_words, st));
         ++n_launch;
     }
     if (!plan.seams.empty()) {
@@ -1433,6 +1484,8 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
     const bool dev_img = is_device_ptr(image);
     const bool dev_counts = is_device_ptr(counts);
     const bool want_norm = (flags & GLCM_NORMALIZE) && normalized;
+    if (want_norm && levels > GLCM_MAX_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "normalized GLCMs need levels <= %d", GLCM_MAX_LEVELS);
     const bool dev_norm = want_norm && is_device_ptr(normalized);
     const size_t nn = (size_t)levels * levels;
     uint32_t* d_counts = counts;
@@ -1543,6 +1596,8 @@ extern "C" int glcm_features(glcm_ctx* ctx, const uint32_t* counts, int levels, 
     if (!ctx)
         return GLCM_ERR_ARG;
     cudaSetDevice(ctx->device);
+    if (levels > GLCM_MAX_LEVELS && levels <= GLCM_MAX_COUNT_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "features need levels <= %d", GLCM_MAX_LEVELS);
     if (!counts || !features || n_glcm < 0 || levels < 2 || levels > GLCM_MAX_LEVELS)
         return fail(ctx, GLCM_ERR_ARG, "glcm_features: bad arguments");
     if (n_glcm == 0)
@@ -1591,6 +1646,9 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
     for (int i = 0; i < n; ++i) {
         const glcm_desc& d = descs[i];
         const int bpp = d.dtype == GLCM_U8 ? 1 : 2;
+        if ((d.normalized || d.features) && d.levels > GLCM_MAX_LEVELS)
+            return fail(ctx, GLCM_ERR_UNSUPPORTED, "desc %d: normalized GLCMs and features need levels <= %d", i,
+                        GLCM_MAX_LEVELS);
         // Work items in proportion to this image's share of the batch.
         const long long rs = (long long)d.height * ((d.width + 32 * (16 / bpp) - 1) / (32 * (16 / bpp)));
         const int tgt = (int)std::max<long long>(1, (long long)target_items(ctx) * 4 * rs /
@@ -1653,9 +1711,11 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
     // launch with the uint8 part.
     sb.p8.fast = plan.fast;
     sb.p8.seams = plan.seams;
+    sb.p8.globals = plan.globals;
     VotePlan all;
     all.fast = plan.fast;
     all.seams = plan.seams;
+    all.globals = plan.globals;
     all.jobs = sb.p8.jobs;
     all.jobs.insert(all.jobs.end(), sb.p16.jobs.begin(), sb.p16.jobs.end());
     for (size_t k = sb.p8.jobs.size(); k < all.jobs.size(); ++k)
@@ -1672,6 +1732,7 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
         sb.p8.fast[c].chunks_off = all.fast[c].chunks_off;
     }
     sb.p8.seams_off = all.seams_off;
+    sb.p8.globals_off = all.globals_off;
     sb.j16.p = static_cast<VoteJob*>(djobs.p) + sb.p8.jobs.size();
     sb.o16.p = doffs.p;  // p16's off0 are already shifted past p8's offsets
     sb.c8 = reinterpret_cast<const int3*>(static_cast<uint8_t*>(djobs.p) + all.chunk_off);
@@ -1937,6 +1998,8 @@ int check_window_args(glcm_ctx* ctx, const void* image, int width, int height, s
                       const void* maps)
 {
     TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, offsets, n_offsets));
+    if (levels > GLCM_MAX_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "window GLCMs need levels <= %d", GLCM_MAX_LEVELS);
     if (n_offsets > GLCM_MAX_WINDOW_OFFSETS)
         return fail(ctx, GLCM_ERR_ARG, "at most %d window offsets", GLCM_MAX_WINDOW_OFFSETS);
     if (win < 1 || stride < 1 || win > width || win > height)
@@ -2189,6 +2252,8 @@ extern "C" int glcm_histogram(glcm_ctx* ctx, const void* image, int width, int h
     cudaSetDevice(ctx->device);
     const glcm_offset unit{1, 0};
     TRY(check_image_args(ctx, image, width, height, pitch_bytes, dtype, levels, &unit, 1));
+    if (levels > GLCM_MAX_LEVELS)
+        return fail(ctx, GLCM_ERR_UNSUPPORTED, "histograms need levels <= %d", GLCM_MAX_LEVELS);
     if (!hist)
         return fail(ctx, GLCM_ERR_ARG, "hist is NULL");
     if ((long long)width * height > 0xFFFFFFFFll)

@@ -235,6 +235,9 @@ size_t vote_fast_smem_bytes(int max_hist_words);
 int vote_fast_hist_words(int log2n, int mode);
 int vote_fast_blocks_per_sm(int bpp, int log2n, size_t smem);
 cudaError_t launch_seams(const SeamJob* jobs, int n_jobs, int blocks_per_job, unsigned* err, cudaStream_t s);
+// N > 256: every in-rectangle pair of each job (one offset of one image, its
+// rows [y_begin, y_end)) voted into global counts (vote_global.cu).
+cudaError_t launch_vote_global(const SeamJob* jobs, int n_jobs, int blocks_per_job, unsigned* err, cudaStream_t s);
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);

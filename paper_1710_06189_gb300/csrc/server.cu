@@ -430,9 +430,12 @@ extern "C" int glcm_server_submit(glcm_server* s, const glcm_desc* r, long long*
         return code;
     };
     if (!r->image || !r->counts || r->width < 1 || r->height < 1 || (r->dtype != GLCM_U8 && r->dtype != GLCM_U16) ||
-        r->levels < 2 || r->levels > GLCM_MAX_LEVELS || !r->offsets || r->n_offsets < 1 ||
-        r->n_offsets > GLCM_MAX_OFFSETS || (r->flags & ~(GLCM_SYMMETRIC | GLCM_NORMALIZE | GLCM_INPUT_LEVELS)))
+        r->levels < 2 || r->levels > GLCM_MAX_COUNT_LEVELS || !r->offsets || r->n_offsets < 1 ||
+        r->n_offsets > GLCM_MAX_OFFSETS ||
+        (r->flags & ~(GLCM_SYMMETRIC | GLCM_NORMALIZE | GLCM_INPUT_LEVELS | GLCM_FLAT_WRAP)))
         return bad(GLCM_ERR_ARG, "invalid request");
+    if ((r->normalized || r->features) && r->levels > GLCM_MAX_LEVELS)
+        return bad(GLCM_ERR_UNSUPPORTED, "normalized GLCMs and features need levels <= 256");
     const int bpp = r->dtype == GLCM_U8 ? 1 : 2;
     if (r->pitch_bytes < (size_t)r->width * bpp)
         return bad(GLCM_ERR_ARG, "pitch_bytes < width * bytes per pixel");
