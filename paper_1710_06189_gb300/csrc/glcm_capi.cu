@@ -1657,7 +1657,8 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
                     d.levels, (d.flags & GLCM_INPUT_LEVELS) ? 1 : 0, d.offsets, d.n_offsets, d.counts, 0,
                     d.height, (d.flags & GLCM_FLAT_WRAP) ? 1 : 0};
         TRY(plan_image(ctx, s, plan, tgt));
-        max_levels = std::max(max_levels, d.levels);
+        if (d.normalized || d.features)
+            max_levels = std::max(max_levels, d.levels);  // the epilogue's shared-memory layout
         const size_t nn = (size_t)d.levels * d.levels;
         if (d.normalized || d.features) {
             for (int o = 0; o < d.n_offsets; ++o)
