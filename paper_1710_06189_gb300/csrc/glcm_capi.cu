@@ -48,9 +48,11 @@ struct GraphEntry {
     int n_kernels = 0;
 };
 
-// Jobs of the column-walk kernel for one (pixel type, N): one launch.
+// Jobs of the column-walk kernel for one (pixel type, N, row alignment): one
+// launch.
 struct FastClass {
     int bpp = 1, log2n = 1;
+    bool aligned = true;  // every row of every job starts on 16 bytes
     std::vector<FastJob> jobs;
     std::vector<int3> chunks;  // (class-local job, first item, end item)
     int n_items = 0;
@@ -92,7 +94,7 @@ struct glcm_ctx {
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
     int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
-    unsigned* d_words = nullptr;  // [0] error bits, [1] general vote chunk counter, [2..15] column-walk counters
+    unsigned* d_words = nullptr;  // [0] error bits, [1] general vote chunk counter, [2..31] column-walk counters
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
     DevBuf slide_tab;             // fixed-point tables of the incremental window kernel
     bool slide_tab_ready = false;
@@ -491,14 +493,15 @@ int canonical_d1(int dx, int dy, bool& transposed)
     return dx == 1 ? 1 : (dx == 0 ? 2 : 3);
 }
 
-FastClass& fast_class(VotePlan& plan, int bpp, int log2n)
+FastClass& fast_class(VotePlan& plan, int bpp, int log2n, bool aligned)
 {
     for (FastClass& c : plan.fast)
-        if (c.bpp == bpp && c.log2n == log2n)
+        if (c.bpp == bpp && c.log2n == log2n && c.aligned == aligned)
             return c;
     plan.fast.emplace_back();
     plan.fast.back().bpp = bpp;
     plan.fast.back().log2n = log2n;
+    plan.fast.back().aligned = aligned;
     return plan.fast.back();
 }
 
@@ -519,7 +522,8 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
             band_override = std::min(it->second.band_rows, 1024);
     }
     const int log2n = ilog2_exact(s.levels);
-    FastClass& fc = fast_class(plan, s.bpp, log2n);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0;
+    FastClass& fc = fast_class(plan, s.bpp, log2n, aligned);
     const int PX = 16 / s.bpp;
     const int n_strips = (s.W + 32 * PX - 1) / (32 * PX);
     if (s.y_end <= s.y_begin || n_strips <= 0)
@@ -569,7 +573,7 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
         j.half_hi = g.half_hi;
         j.row_half = g.row_half;
         j.transposed = g.transposed;
-        j.aligned = ((reinterpret_cast<uintptr_t>(s.img) | (uintptr_t)s.pitch) & 15) == 0 ? 1 : 0;
+        j.aligned = aligned ? 1 : 0;
         for (int k = 0; k < 4; ++k) {
             const bool in = (g.present >> k) & 1;
             j.slot[k] = in ? (g.mode == kFastWide ? g.slot : slot[k]) : -1;
@@ -829,7 +833,7 @@ int zero_words(glcm_ctx* ctx, uint32_t* p, long long n, cudaStream_t st)
 
 // Chunk counters in the context's device words: [1] the general vote kernel,
 // [2 + c] column-walk class c.
-constexpr int kCounterWords = 16;
+constexpr int kCounterWords = 32;  // the context's 128 bytes of device words
 constexpr int kMaxFastClasses = kCounterWords - 2;
 
 // Blocks [0, n_gen) zero general job b's outputs, blocks [n_gen, n_gen +
@@ -968,7 +972,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve);
         if (plan.max_ctas > 0)
             ctas = std::min(ctas, plan.max_ctas);
-        CK(launch_vote_fast(fp, c.bpp, c.log2n, std::max(1, std::min(fp.n_chunks, ctas)), fsmem, st));
+        CK(launch_vote_fast(fp, c.bpp, c.log2n, c.aligned, std::max(1, std::min(fp.n_chunks, ctas)), fsmem, st));
         ++n_launch;
     }
     if (!plan.jobs.empty()) {

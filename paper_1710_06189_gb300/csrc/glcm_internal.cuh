@@ -230,10 +230,12 @@ cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, siz
                         cudaStream_t s, bool packed = false);
 // Column-walk votes: one launch per pixel type and N (every job of the launch
 // has them).
-cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, int grid, size_t smem, cudaStream_t s);
+cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, bool aligned, int grid, size_t smem,
+                             cudaStream_t s);
 size_t vote_fast_smem_bytes(int max_hist_words);
 int vote_fast_hist_words(int log2n, int mode);
-int vote_fast_blocks_per_sm(int bpp, int log2n, size_t smem);
+// The column-walk kernel for rows at any byte address (vote_fast_unaligned.cu).
+const void* vote_fast_kernel_unaligned(int bpp, int log2n);
 cudaError_t launch_seams(const SeamJob* jobs, int n_jobs, int blocks_per_job, unsigned* err, cudaStream_t s);
 // N > 256: every in-rectangle pair of each job (one offset of one image, its
 // rows [y_begin, y_end)) voted into global counts (vote_global.cu).
