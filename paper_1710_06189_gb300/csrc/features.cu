@@ -33,12 +33,14 @@
 //    levels instead square G = A'^T A' (or A' A'^T) repeatedly with the
 //    whole block and take a Rayleigh quotient: a few dozen barrier-separated
 //    steps instead of a serial chain of Lanczos steps in one warp.
-//  * Symmetric GLCMs with N > 128 (A' symmetric, too large for shared
-//    memory as a full matrix) keep A' as its upper 32 x 32 blocks in shared
-//    memory and find max |eigenvalue| of A' -- its largest singular value --
-//    by symmetric Lanczos without reorthogonalization: in finite precision
-//    the extreme Ritz values still converge (lost orthogonality only adds
-//    copies of converged values), so no basis has to be stored.
+//  * Symmetric GLCMs with 128 < N <= 256 (A' symmetric, too large for one
+//    CTA's shared memory as a full matrix) are spread over a cluster of
+//    eight CTAs (k_haralick_cluster, below): each keeps 32 rows of A' in
+//    shared memory, and max |eigenvalue| of A' -- its largest singular
+//    value -- comes from symmetric Lanczos without reorthogonalization: in
+//    finite precision the extreme Ritz values still converge (lost
+//    orthogonality only adds copies of converged values), so no basis has
+//    to be stored.
 #include <cmath>
 
 #include "glcm_internal.cuh"
@@ -54,11 +56,6 @@ constexpr int kMaxLanczos = 96;
 constexpr int kSmemAFloats = 128 * 128;
 constexpr int kSmemUVFloats = (2 * kMaxLanczos + 1) * 128;
 constexpr int kColGroups = 4;
-// Blocked symmetric path: N <= kBigN, 32 x 32 blocks padded to 33 columns.
-constexpr int kBigN = 256;
-constexpr int kBigNB = kBigN / 32;
-constexpr int kBigTiles = kBigNB * (kBigNB + 1) / 2;
-constexpr int kTileFloats = 32 * 33;
 constexpr int kMaxSymSteps = 384;
 constexpr int kMaxLevelsPerLane = 256 / 32;  // N <= 256
 // Repeated squaring for supports of at most 32 levels: row stride (16-byte
@@ -173,6 +170,15 @@ __device__ __forceinline__ unsigned long long cell(const uint32_t* C, int N, int
     if (sym)
         s += __ldg(C + j * N + i);
     return s;
+}
+
+// m / T for exact integer sums: the integer quotient plus the remainder's
+// fraction, so an integral mean comes out exact however large T is (a float
+// quotient of the two rounded integers can miss it by an ulp).
+__device__ __forceinline__ float ratio_u64(unsigned long long m, unsigned long long T)
+{
+    const unsigned long long q = m / T;
+    return __fadd_rn((float)q, __fdiv_rn((float)(m - q * T), (float)T));
 }
 
 __device__ __forceinline__ float neg_plogp(float p)
@@ -636,160 +642,6 @@ __device__ float lanczos_sigma_max(const float* A, int m, int n, const LanczosWo
     return gk_sigma_max_block(w.ab, steps, w.msk);
 }
 
-// ---- Blocked symmetric path (symmetric GLCMs with 128 < N <= 256) ----------
-//
-// A' is kept as its upper 32 x 32 blocks (I <= J), each padded to 33 columns
-// so that a lane can walk either a row or a column of a block without bank
-// conflicts.  Levels outside the support give zero rows and columns of A',
-// which only add zero eigenvalues.
-
-// (I, J) of upper block t in row-major order of the upper triangle.
-__device__ __forceinline__ void tile_of(int t, int nb, int& I, int& J)
-{
-    I = 0;
-    while (t >= nb - I) {
-        t -= nb - I;
-        ++I;
-    }
-    J = I + t;
-}
-
-__device__ __forceinline__ int tile_index(int I, int J, int nb)
-{
-    return I * nb - I * (I - 1) / 2 + (J - I);
-}
-
-// Cell pass of a symmetric GLCM: S = P + P^T staged block by block (both
-// global reads coalesced), the cell sums (an off-diagonal block stands for
-// itself and its mirror image, whose terms are equal, so they count twice),
-// the normalized output, and A' written over each staged block.
-// Requires T < 2^32 so that every S entry fits 32 bits.
-__device__ void sym_cell_pass(const FeatJob& J, int N, unsigned long long T, const unsigned long long* rs,
-                              const unsigned long long* cs, float* blk, Kahan& k_asm, Kahan& k_ent, Kahan& k_mi,
-                              unsigned long long& cij)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int nb = (N + 31) >> 5;
-    const int ntiles = nb * (nb + 1) / 2;
-    const uint32_t* C = J.counts;
-    const float Tf = (float)T;
-    for (int t = warp; t < ntiles; t += nw) {
-        int I, Jb;
-        tile_of(t, nb, I, Jb);
-        uint32_t* Bu = reinterpret_cast<uint32_t*>(blk + (size_t)t * kTileFloats);
-        float* Bf = blk + (size_t)t * kTileFloats;
-        const int jc = Jb * 32 + lane;
-        const int ic = I * 32 + lane;
-        // Block (I, Jb) of P first (all 32 rows), then block (Jb, I) added
-        // transposed; 16 loads in flight per batch.
-        for (int r0 = 0; r0 < 32; r0 += 16) {
-            uint32_t va[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                const int i = I * 32 + r0 + u;
-                va[u] = (i < N && jc < N) ? __ldg(C + (size_t)i * N + jc) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                Bu[(r0 + u) * 33 + lane] = va[u];
-        }
-        __syncwarp();
-        for (int r0 = 0; r0 < 32; r0 += 16) {
-            uint32_t vb[16];
-#pragma unroll
-            for (int u = 0; u < 16; ++u) {
-                // Row Jb*32 + r of P, column I*32 + lane: P(j, i) for S(i, j).
-                const int iT = Jb * 32 + r0 + u;
-                vb[u] = (iT < N && ic < N) ? __ldg(C + (size_t)iT * N + ic) : 0u;
-            }
-#pragma unroll
-            for (int u = 0; u < 16; ++u)
-                Bu[lane * 33 + r0 + u] += vb[u];
-        }
-        __syncwarp();
-        const bool twice = I != Jb;
-        for (int r = 0; r < 32; ++r) {
-            const int i = I * 32 + r;
-            float a = 0.f;
-            if (i < N && jc < N) {
-                const unsigned long long sv = Bu[r * 33 + lane];
-                const float pv = __fdiv_rn((float)sv, Tf);
-                if (J.normalized) {
-                    J.normalized[(size_t)i * N + jc] = pv;
-                    if (twice)
-                        J.normalized[(size_t)jc * N + i] = pv;
-                }
-                if (sv) {
-                    const float t1 = __fmul_rn(pv, pv), t2 = neg_plogp(pv);
-                    k_asm.add(twice ? 2.f * t1 : t1);
-                    k_ent.add(twice ? 2.f * t2 : t2);
-                    cij += (twice ? 2ull : 1ull) * (unsigned long long)(i * jc) * sv;
-                }
-                const unsigned long long ri = rs[i], cj = cs[jc];
-                if (ri && cj) {
-                    const float rc = __fmul_rn((float)ri, (float)cj);
-                    float numf;
-                    if (T < (1ull << 31))
-                        numf = (float)((long long)(sv * T) - (long long)(ri * cj));
-                    else
-                        numf = __fsub_rn(__fmul_rn((float)sv, Tf), rc);
-                    const float x = __fdiv_rn(numf, rc);
-                    const float q = __fmul_rn(__fdiv_rn((float)ri, Tf), __fdiv_rn((float)cj, Tf));
-                    const float tm = __fmul_rn(q, phi(x));
-                    k_mi.add(twice ? 2.f * tm : tm);
-                    a = __fdiv_rn(numf, __fmul_rn(Tf, sqrtf(rc)));
-                }
-            }
-            Bf[r * 33 + lane] = a;
-        }
-    }
-    __syncthreads();
-}
-
-// y = A' x over the blocked upper triangle (x, y: nb * 32 floats).  Block
-// (I, J) gives B x_J to y_I and, off the diagonal, B^T x_I to y_J; the
-// pieces are summed per element in a fixed order (deterministic).
-__device__ void sym_block_matvec(const float* blk, int nb, const float* x, float* y, float* bpart)
-{
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    const int ntiles = nb * (nb + 1) / 2;
-    for (int t = warp; t < ntiles; t += nw) {
-        int I, Jb;
-        tile_of(t, nb, I, Jb);
-        const float* B = blk + (size_t)t * kTileFloats;
-        const float* xJ = x + Jb * 32;
-        const float* xI = x + I * 32;
-        float r0 = 0.f, r1 = 0.f, c0 = 0.f, c1 = 0.f;
-#pragma unroll
-        for (int k = 0; k < 32; k += 4) {
-            // Vector entries as broadcast float4 loads; block rows and
-            // columns as conflict-free scalar loads.
-            const float4 vj = *reinterpret_cast<const float4*>(xJ + k);
-            const float4 vi = *reinterpret_cast<const float4*>(xI + k);
-            r0 = fmaf(B[lane * 33 + k], vj.x, r0);
-            r1 = fmaf(B[lane * 33 + k + 1], vj.y, r1);
-            r0 = fmaf(B[lane * 33 + k + 2], vj.z, r0);
-            r1 = fmaf(B[lane * 33 + k + 3], vj.w, r1);
-            c0 = fmaf(B[k * 33 + lane], vi.x, c0);
-            c1 = fmaf(B[(k + 1) * 33 + lane], vi.y, c1);
-            c0 = fmaf(B[(k + 2) * 33 + lane], vi.z, c0);
-            c1 = fmaf(B[(k + 3) * 33 + lane], vi.w, c1);
-        }
-        bpart[t * 32 + lane] = r0 + r1;
-        bpart[(kBigTiles + t) * 32 + lane] = c0 + c1;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nb * 32; e += blockDim.x) {
-        const int I = e >> 5, l = e & 31;
-        float acc = 0.f;
-        for (int Jb = 0; Jb < nb; ++Jb)
-            acc += Jb >= I ? bpart[tile_index(I, Jb, nb) * 32 + l]
-                           : bpart[(kBigTiles + tile_index(Jb, I, nb)) * 32 + l];
-        y[e] = acc;
-    }
-    __syncthreads();
-}
-
 // Eigenvalues below x of the L x L symmetric tridiagonal matrix with
 // diagonal al[] and off-diagonal be[] (Sturm sequence).
 __device__ __forceinline__ int tri_count_below(const float* al, const float* be, int L, float x)
@@ -840,91 +692,46 @@ __device__ void tri_absmax_block(const float* al, const float* be, int L, float*
     __syncthreads();
 }
 
-// Largest |eigenvalue| of the blocked symmetric A' (N levels) by Lanczos
-// without reorthogonalization; stops once the estimate moved by less than
-// 4e-7 of itself over 8 steps (after at least 16) or after kMaxSymSteps.
-__device__ float sym_lanczos_absmax(const float* blk, int N, float* qv, float* tri, float* bpart, float* s_red,
-                                    float* s_sig, int* s_stop, unsigned (*s_msk)[32])
+// The 14 features from the exact totals and moments (m: sum i r_i,
+// sum j c_j, sum k^2 d_k, sum k s_k, sum k d_k, sum i^2 r_i, sum j^2 c_j),
+// the exact sum of i j S(i, j) and the ten compensated sums v (ASM, entropy,
+// mutual information, IDM, sum variance, sum entropy, difference variance,
+// difference entropy, HX, HY).  One thread.
+__device__ void write_features(float* feat, unsigned long long T, const unsigned long long* m,
+                               unsigned long long cij, const DF (&v)[10], float f6, float mcc)
 {
-    const int nb = (N + 31) >> 5, n = nb * 32;
-    float* q = qv;
-    float* qp = qv + kBigN;
-    float* y = qv + 2 * kBigN;
-    float* al = tri;
-    float* be = tri + kMaxSymSteps;
-    float* ends = tri + 2 * kMaxSymSteps;  // 3 floats
-    for (int c = threadIdx.x; c < n; c += blockDim.x) {
-        // Fixed zero-mean pseudo-random start (multiplicative hash of c): a
-        // near-constant start would be almost orthogonal to the top
-        // eigenvectors of a deflated A' and could stall on a lower one.
-        const unsigned h = (unsigned)c * 2654435761u + 12345u;
-        q[c] = c < N ? (float)h * 2.3283064e-10f - 0.5f : 0.f;
-        qp[c] = 0.f;
-    }
-    if (threadIdx.x == 0) {
-        *s_sig = -1.f;
-        *s_stop = 0;
-    }
-    float ss = 0.f;
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        ss = fmaf(q[c], q[c], ss);
-    const float inv = rsqrtf(block_sum(ss, s_red));
-    for (int c = threadIdx.x; c < n; c += blockDim.x)
-        q[c] *= inv;
-    __syncthreads();
-    float beta = 0.f;
-    int L = 0;
-    for (int k = 0; k < kMaxSymSteps; ++k) {
-        sym_block_matvec(blk, nb, q, y, bpart);
-        float d = 0.f;
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            const float w = fmaf(-beta, qp[c], y[c]);
-            y[c] = w;
-            d = fmaf(w, q[c], d);
-        }
-        const float alpha = block_sum(d, s_red);
-        float s2 = 0.f;
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            const float w = fmaf(-alpha, q[c], y[c]);
-            y[c] = w;
-            s2 = fmaf(w, w, s2);
-        }
-        const float bn = sqrtf(block_sum(s2, s_red));
-        if (threadIdx.x == 0) {
-            al[k] = alpha;
-            be[k] = bn;
-        }
-        L = k + 1;
-        if (!(bn > 1e-30f))
-            break;  // invariant subspace: the tridiagonal matrix is exact
-        const float ib = 1.f / bn;
-        for (int c = threadIdx.x; c < n; c += blockDim.x) {
-            qp[c] = q[c];
-            q[c] = y[c] * ib;
-        }
-        beta = bn;
-        __syncthreads();
-        if ((L & 7) == 0 && L >= 16) {
-            tri_absmax_block(al, be, L, ends, ends + 2, s_msk);
-            if (threadIdx.x == 0) {
-                *s_stop = fabsf(ends[2] - *s_sig) <= 4e-7f * ends[2] ? 1 : 0;
-                *s_sig = ends[2];
-            }
-            __syncthreads();
-            if (*s_stop)
-                break;
-        }
-    }
-    __syncthreads();
-    tri_absmax_block(al, be, L, ends, ends + 2, s_msk);
-    return ends[2];
+    const float Tf = (float)T;
+    // f3 and f4 from exact integer moments: T^2 var_x = T sum i^2 r_i -
+    // (sum i r_i)^2, T^2 cov = T sum i j S(i, j) - (sum i r_i)(sum j c_j).
+    const __int128 Ti = (__int128)T;
+    const __int128 vxn = Ti * (__int128)m[5] - (__int128)m[0] * (__int128)m[0];
+    const __int128 vyn = Ti * (__int128)m[6] - (__int128)m[1] * (__int128)m[1];
+    const __int128 cvn = Ti * (__int128)cij - (__int128)m[0] * (__int128)m[1];
+    const double Td = (double)T;
+    const double varx = i128_to_double(vxn) / (Td * Td);
+    const double vxy = i128_to_double(vxn) * i128_to_double(vyn);
+    const float mi = fmaxf(0.f, v[2].hi + v[2].lo);
+    const float hx = v[8].hi + v[8].lo, hy = v[9].hi + v[9].lo;
+    const float hmax = fmaxf(hx, hy);
+    feat[0] = v[0].hi + v[0].lo;
+    feat[1] = (float)m[2] / Tf;
+    feat[2] = vxy > 0.0 ? (float)(i128_to_double(cvn) / sqrt(vxy)) : 1.f;
+    feat[3] = (float)varx;
+    feat[4] = v[3].hi + v[3].lo;
+    feat[5] = f6;
+    feat[6] = v[4].hi + v[4].lo;
+    feat[7] = v[5].hi + v[5].lo;
+    feat[8] = v[1].hi + v[1].lo;
+    feat[9] = v[6].hi + v[6].lo;
+    feat[10] = v[7].hi + v[7].lo;
+    feat[11] = hmax > 0.f ? -mi / hmax : 0.f;
+    feat[12] = sqrtf(fmaxf(0.f, -expm1f(-2.f * mi)));
+    feat[13] = mcc;
 }
 
 // Dynamic shared memory layout for a launch whose largest N is `N`.
 struct FeatLayout {
     size_t marg, maps, dscr, xs, ys, part, a, uv, total;
-    // Blocked symmetric path (N > 128), overlapping a and uv.
-    size_t blk, bpart, qv, tri;
 };
 
 __host__ __device__ inline FeatLayout feat_layout(int N)
@@ -945,22 +752,10 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     L.xs = take((size_t)N * 4);
     L.ys = take((size_t)N * 4);
     L.part = take((size_t)kColGroups * 256 * 4);
-    const size_t u0 = o;
     L.a = take((size_t)(nn < kSmemAFloats ? nn : kSmemAFloats) * 4);
     // At least kSqFloats: the squaring path for supports <= 32.
     const long long uvf = uv < kSmemUVFloats ? uv : kSmemUVFloats;
     L.uv = take((size_t)(uvf > kSqFloats ? uvf : kSqFloats) * 4);
-    const size_t u1 = o;
-    L.blk = L.bpart = L.qv = L.tri = 0;
-    if (N > 128) {
-        o = u0;
-        const int nb = (N + 31) / 32;
-        L.blk = take((size_t)nb * (nb + 1) / 2 * kTileFloats * 4);
-        L.bpart = take((size_t)2 * kBigTiles * 32 * 4);
-        L.qv = take((size_t)3 * kBigN * 4);
-        L.tri = take((size_t)(2 * kMaxSymSteps + 4) * 4);
-        o = o > u1 ? o : u1;
-    }
     L.total = o;
     return L;
 }
@@ -1107,9 +902,6 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
     }
     const int nr = s_nr, nc = s_nc;
     const int K = min(kMaxLanczos, min(nr, nc));
-    // Symmetric GLCMs too large for a full A' in shared memory take the
-    // blocked path (every S entry < 2^32 when T < 2^32).
-    const bool big_sym = sym && N > 128 && N <= kBigN && maxN > 128 && T < (1ull << 32);
     // A' and the Lanczos vectors: shared memory when they fit, else scratch.
     float* gwork = p.work ? p.work + (long long)blockIdx.x * p.work_stride : nullptr;
     const bool a_smem = (long long)nr * nc <= kSmemAFloats && (long long)nr * nc <= (long long)maxN * maxN;
@@ -1119,15 +911,12 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
     float* A = a_smem ? reinterpret_cast<float*>(smem_raw + Lo.a) : gwork;
     float* UV = uv_smem ? reinterpret_cast<float*>(smem_raw + Lo.uv)
                         : (gwork ? gwork + (long long)maxN * maxN : nullptr);
-    const bool have_work = big_sym || (A != nullptr && UV != nullptr);
-    float* blk = reinterpret_cast<float*>(smem_raw + Lo.blk);
+    const bool have_work = A != nullptr && UV != nullptr;
 
     // Cell pass: normalized output, f1, f9, MI terms, covariance, A'.
     Kahan k_asm, k_ent, k_mi;
     unsigned long long cij = 0;  // sum of i j S(i, j), exact
-    if (big_sym)
-        sym_cell_pass(J, N, T, rs, cs, blk, k_asm, k_ent, k_mi, cij);
-    for (int t = threadIdx.x; !big_sym && t < NN; t += blockDim.x) {
+    for (int t = threadIdx.x; t < NN; t += blockDim.x) {
         const int i = t / N, j = t - (t / N) * N;
         const unsigned long long s = cell(C, N, i, j, sym);
         const float pv = __fdiv_rn((float)s, Tf);
@@ -1159,8 +948,8 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
 
     // Marginal passes (length N or 2N-1).
     Kahan k_idm, k_svar, k_sent, k_dvar, k_dent, k_hx, k_hy;
-    const float f6 = __fdiv_rn((float)s_m[3], Tf);
-    const float mean_d = __fdiv_rn((float)s_m[4], Tf);
+    const float f6 = ratio_u64(s_m[3], T);
+    const float mean_d = ratio_u64(s_m[4], T);
     for (int k = threadIdx.x; k < 2 * N - 1; k += blockDim.x) {
         const float ps = __fdiv_rn((float)ss[k], Tf);
         const float dk = __fsub_rn((float)k, f6);
@@ -1185,11 +974,7 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
     block_reduce_df<10>(v, dscr);
 
     float mcc = 0.f;
-    if (big_sym && nr >= 2) {
-        mcc = sym_lanczos_absmax(blk, N, reinterpret_cast<float*>(smem_raw + Lo.qv),
-                                 reinterpret_cast<float*>(smem_raw + Lo.tri),
-                                 reinterpret_cast<float*>(smem_raw + Lo.bpart), s_red, &s_sig, &s_stop, s_msk);
-    } else if (nr >= 2 && nr <= 32 && nc <= 32 && a_smem) {
+    if (nr >= 2 && nr <= 32 && nc <= 32 && a_smem) {
         // Small supports: repeated squaring by the whole block.
         mcc = sigma_max_squaring(A, nr, nc, reinterpret_cast<float*>(smem_raw + Lo.uv), &s_sig);
     } else if (nr >= 2 && have_work) {
@@ -1210,36 +995,447 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
     if (!have_work && nr >= 2 && threadIdx.x == 0)
         atomicOr(p.err, kErrInternal);
 
-    if (threadIdx.x == 0) {
-        // f3 and f4 from exact integer moments: T^2 var_x = T sum i^2 r_i -
-        // (sum i r_i)^2, T^2 cov = T sum i j S(i, j) - (sum i r_i)(sum j c_j).
-        const __int128 Ti = (__int128)T;
-        const __int128 vxn = Ti * (__int128)s_m[5] - (__int128)s_m[0] * (__int128)s_m[0];
-        const __int128 vyn = Ti * (__int128)s_m[6] - (__int128)s_m[1] * (__int128)s_m[1];
-        const __int128 cvn = Ti * (__int128)s_cij - (__int128)s_m[0] * (__int128)s_m[1];
-        const double Td = (double)T;
-        const double varx = i128_to_double(vxn) / (Td * Td);
-        const double vxy = i128_to_double(vxn) * i128_to_double(vyn);
-        const float mi = fmaxf(0.f, v[2].hi + v[2].lo);
-        const float hx = v[8].hi + v[8].lo, hy = v[9].hi + v[9].lo;
-        const float hmax = fmaxf(hx, hy);
-        feat[0] = v[0].hi + v[0].lo;
-        feat[1] = (float)s_m[2] / Tf;
-        feat[2] = vxy > 0.0 ? (float)(i128_to_double(cvn) / sqrt(vxy)) : 1.f;
-        feat[3] = (float)varx;
-        feat[4] = v[3].hi + v[3].lo;
-        feat[5] = f6;
-        feat[6] = v[4].hi + v[4].lo;
-        feat[7] = v[5].hi + v[5].lo;
-        feat[8] = v[1].hi + v[1].lo;
-        feat[9] = v[6].hi + v[6].lo;
-        feat[10] = v[7].hi + v[7].lo;
-        feat[11] = hmax > 0.f ? -mi / hmax : 0.f;
-        feat[12] = sqrtf(fmaxf(0.f, -expm1f(-2.f * mi)));
-        feat[13] = mcc;
-    }
+    if (threadIdx.x == 0)
+        write_features(feat, T, s_m, s_cij, v, f6, mcc);
 }
 
+
+// ---- Symmetric GLCMs with 128 < N <= 256: one cluster of CTAs per GLCM -----
+//
+// S = P + P^T, padded to order 256 with zero rows and columns, is split by
+// rows over the kClu CTAs of a thread-block cluster: CTA r owns rows
+// [32 r, 32 r + 32).  It stages those rows of P and the same columns of P
+// (rows of P^T) in shared memory and forms exact integer partial sums of P's
+// marginals from them -- one index per thread, no atomics -- then reads the
+// other CTAs' partial sums from their shared memory (distributed shared
+// memory).  Every CTA thus holds the full marginals and the same totals, so
+// every branch below goes the same way in all of them and they all pass the
+// same cluster barriers.  Each CTA does the cell pass of its rows (normalized
+// output, f1, f9, the mutual-information terms, sum i j S) and keeps its rows
+// of A' in shared memory.  f14 is max |eigenvalue| of A' by symmetric Lanczos
+// without reorthogonalization: each step multiplies the CTA's rows of A' by
+// the current vector, and two cluster barriers exchange the step's two dot
+// products and the next vector's pieces, written by plain stores into every
+// CTA's shared memory.  Sums across CTAs are taken in rank order, and CTA 0
+// writes the features, so a GLCM's features do not depend on its batch.
+
+constexpr int kClu = 8;                  // CTAs per GLCM
+constexpr int kCR = 32;                  // rows of S per CTA
+constexpr int kCN = kClu * kCR;          // padded order of S
+constexpr int kCluThreads = 512;
+constexpr int kCluWarps = kCluThreads / 32;
+// Partial sums of P over a CTA's rows: column sums, i + j sums, |i - j|
+// sums, then the row sums of its own rows.
+constexpr int kPartCS = 0, kPartSS = kCN, kPartDS = 3 * kCN, kPartRS = 4 * kCN;
+constexpr int kPartWords = 4 * kCN + kCR;
+
+struct CluSmem {
+    uint32_t pb[kCR * kCN];               // P rows of this CTA; then A' rows (float)
+    uint32_t pt[kCN * (kCR + 1)];         // pt[j * 33 + c] = P(j, 32 r + c)
+    unsigned long long part[kPartWords];  // read by every CTA of the cluster
+    unsigned long long rs[kCN];           // row sums of S (= column sums)
+    unsigned long long ss[2 * kCN];       // i + j sums of S
+    unsigned long long ds[kCN];           // |i - j| sums of S
+    unsigned long long mom[7], T, cij, fin_cij[kClu];
+    float q[kCN], w[kCN];                 // Lanczos vector; the next one's pieces (written by all CTAs)
+    float qp[kCR], y[kCR];
+    float sa[kClu], sb[kClu];             // each CTA's part of the step's two dot products
+    float al[kMaxSymSteps], be[kMaxSymSteps], ends[4];
+    DF fin[kClu][10];                     // CTA 0: each CTA's compensated sums
+    DF dscr[10 * 32];
+    float red[32];
+    unsigned msk[2][32];
+    int nr, stop;
+    float sig;
+};
+
+__device__ __forceinline__ uint32_t clu_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t clu_id()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Address in CTA `rank`'s shared memory of the variable at p in this CTA's.
+__device__ __forceinline__ uint32_t clu_addr(const void* p, uint32_t rank)
+{
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(p);
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void clu_st(uint32_t a, float v)
+{
+    asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void clu_st64(uint32_t a, unsigned long long v)
+{
+    asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long clu_ld64(uint32_t a)
+{
+    unsigned long long v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(a) : "memory");
+    return v;
+}
+
+// Every thread of every CTA of the cluster; stores before it (local or into
+// other CTAs) are visible to all of them after it.
+__device__ __forceinline__ void clu_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long s)
+{
+    for (int o = 16; o > 0; o >>= 1)
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+    return s;
+}
+
+// max |eigenvalue| of A' (rows of this CTA in A, row stride kCN) by symmetric
+// Lanczos without reorthogonalization from a fixed zero-mean pseudo-random
+// start: w = A' q - beta q_prev, alpha = w . q, w -= alpha q, beta = |w|,
+// q = w / beta; every 8 steps (after 16) the tridiagonal matrix's extreme
+// eigenvalues are bracketed, and the iteration stops once max |eigenvalue|
+// moved by less than 4e-7 of itself.  Every CTA holds the whole vector q
+// and the whole tridiagonal matrix and takes the same decisions.
+__device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = (int)r * kCR;
+    for (int c = tid; c < kCN; c += kCluThreads) {
+        // A near-constant start would be almost orthogonal to the top
+        // eigenvectors of a deflated A' and could stall on a lower one.
+        const unsigned h = (unsigned)c * 2654435761u + 12345u;
+        sm.q[c] = c < N ? (float)h * 2.3283064e-10f - 0.5f : 0.f;
+    }
+    if (tid < kCR)
+        sm.qp[tid] = 0.f;
+    if (tid == 0) {
+        sm.sig = -1.f;
+        sm.stop = 0;
+    }
+    __syncthreads();
+    float ss = 0.f;
+    for (int c = tid; c < kCN; c += kCluThreads)
+        ss = fmaf(sm.q[c], sm.q[c], ss);
+    const float inv = rsqrtf(block_sum(ss, sm.red));
+    for (int c = tid; c < kCN; c += kCluThreads)
+        sm.q[c] *= inv;
+    __syncthreads();
+    // Warp 0, lane l: row i0 + l.  Where this CTA's pieces go in every CTA.
+    const uint32_t to_sa = clu_addr(&sm.sa[r], (uint32_t)lane & (kClu - 1));
+    const uint32_t to_sb = clu_addr(&sm.sb[r], (uint32_t)lane & (kClu - 1));
+    float beta = 0.f;
+    int L = 0;
+    for (int k = 0; k < kMaxSymSteps; ++k) {
+        for (int rr = warp; rr < kCR; rr += kCluWarps) {
+            float acc = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCN / 32; ++u)
+                acc = fmaf(A[rr * kCN + lane + 32 * u], sm.q[lane + 32 * u], acc);
+            acc = warp_sum(acc);
+            if (lane == 0)
+                sm.y[rr] = acc;
+        }
+        __syncthreads();
+        float wv = 0.f;
+        if (warp == 0) {
+            wv = fmaf(-beta, sm.qp[lane], sm.y[lane]);
+            const float d = warp_sum(wv * sm.q[i0 + lane]);
+            if (lane < kClu)
+                clu_st(to_sa, d);
+        }
+        clu_sync();
+        float alpha = 0.f;
+        for (int c = 0; c < kClu; ++c)
+            alpha += sm.sa[c];
+        if (warp == 0) {
+            wv = fmaf(-alpha, sm.q[i0 + lane], wv);
+            const float s2 = warp_sum(wv * wv);
+            for (int c = 0; c < kClu; ++c)
+                clu_st(clu_addr(&sm.w[i0 + lane], (uint32_t)c), wv);
+            if (lane < kClu)
+                clu_st(to_sb, s2);
+        }
+        if (tid == 0)
+            sm.al[k] = alpha;
+        clu_sync();
+        float s2t = 0.f;
+        for (int c = 0; c < kClu; ++c)
+            s2t += sm.sb[c];
+        const float bn = sqrtf(s2t);
+        if (tid == 0)
+            sm.be[k] = bn;
+        L = k + 1;
+        if (!(bn > 1e-30f))
+            break;  // invariant subspace: the tridiagonal matrix is exact
+        const float ib = 1.f / bn;
+        for (int c = tid; c < kCN; c += kCluThreads) {
+            if ((c >> 5) == (int)r)
+                sm.qp[c & 31] = sm.q[c];
+            sm.q[c] = sm.w[c] * ib;
+        }
+        beta = bn;
+        __syncthreads();
+        if ((L & 7) == 0 && L >= 16) {
+            tri_absmax_block(sm.al, sm.be, L, sm.ends, sm.ends + 2, sm.msk);
+            if (tid == 0) {
+                sm.stop = fabsf(sm.ends[2] - sm.sig) <= 4e-7f * sm.ends[2] ? 1 : 0;
+                sm.sig = sm.ends[2];
+            }
+            __syncthreads();
+            if (sm.stop)
+                break;
+        }
+    }
+    __syncthreads();
+    tri_absmax_block(sm.al, sm.be, L, sm.ends, sm.ends + 2, sm.msk);
+    return sm.ends[2];
+}
+
+__global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads, 1)
+    k_haralick_cluster(FeatParams p)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    CluSmem& sm = *reinterpret_cast<CluSmem*>(smem_raw);
+    const uint32_t r = clu_rank();
+    const FeatJob J = p.jobs[clu_id()];
+    const int N = J.levels;
+    const uint32_t* P = J.counts;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = (int)r * kCR;
+
+    // Stage P's rows [i0, i0 + 32) and columns [i0, i0 + 32), zero outside N.
+    {
+        uint32_t v[kCR * kCN / kCluThreads];
+#pragma unroll
+        for (int u = 0; u < kCR * kCN / kCluThreads; ++u) {
+            const int e = tid + u * kCluThreads, i = i0 + (e >> 8), j = e & 255;
+            v[u] = (i < N && j < N) ? __ldg(P + i * N + j) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kCR * kCN / kCluThreads; ++u)
+            sm.pb[tid + u * kCluThreads] = v[u];
+#pragma unroll
+        for (int u = 0; u < kCR * kCN / kCluThreads; ++u) {
+            const int e = tid + u * kCluThreads, j = e >> 5, i = i0 + (e & 31);
+            v[u] = (i < N && j < N) ? __ldg(P + j * N + i) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kCR * kCN / kCluThreads; ++u) {
+            const int e = tid + u * kCluThreads;
+            sm.pt[(e >> 5) * (kCR + 1) + (e & 31)] = v[u];
+        }
+    }
+    if (tid == 0)
+        sm.cij = 0ull;
+    __syncthreads();
+    // Partial marginals of P over this CTA's rows (level i = i0 + rr): row
+    // sums by warps; column, i + j and |i - j| sums one index per thread
+    // (consecutive indices read consecutive words: no bank conflict).
+    for (int rr = warp; rr < kCR; rr += kCluWarps) {
+        unsigned long long s = 0;
+#pragma unroll
+        for (int u = 0; u < kCN / 32; ++u)
+            s += sm.pb[rr * kCN + lane + 32 * u];
+        s = warp_sum_u64(s);
+        if (lane == 0)
+            sm.part[kPartRS + rr] = s;
+    }
+    if (tid < kCN) {
+        const int x = tid;
+        unsigned long long cs = 0, ds = 0;
+        for (int rr = 0; rr < kCR; ++rr) {
+            const int i = i0 + rr;
+            cs += sm.pb[rr * kCN + x];
+            if (i + x < kCN)
+                ds += sm.pb[rr * kCN + i + x];
+            if (x > 0 && i - x >= 0)
+                ds += sm.pb[rr * kCN + i - x];
+        }
+        sm.part[kPartCS + x] = cs;
+        sm.part[kPartDS + x] = ds;
+    }
+    for (int x = tid; x < 2 * kCN; x += kCluThreads) {
+        unsigned long long s = 0;
+        for (int rr = 0; rr < kCR; ++rr) {
+            const int j = x - (i0 + rr);
+            if (j >= 0 && j < kCN)
+                s += sm.pb[rr * kCN + j];
+        }
+        sm.part[kPartSS + x] = s;
+    }
+    clu_sync();
+    // Marginals of S = P + P^T from every CTA's partial sums: row (= column)
+    // sums are P's row plus column sums, the i + j and |i - j| sums twice P's.
+    for (int x = tid; x < 4 * kCN; x += kCluThreads) {
+        unsigned long long s = 0;
+        for (int c = 0; c < kClu; ++c)
+            s += clu_ld64(clu_addr(&sm.part[x], (uint32_t)c));
+        if (x < kPartSS) {
+            s += clu_ld64(clu_addr(&sm.part[kPartRS + (x & (kCR - 1))], (uint32_t)(x / kCR)));
+            sm.rs[x] = s;
+        } else if (x < kPartDS) {
+            sm.ss[x - kPartSS] = 2ull * s;
+        } else {
+            sm.ds[x - kPartDS] = 2ull * s;
+        }
+    }
+    clu_sync();  // no CTA reads another's partial sums after this
+    // Totals and exact moments (warp 0 of every CTA, the same values).
+    if (warp == 0) {
+        unsigned long long T = 0, m_i = 0, c2 = 0, m_s = 0, m_d = 0, q_i = 0;
+        int nr = 0;
+        for (int k0 = 0; k0 < 2 * kCN; k0 += 32) {
+            const int k = k0 + lane;
+            const bool in = k < kCN;
+            const unsigned long long rv = in ? sm.rs[k] : 0ull, d = in ? sm.ds[k] : 0ull, sv = sm.ss[k];
+            T += rv;
+            m_i += (unsigned long long)k * rv;
+            q_i += (unsigned long long)k * k * rv;
+            c2 += (unsigned long long)k * k * d;
+            m_d += (unsigned long long)k * d;
+            m_s += (unsigned long long)k * sv;
+            nr += __popc(__ballot_sync(0xffffffffu, rv != 0ull));
+        }
+        T = warp_sum_u64(T);
+        m_i = warp_sum_u64(m_i);
+        q_i = warp_sum_u64(q_i);
+        c2 = warp_sum_u64(c2);
+        m_d = warp_sum_u64(m_d);
+        m_s = warp_sum_u64(m_s);
+        if (lane == 0) {
+            sm.T = T;
+            sm.mom[0] = m_i;
+            sm.mom[1] = m_i;
+            sm.mom[2] = c2;
+            sm.mom[3] = m_s;
+            sm.mom[4] = m_d;
+            sm.mom[5] = q_i;
+            sm.mom[6] = q_i;
+            sm.nr = nr;
+        }
+    }
+    __syncthreads();
+    const unsigned long long T = sm.T;
+    if (T == 0ull) {
+        for (int e = tid; e < kCR * kCN && J.normalized; e += kCluThreads) {
+            const int i = i0 + (e >> 8), j = e & 255;
+            if (i < N && j < N)
+                J.normalized[(size_t)i * N + j] = 0.f;
+        }
+        if (r == 0 && tid < kNumFeat)
+            J.features[tid] = 0.f;
+        return;  // every CTA of the cluster returns here
+    }
+    const float Tf = (float)T;
+    // Cell pass over this CTA's rows: warp w rows w and w + 16, lane l
+    // columns l + 32 u.  A' overwrites the staged row of P cell by cell.
+    float* A = reinterpret_cast<float*>(sm.pb);
+    Kahan k_asm, k_ent, k_mi;
+    unsigned long long cij = 0;
+    for (int rr = warp; rr < kCR; rr += kCluWarps) {
+        const int i = i0 + rr;
+#pragma unroll 2
+        for (int u = 0; u < kCN / 32; ++u) {
+            const int j = lane + 32 * u;
+            float a = 0.f;
+            if (i < N && j < N) {
+                const unsigned long long sv =
+                    (unsigned long long)sm.pb[rr * kCN + j] + sm.pt[j * (kCR + 1) + rr];
+                const float pv = __fdiv_rn((float)sv, Tf);
+                if (J.normalized)
+                    J.normalized[(size_t)i * N + j] = pv;
+                if (sv) {
+                    k_asm.add(__fmul_rn(pv, pv));
+                    k_ent.add(neg_plogp(pv));
+                    cij += (unsigned long long)(i * j) * sv;
+                }
+                const unsigned long long ri = sm.rs[i], cj = sm.rs[j];
+                if (ri && cj) {
+                    // Exact numerator S*T - r*c while T < 2^31 (products < 2^62).
+                    const float rc = __fmul_rn((float)ri, (float)cj);
+                    float numf;
+                    if (T < (1ull << 31))
+                        numf = (float)((long long)(sv * T) - (long long)(ri * cj));
+                    else
+                        numf = __fsub_rn(__fmul_rn((float)sv, Tf), rc);
+                    const float x = __fdiv_rn(numf, rc);
+                    const float q = __fmul_rn(__fdiv_rn((float)ri, Tf), __fdiv_rn((float)cj, Tf));
+                    k_mi.add(__fmul_rn(q, phi(x)));
+                    a = __fdiv_rn(numf, __fmul_rn(Tf, sqrtf(rc)));
+                }
+            }
+            A[rr * kCN + j] = a;
+        }
+    }
+    // Terms of the marginal distributions, indices [64 r, 64 r + 64).
+    Kahan k_idm, k_svar, k_sent, k_dvar, k_dent, k_hx, k_hy;
+    const float f6 = ratio_u64(sm.mom[3], T);
+    const float mean_d = ratio_u64(sm.mom[4], T);
+    for (int k = (int)r * 64 + tid; tid < 64 && k < 2 * N - 1; k += kCluThreads) {
+        const float ps = __fdiv_rn((float)sm.ss[k], Tf);
+        const float dk = __fsub_rn((float)k, f6);
+        k_svar.add(__fmul_rn(__fmul_rn(dk, dk), ps));
+        k_sent.add(neg_plogp(ps));
+        if (k < N) {
+            const float pd = __fdiv_rn((float)sm.ds[k], Tf);
+            k_idm.add(__fdiv_rn(pd, (float)(1 + k * k)));
+            const float dd2 = __fsub_rn((float)k, mean_d);
+            k_dvar.add(__fmul_rn(__fmul_rn(dd2, dd2), pd));
+            k_dent.add(neg_plogp(pd));
+            const float pr = neg_plogp(__fdiv_rn((float)sm.rs[k], Tf));
+            k_hx.add(pr);
+            k_hy.add(pr);
+        }
+    }
+    cij = warp_sum_u64(cij);
+    if (lane == 0 && cij)
+        atomicAdd(&sm.cij, cij);  // complete after the block reduction's barriers
+    DF v[10] = {k_asm.df(), k_ent.df(), k_mi.df(), k_idm.df(), k_svar.df(),
+                k_sent.df(), k_dvar.df(), k_dent.df(), k_hx.df(), k_hy.df()};
+    block_reduce_df<10>(v, sm.dscr);
+    // This CTA's sums into CTA 0 (read there after the last cluster barrier).
+    if (tid < 10) {
+        const uint32_t a = clu_addr(&sm.fin[r][tid], 0u);
+        clu_st(a, v[tid].hi);
+        clu_st(a + 4u, v[tid].lo);
+    } else if (tid == 10) {
+        clu_st64(clu_addr(&sm.fin_cij[r], 0u), sm.cij);
+    }
+    __syncthreads();
+    float mcc = 0.f;
+    if (sm.nr >= 2)
+        mcc = clu_lanczos(sm, A, N, r);
+    clu_sync();  // the last access to another CTA's shared memory precedes this
+    if (r != 0)
+        return;
+    if (tid == 0) {
+        DF tot[10];
+        unsigned long long cij_t = 0;
+        for (int k = 0; k < 10; ++k)
+            tot[k] = sm.fin[0][k];
+        cij_t = sm.fin_cij[0];
+        for (int c = 1; c < kClu; ++c) {
+            for (int k = 0; k < 10; ++k)
+                tot[k] = df_add(tot[k], sm.fin[c][k]);
+            cij_t += sm.fin_cij[c];
+        }
+        write_features(J.features, T, sm.mom, cij_t, tot, f6, mcc);
+    }
+}
 }  // namespace
 
 // Global scratch per GLCM for supports too large for shared memory: A' (N^2)
@@ -1253,6 +1449,19 @@ long long features_work_floats(int levels)
 size_t features_smem_bytes(int max_levels)
 {
     return feat_layout(max_levels).total;
+}
+
+// Symmetric feature jobs with 128 < N <= 256: one cluster of kClu CTAs each.
+cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s)
+{
+    if (p.n_jobs <= 0)
+        return cudaSuccess;
+    static SmemLimit lim;
+    const cudaError_t e = lim.raise((const void*)k_haralick_cluster, sizeof(CluSmem));
+    if (e != cudaSuccess)
+        return e;
+    k_haralick_cluster<<<p.n_jobs * kClu, kCluThreads, sizeof(CluSmem), s>>>(p);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)

@@ -1029,6 +1029,14 @@ int capture_mark(glcm_ctx* ctx, GraphEntry* ge, bool start)
     return GLCM_OK;
 }
 
+// Feature jobs in launch order: the one-CTA epilogue's, then the cluster
+// epilogue's (symmetric, 128 < N <= 256).  Each job names its own outputs,
+// so the order changes nothing else.
+void order_feats(std::vector<FeatJob>& feats)
+{
+    std::stable_partition(feats.begin(), feats.end(), [](const FeatJob& f) { return !feat_job_clustered(f); });
+}
+
 int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const DevBuf& dfeat, int max_levels,
                      bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
 {
@@ -1036,26 +1044,51 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
         return GLCM_OK;
     if (!st)
         st = ctx->stream;
-    FeatParams fp{};
-    fp.jobs = static_cast<const FeatJob*>(dfeat.p);
-    fp.n_jobs = (int)feats.size();
-    fp.err = ctx->d_words;
-    if (max_levels > 64) {
-        bool any_feat = false;
-        for (const auto& f : feats)
-            any_feat |= f.features != nullptr;
-        if (any_feat) {
-            const long long per = features_work_floats(max_levels);
-            TRY(ensure(ctx, ctx->work, feats.size() * (size_t)per * sizeof(float)));
-            fp.work = static_cast<float*>(ctx->work.p);
-            fp.work_stride = per;
+    // The jobs of the cluster epilogue come last (order_feats).
+    int n_one = 0;
+    while (n_one < (int)feats.size() && !feat_job_clustered(feats[n_one]))
+        ++n_one;
+    for (size_t i = n_one; i < feats.size(); ++i)
+        if (!feat_job_clustered(feats[i]))
+            return fail(ctx, GLCM_ERR_CUDA, "internal: feature jobs out of launch order");
+    if (n_one > 0) {
+        int one_max = 2;
+        for (int i = 0; i < n_one; ++i)
+            one_max = std::max(one_max, feats[i].levels);
+        if (one_max > max_levels)
+            return fail(ctx, GLCM_ERR_CUDA, "internal: a feature job beyond the launch's levels");
+        FeatParams fp{};
+        fp.jobs = static_cast<const FeatJob*>(dfeat.p);
+        fp.n_jobs = n_one;
+        fp.err = ctx->d_words;
+        if (one_max > 64) {
+            bool any_feat = false;
+            for (int i = 0; i < n_one; ++i)
+                any_feat |= feats[i].features != nullptr;
+            if (any_feat) {
+                const long long per = features_work_floats(one_max);
+                TRY(ensure(ctx, ctx->work, (size_t)n_one * (size_t)per * sizeof(float)));
+                fp.work = static_cast<float*>(ctx->work.p);
+                fp.work_stride = per;
+            }
         }
+        CK(launch_features(fp, one_max, st));
+        if (!capturing)
+            ctx->kernel_launches += 1;
+        if (ge)
+            ge->n_kernels++;
     }
-    CK(launch_features(fp, max_levels, st));
-    if (!capturing)
-        ctx->kernel_launches += 1;
-    if (ge)
-        ge->n_kernels++;
+    if (n_one < (int)feats.size()) {
+        FeatParams fc{};
+        fc.jobs = static_cast<const FeatJob*>(dfeat.p) + n_one;
+        fc.n_jobs = (int)feats.size() - n_one;
+        fc.err = ctx->d_words;
+        CK(launch_features_cluster(fc, st));
+        if (!capturing)
+            ctx->kernel_launches += 1;
+        if (ge)
+            ge->n_kernels++;
+    }
     return GLCM_OK;
 }
 
@@ -1672,6 +1705,7 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
         }
     }
     finalize_fast(plan, ctx->sm_count);
+    order_feats(feats);
     return GLCM_OK;
 }
 

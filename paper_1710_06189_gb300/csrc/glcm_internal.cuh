@@ -244,6 +244,12 @@ cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int 
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);
 cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s);
+// Symmetric feature jobs with 128 < N <= 256, one cluster of CTAs per GLCM.
+cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s);
+inline bool feat_job_clustered(const FeatJob& f)
+{
+    return f.features != nullptr && f.symmetric && f.levels > 128 && f.levels <= 256;
+}
 size_t features_smem_bytes(int max_levels);
 long long features_work_floats(int levels);
 cudaError_t launch_windows(const WindowParams& p, cudaStream_t s);

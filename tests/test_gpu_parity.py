@@ -154,7 +154,8 @@ def test_normalize_and_features(gctx, sym, n):
 
 @pytest.mark.parametrize("n", [129, 160, 200, 255, 256])
 def test_symmetric_features_large_levels(gctx, n):
-    """Symmetric GLCMs with N > 128: A' kept blockwise, symmetric Lanczos."""
+    """Symmetric GLCMs with N > 128: one cluster of CTAs per GLCM, A' kept by
+    rows across it, symmetric Lanczos."""
     imgs = [S.iid(n, 300, 700, np.uint8), S.smooth(n + 1, 300, 700, 2.0, np.uint8),
             S.smooth(n + 2, 300, 700, 8.0, np.uint8), (S.iid(n + 3, 200, 300, np.uint8) & 0xF0),
             (np.indices((64, 96)).sum(0) % 2 * 255).astype(np.uint8),   # checkerboard: f14 = 1
@@ -168,6 +169,40 @@ def test_symmetric_features_large_levels(gctx, n):
         assert np.array_equal(to_u32(counts), P)
         assert_normalized(norm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)), f"n={n} img={k}")
         assert_features(feats.cpu().numpy(), oracle.haralick_batch(P, True), n, what=f"n={n} img={k}")
+
+
+def test_cluster_epilogue_large_totals_and_mixed_launch(gctx):
+    """Symmetric GLCMs with 128 < N <= 256 take one cluster of CTAs each: count
+    matrices whose symmetric total passes 2^32 (S entries beyond 32 bits, the
+    rounded numerator), sparse and single-cell supports, in one call beside
+    jobs of the one-CTA epilogue; every GLCM again alone, bit-identical."""
+    rng = np.random.default_rng(4242)
+    for n in (129, 200, 256):
+        mats = [rng.integers(0, 1 << 24, size=(n, n), dtype=np.uint64).astype(np.uint32),
+                (rng.random((n, n)) < 0.02) * rng.integers(1, 1 << 31, size=(n, n)),
+                np.zeros((n, n), np.uint64)]
+        mats[2][n - 1, 0] = 3_000_000_000
+        mats = np.stack([m.astype(np.uint32) for m in mats])
+        c = torch.from_numpy(mats.view(np.int32)).cuda()
+        f = gctx.features(c, n, symmetric=True)
+        torch.cuda.synchronize()
+        assert_features(f.cpu().numpy(), oracle.haralick_batch(mats, True), n, what=f"n={n} large totals")
+        for k in range(len(mats)):
+            alone = gctx.features(c[k:k + 1], n, symmetric=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(alone.cpu().numpy()[0], f.cpu().numpy()[k]), (n, k)
+    # One batch: N = 256 and N = 64 symmetric feature jobs, and N = 256 plain.
+    img = S.smooth(77, 300, 600, 3.0, np.uint8)
+    jobs = [dict(image=dev(img), levels=256, offsets=C4, flags=G.GLCM_SYMMETRIC, features=True),
+            dict(image=dev(img), levels=64, offsets=C4, flags=G.GLCM_SYMMETRIC, features=True),
+            dict(image=dev(img), levels=256, offsets=C4[:2], flags=0, features=True)]
+    outs = gctx.batch(jobs)
+    torch.cuda.synchronize()
+    for jb, (c, _, f) in zip(jobs, outs):
+        P = oracle.glcm(img, jb["levels"], jb["offsets"])
+        assert np.array_equal(to_u32(c), P)
+        assert_features(f.cpu().numpy(), oracle.haralick_batch(P, jb["flags"] == G.GLCM_SYMMETRIC), jb["levels"],
+                        what=f"batch n={jb['levels']}")
 
 
 def test_features_of_special_matrices(gctx):
