@@ -43,8 +43,10 @@
 //    levels, or partner levels for a transposed offset) in one copy of 32768
 //    32-bit counters (128 KB), laid out as those rows of the output.  A vote
 //    is one byte permute for row * 256 + column, one multiply-add for the
-//    address and one reduction predicated on the row half; four offsets take
-//    eight jobs.  The merge is a single bulk reduction of the 128 KB into the
+//    address and one unconditional reduction: a vote of the other row half
+//    goes to a spare word of its lane past the 128 KB (one unsigned min), as
+//    a reduction predicated per lane costs a divergent branch; four offsets
+//    take eight jobs.  The merge is a single bulk reduction of the 128 KB into the
 //    output rows (cp.reduce.async.bulk ... add.u32, done at L2), not one
 //    global atomic per bin.
 //  * Persistent CTAs (one per SM, 16 warps) pull chunks of consecutive items
@@ -65,6 +67,7 @@ constexpr int kFT = 512;            // threads per CTA
 constexpr int kFW = kFT / 32;       // warps per CTA
 constexpr int kPF = 4;              // rows in flight per lane
 constexpr int kMargWords = 4 * 64;  // joint-code merge: 4 offsets x N^2 (N <= 8)
+static_assert(kMargWords >= 32, "N = 256 jobs use the first 32 marginal words as spare words");
 // 16-bit halves: anchor rows a lane may vote between merges (16 votes per
 // row into one copy at most: 4000 * 16 < 65536).
 constexpr unsigned kHalfRows = 4000;
@@ -85,21 +88,18 @@ __device__ __forceinline__ void red1_if(uint32_t a, uint32_t mask, uint32_t bit)
 
 // N = 256: reduction at hb + rel if rel, the byte offset of the code within
 // the job's 128 rows, lies inside them (unsigned: codes of the other half
-// fall below or above).
-__device__ __forceinline__ void red_row(uint32_t hb, uint32_t rel)
+// fall below or above); else into `spare`, the lane's own word past the rows
+// (never read).  No predicate: a predicated reduction whose predicate differs
+// between lanes costs a divergent branch around it.
+__device__ __forceinline__ void red_row(uint32_t hb, uint32_t rel, uint32_t spare)
 {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.lt.u32 p, %1, 131072;\n\t@p red.shared.add.u32 [%0], 1;\n\t}" ::"r"(hb + rel),
-        "r"(rel));
+    red1(hb + min(rel, spare));
 }
 
-// ... and if bit `bit` of the lane's anchor mask is set (edge strips).
-__device__ __forceinline__ void red_row_if(uint32_t hb, uint32_t rel, uint32_t mask, uint32_t bit)
+// ... and only if bit `bit` of the lane's anchor mask is set (edge strips).
+__device__ __forceinline__ void red_row_if(uint32_t hb, uint32_t rel, uint32_t spare, uint32_t mask, uint32_t bit)
 {
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\t.reg .b32 u;\n\tsetp.lt.u32 p, %1, 131072;\n\t"
-        "and.b32 u, %2, %3;\n\tsetp.ne.and.u32 q, u, 0, p;\n\t@q red.shared.add.u32 [%0], 1;\n\t}" ::"r"(hb + rel),
-        "r"(rel), "r"(mask), "r"(bit));
+    red1(hb + ((mask & bit) ? min(rel, spare) : spare));
 }
 
 __device__ __forceinline__ void red_hi(uint32_t a)
@@ -312,7 +312,7 @@ __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[L
 template <int LW, bool EDGE>
 __device__ __forceinline__ void votes_wide(int k, bool tr, const uint32_t (&C)[LW], uint32_t CR,
                                            const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
-                                           uint32_t rbase, uint32_t mask)
+                                           uint32_t rbase, uint32_t spare, uint32_t mask)
 {
     const uint32_t sel = k == 3 ? 0x6543u : (k == 2 ? 0x3210u : 0x4321u);
 #pragma unroll
@@ -329,15 +329,15 @@ __device__ __forceinline__ void votes_wide(int k, bool tr, const uint32_t (&C)[L
         const uint32_t r2 = 4u * __byte_perm(col, shi, 0x5542) + rbase;
         const uint32_t r3 = 4u * __byte_perm(col, shi, 0x5563) + rbase;
         if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
-            red_row_if(hb, r0, mask, 1u << (4 * m));
-            red_row_if(hb, r1, mask, 1u << (4 * m + 1));
-            red_row_if(hb, r2, mask, 1u << (4 * m + 2));
-            red_row_if(hb, r3, mask, 1u << (4 * m + 3));
+            red_row_if(hb, r0, spare, mask, 1u << (4 * m));
+            red_row_if(hb, r1, spare, mask, 1u << (4 * m + 1));
+            red_row_if(hb, r2, spare, mask, 1u << (4 * m + 2));
+            red_row_if(hb, r3, spare, mask, 1u << (4 * m + 3));
         } else {
-            red_row(hb, r0);
-            red_row(hb, r1);
-            red_row(hb, r2);
-            red_row(hb, r3);
+            red_row(hb, r0, spare);
+            red_row(hb, r1, spare);
+            red_row(hb, r2, spare);
+            red_row(hb, r3, spare);
         }
     }
 }
@@ -379,7 +379,8 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         const int k = (pr & 1) ? 0 : ((pr & 2) ? 1 : ((pr & 4) ? 2 : 3));
         if (top && k != 0)
             return;  // no row above the image's first row
-        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase,
+        // Spare words: the lane's word of the 32 after the job's 32768.
+        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase, 131072u + l4,
                              k == 2 ? em.in : (k == 3 ? em.left : em.right));
     } else if constexpr (LOG2N == 4) {
         uint32_t A16[LW];
