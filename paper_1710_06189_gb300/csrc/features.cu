@@ -1037,9 +1037,9 @@ struct CluSmem {
     unsigned long long ss[2 * kCN];       // i + j sums of S
     unsigned long long ds[kCN];           // |i - j| sums of S
     unsigned long long mom[7], T, cij, fin_cij[kClu];
-    float q[kCN], w[kCN];                 // Lanczos vector; the next one's pieces (written by all CTAs)
-    float qp[kCR], y[kCR];
-    float sa[kClu], sb[kClu];             // each CTA's part of the step's two dot products
+    float q[kCN], qp[kCN], y[kCR];        // Lanczos vector, the previous one, this CTA's rows of A' q
+    float w[2][kCN];                      // A' q - beta q_prev, pieces written by every CTA (by step parity)
+    float sa[2][kClu];                    // each CTA's part of (A' q - beta q_prev) . q (by step parity)
     float al[kMaxSymSteps], be[kMaxSymSteps], ends[4];
     DF fin[kClu][10];                     // CTA 0: each CTA's compensated sums
     DF dscr[10 * 32];
@@ -1096,6 +1096,13 @@ __device__ __forceinline__ void clu_sync()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The same barrier for a warp whose stores nobody reads across it: it
+// arrives without release ordering (no fence), and still waits with acquire.
+__device__ __forceinline__ void clu_sync_relaxed()
+{
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long s)
 {
     for (int o = 16; o > 0; o >>= 1)
@@ -1105,11 +1112,15 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long s)
 
 // max |eigenvalue| of A' (rows of this CTA in A, row stride kCN) by symmetric
 // Lanczos without reorthogonalization from a fixed zero-mean pseudo-random
-// start: w = A' q - beta q_prev, alpha = w . q, w -= alpha q, beta = |w|,
-// q = w / beta; every 8 steps (after 16) the tridiagonal matrix's extreme
-// eigenvalues are bracketed, and the iteration stops once max |eigenvalue|
-// moved by less than 4e-7 of itself.  Every CTA holds the whole vector q
-// and the whole tridiagonal matrix and takes the same decisions.
+// start: w' = A' q - beta q_prev, alpha = w' . q, w = w' - alpha q,
+// beta = |w|, q = w / beta; every 8 steps (after 16) the tridiagonal
+// matrix's extreme eigenvalues are bracketed, and the iteration stops once
+// max |eigenvalue| moved by less than 4e-7 of itself.  One cluster barrier
+// per step: each CTA writes its rows of w' and its part of alpha into every
+// CTA (buffers alternate by step parity, so a CTA a step ahead never
+// overwrites what another still reads); then every CTA forms all of w, beta
+// and q from the same numbers in the same order, so all hold the same
+// vector and tridiagonal matrix and take the same decisions.
 __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1119,9 +1130,8 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
         // eigenvectors of a deflated A' and could stall on a lower one.
         const unsigned h = (unsigned)c * 2654435761u + 12345u;
         sm.q[c] = c < N ? (float)h * 2.3283064e-10f - 0.5f : 0.f;
+        sm.qp[c] = 0.f;
     }
-    if (tid < kCR)
-        sm.qp[tid] = 0.f;
     if (tid == 0) {
         sm.sig = -1.f;
         sm.stop = 0;
@@ -1134,12 +1144,10 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
     for (int c = tid; c < kCN; c += kCluThreads)
         sm.q[c] *= inv;
     __syncthreads();
-    // Warp 0, lane l: row i0 + l.  Where this CTA's pieces go in every CTA.
-    const uint32_t to_sa = clu_addr(&sm.sa[r], (uint32_t)lane & (kClu - 1));
-    const uint32_t to_sb = clu_addr(&sm.sb[r], (uint32_t)lane & (kClu - 1));
     float beta = 0.f;
     int L = 0;
     for (int k = 0; k < kMaxSymSteps; ++k) {
+        const int par = k & 1;
         for (int rr = warp; rr < kCR; rr += kCluWarps) {
             float acc = 0.f;
 #pragma unroll
@@ -1150,42 +1158,35 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
                 sm.y[rr] = acc;
         }
         __syncthreads();
-        float wv = 0.f;
         if (warp == 0) {
-            wv = fmaf(-beta, sm.qp[lane], sm.y[lane]);
+            // Lane l: row i0 + l.
+            const float wv = fmaf(-beta, sm.qp[i0 + lane], sm.y[lane]);
             const float d = warp_sum(wv * sm.q[i0 + lane]);
+            for (int c = 0; c < kClu; ++c)
+                clu_st(clu_addr(&sm.w[par][i0 + lane], (uint32_t)c), wv);
             if (lane < kClu)
-                clu_st(to_sa, d);
+                clu_st(clu_addr(&sm.sa[par][r], (uint32_t)lane), d);
+            clu_sync();
+        } else {
+            clu_sync_relaxed();
         }
-        clu_sync();
         float alpha = 0.f;
         for (int c = 0; c < kClu; ++c)
-            alpha += sm.sa[c];
-        if (warp == 0) {
-            wv = fmaf(-alpha, sm.q[i0 + lane], wv);
-            const float s2 = warp_sum(wv * wv);
-            for (int c = 0; c < kClu; ++c)
-                clu_st(clu_addr(&sm.w[i0 + lane], (uint32_t)c), wv);
-            if (lane < kClu)
-                clu_st(to_sb, s2);
-        }
-        if (tid == 0)
+            alpha += sm.sa[par][c];
+        float wt = 0.f;
+        if (tid < kCN)
+            wt = fmaf(-alpha, sm.q[tid], sm.w[par][tid]);
+        const float bn = sqrtf(block_sum(wt * wt, sm.red));
+        if (tid == 0) {
             sm.al[k] = alpha;
-        clu_sync();
-        float s2t = 0.f;
-        for (int c = 0; c < kClu; ++c)
-            s2t += sm.sb[c];
-        const float bn = sqrtf(s2t);
-        if (tid == 0)
             sm.be[k] = bn;
+        }
         L = k + 1;
         if (!(bn > 1e-30f))
             break;  // invariant subspace: the tridiagonal matrix is exact
-        const float ib = 1.f / bn;
-        for (int c = tid; c < kCN; c += kCluThreads) {
-            if ((c >> 5) == (int)r)
-                sm.qp[c & 31] = sm.q[c];
-            sm.q[c] = sm.w[c] * ib;
+        if (tid < kCN) {
+            sm.qp[tid] = sm.q[tid];
+            sm.q[tid] = wt * (1.f / bn);
         }
         beta = bn;
         __syncthreads();
