@@ -505,6 +505,23 @@ FastClass& fast_class(VotePlan& plan, int bpp, int log2n, bool aligned)
     return plan.fast.back();
 }
 
+// CTAs of a vote launch: every SM but the context's reserve (left to a
+// concurrent copy kernel), and at most max_ctas when that is given.
+int launch_ctas(const glcm_ctx* ctx, int max_ctas = 0)
+{
+    int c = std::max(1, ctx->sm_count - ctx->sm_reserve);
+    if (max_ctas > 0)
+        c = std::min(c, max_ctas);
+    return std::max(1, c);
+}
+
+// SMs the rest of a split batch leaves to the expensive epilogues of its
+// first part (n_glcm GLCMs) while it votes.
+int split_reserve(const glcm_ctx* ctx, int n_glcm)
+{
+    return std::min(n_glcm, ctx->sm_count / 4);
+}
+
 // Items per chunk of the column-walk kernel: one per warp of a CTA.
 constexpr int kFastChunkItems = 16;
 
@@ -591,21 +608,37 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
 }
 
 // Bands, items and chunks of every column-walk class of a plan.  One band
-// height per class, chosen so that the class's items come to whole chunks of
-// kFastChunkItems (one item per warp of a CTA) spread evenly over `ctas`
-// CTAs: one chunk per CTA while a warp's share of the class is at most 64
-// rows, else the fewest chunks per CTA that keep bands at most 64 rows (at
-// least 4 rows: the row above a band is loaded too).
+// height per class (4..64 rows), chosen for the shortest launch on `ctas`
+// CTAs: with c(b) chunks of kFastChunkItems items (one item per warp, chunks
+// never span jobs) a CTA takes ceil(c(b) / ctas) chunks, each costing about
+// b rows plus the row above the band and the item's start, so b minimizes
+// ceil(c(b) / ctas) * (b + kItemRowsExtra).  (Rounding b up from rows per
+// warp can leave one chunk more than CTAs, and one CTA twice the work.)
+constexpr int kItemRowsExtra = 3;
+
 void finalize_fast(VotePlan& plan, int ctas)
 {
+    ctas = std::max(1, ctas);
     for (FastClass& fc : plan.fast) {
-        long long strip_rows = 0;
-        for (const FastJob& j : fc.jobs)
-            strip_rows += (long long)j.n_strips * (j.y_end - j.y_begin);
-        const long long warps = (long long)kFastChunkItems * std::max(1, ctas);
-        const long long per_warp = std::max(1ll, (strip_rows + warps - 1) / warps);
-        const long long k = std::max(1ll, (per_warp + 63) / 64);
-        const int band = (int)std::max(4ll, std::min(64ll, (per_warp + k - 1) / k));
+        auto chunks_for = [&](int b) {
+            long long c = 0;
+            for (const FastJob& j : fc.jobs) {
+                const int bj = j.band > 0 ? j.band : b;
+                const long long items = (long long)j.n_strips * ((j.y_end - j.y_begin + bj - 1) / bj);
+                c += (items + kFastChunkItems - 1) / kFastChunkItems;
+            }
+            return c;
+        };
+        int band = 64;
+        long long best = -1;
+        for (int b = 4; b <= 64; ++b) {
+            const long long per_cta = (chunks_for(b) + ctas - 1) / ctas;
+            const long long cost = per_cta * (b + kItemRowsExtra);
+            if (best < 0 || cost < best) {
+                best = cost;
+                band = b;
+            }
+        }
         fc.n_items = 0;
         fc.chunks.clear();
         for (int jb = 0; jb < (int)fc.jobs.size(); ++jb) {
@@ -1580,7 +1613,7 @@ extern "C" int glcm_compute(glcm_ctx* ctx, const void* image, int width, int hei
         ImageSpec s{d_img, (long long)dpitch, width, height, bpp, levels, (flags & GLCM_INPUT_LEVELS) ? 1 : 0,
                     offsets, n_offsets, d_counts, r0, r1, flat ? 1 : 0};
         TRY(plan_image(ctx, s, plan, target_items(ctx)));
-        finalize_fast(plan, ctx->sm_count);
+        finalize_fast(plan, launch_ctas(ctx));
         build_chunks(plan, ctx->sm_count);
         std::vector<FeatJob> none;
         TRY(upload_tables(ctx, plan, none, ctx->jobs, ctx->offs, ctx->feat));
@@ -1672,7 +1705,7 @@ namespace {
 // Build the plan and feature jobs of a batch whose images and outputs are on
 // the device.
 int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std::vector<FeatJob>& feats,
-               int& max_levels)
+               int& max_levels, int ctas)
 {
     max_levels = 2;
     long long total_rows_strips = 0;
@@ -1704,7 +1737,7 @@ int plan_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, VotePlan& plan, std
                                         (d.flags & GLCM_SYMMETRIC) ? 1 : 0});
         }
     }
-    finalize_fast(plan, ctx->sm_count);
+    finalize_fast(plan, ctas);
     order_feats(feats);
     return GLCM_OK;
 }
@@ -1721,11 +1754,13 @@ struct SplitBatch {
     const int3* c16 = nullptr;
 };
 
+// ctas: the CTAs the batch's column-walk launches will have (its chunks are
+// cut for exactly that many); 0: every SM the context's launches use.
 int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, DevBuf& djobs, DevBuf& doffs,
-                  DevBuf& dfeat)
+                  DevBuf& dfeat, int ctas = 0)
 {
     VotePlan plan;
-    TRY(plan_batch(ctx, descs, n, plan, sb.feats, sb.max_levels));
+    TRY(plan_batch(ctx, descs, n, plan, sb.feats, sb.max_levels, ctas > 0 ? ctas : launch_ctas(ctx)));
     for (int pass = 0; pass < 2; ++pass) {
         VotePlan& dst = pass == 0 ? sb.p8 : sb.p16;
         dst.threads = plan.threads;
@@ -1810,8 +1845,7 @@ int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, Sp
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
     TRY(enqueue_features(ctx, h.feats, th[2], h.max_levels, capturing, ge, ctx->side_stream));
-    const int reserve = std::min((int)h.feats.size(), ctx->sm_count / 4);
-    r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - reserve);
+    r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - split_reserve(ctx, (int)h.feats.size()));
     if (!plan_empty(r.p8))
         TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge));
     if (!plan_empty(r.p16))
@@ -1963,18 +1997,20 @@ int run_host_batch(glcm_ctx* ctx, const glcm_desc* descs_in, int n)
     // Plans and tables of every group while the copies run (the copies go
     // through a copy kernel for registered memory, so the tables' small
     // uploads do not queue behind them on a copy engine).
-    const int reserve = std::min(n_heavy_glcm, ctx->sm_count / 4);
+    const int reserve = split_reserve(ctx, n_heavy_glcm);
     std::vector<SplitBatch> sbs(gend.size());
     first = 0;
     for (size_t g = 0; g < gend.size(); ++g) {
         auto& tab = ctx->hb_tab[g];
-        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sbs[g], tab[0], tab[1], tab[2]));
         // While later groups' copies are in flight, kCopySMs SMs stay free for the
         // copy kernel: a vote CTA fills its SM's register file, so without them
         // the copies stall behind the votes (measured).
         const int copy_sms = g + 1 < gend.size() ? kCopySMs : 0;
+        const int group_ctas = ctx->sm_count - reserve - copy_sms;
+        TRY(prepare_batch(ctx, dd.data() + first, gend[g] - first, sbs[g], tab[0], tab[1], tab[2],
+                          launch_ctas(ctx, group_ctas)));
         if (reserve + copy_sms > 0)
-            sbs[g].p8.max_ctas = sbs[g].p16.max_ctas = ctx->sm_count - reserve - copy_sms;
+            sbs[g].p8.max_ctas = sbs[g].p16.max_ctas = group_ctas;
         first = gend[g];
     }
     // Results of images [i0, i1) to the caller's host buffers on stream st.
@@ -2137,9 +2173,13 @@ int run_graph_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, const std::vec
         // attribute before capture.
         int rc0;
         if (split) {
+            int n_heavy_glcm = 0;
+            for (const glcm_desc& d : heavy)
+                n_heavy_glcm += d.n_offsets;
             rc0 = prepare_batch(ctx, heavy.data(), (int)heavy.size(), sb, ge.jobs, ge.offs, ge.feat);
             if (rc0 == GLCM_OK)
-                rc0 = prepare_batch(ctx, rest.data(), (int)rest.size(), sb2, ge.jobs2, ge.offs2, ge.feat2);
+                rc0 = prepare_batch(ctx, rest.data(), (int)rest.size(), sb2, ge.jobs2, ge.offs2, ge.feat2,
+                                    launch_ctas(ctx, ctx->sm_count - split_reserve(ctx, n_heavy_glcm)));
         } else if (n > 0) {
             rc0 = prepare_batch(ctx, descs, n, sb, ge.jobs, ge.offs, ge.feat);
         } else {
