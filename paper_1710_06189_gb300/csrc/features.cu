@@ -407,6 +407,52 @@ __device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk
 // the error stays within a few float roundings either way.
 // Buffers: three 32 x kSqLD matrices and two diagonals (kSqFloats floats,
 // 16-byte aligned).  Returns sigma_max in every thread.
+// One squaring X' = X^2 * sc of the symmetric D x D block (rows kSqLD floats
+// apart; entries beyond the support are zero): warp w takes rows w, w + nw,
+// ... (two rows at a time for D = 32, sharing the loads of X's rows k), lane
+// b column b, so a row k is read without bank conflicts and X[a][k] is a
+// broadcast.  The new diagonal goes to dn.
+template <int D>
+__device__ __forceinline__ void square_step(const float* __restrict__ X, float* __restrict__ Xn, float* dn,
+                                            float sc)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if (D == 32 && nw == 16) {
+        const int a0 = warp, a1 = warp + 16;
+        float p0 = 0.f, p1 = 0.f, q0 = 0.f, q1 = 0.f;
+#pragma unroll
+        for (int k = 0; k < 32; k += 2) {
+            const float xk0 = X[k * kSqLD + lane], xk1 = X[(k + 1) * kSqLD + lane];
+            p0 = fmaf(X[a0 * kSqLD + k], xk0, p0);
+            p1 = fmaf(X[a0 * kSqLD + k + 1], xk1, p1);
+            q0 = fmaf(X[a1 * kSqLD + k], xk0, q0);
+            q1 = fmaf(X[a1 * kSqLD + k + 1], xk1, q1);
+        }
+        const float v0 = (p0 + p1) * sc, v1 = (q0 + q1) * sc;
+        Xn[a0 * kSqLD + lane] = v0;
+        Xn[a1 * kSqLD + lane] = v1;
+        if (lane == a0)
+            dn[a0] = v0;
+        if (lane == a1)
+            dn[a1] = v1;
+        return;
+    }
+    for (int a = warp; a < D; a += nw) {
+        if (lane < D) {
+            float p0 = 0.f, p1 = 0.f;
+#pragma unroll
+            for (int k = 0; k < D; k += 2) {
+                p0 = fmaf(X[a * kSqLD + k], X[k * kSqLD + lane], p0);
+                p1 = fmaf(X[a * kSqLD + k + 1], X[(k + 1) * kSqLD + lane], p1);
+            }
+            const float v = (p0 + p1) * sc;
+            Xn[a * kSqLD + lane] = v;
+            if (a == lane)
+                dn[a] = v;
+        }
+    }
+}
+
 __device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, float* s_out)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -474,32 +520,18 @@ __device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, fl
     int cur = 0;
     float prev = 2.f;
     for (int step = 0; step < kSqMax; ++step) {
-        const float trc = trace32(Db(cur), 1);
+        // tr X by a warp sum in every warp: the same value in every thread.
+        const float trc = warp_sum(lane < 32 ? Db(cur)[lane] : 0.f);
         if (step >= kSqMin && fabsf(trc - prev) <= 1e-6f * trc)
             break;
         prev = trc;
         const float sc = 1.f / (trc * trc);
-        const float* Xc = Xb(cur);
-        float* Xn = Xb(cur ^ 1);
-        float* dn = Db(cur ^ 1);
-        for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
-            const int a = t >> 5, b = t & 31;
-            const float4* ra = reinterpret_cast<const float4*>(Xc + a * kSqLD);
-            const float4* rb = reinterpret_cast<const float4*>(Xc + b * kSqLD);
-            float p[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const float4 xa = ra[k], xb = rb[k];
-                p[0] = fmaf(xa.x, xb.x, p[0]);
-                p[1] = fmaf(xa.y, xb.y, p[1]);
-                p[2] = fmaf(xa.z, xb.z, p[2]);
-                p[3] = fmaf(xa.w, xb.w, p[3]);
-            }
-            const float v = ((p[0] + p[1]) + (p[2] + p[3])) * sc;
-            Xn[a * kSqLD + b] = v;
-            if (a == b)
-                dn[a] = v;
-        }
+        if (d <= 8)
+            square_step<8>(Xb(cur), Xb(cur ^ 1), Db(cur ^ 1), sc);
+        else if (d <= 16)
+            square_step<16>(Xb(cur), Xb(cur ^ 1), Db(cur ^ 1), sc);
+        else
+            square_step<32>(Xb(cur), Xb(cur ^ 1), Db(cur ^ 1), sc);
         __syncthreads();
         cur ^= 1;
     }
@@ -514,7 +546,9 @@ __device__ float sigma_max_squaring(const float* A, int m, int n, float* buf, fl
     float gx = 0.f, xx = 0.f;
     for (int t = threadIdx.x; t < 32 * 32; t += blockDim.x) {
         const int a = t >> 5, k = t & 31;
-        const float xa = Xf[a * kSqLD + c], xk = Xf[k * kSqLD + c];
+        // (Beyond the support the squarings wrote nothing; the second X
+        // buffer may still hold the copy of A's columns there.)
+        const float xa = a < d ? Xf[a * kSqLD + c] : 0.f, xk = k < d ? Xf[k * kSqLD + c] : 0.f;
         gx = fmaf(G[a * kSqLD + k] * xa, xk, gx);
         if (k == 0)
             xx = fmaf(xa, xa, xx);

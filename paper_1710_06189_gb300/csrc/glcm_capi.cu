@@ -869,22 +869,31 @@ int zero_words(glcm_ctx* ctx, uint32_t* p, long long n, cudaStream_t st)
 constexpr int kCounterWords = 32;  // the context's 128 bytes of device words
 constexpr int kMaxFastClasses = kCounterWords - 2;
 
-// Blocks [0, n_gen) zero general job b's outputs, blocks [n_gen, n_gen +
-// n_fast) the outputs of column-walk job b - n_gen; block 0 also clears the
-// chunk counters.
+// Blocks x in [0, n_gen) zero general job x's outputs, blocks x in [n_gen,
+// n_gen + n_fast) the outputs of column-walk job x - n_gen, each in
+// kZeroSlices slices (blockIdx.y); an N = 256 job zeroes only the 128 rows it
+// counts (its twin job for the other half zeroes the rest).  Block (0, 0)
+// also clears the chunk counters.
+constexpr int kZeroSlices = 8;
+
+__device__ __forceinline__ void zero_slice(uint32_t* dst, long long n)
+{
+    const long long per = (n + kZeroSlices - 1) / kZeroSlices;
+    const long long lo = per * blockIdx.y, hi = lo + per < n ? lo + per : n;
+    for (long long e = lo + threadIdx.x; e < hi; e += blockDim.x)
+        dst[e] = 0u;
+}
+
 __global__ void k_zero_job_outputs(const VoteJob* jobs, int n_gen, const VoteOffset* offs, const FastJob* fjobs,
                                    unsigned* counters)
 {
-    if (blockIdx.x == 0 && threadIdx.x < kCounterWords - 1)
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < kCounterWords - 1)
         counters[threadIdx.x] = 0u;
     if ((int)blockIdx.x < n_gen) {
         const VoteJob j = jobs[blockIdx.x];
         const long long NN = (long long)j.levels * j.levels;
-        for (int o = 0; o < j.n_off; ++o) {
-            uint32_t* dst = j.out + offs[j.off0 + o].slot * NN;
-            for (long long k = threadIdx.x; k < NN; k += blockDim.x)
-                dst[k] = 0u;
-        }
+        for (int o = 0; o < j.n_off; ++o)
+            zero_slice(j.out + offs[j.off0 + o].slot * NN, NN);
         return;
     }
     const FastJob& f = fjobs[blockIdx.x - n_gen];
@@ -894,9 +903,10 @@ __global__ void k_zero_job_outputs(const VoteJob* jobs, int n_gen, const VoteOff
             const int sl = t ? f.slot_t[k] : f.slot[k];
             if (sl < 0)
                 continue;
-            uint32_t* dst = f.out + sl * NN;
-            for (long long e = threadIdx.x; e < NN; e += blockDim.x)
-                dst[e] = 0u;
+            if (f.mode == kFastWide)
+                zero_slice(f.out + sl * NN + (long long)f.row_half * (NN / 2), NN / 2);
+            else
+                zero_slice(f.out + sl * NN, NN);
         }
 }
 
@@ -960,7 +970,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
     if (zero && plan.jobs.empty() && plan.fast.empty()) {
         k_clear_counters<<<1, 32, 0, st>>>(ctx->d_words + 1);
     } else if (zero) {
-        k_zero_job_outputs<<<(int)plan.jobs.size() + n_fast_jobs, 256, 0, st>>>(
+        k_zero_job_outputs<<<dim3((int)plan.jobs.size() + n_fast_jobs, kZeroSlices), 256, 0, st>>>(
             static_cast<const VoteJob*>(djobs.p), (int)plan.jobs.size(), static_cast<const VoteOffset*>(doffs.p),
             fjobs0, ctx->d_words + 1);
     } else {
