@@ -93,9 +93,19 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
+# The vote kernels' sources (the column walk and the general kernel).
+VOTE_SOURCES = ("vote.cu", "vote_fast.cuh", "vote_fast.cu", "vote_fast_unaligned.cu")
+
+
+def vote_code_sha256() -> str:
+    """code_sha256 of the vote kernels' sources, concatenated in VOTE_SOURCES order."""
+    csrc = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc")
+    return code_sha256("\n".join(open(os.path.join(csrc, f)).read() for f in VOTE_SOURCES))
+
+
 def profiled_traffic(name: str):
     """DRAM bytes of a step's vote launches from the committed ncu summary,
-    valid only while the kernel's code is unchanged since the capture."""
+    valid only while the vote kernels' code is unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", name)
     if not os.path.exists(path):
         return None
@@ -104,8 +114,7 @@ def profiled_traffic(name: str):
     s = re.search(r"vote_code_sha256:\s*([0-9a-f]{64})", text)
     if not m or not s:
         return None
-    src = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc", "vote.cu")
-    return float(m.group(1)) if code_sha256(open(src).read()) == s.group(1) else None
+    return float(m.group(1)) if vote_code_sha256() == s.group(1) else None
 
 
 def code_sha256(text: str) -> str:
@@ -428,38 +437,48 @@ def _timed(stream, fn, warm=2, reps=5):
     return e0.elapsed_time(e1) / reps
 
 
-def other_workloads(G, S, torch, local: int):
+EXTRA_LEGS = ("plain_512", "multispectral", "windows", "histogram", "uneven")
+
+
+def other_workloads(G, S, torch, local: int, only=None):
     """Device-resident throughput of the other workload shapes (each through
     the same public calls a user makes, inputs already in HBM):
     plain 512^2 N=8 levels-mode single offset; 8 bands of 8192^2 uint16 x 12
     offsets with symmetric normalized GLCMs and features in one batch; the
     2048^2 sliding-window texture maps (259,081 windows x 4 offsets), also
     without counts; the gray-level histogram of a 16384^2 uint8 image; 1000
-    uneven uint8 images (64..2048) in one batch."""
+    uneven uint8 images (64..2048) in one batch, and with the windows in one
+    graph.  only: a set of EXTRA_LEGS names to run (None: all)."""
     import numpy as np
     from concurrent.futures import ThreadPoolExecutor
+
+    def want(name):
+        return only is None or name in only
+
     out = {}
     stream = torch.cuda.Stream(device=local)
     ctx = G.Context(local, hbm_budget_bytes=8 << 30, stream=stream)
     with torch.cuda.stream(stream):
         # Plain method: one small image per call.
-        img, n, offs = S.plain_512()
-        d = torch.from_numpy(img).cuda(local)
-        c = torch.empty((1, n, n), dtype=torch.int32, device=f"cuda:{local}")
-        ms = _timed(stream, lambda: ctx.compute(d, n, offs, G.GLCM_INPUT_LEVELS, out=c), warm=3, reps=50)
-        out["plain_512"] = {"us_per_image": ms * 1e3, "gpairs_s": pairs_of(512, 512, offs) / (ms * 1e-3) / 1e9}
+        if want("plain_512"):
+            img, n, offs = S.plain_512()
+            d = torch.from_numpy(img).cuda(local)
+            c = torch.empty((1, n, n), dtype=torch.int32, device=f"cuda:{local}")
+            ms = _timed(stream, lambda: ctx.compute(d, n, offs, G.GLCM_INPUT_LEVELS, out=c), warm=3, reps=50)
+            out["plain_512"] = {"us_per_image": ms * 1e3, "gpairs_s": pairs_of(512, 512, offs) / (ms * 1e-3) / 1e9}
         # Multispectral bands.
-        with ThreadPoolExecutor(8) as ex:
-            bands = list(ex.map(S.multispectral_band, range(8)))
-        offs = S.MULTISPECTRAL_OFFSETS
-        spec = [dict(image=torch.from_numpy(b).cuda(local), levels=32, offsets=offs, flags=G.GLCM_SYMMETRIC,
-                     normalized=True, features=True) for b in bands]
-        prepared = ctx.prepare(spec)
-        ms = _timed(stream, lambda: ctx.run(prepared))
-        pairs = 8 * pairs_of(8192, 8192, offs)
-        out["multispectral_8x8192_u16"] = {"ms_per_batch": ms, "gpairs_s": pairs / (ms * 1e-3) / 1e9,
-                                           "hbm_read_gbs": 8 * 8192 * 8192 * 2 / (ms * 1e-3) / 1e9}
-        del spec, prepared, bands
+        if want("multispectral"):
+            with ThreadPoolExecutor(8) as ex:
+                bands = list(ex.map(S.multispectral_band, range(8)))
+            offs = S.MULTISPECTRAL_OFFSETS
+            spec = [dict(image=torch.from_numpy(b).cuda(local), levels=32, offsets=offs, flags=G.GLCM_SYMMETRIC,
+                         normalized=True, features=True) for b in bands]
+            prepared = ctx.prepare(spec)
+            ms = _timed(stream, lambda: ctx.run(prepared))
+            pairs = 8 * pairs_of(8192, 8192, offs)
+            out["multispectral_8x8192_u16"] = {"ms_per_batch": ms, "gpairs_s": pairs / (ms * 1e-3) / 1e9,
+                                               "hbm_read_gbs": 8 * 8192 * 8192 * 2 / (ms * 1e-3) / 1e9}
+            del spec, prepared, bands
         # Sliding-window texture maps.
         wimg = torch.from_numpy(S.window_image()).cuda(local)
         offs = S.CONTENTION_OFFSETS
@@ -467,26 +486,34 @@ def other_workloads(G, S, torch, local: int):
         cw = torch.empty((509, 509, 4, 16, 16), dtype=torch.int32, device=f"cuda:{local}")
         mw = torch.empty((4, 4, 509, 509), dtype=torch.float32, device=f"cuda:{local}")
         src, w, h, pitch, dt = G.image_args(wimg)
-        ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
-                                                    G.GLCM_SYMMETRIC, cw, mw))
         wp = nw * sum((15 - abs(dx)) * (15 - abs(dy)) for dx, dy in offs)
-        out["windows_2048_15x15_s4"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3), "gpairs_s": wp / (ms * 1e-3) / 1e9}
+        if want("windows"):
+            ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
+                                                        G.GLCM_SYMMETRIC, cw, mw))
+            out["windows_2048_15x15_s4"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3),
+                                            "gpairs_s": wp / (ms * 1e-3) / 1e9}
         # Gray-level histogram of a 16384^2 uint8 image (268 MB, above L2), N = 256.
-        himg = torch.from_numpy(S.iid(S.BASE_SEED + 900, 16384, 16384, np.uint8)).cuda(local)
-        hh = torch.empty(256, dtype=torch.int32, device=f"cuda:{local}")
-        hsrc, hw, hhgt, hpitch, hdt = G.image_args(himg)
-        ms = _timed(stream, lambda: G.glcm_histogram(ctx.ctx, hsrc, hw, hhgt, hpitch, hdt, 256, 0, hh))
-        hpeak, hkind = load_peaks()
-        gbs = 16384 * 16384 / (ms * 1e-3) / 1e9
-        out["histogram_16384_u8_n256"] = {"ms": ms, "gpixels_s": gbs, "hbm_read_gbs": gbs,
-                                          "frac_of_hbm": gbs / hpeak, "peak_kind": f"{hkind} hbm_gbs (copy)"}
-        del himg, hh
+        if want("histogram"):
+            himg = torch.from_numpy(S.iid(S.BASE_SEED + 900, 16384, 16384, np.uint8)).cuda(local)
+            hh = torch.empty(256, dtype=torch.int32, device=f"cuda:{local}")
+            hsrc, hw, hhgt, hpitch, hdt = G.image_args(himg)
+            ms = _timed(stream, lambda: G.glcm_histogram(ctx.ctx, hsrc, hw, hhgt, hpitch, hdt, 256, 0, hh))
+            hpeak, hkind = load_peaks()
+            gbs = 16384 * 16384 / (ms * 1e-3) / 1e9
+            out["histogram_16384_u8_n256"] = {"ms": ms, "gpixels_s": gbs, "hbm_read_gbs": gbs,
+                                              "frac_of_hbm": gbs / hpeak, "peak_kind": f"{hkind} hbm_gbs (copy)"}
+            del himg, hh
         # The same maps without the per-window counts (1.06 GB not written).
-        ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
-                                                    G.GLCM_SYMMETRIC, None, mw))
-        out["windows_2048_15x15_s4_maps_only"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3),
-                                                  "gpairs_s": wp / (ms * 1e-3) / 1e9}
+        if want("windows"):
+            ms = _timed(stream, lambda: G.glcm_windows(ctx.ctx, src, w, h, pitch, dt, 16, 15, 4, offs,
+                                                        G.GLCM_SYMMETRIC, None, mw))
+            out["windows_2048_15x15_s4_maps_only"] = {"ms": ms, "windows_per_s": nw / (ms * 1e-3),
+                                                      "gpairs_s": wp / (ms * 1e-3) / 1e9}
         del cw, mw
+        if not want("uneven"):
+            stream.synchronize()
+            ctx.close()
+            return out
         # 1000 uneven images.
         recipe = S.uneven_batch()
         with ThreadPoolExecutor(8) as ex:
@@ -612,6 +639,8 @@ def main():
                     help="seconds of the all-core oracle run beside the 1-thread one (0: skip)")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the other workload shapes")
+    ap.add_argument("--extra", default="", help="comma-separated subset of the other workload shapes to run: "
+                    + ", ".join(EXTRA_LEGS) + " (default: all)")
     ap.add_argument("--no-tune", action="store_true", help="use the planner's default vote configurations")
     ap.add_argument("--no-classes", action="store_true", help="skip the per-class single-image lines")
     ap.add_argument("--no-ceilings", action="store_true", help="skip the shared-reduction / HBM ceilings")
@@ -775,7 +804,11 @@ def main():
     if not args.no_serving:
         line["serving"] = serving_leg(G, S, torch, local)
     if not args.no_extra:
-        line["other_workloads"] = other_workloads(G, S, torch, local)
+        only = {x for x in args.extra.split(",") if x} or None
+        bad = sorted(only - set(EXTRA_LEGS)) if only else []
+        if bad:
+            raise SystemExit(f"unknown --extra leg(s): {bad}")
+        line["other_workloads"] = other_workloads(G, S, torch, local, only)
     parity = None
     if not args.no_cpu_baseline and world == 1:
         # The oracle, first on the timed batch's own results (untimed), then timed.

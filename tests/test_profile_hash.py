@@ -1,6 +1,7 @@
-"""The benchmark reports the vote kernel's DRAM traffic from the committed ncu
-summary only while the kernel's code is the code that was captured: the hash
-ignores // comments and blank lines, and any code change invalidates it."""
+"""The benchmark reports the vote kernels' DRAM traffic from the committed ncu
+summary only while their code is the code that was captured: the hash covers
+every vote source, ignores // comments and blank lines, and any code change
+invalidates it."""
 import os
 import sys
 
@@ -19,8 +20,7 @@ def test_code_hash_ignores_comments_only():
 def test_traffic_reported_only_for_the_captured_code(tmp_path, monkeypatch):
     """profiled_traffic() gives the summary's figure when its hash is the
     current source's, and None (traffic unknown) once the code has changed."""
-    src = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc", "vote.cu")
-    good = bench.code_sha256(open(src).read())
+    good = bench.vote_code_sha256()
     prof = tmp_path / "profiles"
     prof.mkdir()
     (prof / "cur.md").write_text(f"traffic_bytes_per_step: 1234\nvote_code_sha256: {good}\n")
@@ -36,3 +36,10 @@ def test_traffic_reported_only_for_the_captured_code(tmp_path, monkeypatch):
     assert bench.profiled_traffic("cur.md") == 1234.0
     assert bench.profiled_traffic("old.md") is None
     assert bench.profiled_traffic("missing.md") is None
+
+
+def test_vote_hash_covers_every_vote_source():
+    csrc = os.path.join(ROOT, "paper_1710_06189_gb300", "csrc")
+    for f in bench.VOTE_SOURCES:
+        assert os.path.exists(os.path.join(csrc, f)), f
+    assert set(bench.VOTE_SOURCES) >= {"vote.cu", "vote_fast.cuh"}
