@@ -1011,7 +1011,7 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         fp.max_hist_words = c.max_hist_words;
         fp.chunk_counter = ctx->d_words + 2 + ci;
         fp.err = ctx->d_words;
-        const size_t fsmem = vote_fast_smem_bytes(c.max_hist_words);
+        const size_t fsmem = vote_fast_smem_bytes(c.max_hist_words, c.log2n);
         int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve);
         if (plan.max_ctas > 0)
             ctas = std::min(ctas, plan.max_ctas);

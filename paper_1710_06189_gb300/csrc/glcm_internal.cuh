@@ -232,7 +232,7 @@ cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, siz
 // has them).
 cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, bool aligned, int grid, size_t smem,
                              cudaStream_t s);
-size_t vote_fast_smem_bytes(int max_hist_words);
+size_t vote_fast_smem_bytes(int max_hist_words, int log2n);
 int vote_fast_hist_words(int log2n, int mode);
 // The column-walk kernel for rows at any byte address (vote_fast_unaligned.cu).
 const void* vote_fast_kernel_unaligned(int bpp, int log2n);

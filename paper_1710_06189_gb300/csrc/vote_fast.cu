@@ -37,10 +37,12 @@ int vote_fast_hist_words(int log2n, int mode)
 }
 
 // Dynamic shared memory of a launch whose largest job histogram has
-// max_hist_words words (the joint merge's marginals follow it).
-size_t vote_fast_smem_bytes(int max_hist_words)
+// max_hist_words words (the joint merge's marginals follow it): room to
+// align the histograms (fast_align), the histograms, the marginals, the
+// chunk index.
+size_t vote_fast_smem_bytes(int max_hist_words, int log2n)
 {
-    return (size_t)(max_hist_words + kMargWords) * 4 + 16;  // + the chunk index
+    return (size_t)fast_align(log2n) + (size_t)(max_hist_words + kMargWords) * 4 + 16;
 }
 
 cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, bool aligned, int grid, size_t smem,

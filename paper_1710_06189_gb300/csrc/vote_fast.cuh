@@ -68,6 +68,14 @@ constexpr int kFW = kFT / 32;       // warps per CTA
 constexpr int kPF = 4;              // rows in flight per lane
 constexpr int kMargWords = 4 * 64;  // joint-code merge: 4 offsets x N^2 (N <= 8)
 static_assert(kMargWords >= 32, "N = 256 jobs use the first 32 marginal words as spare words");
+
+// Alignment of the histograms' shared address: 64 KB for N = 16 (a byte
+// code's vote address is one byte permute with the region's upper bytes),
+// else 256 bytes (the base folded into 16-bit codes).
+__host__ __device__ constexpr uint32_t fast_align(int log2n)
+{
+    return log2n == 4 ? 65536u : 256u;
+}
 // 16-bit halves: anchor rows a lane may vote between merges (16 votes per
 // row into one copy at most: 4000 * 16 < 65536).
 constexpr unsigned kHalfRows = 4000;
@@ -86,20 +94,22 @@ __device__ __forceinline__ void red1_if(uint32_t a, uint32_t mask, uint32_t bit)
         "r"(mask), "r"(bit));
 }
 
-// N = 256: reduction at hb + rel if rel, the byte offset of the code within
-// the job's 128 rows, lies inside them (unsigned: codes of the other half
-// fall below or above); else into `spare`, the lane's own word past the rows
-// (never read).  No predicate: a predicated reduction whose predicate differs
-// between lanes costs a divergent branch around it.
-__device__ __forceinline__ void red_row(uint32_t hb, uint32_t rel, uint32_t spare)
+// N = 256: reduction at address a (hb + the byte offset of the code within
+// the job's 128 rows, hb < 131072) if it lies inside the rows, else into
+// `spare`, the lane's own word past the rows (never read).  A code of the
+// other half lies above the spare words, or -- for the upper half's job --
+// below hb, which wraps around to above them (unsigned); so one min picks.
+// No predicate: a predicated reduction whose predicate differs between
+// lanes costs a divergent branch around it.
+__device__ __forceinline__ void red_row(uint32_t a, uint32_t spare)
 {
-    red1(hb + min(rel, spare));
+    red1(min(a, spare));
 }
 
 // ... and only if bit `bit` of the lane's anchor mask is set (edge strips).
-__device__ __forceinline__ void red_row_if(uint32_t hb, uint32_t rel, uint32_t spare, uint32_t mask, uint32_t bit)
+__device__ __forceinline__ void red_row_if(uint32_t a, uint32_t spare, uint32_t mask, uint32_t bit)
 {
-    red1(hb + ((mask & bit) ? min(rel, spare) : spare));
+    red1((mask & bit) ? min(a, spare) : spare);
 }
 
 __device__ __forceinline__ void red_hi(uint32_t a)
@@ -189,23 +199,26 @@ __device__ __forceinline__ void votes_joint(const uint32_t (&C)[LW], uint32_t CR
 {
     constexpr uint32_t M = (1u << LOG2N) + 1u, M2 = M * M;
     const uint32_t l4b = l4 + 128u;
+    // hb / 256 added to both 16-bit codes, so a byte permute gives the whole
+    // address hb + code * 256 + lane * 4 (hb is a multiple of 256).
+    const uint32_t hp = (hb >> 8) * 0x00010001u;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
         // Packed bytes j0*M + j1 <= N*M + N < 256: no carries between bytes.
         const uint32_t ta = partner<0>(m, C, CR, P, PL, PR) * M + partner<1>(m, C, CR, P, PL, PR);
         const uint32_t tb = partner<2>(m, C, CR, P, PL, PR) * M + partner<3>(m, C, CR, P, PL, PR);
-        const uint32_t alo = spread_lo(C[m]) * M2, ahi = spread_hi(C[m]) * M2;
+        const uint32_t alo = spread_lo(C[m]) * M2 + hp, ahi = spread_hi(C[m]) * M2 + hp;
         const uint32_t ca0 = alo + spread_lo(ta), ca1 = ahi + spread_hi(ta);
         const uint32_t cb0 = alo + spread_lo(tb), cb1 = ahi + spread_hi(tb);
-        // Byte offset code*256 + lane*4 (+128): the 16-bit code above the lane byte.
-        red1(hb + __byte_perm(ca0, l4, 0x5104));
-        red1(hb + __byte_perm(cb0, l4b, 0x5104));
-        red1(hb + __byte_perm(ca0, l4, 0x5324));
-        red1(hb + __byte_perm(cb0, l4b, 0x5324));
-        red1(hb + __byte_perm(ca1, l4, 0x5104));
-        red1(hb + __byte_perm(cb1, l4b, 0x5104));
-        red1(hb + __byte_perm(ca1, l4, 0x5324));
-        red1(hb + __byte_perm(cb1, l4b, 0x5324));
+        // Address hb + code*256 + lane*4 (+128): the 16-bit code above the lane byte.
+        red1(__byte_perm(ca0, l4, 0x5104));
+        red1(__byte_perm(cb0, l4b, 0x5104));
+        red1(__byte_perm(ca0, l4, 0x5324));
+        red1(__byte_perm(cb0, l4b, 0x5324));
+        red1(__byte_perm(ca1, l4, 0x5104));
+        red1(__byte_perm(cb1, l4b, 0x5104));
+        red1(__byte_perm(ca1, l4, 0x5324));
+        red1(__byte_perm(cb1, l4b, 0x5324));
     }
 }
 
@@ -237,15 +250,17 @@ __device__ __forceinline__ void votes_one16(const uint32_t (&A16)[LW], const uin
                                             const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
                                             uint32_t l4, uint32_t mask)
 {
-    const uint32_t base = hb + (uint32_t)(K >> 1) * 65536u;
-    const uint32_t lq = l4 + (uint32_t)(K & 1) * 128u;
+    // hb is a multiple of 65536 here: the region's address hb + (K >> 1) *
+    // 65536 has a zero low half, so one byte permute of the code byte, the
+    // lane byte and the region's upper bytes gives the whole address.
+    const uint32_t x = hb + (uint32_t)(K >> 1) * 65536u + l4 + (uint32_t)(K & 1) * 128u;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
         const uint32_t code = A16[m] | partner<K>(m, C, CR, P, PL, PR);
-        const uint32_t a0 = base + __byte_perm(code, lq, 0x5504);
-        const uint32_t a1 = base + __byte_perm(code, lq, 0x5514);
-        const uint32_t a2 = base + __byte_perm(code, lq, 0x5524);
-        const uint32_t a3 = base + __byte_perm(code, lq, 0x5534);
+        const uint32_t a0 = __byte_perm(code, x, 0x7604);
+        const uint32_t a1 = __byte_perm(code, x, 0x7614);
+        const uint32_t a2 = __byte_perm(code, x, 0x7624);
+        const uint32_t a3 = __byte_perm(code, x, 0x7634);
         // In an edge strip only a few words have a masked-out anchor: the
         // others take the unmasked votes, decided for the whole warp.
         if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
@@ -274,10 +289,11 @@ __device__ __forceinline__ void votes_one32(const uint32_t (&Alo)[LW], const uin
     for (int m = 0; m < LW; ++m) {
         const uint32_t w = partner<K>(m, C, CR, P, PL, PR);
         const uint32_t c0 = Alo[m] + spread_lo(w), c1 = Ahi[m] + spread_hi(w);
-        const uint32_t a0 = hb + (__byte_perm(c0, l8, 0x5104) >> 1);
-        const uint32_t a1 = hb + (__byte_perm(c0, l8, 0x5324) >> 1);
-        const uint32_t a2 = hb + (__byte_perm(c1, l8, 0x5104) >> 1);
-        const uint32_t a3 = hb + (__byte_perm(c1, l8, 0x5324) >> 1);
+        // Alo / Ahi carry hb / 128: these are whole addresses.
+        const uint32_t a0 = __byte_perm(c0, l8, 0x5104) >> 1;
+        const uint32_t a1 = __byte_perm(c0, l8, 0x5324) >> 1;
+        const uint32_t a2 = __byte_perm(c1, l8, 0x5104) >> 1;
+        const uint32_t a3 = __byte_perm(c1, l8, 0x5324) >> 1;
         if (HI) {
             red_hi(a0);
             red_hi(a1);
@@ -324,20 +340,20 @@ __device__ __forceinline__ void votes_wide(int k, bool tr, const uint32_t (&C)[L
         const uint32_t col = tr ? C[m] : w;
         const uint32_t rw = tr ? w : C[m];
         const uint32_t slo = spread_lo(rw), shi = spread_hi(rw);
-        const uint32_t r0 = 4u * __byte_perm(col, slo, 0x5540) + rbase;
+        const uint32_t r0 = 4u * __byte_perm(col, slo, 0x5540) + rbase;  // hb + byte offset
         const uint32_t r1 = 4u * __byte_perm(col, slo, 0x5561) + rbase;
         const uint32_t r2 = 4u * __byte_perm(col, shi, 0x5542) + rbase;
         const uint32_t r3 = 4u * __byte_perm(col, shi, 0x5563) + rbase;
         if (EDGE && !__all_sync(0xffffffffu, ((mask >> (4 * m)) & 0xFu) == 0xFu)) {
-            red_row_if(hb, r0, spare, mask, 1u << (4 * m));
-            red_row_if(hb, r1, spare, mask, 1u << (4 * m + 1));
-            red_row_if(hb, r2, spare, mask, 1u << (4 * m + 2));
-            red_row_if(hb, r3, spare, mask, 1u << (4 * m + 3));
+            red_row_if(r0, spare, mask, 1u << (4 * m));
+            red_row_if(r1, spare, mask, 1u << (4 * m + 1));
+            red_row_if(r2, spare, mask, 1u << (4 * m + 2));
+            red_row_if(r3, spare, mask, 1u << (4 * m + 3));
         } else {
-            red_row(hb, r0, spare);
-            red_row(hb, r1, spare);
-            red_row(hb, r2, spare);
-            red_row(hb, r3, spare);
+            red_row(r0, spare);
+            red_row(r1, spare);
+            red_row(r2, spare);
+            red_row(r3, spare);
         }
     }
 }
@@ -375,12 +391,12 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
             votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
     } else if constexpr (LOG2N == 8) {
         // One offset and orientation per job, fixed for this loop instance.
-        const uint32_t rbase = 0u - 4u * 32768u * (uint32_t)j.row_half;
+        const uint32_t rbase = hb - 4u * 32768u * (uint32_t)j.row_half;
         const int k = (pr & 1) ? 0 : ((pr & 2) ? 1 : ((pr & 4) ? 2 : 3));
         if (top && k != 0)
             return;  // no row above the image's first row
         // Spare words: the lane's word of the 32 after the job's 32768.
-        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase, 131072u + l4,
+        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase, hb + 131072u + l4,
                              k == 2 ? em.in : (k == 3 ? em.left : em.right));
     } else if constexpr (LOG2N == 4) {
         uint32_t A16[LW];
@@ -402,8 +418,9 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         uint32_t Alo[LW], Ahi[LW];
 #pragma unroll
         for (int m = 0; m < LW; ++m) {
-            Alo[m] = spread_lo(C[m]) * M;
-            Ahi[m] = spread_hi(C[m]) * M;
+            // hb / 128 (hb a multiple of 256) added to both 16-bit codes.
+            Alo[m] = spread_lo(C[m]) * M + (hb >> 7) * 0x00010001u;
+            Ahi[m] = spread_hi(C[m]) * M + (hb >> 7) * 0x00010001u;
         }
         const uint32_t l8 = 2u * l4;
         const int hk = j.half_hi;
@@ -726,15 +743,25 @@ template <int BPP, int LOG2N, bool ALIGNED>
 __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
 {
     extern __shared__ __align__(16) uint32_t sh[];
-    uint32_t* marg = sh + p.max_hist_words;
+    // The histograms start at a shared address that is a multiple of
+    // fast_align(LOG2N), so that vote addresses need no add (see the votes).
+    const uint32_t base0 = (uint32_t)__cvta_generic_to_shared(sh);
+    const uint32_t pad = (fast_align(LOG2N) - (base0 & (fast_align(LOG2N) - 1u))) & (fast_align(LOG2N) - 1u);
+    uint32_t* hist = sh + pad / 4u;
+    const uint32_t hb = base0 + pad;
+    if (LOG2N == 8 && hb >= 131072u) {  // the N = 256 votes' wrap-around needs hb < 128 KB
+        if (threadIdx.x == 0)
+            atomicOr(p.err, kErrInternal);
+        return;
+    }
+    uint32_t* marg = hist + p.max_hist_words;
     int* s_chunk = reinterpret_cast<int*>(marg + kMargWords);
     {
-        uint4* z = reinterpret_cast<uint4*>(sh);
+        uint4* z = reinterpret_cast<uint4*>(hist);
         for (int i = threadIdx.x; i < (p.max_hist_words + kMargWords) / 4; i += kFT)
             z[i] = make_uint4(0u, 0u, 0u, 0u);
     }
     __syncthreads();
-    const uint32_t hb = (uint32_t)__cvta_generic_to_shared(sh);
     const int warp = threadIdx.x >> 5;
     int cur = -1;
     unsigned acc_rows = 0;
@@ -751,7 +778,7 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
         const FastJob j = p.jobs[ch.x];
         const unsigned rows_w = (unsigned)((ch.z - ch.y + kFW - 1) / kFW) * (unsigned)(j.band + 1);
         if (cur >= 0 && (cur != ch.x || (j.mode == kFastHalf && acc_rows + rows_w > kHalfRows))) {
-            flush_t<LOG2N>(p.jobs[cur], sh, marg);
+            flush_t<LOG2N>(p.jobs[cur], hist, marg);
             __syncthreads();
             cur = -1;
         }
@@ -771,7 +798,7 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
         __syncthreads();
     }
     if (cur >= 0)
-        flush_t<LOG2N>(p.jobs[cur], sh, marg);
+        flush_t<LOG2N>(p.jobs[cur], hist, marg);
     if (LOG2N == 8 && threadIdx.x == 0)
         asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");  // the bulk reductions have landed
 }
