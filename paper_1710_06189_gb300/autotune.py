@@ -32,18 +32,25 @@ def class_key(levels: int, n_offsets: int, dtype: int) -> str:
 
 
 def _time_config(ctx, images, levels, offsets, flags, reps):
-    """Summed vote-kernel milliseconds per pass over `images` (device tensors)."""
-    import torch
-    outs = [torch.empty((len(offsets), levels, levels), dtype=torch.int32, device=im.device) for im in images]
-    for im, out in zip(images, outs):  # warm-up (plans, attributes)
-        ctx.compute(im, levels, offsets, flags, out=out)
+    """Vote-kernel milliseconds per pass over `images` (device tensors), run as
+    one batch -- the way a batch of the class's images votes: one launch for
+    all of them, its chunks spread over the GPU -- from a prepared (and after
+    its first run, graph-captured) batch."""
+    prepared = ctx.prepare([dict(image=im, levels=levels, offsets=offsets, flags=flags) for im in images])
+    ctx.run(prepared)  # plan, attributes, capture
     ctx.synchronize()
     B.glcm_get_timing(ctx.ctx, reset=True)
     for _ in range(reps):
-        for im, out in zip(images, outs):
-            ctx.compute(im, levels, offsets, flags, out=out)
+        ctx.run(prepared)
+    ctx.synchronize()
     ms, _, _ = B.glcm_get_timing(ctx.ctx, reset=True)
     return ms / max(1, reps)
+
+
+# A band height other than the planner's own choice (0) must be this much
+# faster to be kept: the planner cuts bands for each launch's CTA count, a
+# fixed height only for the tuning run's.
+BAND_MARGIN = 0.03
 
 
 def tune(ctx, images, levels: int, offsets, flags: int = 0, reps: int = 3, candidates=DEFAULT_CANDIDATES):
@@ -78,11 +85,86 @@ def tune(ctx, images, levels: int, offsets, flags: int = 0, reps: int = 3, candi
         ms = _time_config(ctx, images, levels, offsets, flags, reps)
         tried.append({"threads": best["threads"], "log2_copies": best["log2_copies"], "layout": best["layout"],
                       "band_rows": band, "ms": ms})
-        if ms < best["ms"]:
+        if ms < best["ms"] * (1.0 - BAND_MARGIN):
             best = tried[-1]
     B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"], best["layout"],
                            best["band_rows"])
     return dict(best, tried=tried)
+
+
+def _time_batch(ctx, prepared, reps):
+    """Milliseconds of one run of a prepared batch: `reps` back-to-back graph
+    replays between two synchronizations of the context's stream (wall clock;
+    the replays queue on the GPU, so their launches overlap the work), after
+    one untimed run that captures the graph for the current configuration."""
+    import time
+    ctx.run(prepared)
+    ctx.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        ctx.run(prepared)
+    ctx.synchronize()
+    return (time.perf_counter() - t0) * 1e3 / max(1, reps)
+
+
+# A configuration replaces the incumbent of its class only if the whole
+# batch gets at least this much faster.
+BATCH_MARGIN = 0.01
+
+
+def tune_batch(ctx, jobs, reps: int = 5, candidates=DEFAULT_CANDIDATES, cache: "TuneCache | None" = None,
+               gpu: str = ""):
+    """Tune every vote class of a batch on the batch itself: for one class at
+    a time (the others at their incumbents), every feasible (threads, copies,
+    layout) and then the winner's band heights are timed as the whole
+    prepared batch (`jobs`: the dicts of Context.prepare), so a class is tuned
+    in the launch shape it has in that batch (e.g. on the SMs a split batch
+    leaves to it).  The incumbent is the planner's default; a candidate
+    replaces it only if the batch is BATCH_MARGIN faster.  Returns {class key:
+    chosen config} and applies the choices to ctx."""
+    from . import image_args
+    classes = {}
+    for j in jobs:
+        dtype = image_args(j["image"])[4]
+        classes[(j["levels"], len(j["offsets"]), dtype)] = True
+    prepared = ctx.prepare(jobs)
+    chosen = {}
+    for (levels, n_off, dtype) in classes:
+        key = class_key(levels, n_off, dtype)
+        if cache is not None and cache.apply(ctx, gpu, levels, n_off, dtype):
+            chosen[key] = cache.get(gpu, key)
+            continue
+        B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, 0, 0, 0, 0)  # planner default
+        best = {"threads": 0, "log2_copies": 0, "layout": 0, "band_rows": 0,
+                "ms": _time_batch(ctx, prepared, reps)}
+        default_ms = best["ms"]
+        for threads, r, layout in candidates:
+            try:
+                B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, threads, r, layout, 0)
+            except B.GlcmError:
+                continue
+            ms = _time_batch(ctx, prepared, reps)
+            if ms < best["ms"] * (1.0 - BATCH_MARGIN):
+                best = {"threads": threads, "log2_copies": r, "layout": layout, "band_rows": 0, "ms": ms}
+        if best["threads"]:
+            for band in BAND_CANDIDATES[4 if best["layout"] == 4 else "general"][1:]:
+                try:
+                    B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"],
+                                           best["layout"], band)
+                except B.GlcmError:
+                    continue
+                ms = _time_batch(ctx, prepared, reps)
+                if ms < best["ms"] * (1.0 - BATCH_MARGIN):
+                    best = dict(best, band_rows=band, ms=ms)
+        B.glcm_set_vote_config(ctx.ctx, levels, n_off, dtype, best["threads"], best["log2_copies"],
+                               best["layout"], best["band_rows"])
+        best["default_ms"] = default_ms
+        chosen[key] = best
+        if cache is not None:
+            cache.put(gpu, key, best)
+    if cache is not None:
+        cache.save()
+    return chosen
 
 
 class TuneCache:

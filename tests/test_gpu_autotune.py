@@ -38,3 +38,24 @@ def test_tune_applies_an_exact_config(gctx, n, tmp_path):
             ctx2.close()
     finally:
         ctx.close()
+
+
+def test_tune_batch_on_the_batch_itself(tmp_path):
+    """tune_batch times whole runs of a mixed batch per class and candidate;
+    every class gets a config (the planner's default when nothing beats it by
+    the margin), and the batch stays bit-exact under the chosen configs."""
+    C4 = S.CONTENTION_OFFSETS
+    specs = [("iid", 8), ("smooth", 16), ("iid", 256), ("smooth", 256)]
+    imgs = [S.image(k, 40 + n, 256, 640, np.uint8, sigma=8.0) for k, n in specs]
+    with G.Context(0, hbm_budget_bytes=2 << 30) as ctx:
+        jobs = [dict(image=torch.from_numpy(im).cuda(), levels=n, offsets=C4, flags=G.GLCM_SYMMETRIC,
+                     features=True) for im, (_, n) in zip(imgs, specs)]
+        cache = autotune.TuneCache(str(tmp_path / "b.json"))
+        chosen = autotune.tune_batch(ctx, jobs, reps=2, cache=cache, gpu="test")
+        assert set(chosen) == {autotune.class_key(n, 4, G.GLCM_U8) for n in (8, 16, 256)}
+        for cfg in chosen.values():
+            assert cfg["ms"] > 0 and cfg["ms"] <= cfg["default_ms"] * 1.0001
+        outs = ctx.batch(jobs)
+        torch.cuda.synchronize()
+        for im, (_, n), (c, _, _) in zip(imgs, specs, outs):
+            assert np.array_equal(to_u32(c), oracle.glcm(im, n, C4))
