@@ -53,6 +53,7 @@ struct GraphEntry {
 struct FastClass {
     int bpp = 1, log2n = 1;
     bool aligned = true;  // every row of every job starts on 16 bytes
+    int max_dist = 1;     // largest partner distance of the class's jobs (row rings when > 1)
     std::vector<FastJob> jobs;
     std::vector<int3> chunks;  // (class-local job, first item, end item)
     int n_items = 0;
@@ -478,10 +479,14 @@ int plan_image_general(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, const 
 // Canonical offset (0: (1, 0), 1: (1, -1), 2: (0, -1), 3: (-1, -1)) of an
 // offset at chessboard distance 1 and whether it is the opposite one (its
 // counts are the canonical counts transposed); -1 for any other offset.
-int canonical_d1(int dx, int dy, bool& transposed)
+// Canonical offset of the column walk: (D, 0) -> 0, (D, -D) -> 1, (0, -D) -> 2,
+// (-D, -D) -> 3 at a distance D of 1 .. 4, or the opposite of one (its
+// counts are the transpose); -1 for any other offset.  dist: D.
+int canonical_fast(int dx, int dy, int& dist, bool& transposed)
 {
     transposed = false;
-    if (std::max(std::abs(dx), std::abs(dy)) != 1)
+    dist = std::max(std::abs(dx), std::abs(dy));
+    if (dist < 1 || dist > 4 || (dx != 0 && std::abs(dx) != dist) || (dy != 0 && std::abs(dy) != dist))
         return -1;
     if (dy > 0 || (dy == 0 && dx < 0)) {
         dx = -dx;
@@ -490,7 +495,7 @@ int canonical_d1(int dx, int dy, bool& transposed)
     }
     if (dy == 0)
         return 0;
-    return dx == 1 ? 1 : (dx == 0 ? 2 : 3);
+    return dx == dist ? 1 : (dx == 0 ? 2 : 3);
 }
 
 FastClass& fast_class(VotePlan& plan, int bpp, int log2n, bool aligned)
@@ -529,8 +534,8 @@ constexpr int kFastChunkItems = 16;
 // (slot / slot_t: the output GLCMs of each canonical offset as counted and
 // transposed).  Items and chunks are made by finalize_fast; a band height
 // configured for the class (the autotuner's tile shape) is kept.
-void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int present, const int (&slot)[4],
-                     const int (&slot_t)[4])
+void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int dist, int present,
+                     const int (&slot)[4], const int (&slot_t)[4])
 {
     int band_override = 0;
     {
@@ -601,8 +606,10 @@ void plan_image_fast(const glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, in
         j.band = band_override;  // 0: set by finalize_fast
         j.y_begin = s.y_begin;
         j.y_end = s.y_end;
+        j.dist = dist;
         j.out = s.out;
         fc.max_hist_words = std::max(fc.max_hist_words, j.hist_words);
+        fc.max_dist = std::max(fc.max_dist, dist);
         fc.jobs.push_back(j);
     }
 }
@@ -682,22 +689,29 @@ int plan_image(glcm_ctx* ctx, const ImageSpec& s, VotePlan& plan, int target_ite
                           !s.levels_mode && s.y_end > s.y_begin;
     (void)aligned;  // rows at any byte address are realigned by the kernel
     std::vector<int> gen;
-    int present = 0;
-    int slot[4] = {-1, -1, -1, -1}, slot_t[4] = {-1, -1, -1, -1};
+    // Column-walk offsets grouped by distance D (index D - 1): one set of
+    // jobs per distance.
+    int present[4] = {0, 0, 0, 0};
+    int slot[4][4], slot_t[4][4];
+    for (int d = 0; d < 4; ++d)
+        for (int c = 0; c < 4; ++c)
+            slot[d][c] = slot_t[d][c] = -1;
     for (int k = 0; k < s.n_off; ++k) {
         bool tr = false;
-        const int c = eligible ? canonical_d1(s.offsets[k].dx, s.offsets[k].dy, tr) : -1;
-        int* dst = c < 0 ? nullptr : (tr ? &slot_t[c] : &slot[c]);
+        int dist = 0;
+        const int c = eligible ? canonical_fast(s.offsets[k].dx, s.offsets[k].dy, dist, tr) : -1;
+        int* dst = c < 0 ? nullptr : (tr ? &slot_t[dist - 1][c] : &slot[dist - 1][c]);
         if (dst && *dst < 0) {
             *dst = k;
-            present |= 1 << c;
+            present[dist - 1] |= 1 << c;
         } else {
             gen.push_back(k);  // any other offset, or a repeat of one already placed
         }
     }
     (void)target_items;
-    if (present)
-        plan_image_fast(ctx, s, plan, present, slot, slot_t);
+    for (int d = 0; d < 4; ++d)
+        if (present[d])
+            plan_image_fast(ctx, s, plan, d + 1, present[d], slot[d], slot_t[d]);
     if (s.flat) {
         // Flat-wrap: the pairs whose partner column leaves [0, W), added after the votes.
         const long long nn = (long long)s.levels * s.levels;
@@ -1011,7 +1025,8 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         fp.max_hist_words = c.max_hist_words;
         fp.chunk_counter = ctx->d_words + 2 + ci;
         fp.err = ctx->d_words;
-        const size_t fsmem = vote_fast_smem_bytes(c.max_hist_words, c.log2n);
+        fp.ring_words = c.max_dist > 1 ? c.max_dist * (4 / c.bpp + 1) * 32 : 0;
+        const size_t fsmem = vote_fast_smem_bytes(c.max_hist_words, c.log2n, fp.ring_words);
         int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve);
         if (plan.max_ctas > 0)
             ctas = std::min(ctas, plan.max_ctas);

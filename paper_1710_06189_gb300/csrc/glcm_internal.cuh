@@ -117,6 +117,7 @@ struct FastJob {
     int n_strips;
     int band;
     int y_begin, y_end;  // anchor rows voted by this job
+    int dist;          // partner distance D (1 .. 4): offsets (D, 0), (D, -D), (0, -D), (-D, -D)
     uint32_t* out;     // counts: GLCM s at out + s*N*N
 };
 
@@ -127,6 +128,7 @@ struct FastParams {
     int max_hist_words;
     unsigned* chunk_counter;  // zeroed before each launch
     unsigned* err;
+    int ring_words;           // shared words per warp for the row rings of distances > 1 (0: none)
 };
 
 // Flat-wrap pairs of one offset (GLCM_FLAT_WRAP): the anchors of rows
@@ -232,7 +234,7 @@ cudaError_t launch_vote(const VoteParams& p, int bpp, int grid, int threads, siz
 // has them).
 cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, bool aligned, int grid, size_t smem,
                              cudaStream_t s);
-size_t vote_fast_smem_bytes(int max_hist_words, int log2n);
+size_t vote_fast_smem_bytes(int max_hist_words, int log2n, int ring_words);
 int vote_fast_hist_words(int log2n, int mode);
 // The column-walk kernel for rows at any byte address (vote_fast_unaligned.cu).
 const void* vote_fast_kernel_unaligned(int bpp, int log2n);

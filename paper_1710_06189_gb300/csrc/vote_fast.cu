@@ -39,10 +39,12 @@ int vote_fast_hist_words(int log2n, int mode)
 // Dynamic shared memory of a launch whose largest job histogram has
 // max_hist_words words (the joint merge's marginals follow it): room to
 // align the histograms (fast_align), the histograms, the marginals, the
-// chunk index.
-size_t vote_fast_smem_bytes(int max_hist_words, int log2n)
+// chunk index, and ring_words per warp of row rings (distances > 1; for
+// N = 16 the rings lie in the alignment padding).
+size_t vote_fast_smem_bytes(int max_hist_words, int log2n, int ring_words)
 {
-    return (size_t)fast_align(log2n) + (size_t)(max_hist_words + kMargWords) * 4 + 16;
+    const size_t rings = fast_align(log2n) == 65536u ? 0 : (size_t)ring_words * kFW * 4;
+    return (size_t)fast_align(log2n) + (size_t)(max_hist_words + kMargWords) * 4 + 16 + rings;
 }
 
 cudaError_t launch_vote_fast(const FastParams& p, int bpp, int log2n, bool aligned, int grid, size_t smem,

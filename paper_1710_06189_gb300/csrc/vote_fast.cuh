@@ -172,20 +172,35 @@ __device__ __forceinline__ uint32_t qword(uint32_t a, uint32_t b)
         return (__byte_perm(a, b, 0x7531) >> S) & MK;
 }
 
-// Partner words of anchor word m of the current row C (left/right edge
-// words CL, CR) and previous row P (PL, PR) for canonical offset K.
+// Partner words of anchor word m of the current row C (right edge word CR)
+// and the row D above, P (edge words PL, PR), for canonical offset K at
+// distance D: (D, 0), (D, -D), (0, -D), (-D, -D).  sr / sl are the byte
+// permutes that shift a word pair D pixels right / left (right_sel(D),
+// left_sel(D)); D <= 4, so a partner never lies beyond the neighbour word.
 template <int K, int LW>
 __device__ __forceinline__ uint32_t partner(int m, const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                            uint32_t PL, uint32_t PR)
+                                            uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl)
 {
     if constexpr (K == 0)
-        return __byte_perm(C[m], m + 1 < LW ? C[m + 1] : CR, 0x4321);
+        return __byte_perm(C[m], m + 1 < LW ? C[m + 1] : CR, sr);
     else if constexpr (K == 1)
-        return __byte_perm(P[m], m + 1 < LW ? P[m + 1] : PR, 0x4321);
+        return __byte_perm(P[m], m + 1 < LW ? P[m + 1] : PR, sr);
     else if constexpr (K == 2)
         return P[m];
     else
-        return __byte_perm(m > 0 ? P[m - 1] : PL, P[m], 0x6543);
+        return __byte_perm(m > 0 ? P[m - 1] : PL, P[m], sl);
+}
+
+// Byte-permute selectors: bytes D .. D + 3 of the pair (w, next word), and
+// bytes 4 - D .. 7 - D of the pair (previous word, w).
+__device__ __forceinline__ uint32_t right_sel(uint32_t D)
+{
+    return D * 0x1111u + 0x3210u;
+}
+
+__device__ __forceinline__ uint32_t left_sel(uint32_t D)
+{
+    return 0x7654u - D * 0x1111u;
 }
 
 // ---- votes of one row ------------------------------------------------------
@@ -195,7 +210,7 @@ __device__ __forceinline__ uint32_t partner(int m, const uint32_t (&C)[LW], uint
 // the (j2, j3) copies.
 template <int LW, int LOG2N>
 __device__ __forceinline__ void votes_joint(const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                            uint32_t PL, uint32_t PR, uint32_t hb, uint32_t l4)
+                                            uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb, uint32_t l4)
 {
     constexpr uint32_t M = (1u << LOG2N) + 1u, M2 = M * M;
     const uint32_t l4b = l4 + 128u;
@@ -205,8 +220,8 @@ __device__ __forceinline__ void votes_joint(const uint32_t (&C)[LW], uint32_t CR
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
         // Packed bytes j0*M + j1 <= N*M + N < 256: no carries between bytes.
-        const uint32_t ta = partner<0>(m, C, CR, P, PL, PR) * M + partner<1>(m, C, CR, P, PL, PR);
-        const uint32_t tb = partner<2>(m, C, CR, P, PL, PR) * M + partner<3>(m, C, CR, P, PL, PR);
+        const uint32_t ta = partner<0>(m, C, CR, P, PL, PR, sr, sl) * M + partner<1>(m, C, CR, P, PL, PR, sr, sl);
+        const uint32_t tb = partner<2>(m, C, CR, P, PL, PR, sr, sl) * M + partner<3>(m, C, CR, P, PL, PR, sr, sl);
         const uint32_t alo = spread_lo(C[m]) * M2 + hp, ahi = spread_hi(C[m]) * M2 + hp;
         const uint32_t ca0 = alo + spread_lo(ta), ca1 = ahi + spread_hi(ta);
         const uint32_t cb0 = alo + spread_lo(tb), cb1 = ahi + spread_hi(tb);
@@ -226,7 +241,7 @@ __device__ __forceinline__ void votes_joint(const uint32_t (&C)[LW], uint32_t CR
 // M*M bin rows of 64 words; offset K & 1 uses words 32 (K & 1) .. + 31.
 template <int K, int LW, int LOG2N>
 __device__ __forceinline__ void votes_one8(const uint32_t (&A9)[LW], const uint32_t (&C)[LW], uint32_t CR,
-                                           const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                           const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb,
                                            uint32_t l4)
 {
     constexpr uint32_t M = (1u << LOG2N) + 1u;
@@ -234,7 +249,7 @@ __device__ __forceinline__ void votes_one8(const uint32_t (&A9)[LW], const uint3
     const uint32_t lq = l4 + (uint32_t)(K & 1) * 128u;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
-        const uint32_t code = A9[m] + partner<K>(m, C, CR, P, PL, PR);
+        const uint32_t code = A9[m] + partner<K>(m, C, CR, P, PL, PR, sr, sl);
         red1(base + __byte_perm(code, lq, 0x5504));
         red1(base + __byte_perm(code, lq, 0x5514));
         red1(base + __byte_perm(code, lq, 0x5524));
@@ -247,7 +262,7 @@ __device__ __forceinline__ void votes_one8(const uint32_t (&A9)[LW], const uint3
 // anchors whose bit is set in `mask` vote (bit 4m + b: byte b of word m).
 template <int K, int LW, bool EDGE>
 __device__ __forceinline__ void votes_one16(const uint32_t (&A16)[LW], const uint32_t (&C)[LW], uint32_t CR,
-                                            const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                            const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb,
                                             uint32_t l4, uint32_t mask)
 {
     // hb is a multiple of 65536 here: the region's address hb + (K >> 1) *
@@ -256,7 +271,7 @@ __device__ __forceinline__ void votes_one16(const uint32_t (&A16)[LW], const uin
     const uint32_t x = hb + (uint32_t)(K >> 1) * 65536u + l4 + (uint32_t)(K & 1) * 128u;
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
-        const uint32_t code = A16[m] | partner<K>(m, C, CR, P, PL, PR);
+        const uint32_t code = A16[m] | partner<K>(m, C, CR, P, PL, PR, sr, sl);
         const uint32_t a0 = __byte_perm(code, x, 0x7604);
         const uint32_t a1 = __byte_perm(code, x, 0x7614);
         const uint32_t a2 = __byte_perm(code, x, 0x7624);
@@ -283,11 +298,11 @@ __device__ __forceinline__ void votes_one16(const uint32_t (&A16)[LW], const uin
 template <int K, int LW, bool HI>
 __device__ __forceinline__ void votes_one32(const uint32_t (&Alo)[LW], const uint32_t (&Ahi)[LW],
                                             const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                            uint32_t PL, uint32_t PR, uint32_t hb, uint32_t l8)
+                                            uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb, uint32_t l8)
 {
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
-        const uint32_t w = partner<K>(m, C, CR, P, PL, PR);
+        const uint32_t w = partner<K>(m, C, CR, P, PL, PR, sr, sl);
         const uint32_t c0 = Alo[m] + spread_lo(w), c1 = Ahi[m] + spread_hi(w);
         // Alo / Ahi carry hb / 128: these are whole addresses.
         const uint32_t a0 = __byte_perm(c0, l8, 0x5104) >> 1;
@@ -311,12 +326,12 @@ __device__ __forceinline__ void votes_one32(const uint32_t (&Alo)[LW], const uin
 template <int K, int LW>
 __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[LW], const uint32_t (&Ahi)[LW],
                                                 const uint32_t (&C)[LW], uint32_t CR, const uint32_t (&P)[LW],
-                                                uint32_t PL, uint32_t PR, uint32_t hb, uint32_t l8)
+                                                uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb, uint32_t l8)
 {
     if (hi)
-        votes_one32<K, LW, true>(Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+        votes_one32<K, LW, true>(Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
     else
-        votes_one32<K, LW, false>(Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+        votes_one32<K, LW, false>(Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
 }
 
 // One offset k, N = 256: code x = row * 256 + column with row the anchor
@@ -327,10 +342,10 @@ __device__ __forceinline__ void votes_one32_sel(bool hi, const uint32_t (&Alo)[L
 // chosen per offset (warp-uniform selects, no branch per row).
 template <int LW, bool EDGE>
 __device__ __forceinline__ void votes_wide(int k, bool tr, const uint32_t (&C)[LW], uint32_t CR,
-                                           const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                           const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb,
                                            uint32_t rbase, uint32_t spare, uint32_t mask)
 {
-    const uint32_t sel = k == 3 ? 0x6543u : (k == 2 ? 0x3210u : 0x4321u);
+    const uint32_t sel = k == 3 ? sl : (k == 2 ? 0x3210u : sr);
 #pragma unroll
     for (int m = 0; m < LW; ++m) {
         const uint32_t cur = k == 0 ? C[m] : P[m];
@@ -367,13 +382,13 @@ struct EdgeMasks {
 
 template <int LW, int LOG2N, bool EDGE>
 __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[LW], uint32_t CR,
-                                         const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t hb,
+                                         const uint32_t (&P)[LW], uint32_t PL, uint32_t PR, uint32_t sr, uint32_t sl, uint32_t hb,
                                          uint32_t l4, bool top, const EdgeMasks& em)
 {
     const int pr = j.present;
     if constexpr (LOG2N <= 3) {
         if (j.mode == kFastJoint) {
-            votes_joint<LW, LOG2N>(C, CR, P, PL, PR, hb, l4);
+            votes_joint<LW, LOG2N>(C, CR, P, PL, PR, sr, sl, hb, l4);
             return;
         }
         constexpr uint32_t M = (1u << LOG2N) + 1u;
@@ -382,13 +397,13 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         for (int m = 0; m < LW; ++m)
             A9[m] = C[m] * M;  // packed bytes a*M <= 72
         if (pr & 1)
-            votes_one8<0, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+            votes_one8<0, LW, LOG2N>(A9, C, CR, P, PL, PR, sr, sl, hb, l4);
         if (pr & 2)
-            votes_one8<1, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+            votes_one8<1, LW, LOG2N>(A9, C, CR, P, PL, PR, sr, sl, hb, l4);
         if (pr & 4)
-            votes_one8<2, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+            votes_one8<2, LW, LOG2N>(A9, C, CR, P, PL, PR, sr, sl, hb, l4);
         if (pr & 8)
-            votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, hb, l4);
+            votes_one8<3, LW, LOG2N>(A9, C, CR, P, PL, PR, sr, sl, hb, l4);
     } else if constexpr (LOG2N == 8) {
         // One offset and orientation per job, fixed for this loop instance.
         const uint32_t rbase = hb - 4u * 32768u * (uint32_t)j.row_half;
@@ -396,7 +411,7 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         if (top && k != 0)
             return;  // no row above the image's first row
         // Spare words: the lane's word of the 32 after the job's 32768.
-        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, hb, rbase, hb + 131072u + l4,
+        votes_wide<LW, EDGE>(k, j.transposed != 0, C, CR, P, PL, PR, sr, sl, hb, rbase, hb + 131072u + l4,
                              k == 2 ? em.in : (k == 3 ? em.left : em.right));
     } else if constexpr (LOG2N == 4) {
         uint32_t A16[LW];
@@ -404,15 +419,15 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         for (int m = 0; m < LW; ++m)
             A16[m] = C[m] << 4;  // packed bytes a*16 <= 240
         if (pr & 1)
-            votes_one16<0, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.right);
+            votes_one16<0, LW, EDGE>(A16, C, CR, P, PL, PR, sr, sl, hb, l4, em.right);
         if (top)
             return;  // no row above the image's first row
         if (pr & 2)
-            votes_one16<1, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.right);
+            votes_one16<1, LW, EDGE>(A16, C, CR, P, PL, PR, sr, sl, hb, l4, em.right);
         if (pr & 4)
-            votes_one16<2, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.in);
+            votes_one16<2, LW, EDGE>(A16, C, CR, P, PL, PR, sr, sl, hb, l4, em.in);
         if (pr & 8)
-            votes_one16<3, LW, EDGE>(A16, C, CR, P, PL, PR, hb, l4, em.left);
+            votes_one16<3, LW, EDGE>(A16, C, CR, P, PL, PR, sr, sl, hb, l4, em.left);
     } else {
         constexpr uint32_t M = (1u << LOG2N) + 1u;
         uint32_t Alo[LW], Ahi[LW];
@@ -425,13 +440,13 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
         const uint32_t l8 = 2u * l4;
         const int hk = j.half_hi;
         if (pr & 1)
-            votes_one32_sel<0, LW>(hk == 0, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+            votes_one32_sel<0, LW>(hk == 0, Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
         if (pr & 2)
-            votes_one32_sel<1, LW>(hk == 1, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+            votes_one32_sel<1, LW>(hk == 1, Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
         if (pr & 4)
-            votes_one32_sel<2, LW>(hk == 2, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+            votes_one32_sel<2, LW>(hk == 2, Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
         if (pr & 8)
-            votes_one32_sel<3, LW>(hk == 3, Alo, Ahi, C, CR, P, PL, PR, hb, l8);
+            votes_one32_sel<3, LW>(hk == 3, Alo, Ahi, C, CR, P, PL, PR, sr, sl, hb, l8);
     }
 }
 
@@ -442,8 +457,11 @@ __device__ __forceinline__ void vote_row(const FastJob& j, const uint32_t (&C)[L
 // interior strips need neither.  ALIGNED: every row starts on 16 bytes, so a
 // lane's bytes are one 16-byte load (a separate instance: the realigning
 // loads of other images cost registers the aligned loop does not spend).
+// ring: this warp's row history for distances D > 1 -- D slots of 32 lanes
+// x (LW level words + the lane's halo word), word-major so that each lane
+// keeps to its own bank; unused for D = 1 (the row above stays in registers).
 template <int BPP, int LOG2N, bool EDGE, bool ALIGNED>
-__device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int y1, uint32_t hb)
+__device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int y1, uint32_t hb, uint32_t* ring)
 {
     constexpr int PX = 16 / BPP, LW = 4 / BPP;
     constexpr uint32_t N = 1u << LOG2N;
@@ -458,13 +476,15 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
     for (int m = 0; m < LW; ++m)
         om[m] = EDGE ? outside_mask(j.W - (xl + 4 * m)) : 0u;
     const uint32_t omr = EDGE ? outside_mask(j.W - xe) : 0u;
+    const int D = j.dist;  // partner distance, 1 .. 4
+    const uint32_t sr = right_sel((uint32_t)D), sl = left_sel((uint32_t)D);
     EdgeMasks em{0xFFFFu, 0xFFFFu, 0xFFFFu};
     if (EDGE && MASKED) {
         const int nin = max(0, min(PX, j.W - xl));           // pixels of the lane inside the image
-        const int nright = max(0, min(PX, j.W - 1 - xl));    // ... with a partner to the right
+        const int nright = max(0, min(PX, j.W - D - xl));    // ... with a partner D to the right
         em.in = (1u << nin) - 1u;
         em.right = (1u << nright) - 1u;
-        em.left = em.in & (xl == 0 ? ~1u : ~0u);
+        em.left = em.in & (xl == 0 ? ~((1u << D) - 1u) : ~0u);  // ... and D to the left
     }
     const bool has_l = lane == 0 && x0 > 0;
     const bool has_r = lane == 31 && xe < j.W;
@@ -504,7 +524,7 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
             }
         }
     };
-    auto levels = [&](const uint4& v, const uint2& h, uint32_t (&L)[LW], uint32_t& ll, uint32_t& lr) {
+    auto levels = [&](const uint4& v, const uint2& h, uint32_t (&L)[LW], uint32_t& ll, uint32_t& lr, uint32_t& hqo) {
         if constexpr (BPP == 1) {
             L[0] = qword<1, LOG2N>(v.x, 0u);
             L[1 % LW] = qword<1, LOG2N>(v.y, 0u);
@@ -526,13 +546,15 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
         const uint32_t dn = __shfl_down_sync(0xffffffffu, L[0], 1);
         ll = lane == 0 ? (has_l ? hq : D4) : up;
         lr = lane == 31 ? (has_r ? hq : D4) : dn;
+        hqo = hq;
     };
 
     uint32_t P[LW], PL = D4, PR = D4;
 #pragma unroll
     for (int m = 0; m < LW; ++m)
         P[m] = D4;
-    const int ys = y0 > 0 ? y0 - 1 : y0;  // the row above the band is its halo
+    const int ys = max(0, y0 - D);  // the D rows above the band are its halo
+    int slot = 0;                   // ring slot of row y: (y - ys) mod D
 #pragma unroll
     for (int k = 0; k < kPF; ++k)
         if (ys + k < y1)
@@ -547,18 +569,47 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
             const uint2 h = qh[k];
             if (y + kPF < y1)
                 load_row(y + kPF, qv[k], qh[k]);
-            uint32_t C[LW], CL, CR;
-            levels(v, h, C, CL, CR);
+            uint32_t C[LW], CL, CR, hq;
+            levels(v, h, C, CL, CR, hq);
+            if (D > 1) {
+                // Row y - D from the ring slot, which then takes row y; rows
+                // y < D have the outside level above them (no partner: their
+                // votes land in ignored bins, or are skipped under masks).
+                uint32_t* rs = ring + slot * ((LW + 1) * 32) + lane;
+                if (y >= D) {
+#pragma unroll
+                    for (int m = 0; m < LW; ++m)
+                        P[m] = rs[m * 32];
+                    const uint32_t hp = rs[LW * 32];
+                    const uint32_t up = __shfl_up_sync(0xffffffffu, P[LW - 1], 1);
+                    const uint32_t dn = __shfl_down_sync(0xffffffffu, P[0], 1);
+                    PL = lane == 0 ? (has_l ? hp : D4) : up;
+                    PR = lane == 31 ? (has_r ? hp : D4) : dn;
+                } else {
+#pragma unroll
+                    for (int m = 0; m < LW; ++m)
+                        P[m] = D4;
+                    PL = D4;
+                    PR = D4;
+                }
+#pragma unroll
+                for (int m = 0; m < LW; ++m)
+                    rs[m * 32] = C[m];
+                rs[LW * 32] = hq;
+                slot = slot + 1 == D ? 0 : slot + 1;
+            }
             // (masked edge strips vote with all lanes -- lanes outside the
             // image have empty masks -- since their word masks are decided
-            // warp-wide.)
+            // warp-wide.)  Rows y < D have no partner row above.
             if (y >= y0 && (on || (EDGE && MASKED)))
-                vote_row<LW, LOG2N, EDGE>(j, C, CR, P, PL, PR, hb, l4, y == 0, em);
+                vote_row<LW, LOG2N, EDGE>(j, C, CR, P, PL, PR, sr, sl, hb, l4, y < D, em);
+            if (D == 1) {
 #pragma unroll
-            for (int m = 0; m < LW; ++m)
-                P[m] = C[m];
-            PL = CL;
-            PR = CR;
+                for (int m = 0; m < LW; ++m)
+                    P[m] = C[m];
+                PL = CL;
+                PR = CR;
+            }
         }
     }
 }
@@ -568,7 +619,7 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
 // items, one per warp, cost about the same and no warp waits long at the
 // chunk's barrier for an edge strip.
 template <int BPP, int LOG2N, bool ALIGNED>
-__device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t hb)
+__device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t hb, uint32_t* ring)
 {
     constexpr int PX = 16 / BPP;
     const int n_int = max(0, j.n_strips - 2);
@@ -589,10 +640,13 @@ __device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t h
     const int y1 = min(j.y_end, y0 + j.band);
     if (y0 >= y1)
         return;
-    if (strip == 0 || strip == j.n_strips - 1)
-        walk_strip<BPP, LOG2N, true, ALIGNED>(j, x0, y0, y1, hb);
+    // Edge strips: the first, and every strip whose partners D pixels past
+    // its right end can leave the image (the last, and the one before it
+    // when the last holds fewer than D pixels).
+    if (strip == 0 || x0 + 32 * PX + j.dist > j.W)
+        walk_strip<BPP, LOG2N, true, ALIGNED>(j, x0, y0, y1, hb, ring);
     else
-        walk_strip<BPP, LOG2N, false, ALIGNED>(j, x0, y0, y1, hb);
+        walk_strip<BPP, LOG2N, false, ALIGNED>(j, x0, y0, y1, hb, ring);
 }
 
 // ---- merge -------------------------------------------------------------------
@@ -756,6 +810,17 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
     }
     uint32_t* marg = hist + p.max_hist_words;
     int* s_chunk = reinterpret_cast<int*>(marg + kMargWords);
+    // Row rings of distances D > 1, ring_words per warp: after the chunk
+    // index, or for N = 16 in the padding before the 64 KB-aligned
+    // histograms (the dynamic shared memory starts near 0, so the padding is
+    // almost 64 KB; the launch's size counts no ring then).
+    const bool ring_in_pad = fast_align(LOG2N) == 65536u;
+    if (ring_in_pad && (uint32_t)p.ring_words * kFW * 4u > pad) {
+        if (threadIdx.x == 0)
+            atomicOr(p.err, kErrInternal);
+        return;
+    }
+    uint32_t* ring = (ring_in_pad ? sh : marg + kMargWords + 4) + (threadIdx.x >> 5) * p.ring_words;
     {
         uint4* z = reinterpret_cast<uint4*>(hist);
         for (int i = threadIdx.x; i < (p.max_hist_words + kMargWords) / 4; i += kFT)
@@ -788,12 +853,13 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
         }
         acc_rows += rows_w;
         if (j.hist_words > p.max_hist_words || j.log2n != LOG2N || j.bpp != BPP || (j.aligned != 0) != ALIGNED ||
-            (j.mode == kFastHalf && rows_w > kHalfRows)) {
+            (j.mode == kFastHalf && rows_w > kHalfRows) || j.dist < 1 || j.dist > 4 ||
+            (j.dist > 1 && j.dist * (4 / BPP + 1) * 32 > p.ring_words)) {
             if (threadIdx.x == 0)
                 atomicOr(p.err, kErrInternal);
         } else {
             for (int it = ch.y + warp; it < ch.z; it += kFW)
-                walk_item<BPP, LOG2N, ALIGNED>(j, it, hb);
+                walk_item<BPP, LOG2N, ALIGNED>(j, it, hb, ring);
         }
         __syncthreads();
     }

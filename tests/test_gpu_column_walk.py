@@ -1,5 +1,6 @@
-"""The column-walk vote kernel (offsets at chessboard distance 1, N a power of
-two up to 32) against the oracle, bit for bit.
+"""The column-walk vote kernel (offsets (D, 0), (D, -D), (0, -D), (-D, -D)
+and their opposites at chessboard distance D = 1 .. 4, N a power of two up
+to 32, or 256) against the oracle, bit for bit.
 
 It is the default path for those offsets, so these cases aim at what is
 special to it: every N and pixel type (joint codes for N <= 8, pairs of
@@ -160,3 +161,63 @@ def test_rows_at_any_byte_address(gctx, n, dt):
         c = gctx.compute(t[:, x0:x1], n, C4)
         torch.cuda.synchronize()
         assert np.array_equal(to_u32(c), oracle.glcm(np.ascontiguousarray(base[:, x0:x1]), n, C4)), (x0, x1)
+
+
+def offsets_at(d):
+    return [(d, 0), (d, -d), (0, -d), (-d, -d)]
+
+
+@pytest.mark.parametrize("dt", [np.uint8, np.uint16])
+@pytest.mark.parametrize("n", [2, 4, 8, 16, 32, 256])
+@pytest.mark.parametrize("d", [2, 3, 4])
+def test_distances_up_to_four(gctx, d, n, dt):
+    """Offsets at chessboard distance 2..4 take the column walk too (the row
+    D above from a ring in shared memory, partner words shifted D pixels):
+    all four angles, their opposites, beside distance 1 and distance 5 (the
+    general kernel) in one call, on noise and smooth halves."""
+    img = _img("smooth", 200 + 10 * d + n, 230, 1037, dt)
+    img[:, 600:] = _img("iid", 300 + d + n, 230, 437, dt)
+    for offs in (offsets_at(d), [(-dx, -dy) for dx, dy in offsets_at(d)],
+                 offsets_at(d) + offsets_at(1) + [(5, 0), (0, -5)]):
+        assert np.array_equal(run(gctx, img, n, offs), oracle.glcm(img, n, offs)), (d, offs)
+
+
+@pytest.mark.parametrize("n", [8, 16, 256])
+@pytest.mark.parametrize("h,w", [(1, 1), (2, 3), (3, 2), (4, 4), (5, 5), (7, 513), (70, 17), (33, 1030)])
+def test_distances_on_small_and_narrow_images(gctx, h, w, n):
+    """Images no larger than the distance, widths around the strips and the
+    N = 16 / 256 edge masks (anchors with no partner D to the left or right)."""
+    for dt in (np.uint8, np.uint16):
+        img = _img("iid", h * 1009 + w + n, h, w, dt)
+        offs = offsets_at(2) + offsets_at(4) + [(-3, 0), (0, 3), (3, 3)]
+        assert np.array_equal(run(gctx, img, n, offs), oracle.glcm(img, n, offs)), (dt, h, w)
+
+
+def test_distances_pitched_views_stripes_and_batches(gctx):
+    base = _img("smooth", 77, 400, 2100, np.uint8)
+    t = torch.from_numpy(base).cuda()
+    offs = S.MULTISPECTRAL_OFFSETS
+    for x0, x1 in [(0, 1000), (16, 1530), (3, 700)]:
+        c = gctx.compute(t[:, x0:x1], 32, offs)
+        torch.cuda.synchronize()
+        assert np.array_equal(to_u32(c), oracle.glcm(np.ascontiguousarray(base[:, x0:x1]), 32, offs)), (x0, x1)
+    big = _img("smooth", 78, 3000, 1500, np.uint8)
+    big[1500:] = _img("iid", 79, 1500, 1500, np.uint8)
+    for n in (8, 32, 256):  # host image in row stripes: the D rows above a stripe come from earlier copies
+        c = gctx.compute(big, n, offsets_at(4) + offsets_at(2))
+        assert np.array_equal(to_u32(c), oracle.glcm(big, n, offsets_at(4) + offsets_at(2))), n
+    u16 = [_img(k, 80 + i, 300, 520, np.uint16) for i, k in enumerate(("iid", "smooth", "constant"))]
+    jobs = [dict(image=dev(im), levels=32, offsets=offs, flags=G.GLCM_SYMMETRIC, normalized=True, features=True)
+            for im in u16]
+    outs = gctx.batch(jobs)
+    torch.cuda.synchronize()
+    for im, (c, _, _) in zip(u16, outs):
+        assert np.array_equal(to_u32(c), oracle.glcm(im, 32, offs))
+
+
+def test_distance_four_constant_image_all_in_one_bin():
+    with G.Context(0, hbm_budget_bytes=1 << 30) as ctx:
+        img = np.full((2048, 2048), 200, np.uint8)
+        for n in (8, 32, 256):
+            offs = offsets_at(4) + offsets_at(3)
+            assert np.array_equal(run(ctx, img, n, offs), oracle.glcm(img, n, offs)), n
