@@ -48,7 +48,6 @@
 namespace glcm {
 namespace {
 
-constexpr int kFeatThreads = 512;
 constexpr int kNumFeat = 14;
 constexpr int kMaxLanczos = 96;
 // A' and the Lanczos vectors stay in shared memory up to these sizes
@@ -1499,16 +1498,22 @@ cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s)
+// threads: kFeatThreads, or kFeatThreadsSmall for jobs with N <= 32 (their
+// epilogue is short and barrier-bound: two such CTAs share an SM).  The
+// block size depends on a job's N only, so its features do not depend on
+// the batch it is in.
+cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads)
 {
     if (p.n_jobs <= 0)
         return cudaSuccess;
+    if (threads != kFeatThreads && (threads != kFeatThreadsSmall || max_levels > kSmallFeatLevels))
+        return cudaErrorInvalidValue;
     const size_t smem = features_smem_bytes(max_levels);
     static SmemLimit lim;
     const cudaError_t e = lim.raise((const void*)k_haralick, smem);
     if (e != cudaSuccess)
         return e;
-    k_haralick<<<p.n_jobs, kFeatThreads, smem, s>>>(p, max_levels);
+    k_haralick<<<p.n_jobs, threads, smem, s>>>(p, max_levels);
     return cudaGetLastError();
 }
 

@@ -1087,12 +1087,13 @@ int capture_mark(glcm_ctx* ctx, GraphEntry* ge, bool start)
     return GLCM_OK;
 }
 
-// Feature jobs in launch order: the one-CTA epilogue's, then the cluster
-// epilogue's (symmetric, 128 < N <= 256).  Each job names its own outputs,
-// so the order changes nothing else.
+// Feature jobs in launch order (feat_job_group): one small CTA each (N <=
+// 32), one CTA each, one cluster of CTAs each (symmetric, 128 < N <= 256).
+// Each job names its own outputs, so the order changes nothing else.
 void order_feats(std::vector<FeatJob>& feats)
 {
-    std::stable_partition(feats.begin(), feats.end(), [](const FeatJob& f) { return !feat_job_clustered(f); });
+    std::stable_sort(feats.begin(), feats.end(),
+                     [](const FeatJob& a, const FeatJob& b) { return feat_job_group(a) < feat_job_group(b); });
 }
 
 int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const DevBuf& dfeat, int max_levels,
@@ -1102,50 +1103,43 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
         return GLCM_OK;
     if (!st)
         st = ctx->stream;
-    // The jobs of the cluster epilogue come last (order_feats).
-    int n_one = 0;
-    while (n_one < (int)feats.size() && !feat_job_clustered(feats[n_one]))
-        ++n_one;
-    for (size_t i = n_one; i < feats.size(); ++i)
-        if (!feat_job_clustered(feats[i]))
+    for (size_t i = 1; i < feats.size(); ++i)
+        if (feat_job_group(feats[i]) < feat_job_group(feats[i - 1]))
             return fail(ctx, GLCM_ERR_CUDA, "internal: feature jobs out of launch order");
-    if (n_one > 0) {
-        int one_max = 2;
-        for (int i = 0; i < n_one; ++i)
-            one_max = std::max(one_max, feats[i].levels);
-        if (one_max > max_levels)
+    // One launch per group, in order.
+    size_t g0 = 0;
+    while (g0 < feats.size()) {
+        const int grp = feat_job_group(feats[g0]);
+        size_t g1 = g0;
+        int gmax = 2;
+        bool any_feat = false;
+        while (g1 < feats.size() && feat_job_group(feats[g1]) == grp) {
+            gmax = std::max(gmax, feats[g1].levels);
+            any_feat |= feats[g1].features != nullptr;
+            ++g1;
+        }
+        if (gmax > max_levels)
             return fail(ctx, GLCM_ERR_CUDA, "internal: a feature job beyond the launch's levels");
         FeatParams fp{};
-        fp.jobs = static_cast<const FeatJob*>(dfeat.p);
-        fp.n_jobs = n_one;
+        fp.jobs = static_cast<const FeatJob*>(dfeat.p) + g0;
+        fp.n_jobs = (int)(g1 - g0);
         fp.err = ctx->d_words;
-        if (one_max > 64) {
-            bool any_feat = false;
-            for (int i = 0; i < n_one; ++i)
-                any_feat |= feats[i].features != nullptr;
-            if (any_feat) {
-                const long long per = features_work_floats(one_max);
-                TRY(ensure(ctx, ctx->work, (size_t)n_one * (size_t)per * sizeof(float)));
+        if (grp == 2) {
+            CK(launch_features_cluster(fp, st));
+        } else {
+            if (gmax > 64 && any_feat) {
+                const long long per = features_work_floats(gmax);
+                TRY(ensure(ctx, ctx->work, (size_t)fp.n_jobs * (size_t)per * sizeof(float)));
                 fp.work = static_cast<float*>(ctx->work.p);
                 fp.work_stride = per;
             }
+            CK(launch_features(fp, gmax, st, grp == 0 ? kFeatThreadsSmall : kFeatThreads));
         }
-        CK(launch_features(fp, one_max, st));
         if (!capturing)
             ctx->kernel_launches += 1;
         if (ge)
             ge->n_kernels++;
-    }
-    if (n_one < (int)feats.size()) {
-        FeatParams fc{};
-        fc.jobs = static_cast<const FeatJob*>(dfeat.p) + n_one;
-        fc.n_jobs = (int)feats.size() - n_one;
-        fc.err = ctx->d_words;
-        CK(launch_features_cluster(fc, st));
-        if (!capturing)
-            ctx->kernel_launches += 1;
-        if (ge)
-            ge->n_kernels++;
+        g0 = g1;
     }
     return GLCM_OK;
 }

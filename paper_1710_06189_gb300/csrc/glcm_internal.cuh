@@ -245,12 +245,23 @@ cudaError_t launch_vote_global(const SeamJob* jobs, int n_jobs, int blocks_per_j
 cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int bpp, int levels,
                          int levels_mode, int dx, int dy, uint32_t* out, unsigned* err,
                          cudaStream_t s);
-cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s);
+// Threads per epilogue CTA: kFeatThreads, or kFeatThreadsSmall for the jobs
+// with N <= kSmallFeatLevels.
+constexpr int kFeatThreads = 512;
+constexpr int kFeatThreadsSmall = 256;
+constexpr int kSmallFeatLevels = 32;
+cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads);
 // Symmetric feature jobs with 128 < N <= 256, one cluster of CTAs per GLCM.
 cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s);
 inline bool feat_job_clustered(const FeatJob& f)
 {
     return f.features != nullptr && f.symmetric && f.levels > 128 && f.levels <= 256;
+}
+// Launch group of a feature job: 0 one small CTA (N <= 32), 1 one CTA,
+// 2 a cluster of CTAs.
+inline int feat_job_group(const FeatJob& f)
+{
+    return feat_job_clustered(f) ? 2 : (f.levels <= kSmallFeatLevels ? 0 : 1);
 }
 size_t features_smem_bytes(int max_levels);
 long long features_work_floats(int levels);
