@@ -1247,7 +1247,7 @@ __global__ void k_copy_rows(uint8_t* __restrict__ dst, size_t dpitch, const uint
 // cudaMemcpyAsync (one flat copy when both sides have the same pitch) or
 // cudaMemcpy2DAsync, as does every copy when allow_kernel is false.
 cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes,
-                                      int rows, cudaStream_t st, bool allow_kernel)
+                                      int rows, cudaStream_t st, bool allow_kernel, int max_ctas)
 {
     if (rows <= 0 || row_bytes == 0)
         return cudaSuccess;
@@ -1259,7 +1259,7 @@ cudaError_t glcm::copy_rows_to_device(void* dst, size_t dpitch, const void* src,
         const uintptr_t b = reinterpret_cast<uintptr_t>(dst);
         if ((b | dpitch) % 16 == 0 && dpitch >= ((row_bytes + 15) & ~(size_t)15)) {
             const long long units = (long long)((row_bytes + 15) / 16) * rows;
-            const int grid = (int)std::max<long long>(1, std::min<long long>(24, (units + 511) / 512));
+            const int grid = (int)std::max<long long>(1, std::min<long long>(max_ctas, (units + 511) / 512));
             k_copy_rows<<<grid, 512, 0, st>>>(static_cast<uint8_t*>(dst), dpitch,
                                               static_cast<const uint8_t*>(pa.devicePointer), spitch, row_bytes, rows);
             return cudaGetLastError();

@@ -276,8 +276,9 @@ int vote_blocks_per_sm(int bpp, int threads, size_t smem, bool packed = false);
 int vote_row_bytes();
 // Host image rows to the device on `st` (a copy kernel for registered host
 // memory, else cudaMemcpy(2D)Async); defined in glcm_capi.cu.
+// max_ctas caps the copy kernel's grid.
 cudaError_t copy_rows_to_device(void* dst, size_t dpitch, const void* src, size_t spitch, size_t row_bytes, int rows,
-                                cudaStream_t st, bool allow_kernel = true);
+                                cudaStream_t st, bool allow_kernel = true, int max_ctas = 24);
 // Every vote launch of `ctx` leaves `sms` SMs free (for a concurrent copy
 // kernel; a vote CTA fills its SM's register file); defined in glcm_capi.cu.
 void set_vote_sm_reserve(::glcm_ctx* ctx, int sms);

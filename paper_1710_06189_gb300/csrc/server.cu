@@ -65,8 +65,13 @@ size_t r256(size_t b) { return glcm_arena::Arena::round_up(b); }
 // while the next batches still copy, instead of copying everything first.
 constexpr size_t kBatchImageBytes = 256ull << 20;
 
-// SMs every lane's vote launches leave to the image copy kernel.
-constexpr int kServerCopySMs = 8;
+// SMs every lane's vote launches leave to the image copy kernel, and the
+// copy kernel's CTAs (two per SM).  A burst of served requests is bound by
+// the copies: measured on the all-at-once burst of the served stream, 8 SMs
+// and 24 CTAs gave 780 Gpairs/s, 16 SMs 864, 24 SMs and 48 CTAs 1042, 32 SMs
+// and 64 CTAs 1024, 48 SMs and 96 CTAs 997.
+constexpr int kServerCopySMs = 24;
+constexpr int kServerCopyCTAs = 2 * kServerCopySMs;
 
 std::string g_server_create_error;
 
@@ -190,7 +195,8 @@ bool admit(glcm_server* s)
     for (Req* r : take) {
         const int bpp = r->d.dtype == GLCM_U8 ? 1 : 2;
         cudaError_t e = glcm::copy_rows_to_device(s->base + r->off, r->dpitch, r->d.image, r->d.pitch_bytes,
-                                                  (size_t)r->d.width * bpp, r->d.height, s->copy);
+                                                  (size_t)r->d.width * bpp, r->d.height, s->copy, true,
+                                                  kServerCopyCTAs);
         r->copied = take_event(s);
         if (e == cudaSuccess && r->copied)
             e = cudaEventRecord(r->copied, s->copy);
