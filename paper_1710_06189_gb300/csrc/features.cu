@@ -317,51 +317,65 @@ __device__ __forceinline__ int sturm_below(const float* ab, int L, float x)
     return cnt;
 }
 
-// Multisection of one end of a spectrum by the warps [w0, w0 + nw): each of
-// the 32 nw points of a round tests whether every eigenvalue (upper) or none
-// (lower) lies below it, and the bracket shrinks to the interval between the
-// two neighbouring points where the answer changes.  A fixed number of rounds,
-// so that every thread of the block passes the same barriers; the returned
-// midpoint is meaningful in the calling warps.  s_msk: 2 x 32 words.
+// One multisection round of one end of a spectrum by the warps [w0, w0 + nw)
+// (mine: the calling warp is one of them) over the points x(0) < ... <
+// x(32 nw - 1) inside the bracket [a, b]: each point tests whether every
+// eigenvalue (upper) or none (lower) lies below it, and the bracket shrinks
+// to the interval between the two neighbouring points where the answer
+// changes.  Every thread of the block calls (one barrier); a and b are
+// meaningful in the calling warps.  msk: 32 words, not reused by the next
+// round.
+template <class F, class X>
+__device__ __forceinline__ void multisect_round(F below, int n_eig, X x, float& a, float& b, bool upper, bool mine,
+                                                int w0, int nw, unsigned* msk)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int P = 32 * nw;
+    if (mine) {
+        const int c = below(x((warp - w0) * 32 + lane));
+        const unsigned m = __ballot_sync(0xffffffffu, upper ? c >= n_eig : c == 0);
+        if (lane == 0)
+            msk[warp - w0 + (upper ? 0 : 16)] = m;
+    }
+    __syncthreads();
+    if (mine) {
+        const unsigned* mk = msk + (upper ? 0 : 16);
+        float na, nb;
+        if (upper) {
+            int idx = P;  // first point above every eigenvalue
+            for (int w = nw - 1; w >= 0; --w)
+                if (mk[w])
+                    idx = 32 * w + __ffs(mk[w]) - 1;
+            na = idx == 0 ? a : x(idx - 1);
+            nb = idx == P ? b : x(idx);
+        } else {
+            int idx = -1;  // last point below every eigenvalue
+            for (int w = 0; w < nw; ++w)
+                if (mk[w])
+                    idx = 32 * w + 31 - __clz(mk[w]);
+            na = idx < 0 ? a : x(idx);
+            nb = idx == P - 1 ? b : x(idx + 1);
+        }
+        a = na;
+        b = nb;
+    }
+}
+
+// Multisection of one end of a spectrum by the warps [w0, w0 + nw): `rounds`
+// rounds, each splitting the bracket evenly into 32 nw + 1 parts.  A fixed
+// number of rounds, so that every thread of the block passes the same
+// barriers; the returned midpoint is meaningful in the calling warps.
+// s_msk: 2 x 32 words.
 template <class F>
 __device__ float block_multisect(F below, int n_eig, float a, float b, bool upper, int w0, int nw, int rounds,
                                  unsigned (*s_msk)[32])
 {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
     const bool mine = warp >= w0 && warp < w0 + nw;
-    const int P = 32 * nw;
-    const float den = (float)(P + 1);
+    const float den = (float)(32 * nw + 1);
     for (int r = 0; r < rounds; ++r) {
-        if (mine) {
-            const int pt = (warp - w0) * 32 + lane;
-            const float x = a + (b - a) * (float)(pt + 1) / den;
-            const int c = below(x);
-            const unsigned m = __ballot_sync(0xffffffffu, upper ? c >= n_eig : c == 0);
-            if (lane == 0)
-                s_msk[r & 1][warp - w0 + (upper ? 0 : 16)] = m;
-        }
-        __syncthreads();
-        if (mine) {
-            const unsigned* mk = s_msk[r & 1] + (upper ? 0 : 16);
-            float na, nb;
-            if (upper) {
-                int idx = P;  // first point above every eigenvalue
-                for (int w = nw - 1; w >= 0; --w)
-                    if (mk[w])
-                        idx = 32 * w + __ffs(mk[w]) - 1;
-                na = idx == 0 ? a : a + (b - a) * (float)idx / den;
-                nb = idx == P ? b : a + (b - a) * (float)(idx + 1) / den;
-            } else {
-                int idx = -1;  // last point below every eigenvalue
-                for (int w = 0; w < nw; ++w)
-                    if (mk[w])
-                        idx = 32 * w + 31 - __clz(mk[w]);
-                na = idx < 0 ? a : a + (b - a) * (float)(idx + 1) / den;
-                nb = idx == P - 1 ? b : a + (b - a) * (float)(idx + 2) / den;
-            }
-            a = na;
-            b = nb;
-        }
+        auto even = [&](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
+        multisect_round(below, n_eig, even, a, b, upper, mine, w0, nw, s_msk[r & 1]);
     }
     return 0.5f * (a + b);
 }
@@ -693,12 +707,28 @@ __device__ __forceinline__ int tri_count_below(const float* al, const float* be,
     return cnt;
 }
 
-// max(|lambda_max|, |lambda_min|) of the tridiagonal matrix: the first half
-// of the warps searches the top end, the second half the bottom end, four
-// rounds each; the result is in *out after the call (every thread of the
-// block must call).
-__device__ void tri_absmax_block(const float* al, const float* be, int L, float* ends, float* out,
-                                 unsigned (*s_msk)[32])
+// Both ends of a growing tridiagonal matrix as last bracketed: estimates
+// (bracket midpoints), max |eigenvalue|, the bound on the inner side of each
+// bracket, and each end's move at that check.
+struct TriEnds {
+    float top, bot, absmax, top_in, bot_in, dtop, dbot;
+};
+
+// max(|lambda_max|, |lambda_min|) of the L x L symmetric tridiagonal matrix
+// with diagonal al[] and off-diagonal be[], into e (every thread of the
+// block calls; e is written by thread 0 and read after the last barrier).
+// The first half of the warps brackets the top end, the second half the
+// bottom end, inside the Gershgorin interval.  Cold: four rounds of even
+// multisection.  Warm, when e holds the ends of the matrix's leading
+// (L - k) x (L - k) block: by Cauchy interlacing the top end can only rise
+// and the bottom end only fall as rows are added, so each lies on the outer
+// side of the previous bracket's inner bound.  The first round then puts
+// half of its points evenly within a reach of that bound (four times the
+// end's last move, at least 1e-5 of max |eigenvalue|), where a converging end
+// lands, and the other half geometrically out to the Gershgorin bound; one
+// even round follows.
+__device__ void tri_ends_block(const float* al, const float* be, int L, bool warm, TriEnds& e,
+                               unsigned (*s_msk)[32])
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     const int half = nw / 2 < 16 ? nw / 2 : 16;
@@ -715,13 +745,51 @@ __device__ void tri_absmax_block(const float* al, const float* be, int L, float*
     if (L <= 0)
         lo = hi = 0.f;
     auto below = [&](float x) { return tri_count_below(al, be, L, x); };
-    const bool up = warp < half;
-    const float e = block_multisect(below, L, lo, hi, up, up ? 0 : half, half, 4, s_msk);
-    if (lane == 0 && (warp == 0 || warp == half))
-        ends[up ? 0 : 1] = e;
+    const bool up = warp < half, mine = warp < 2 * half;
+    const int w0 = up ? 0 : half;
+    float a = lo, b = hi;
+    int rounds = 4;
+    if (warm) {
+        // The inner bound moves in by a little more than the counts'
+        // rounding, so that the end cannot lie on its inner side.
+        const float v = e.absmax, eps = 1e-6f * v + 1e-30f;
+        const float in = up ? fminf(fmaxf(e.top_in - eps, lo), hi) : fmaxf(fminf(e.bot_in + eps, hi), lo);
+        const float span = up ? hi - in : in - lo;
+        const float R = fminf(fmaxf(4.f * (up ? e.dtop : e.dbot), 1e-5f * v) + 1e-30f, span);
+        const float lg = R > 0.f ? log2f(span / R) : 0.f;
+        const int H = 16 * half, P = 32 * half;
+        // Distance from the inner bound of the q-th point outward.
+        auto off = [&](int q) {
+            return q < H ? R * (float)(q + 1) / (float)H : R * exp2f(lg * (float)(q + 1 - H) / (float)H);
+        };
+        auto warm_x = [&](int pt) { return up ? in + off(pt) : in - off(P - 1 - pt); };
+        if (up)
+            a = in;
+        else
+            b = in;
+        multisect_round(below, L, warm_x, a, b, up, mine, w0, half, s_msk[0]);
+        rounds = 1;
+    }
+    const float den = (float)(32 * half + 1);
+    for (int r = warm ? 1 : 0; r < (warm ? 1 : 0) + rounds; ++r) {
+        auto even = [&](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
+        multisect_round(below, L, even, a, b, up, mine, w0, half, s_msk[r & 1]);
+    }
+    if (mine && warp == w0 && lane == 0) {
+        const float mid = 0.5f * (a + b);
+        if (up) {
+            e.dtop = warm ? mid - e.top : 0.f;
+            e.top = mid;
+            e.top_in = a;
+        } else {
+            e.dbot = warm ? e.bot - mid : 0.f;
+            e.bot = mid;
+            e.bot_in = b;
+        }
+    }
     __syncthreads();
     if (threadIdx.x == 0)
-        *out = fmaxf(fabsf(ends[0]), fabsf(ends[1]));
+        e.absmax = fmaxf(fabsf(e.top), fabsf(e.bot));
     __syncthreads();
 }
 
@@ -1047,9 +1115,9 @@ __global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int 
 // output, f1, f9, the mutual-information terms, sum i j S) and keeps its rows
 // of A' in shared memory.  f14 is max |eigenvalue| of A' by symmetric Lanczos
 // without reorthogonalization: each step multiplies the CTA's rows of A' by
-// the current vector, and two cluster barriers exchange the step's two dot
-// products and the next vector's pieces, written by plain stores into every
-// CTA's shared memory.  Sums across CTAs are taken in rank order, and CTA 0
+// the current vector, and one cluster barrier exchanges the pieces of the
+// result and of its dot product with the vector, written by plain stores
+// into every CTA's shared memory.  Sums across CTAs are taken in rank order, and CTA 0
 // writes the features, so a GLCM's features do not depend on its batch.
 
 constexpr int kClu = 8;                  // CTAs per GLCM
@@ -1073,13 +1141,13 @@ struct CluSmem {
     float q[kCN], qp[kCN], y[kCR];        // Lanczos vector, the previous one, this CTA's rows of A' q
     float w[2][kCN];                      // A' q - beta q_prev, pieces written by every CTA (by step parity)
     float sa[2][kClu];                    // each CTA's part of (A' q - beta q_prev) . q (by step parity)
-    float al[kMaxSymSteps], be[kMaxSymSteps], ends[4];
+    float al[kMaxSymSteps], be[kMaxSymSteps];
+    TriEnds te;                           // ends of the tridiagonal matrix at the last check
     DF fin[kClu][10];                     // CTA 0: each CTA's compensated sums
     DF dscr[10 * 32];
     float red[32];
     unsigned msk[2][32];
     int nr, stop;
-    float sig;
 };
 
 __device__ __forceinline__ uint32_t clu_rank()
@@ -1147,7 +1215,8 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long s)
 // Lanczos without reorthogonalization from a fixed zero-mean pseudo-random
 // start: w' = A' q - beta q_prev, alpha = w' . q, w = w' - alpha q,
 // beta = |w|, q = w / beta; every 8 steps (after 16) the tridiagonal
-// matrix's extreme eigenvalues are bracketed, and the iteration stops once
+// matrix's extreme eigenvalues are bracketed, each check after the first
+// starting from the last one's brackets, and the iteration stops once
 // max |eigenvalue| moved by less than 4e-7 of itself.  One cluster barrier
 // per step: each CTA writes its rows of w' and its part of alpha into every
 // CTA (buffers alternate by step parity, so a CTA a step ahead never
@@ -1166,7 +1235,7 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
         sm.qp[c] = 0.f;
     }
     if (tid == 0) {
-        sm.sig = -1.f;
+        sm.te.absmax = -1.f;
         sm.stop = 0;
     }
     __syncthreads();
@@ -1178,7 +1247,7 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
         sm.q[c] *= inv;
     __syncthreads();
     float beta = 0.f;
-    int L = 0;
+    int L = 0, checked = 0;
     for (int k = 0; k < kMaxSymSteps; ++k) {
         const int par = k & 1;
         for (int rr = warp; rr < kCR; rr += kCluWarps) {
@@ -1224,19 +1293,20 @@ __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
         beta = bn;
         __syncthreads();
         if ((L & 7) == 0 && L >= 16) {
-            tri_absmax_block(sm.al, sm.be, L, sm.ends, sm.ends + 2, sm.msk);
-            if (tid == 0) {
-                sm.stop = fabsf(sm.ends[2] - sm.sig) <= 4e-7f * sm.ends[2] ? 1 : 0;
-                sm.sig = sm.ends[2];
-            }
+            const float prev = sm.te.absmax;
+            tri_ends_block(sm.al, sm.be, L, checked > 0, sm.te, sm.msk);
+            checked = L;
+            if (tid == 0)
+                sm.stop = fabsf(sm.te.absmax - prev) <= 4e-7f * sm.te.absmax ? 1 : 0;
             __syncthreads();
             if (sm.stop)
                 break;
         }
     }
     __syncthreads();
-    tri_absmax_block(sm.al, sm.be, L, sm.ends, sm.ends + 2, sm.msk);
-    return sm.ends[2];
+    if (checked != L)
+        tri_ends_block(sm.al, sm.be, L, false, sm.te, sm.msk);
+    return sm.te.absmax;
 }
 
 __global__ void __cluster_dims__(kClu, 1, 1) __launch_bounds__(kCluThreads, 1)
