@@ -374,7 +374,7 @@ __device__ float block_multisect(F below, int n_eig, float a, float b, bool uppe
     const bool mine = warp >= w0 && warp < w0 + nw;
     const float den = (float)(32 * nw + 1);
     for (int r = 0; r < rounds; ++r) {
-        auto even = [&](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
+        auto even = [=](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
         multisect_round(below, n_eig, even, a, b, upper, mine, w0, nw, s_msk[r & 1]);
     }
     return 0.5f * (a + b);
@@ -399,7 +399,7 @@ __device__ float gk_sigma_max_block(const float* ab, int steps, unsigned (*s_msk
     for (int o = 16; o > 0; o >>= 1)
         hi = fmaxf(hi, __shfl_xor_sync(0xffffffffu, hi, o));
     hi *= 2.f;
-    auto below = [&](float x) { return sturm_below(ab, L, x); };
+    auto below = [=](float x) { return sturm_below(ab, L, x); };
     return block_multisect(below, L + 1, 0.f, hi, true, 0, nw < 16 ? nw : 16, 3, s_msk);
 }
 
@@ -744,7 +744,7 @@ __device__ void tri_ends_block(const float* al, const float* be, int L, bool war
     }
     if (L <= 0)
         lo = hi = 0.f;
-    auto below = [&](float x) { return tri_count_below(al, be, L, x); };
+    auto below = [=](float x) { return tri_count_below(al, be, L, x); };
     const bool up = warp < half, mine = warp < 2 * half;
     const int w0 = up ? 0 : half;
     float a = lo, b = hi;
@@ -759,10 +759,10 @@ __device__ void tri_ends_block(const float* al, const float* be, int L, bool war
         const float lg = R > 0.f ? log2f(span / R) : 0.f;
         const int H = 16 * half, P = 32 * half;
         // Distance from the inner bound of the q-th point outward.
-        auto off = [&](int q) {
+        auto off = [=](int q) {
             return q < H ? R * (float)(q + 1) / (float)H : R * exp2f(lg * (float)(q + 1 - H) / (float)H);
         };
-        auto warm_x = [&](int pt) { return up ? in + off(pt) : in - off(P - 1 - pt); };
+        auto warm_x = [=](int pt) { return up ? in + off(pt) : in - off(P - 1 - pt); };
         if (up)
             a = in;
         else
@@ -772,7 +772,7 @@ __device__ void tri_ends_block(const float* al, const float* be, int L, bool war
     }
     const float den = (float)(32 * half + 1);
     for (int r = warm ? 1 : 0; r < (warm ? 1 : 0) + rounds; ++r) {
-        auto even = [&](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
+        auto even = [=](int pt) { return a + (b - a) * (float)(pt + 1) / den; };
         multisect_round(below, L, even, a, b, up, mine, w0, half, s_msk[r & 1]);
     }
     if (mine && warp == w0 && lane == 0) {
@@ -1138,9 +1138,9 @@ struct CluSmem {
     unsigned long long ss[2 * kCN];       // i + j sums of S
     unsigned long long ds[kCN];           // |i - j| sums of S
     unsigned long long mom[7], T, cij, fin_cij[kClu];
-    float q[kCN], qp[kCN], y[kCR];        // Lanczos vector, the previous one, this CTA's rows of A' q
-    float w[2][kCN];                      // A' q - beta q_prev, pieces written by every CTA (by step parity)
-    float sa[2][kClu];                    // each CTA's part of (A' q - beta q_prev) . q (by step parity)
+    float qv[2][kCN];                     // Lanczos vectors q_k and q_(k-1) (by step parity)
+    __align__(16) float w[2][kCN];        // A' q - beta q_prev, pieces written by every CTA (by step parity)
+    __align__(16) float stg[kCR];         // this CTA's entries of A' q - beta q_prev
     float al[kMaxSymSteps], be[kMaxSymSteps];
     TriEnds te;                           // ends of the tridiagonal matrix at the last check
     DF fin[kClu][10];                     // CTA 0: each CTA's compensated sums
@@ -1176,6 +1176,13 @@ __device__ __forceinline__ uint32_t clu_addr(const void* p, uint32_t rank)
 __device__ __forceinline__ void clu_st(uint32_t a, float v)
 {
     asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+__device__ __forceinline__ void clu_st4(uint32_t a, float4 v)
+{
+    asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+                 "f"(v.w)
+                 : "memory");
 }
 
 __device__ __forceinline__ void clu_st64(uint32_t a, unsigned long long v)
@@ -1217,81 +1224,117 @@ __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long s)
 // beta = |w|, q = w / beta; every 8 steps (after 16) the tridiagonal
 // matrix's extreme eigenvalues are bracketed, each check after the first
 // starting from the last one's brackets, and the iteration stops once
-// max |eigenvalue| moved by less than 4e-7 of itself.  One cluster barrier
-// per step: each CTA writes its rows of w' and its part of alpha into every
-// CTA (buffers alternate by step parity, so a CTA a step ahead never
-// overwrites what another still reads); then every CTA forms all of w, beta
-// and q from the same numbers in the same order, so all hold the same
-// vector and tridiagonal matrix and take the same decisions.
+// max |eigenvalue| moved by less than 4e-7 of itself.
+// Warp v of the CTA owns rows 2 v and 2 v + 1 of the CTA's 32, held in
+// registers (lane l: columns l + 32 u); q and the previous q alternate
+// between two shared buffers by step parity.  A step: every warp multiplies
+// its rows by q, forms its two entries of w' and writes them into every
+// CTA; one cluster barrier; warp 0 of every CTA reads all of w' and forms
+// alpha, beta and the next q from the same numbers in the same order, so all
+// CTAs hold the same vector and tridiagonal matrix and take the same
+// decisions; one CTA barrier.  A CTA a step ahead cannot overwrite a w'
+// buffer another still reads: w' alternates by step parity too, and every
+// CTA reads its buffer before it arrives at the next cluster barrier.
 __device__ float clu_lanczos(CluSmem& sm, const float* A, int N, uint32_t r)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i0 = (int)r * kCR;
-    for (int c = tid; c < kCN; c += kCluThreads) {
-        // A near-constant start would be almost orthogonal to the top
-        // eigenvectors of a deflated A' and could stall on a lower one.
-        const unsigned h = (unsigned)c * 2654435761u + 12345u;
-        sm.q[c] = c < N ? (float)h * 2.3283064e-10f - 0.5f : 0.f;
-        sm.qp[c] = 0.f;
+    const int j = lane >> 4;                       // this lane's row of the warp's two ...
+    const int gi = (int)r * kCR + 2 * warp + j;    // ... as an index of A'
+    float a0[kCN / 32], a1[kCN / 32];
+#pragma unroll
+    for (int u = 0; u < kCN / 32; ++u) {
+        a0[u] = A[(2 * warp) * kCN + lane + 32 * u];
+        a1[u] = A[(2 * warp + 1) * kCN + lane + 32 * u];
     }
-    if (tid == 0) {
-        sm.te.absmax = -1.f;
-        sm.stop = 0;
+    // Warp 0 keeps q in registers too (lane l: entries l + 32 u).
+    float q[kCN / 32];
+    if (warp == 0) {
+        float ss = 0.f;
+#pragma unroll
+        for (int u = 0; u < kCN / 32; ++u) {
+            // A near-constant start would be almost orthogonal to the top
+            // eigenvectors of a deflated A' and could stall on a lower one.
+            const int c = lane + 32 * u;
+            const unsigned hs = (unsigned)c * 2654435761u + 12345u;
+            q[u] = c < N ? (float)hs * 2.3283064e-10f - 0.5f : 0.f;
+            ss = fmaf(q[u], q[u], ss);
+        }
+        const float inv = rsqrtf(warp_sum(ss));
+#pragma unroll
+        for (int u = 0; u < kCN / 32; ++u) {
+            q[u] *= inv;
+            sm.qv[0][lane + 32 * u] = q[u];
+            sm.qv[1][lane + 32 * u] = 0.f;
+        }
+        if (lane == 0) {
+            sm.te.absmax = -1.f;
+            sm.stop = 0;
+        }
     }
-    __syncthreads();
-    float ss = 0.f;
-    for (int c = tid; c < kCN; c += kCluThreads)
-        ss = fmaf(sm.q[c], sm.q[c], ss);
-    const float inv = rsqrtf(block_sum(ss, sm.red));
-    for (int c = tid; c < kCN; c += kCluThreads)
-        sm.q[c] *= inv;
     __syncthreads();
     float beta = 0.f;
     int L = 0, checked = 0;
     for (int k = 0; k < kMaxSymSteps; ++k) {
         const int par = k & 1;
-        for (int rr = warp; rr < kCR; rr += kCluWarps) {
-            float acc = 0.f;
+        float y0 = 0.f, y1 = 0.f;
 #pragma unroll
-            for (int u = 0; u < kCN / 32; ++u)
-                acc = fmaf(A[rr * kCN + lane + 32 * u], sm.q[lane + 32 * u], acc);
-            acc = warp_sum(acc);
-            if (lane == 0)
-                sm.y[rr] = acc;
+        for (int u = 0; u < kCN / 32; ++u) {
+            const float qc = sm.qv[par][lane + 32 * u];
+            y0 = fmaf(a0[u], qc, y0);
+            y1 = fmaf(a1[u], qc, y1);
         }
+        // Lanes 0-15 sum row 2 v, lanes 16-31 row 2 v + 1.
+        float y = (j ? y1 : y0) + __shfl_xor_sync(0xffffffffu, j ? y0 : y1, 16);
+        for (int o = 8; o > 0; o >>= 1)
+            y += __shfl_xor_sync(0xffffffffu, y, o);
+        const float wv = fmaf(-beta, sm.qv[par ^ 1][gi], y);
+        if ((lane & 15) == 0)
+            sm.stg[2 * warp + j] = wv;
         __syncthreads();
         if (warp == 0) {
-            // Lane l: row i0 + l.
-            const float wv = fmaf(-beta, sm.qp[i0 + lane], sm.y[lane]);
-            const float d = warp_sum(wv * sm.q[i0 + lane]);
-            for (int c = 0; c < kClu; ++c)
-                clu_st(clu_addr(&sm.w[par][i0 + lane], (uint32_t)c), wv);
-            if (lane < kClu)
-                clu_st(clu_addr(&sm.sa[par][r], (uint32_t)lane), d);
+            // Lane l: entries [8 (l / 8), 8 (l / 8) + 8) of this CTA's 32, into CTA l % 8.
+            const int c = lane & 7, e = 8 * (lane >> 3);
+            const uint32_t dst = clu_addr(&sm.w[par][(int)r * kCR + e], (uint32_t)c);
+            clu_st4(dst, *reinterpret_cast<const float4*>(&sm.stg[e]));
+            clu_st4(dst + 16u, *reinterpret_cast<const float4*>(&sm.stg[e + 4]));
             clu_sync();
         } else {
-            clu_sync_relaxed();
+            clu_sync_relaxed();  // these warps wrote nothing another CTA reads
         }
-        float alpha = 0.f;
-        for (int c = 0; c < kClu; ++c)
-            alpha += sm.sa[par][c];
-        float wt = 0.f;
-        if (tid < kCN)
-            wt = fmaf(-alpha, sm.q[tid], sm.w[par][tid]);
-        const float bn = sqrtf(block_sum(wt * wt, sm.red));
-        if (tid == 0) {
-            sm.al[k] = alpha;
-            sm.be[k] = bn;
+        if (warp == 0) {
+            float wc[kCN / 32], d = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCN / 32; ++u) {
+                wc[u] = sm.w[par][lane + 32 * u];
+                d = fmaf(wc[u], q[u], d);
+            }
+            const float alpha = warp_sum(d);
+            float s2 = 0.f;
+#pragma unroll
+            for (int u = 0; u < kCN / 32; ++u) {
+                wc[u] = fmaf(-alpha, q[u], wc[u]);
+                s2 = fmaf(wc[u], wc[u], s2);
+            }
+            const float bn = sqrtf(warp_sum(s2));
+            if (lane == 0) {
+                sm.al[k] = alpha;
+                sm.be[k] = bn;
+            }
+            if (bn > 1e-30f) {
+                const float ib = 1.f / bn;
+#pragma unroll
+                for (int u = 0; u < kCN / 32; ++u) {
+                    q[u] = wc[u] * ib;
+                    sm.qv[par ^ 1][lane + 32 * u] = q[u];
+                }
+            }
         }
+        __syncthreads();
+        const float bn = sm.be[k];
         L = k + 1;
         if (!(bn > 1e-30f))
             break;  // invariant subspace: the tridiagonal matrix is exact
-        if (tid < kCN) {
-            sm.qp[tid] = sm.q[tid];
-            sm.q[tid] = wt * (1.f / bn);
-        }
         beta = bn;
-        __syncthreads();
         if ((L & 7) == 0 && L >= 16) {
             const float prev = sm.te.absmax;
             tri_ends_block(sm.al, sm.be, L, checked > 0, sm.te, sm.msk);
