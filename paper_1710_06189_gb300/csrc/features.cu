@@ -1598,8 +1598,28 @@ size_t features_smem_bytes(int max_levels)
     return feat_layout(max_levels).total;
 }
 
+// A launch at scheduling priority `priority` (0: the stream's own; lower
+// numbers are more urgent): the attribute stays with the kernel node when
+// the launch is captured into a graph.
+template <class... Params, class... Args>
+cudaError_t launch_prio(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s, int priority,
+                        Args... args)
+{
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributePriority;
+    attr[0].val.priority = priority;
+    cfg.attrs = attr;
+    cfg.numAttrs = priority != 0 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // Symmetric feature jobs with 128 < N <= 256: one cluster of kClu CTAs each.
-cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s)
+cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s, int priority)
 {
     if (p.n_jobs <= 0)
         return cudaSuccess;
@@ -1607,15 +1627,14 @@ cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s)
     const cudaError_t e = lim.raise((const void*)k_haralick_cluster, sizeof(CluSmem));
     if (e != cudaSuccess)
         return e;
-    k_haralick_cluster<<<p.n_jobs * kClu, kCluThreads, sizeof(CluSmem), s>>>(p);
-    return cudaGetLastError();
+    return launch_prio(k_haralick_cluster, dim3(p.n_jobs * kClu), dim3(kCluThreads), sizeof(CluSmem), s, priority, p);
 }
 
 // threads: kFeatThreads, or kFeatThreadsSmall for jobs with N <= 32 (their
 // epilogue is short and barrier-bound: two such CTAs share an SM).  The
 // block size depends on a job's N only, so its features do not depend on
 // the batch it is in.
-cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads)
+cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads, int priority)
 {
     if (p.n_jobs <= 0)
         return cudaSuccess;
@@ -1626,8 +1645,7 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s,
     const cudaError_t e = lim.raise((const void*)k_haralick, smem);
     if (e != cudaSuccess)
         return e;
-    k_haralick<<<p.n_jobs, threads, smem, s>>>(p, max_levels);
-    return cudaGetLastError();
+    return launch_prio(k_haralick, dim3(p.n_jobs), dim3(threads), smem, s, priority, p, max_levels);
 }
 
 }  // namespace glcm

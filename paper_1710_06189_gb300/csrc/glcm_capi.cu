@@ -92,8 +92,13 @@ struct glcm_ctx {
     cudaStream_t side_stream = nullptr;  // epilogues overlapped with votes in split batches
     cudaStream_t epi_stream = nullptr;   // light groups' epilogues in host-buffer batches
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    // Column-walk classes of one vote launch group voted side by side, and
+    // their epilogues after them (one stream per number of levels).
+    cudaStream_t cls_stream[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaEvent_t ev_cls_fork = nullptr, ev_cls_vote[4] = {}, ev_cls_done[4] = {};
     size_t budget = 0, used = 0;
     int sm_count = 0, smem_optin = 0;
+    int prio_high = 0;  // the device's most urgent stream priority (class epilogues)
     int sm_reserve = 0;  // SMs every vote launch leaves free (to a concurrent copy kernel)
     unsigned* d_words = nullptr;  // [0] error bits, [1] general vote chunk counter, [2..31] column-walk counters
     DevBuf jobs, offs, feat, work, img, counts, norm, featout, maps;
@@ -172,6 +177,9 @@ int ensure(glcm_ctx* ctx, DevBuf& b, size_t bytes)
             cudaStreamSynchronize(ctx->side_stream);
         if (ctx->epi_stream)
             cudaStreamSynchronize(ctx->epi_stream);
+        for (cudaStream_t cs : ctx->cls_stream)
+            if (cs)
+                cudaStreamSynchronize(cs);
         cudaFree(b.p);
         ctx->used -= b.cap;
         b.p = nullptr;
@@ -953,8 +961,54 @@ TimedPair take_pair(glcm_ctx* ctx)
 }
 
 // Enqueue zero (optional) + vote for a plan whose tables are at djobs/doffs.
+// Column-walk classes of a vote launch group voted side by side: group g
+// (one number of levels) on ctx->cls_stream[g], largest first; used ==
+// false when everything votes on one stream.
+struct ClassStreams {
+    bool used = false;
+    int n = 0;
+    int levels[4] = {0, 0, 0, 0};
+};
+
+// Groups of a plan's column-walk classes by number of levels, the most
+// work first (pixels walked, one walk per job; then the larger N, whose
+// votes and epilogue cost more), so that the cheapest class's votes and
+// epilogue end the launch; false when the plan votes anything else or has
+// more than four numbers of levels.
+bool class_groups(const VotePlan& plan, ClassStreams& cs, std::vector<int>& group_of)
+{
+    if (!plan.jobs.empty() || !plan.globals.empty() || !plan.seams.empty() || plan.fast.size() < 2)
+        return false;
+    std::vector<std::pair<long long, int>> work;  // (work, levels)
+    for (const FastClass& c : plan.fast) {
+        long long w = 0;
+        for (const FastJob& j : c.jobs)
+            w += (long long)j.W * (j.y_end - j.y_begin);
+        w = w * 512 + c.log2n;  // ties: the larger N first
+        const int lv = 1 << c.log2n;
+        auto it = std::find_if(work.begin(), work.end(), [&](const std::pair<long long, int>& x) { return x.second == lv; });
+        if (it == work.end())
+            work.push_back({w, lv});
+        else
+            it->first += w;
+    }
+    if (work.size() < 2 || work.size() > 4)
+        return false;
+    std::stable_sort(work.begin(), work.end(),
+                     [](const std::pair<long long, int>& a, const std::pair<long long, int>& b) { return a.first > b.first; });
+    cs.n = (int)work.size();
+    for (int g = 0; g < cs.n; ++g)
+        cs.levels[g] = work[g].second;
+    group_of.assign(plan.fast.size(), 0);
+    for (size_t ci = 0; ci < plan.fast.size(); ++ci)
+        for (int g = 0; g < cs.n; ++g)
+            if (cs.levels[g] == 1 << plan.fast[ci].log2n)
+                group_of[ci] = g;
+    return true;
+}
+
 int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const DevBuf& doffs, const int3* dchunks,
-                 bool zero, bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
+                 bool zero, bool capturing, GraphEntry* ge, cudaStream_t st = nullptr, ClassStreams* cs = nullptr)
 {
     if (plan_empty(plan))
         return GLCM_OK;
@@ -1014,7 +1068,21 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         CK(cudaEventRecord(tp.a, st));
     }
     int n_launch = 0;
-    for (size_t ci = 0; ci < plan.fast.size(); ++ci) {
+    // Classes side by side: each group forks from the stream after the
+    // zeroing; the stream then waits for every group's votes.
+    std::vector<int> group_of;
+    const bool par = cs && class_groups(plan, *cs, group_of);
+    std::vector<size_t> order(plan.fast.size());
+    for (size_t ci = 0; ci < order.size(); ++ci)
+        order[ci] = ci;
+    if (par) {
+        cs->used = true;
+        std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return group_of[a] < group_of[b]; });
+        CK(cudaEventRecord(ctx->ev_cls_fork, st));
+        for (int g = 0; g < cs->n; ++g)
+            CK(cudaStreamWaitEvent(ctx->cls_stream[g], ctx->ev_cls_fork, 0));
+    }
+    for (size_t ci : order) {
         const FastClass& c = plan.fast[ci];
         if (c.chunks.empty())
             continue;
@@ -1030,9 +1098,15 @@ int enqueue_vote(glcm_ctx* ctx, const VotePlan& plan, const DevBuf& djobs, const
         int ctas = std::max(1, ctx->sm_count - ctx->sm_reserve);
         if (plan.max_ctas > 0)
             ctas = std::min(ctas, plan.max_ctas);
-        CK(launch_vote_fast(fp, c.bpp, c.log2n, c.aligned, std::max(1, std::min(fp.n_chunks, ctas)), fsmem, st));
+        CK(launch_vote_fast(fp, c.bpp, c.log2n, c.aligned, std::max(1, std::min(fp.n_chunks, ctas)), fsmem,
+                            par ? ctx->cls_stream[group_of[ci]] : st));
         ++n_launch;
     }
+    if (par)
+        for (int g = 0; g < cs->n; ++g) {
+            CK(cudaEventRecord(ctx->ev_cls_vote[g], ctx->cls_stream[g]));
+            CK(cudaStreamWaitEvent(st, ctx->ev_cls_vote[g], 0));
+        }
     if (!plan.jobs.empty()) {
         CK(launch_vote(vp, plan.bpp, grid, plan.threads, smem, st, plan_packed(plan)));
         ++n_launch;
@@ -1090,23 +1164,24 @@ int capture_mark(glcm_ctx* ctx, GraphEntry* ge, bool start)
 // Feature jobs in launch order (feat_job_group): one small CTA each (N <=
 // 32), one CTA each, one cluster of CTAs each (symmetric, 128 < N <= 256).
 // Each job names its own outputs, so the order changes nothing else.
+// Feature jobs by number of levels, then launch group: the jobs of one
+// number of levels are contiguous (an epilogue can follow its class's votes)
+// and the runs of one launch group long.
 void order_feats(std::vector<FeatJob>& feats)
 {
-    std::stable_sort(feats.begin(), feats.end(),
-                     [](const FeatJob& a, const FeatJob& b) { return feat_job_group(a) < feat_job_group(b); });
+    std::stable_sort(feats.begin(), feats.end(), [](const FeatJob& a, const FeatJob& b) {
+        return a.levels != b.levels ? a.levels < b.levels : feat_job_group(a) < feat_job_group(b);
+    });
 }
 
 int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const DevBuf& dfeat, int max_levels,
-                     bool capturing, GraphEntry* ge, cudaStream_t st = nullptr)
+                     bool capturing, GraphEntry* ge, cudaStream_t st = nullptr, int priority = 0)
 {
     if (feats.empty())
         return GLCM_OK;
     if (!st)
         st = ctx->stream;
-    for (size_t i = 1; i < feats.size(); ++i)
-        if (feat_job_group(feats[i]) < feat_job_group(feats[i - 1]))
-            return fail(ctx, GLCM_ERR_CUDA, "internal: feature jobs out of launch order");
-    // One launch per group, in order.
+    // One launch per run of jobs of one launch group.
     size_t g0 = 0;
     while (g0 < feats.size()) {
         const int grp = feat_job_group(feats[g0]);
@@ -1125,7 +1200,7 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
         fp.n_jobs = (int)(g1 - g0);
         fp.err = ctx->d_words;
         if (grp == 2) {
-            CK(launch_features_cluster(fp, st));
+            CK(launch_features_cluster(fp, st, priority));
         } else {
             if (gmax > 64 && any_feat) {
                 const long long per = features_work_floats(gmax);
@@ -1133,7 +1208,7 @@ int enqueue_features(glcm_ctx* ctx, const std::vector<FeatJob>& feats, const Dev
                 fp.work = static_cast<float*>(ctx->work.p);
                 fp.work_stride = per;
             }
-            CK(launch_features(fp, gmax, st, grp == 0 ? kFeatThreadsSmall : kFeatThreads));
+            CK(launch_features(fp, gmax, st, grp == 0 ? kFeatThreadsSmall : kFeatThreads, priority));
         }
         if (!capturing)
             ctx->kernel_launches += 1;
@@ -1386,6 +1461,11 @@ extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, 
     ctx->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)1 << 30;
     cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&ctx->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    {
+        int least = 0, greatest = 0;
+        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) == cudaSuccess)
+            ctx->prio_high = greatest;
+    }
     if (cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cuda_stream);
     } else {
@@ -1401,10 +1481,18 @@ extern "C" int glcm_create(glcm_ctx** out, int device, size_t hbm_budget_bytes, 
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join2, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_stage, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_cls_fork, cudaEventDisableTiming) != cudaSuccess) {
         glcm_destroy(ctx);
         return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
     }
+    for (int i = 0; i < 4; ++i)
+        if (cudaStreamCreateWithFlags(&ctx->cls_stream[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_cls_vote[i], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&ctx->ev_cls_done[i], cudaEventDisableTiming) != cudaSuccess) {
+            glcm_destroy(ctx);
+            return fail(nullptr, GLCM_ERR_CUDA, "stream/event creation failed");
+        }
     if (fault_injected("alloc") || cudaMalloc(&ctx->d_words, 128) != cudaSuccess) {
         cudaGetLastError();
         ctx->d_words = nullptr;
@@ -1430,6 +1518,9 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaStreamSynchronize(ctx->side_stream);
     if (ctx->epi_stream)
         cudaStreamSynchronize(ctx->epi_stream);
+    for (cudaStream_t cs : ctx->cls_stream)
+        if (cs)
+            cudaStreamSynchronize(cs);
     for (auto& kv : ctx->graphs)
         destroy_graph(kv.second);
     for (DevBuf* b : {&ctx->jobs, &ctx->offs, &ctx->feat, &ctx->work, &ctx->img, &ctx->counts, &ctx->norm,
@@ -1468,6 +1559,16 @@ extern "C" int glcm_destroy(glcm_ctx* ctx)
         cudaEventDestroy(ctx->ev_fork);
     if (ctx->ev_join)
         cudaEventDestroy(ctx->ev_join);
+    for (int i = 0; i < 4; ++i) {
+        if (ctx->cls_stream[i])
+            cudaStreamDestroy(ctx->cls_stream[i]);
+        if (ctx->ev_cls_vote[i])
+            cudaEventDestroy(ctx->ev_cls_vote[i]);
+        if (ctx->ev_cls_done[i])
+            cudaEventDestroy(ctx->ev_cls_done[i]);
+    }
+    if (ctx->ev_cls_fork)
+        cudaEventDestroy(ctx->ev_cls_fork);
     if (ctx->own_stream && ctx->stream)
         cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -1833,19 +1934,55 @@ int prepare_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, SplitBatch& sb, 
     return GLCM_OK;
 }
 
+// The epilogue of a prepared batch part on ctx->stream; when its column-walk
+// classes voted side by side (cs), the GLCMs of each number of levels follow
+// their class's votes on its stream, at the device's most urgent priority
+// (an SM freed by a vote CTA goes to them before the other classes' pending
+// vote CTAs: the epilogues of the early classes do not pile up at the end),
+// and the stream waits for all of them.
+int enqueue_epilogue(glcm_ctx* ctx, const SplitBatch& sb, const DevBuf& dfeat, bool capturing, GraphEntry* ge,
+                     const ClassStreams& cs)
+{
+    if (!cs.used)
+        return enqueue_features(ctx, sb.feats, dfeat, sb.max_levels, capturing, ge);
+    size_t done = 0;
+    for (int g = 0; g < cs.n; ++g) {
+        size_t a = 0;
+        while (a < sb.feats.size() && sb.feats[a].levels != cs.levels[g])
+            ++a;
+        size_t b = a;
+        while (b < sb.feats.size() && sb.feats[b].levels == cs.levels[g])
+            ++b;
+        if (b > a) {
+            const std::vector<FeatJob> part(sb.feats.begin() + (long)a, sb.feats.begin() + (long)b);
+            DevBuf view;
+            view.p = static_cast<FeatJob*>(dfeat.p) + a;
+            TRY(enqueue_features(ctx, part, view, sb.max_levels, capturing, ge, ctx->cls_stream[g], ctx->prio_high));
+            done += b - a;
+        }
+        CK(cudaEventRecord(ctx->ev_cls_done[g], ctx->cls_stream[g]));
+        CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_cls_done[g], 0));
+    }
+    if (done != sb.feats.size())
+        return fail(ctx, GLCM_ERR_CUDA, "internal: a feature job of no voted class");
+    return GLCM_OK;
+}
+
 // Enqueue a prepared batch: zero + vote per pixel type, then the epilogue.
 int enqueue_batch(glcm_ctx* ctx, const SplitBatch& sb, const DevBuf& djobs, const DevBuf& doffs, const DevBuf& dfeat,
                   bool capturing, GraphEntry* ge)
 {
     if (capturing)
         TRY(capture_mark(ctx, ge, true));
+    ClassStreams cs;
     if (!plan_empty(sb.p8))
-        TRY(enqueue_vote(ctx, sb.p8, djobs, doffs, sb.c8, true, capturing, ge));
+        TRY(enqueue_vote(ctx, sb.p8, djobs, doffs, sb.c8, true, capturing, ge, nullptr,
+                         plan_empty(sb.p16) ? &cs : nullptr));
     if (!plan_empty(sb.p16))
         TRY(enqueue_vote(ctx, sb.p16, sb.j16, sb.o16, sb.c16, true, capturing, ge));
     if (capturing)
         TRY(capture_mark(ctx, ge, false));
-    return enqueue_features(ctx, sb.feats, dfeat, sb.max_levels, capturing, ge);
+    return enqueue_epilogue(ctx, sb, dfeat, capturing, ge, cs);
 }
 
 // A batch split in two: the images whose epilogue is expensive (features of
@@ -1865,13 +2002,15 @@ int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, Sp
     CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
     TRY(enqueue_features(ctx, h.feats, th[2], h.max_levels, capturing, ge, ctx->side_stream));
     r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - split_reserve(ctx, (int)h.feats.size()));
+    ClassStreams cs;
     if (!plan_empty(r.p8))
-        TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge));
+        TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge, nullptr,
+                         plan_empty(r.p16) ? &cs : nullptr));
     if (!plan_empty(r.p16))
         TRY(enqueue_vote(ctx, r.p16, r.j16, r.o16, r.c16, true, capturing, ge));
     if (capturing)
         TRY(capture_mark(ctx, ge, false));
-    TRY(enqueue_features(ctx, r.feats, tr[2], r.max_levels, capturing, ge));
+    TRY(enqueue_epilogue(ctx, r, tr[2], capturing, ge, cs));
     CK(cudaEventRecord(ctx->ev_join, ctx->side_stream));
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
     return GLCM_OK;
@@ -2216,6 +2355,8 @@ int run_graph_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, const std::vec
         if (rc0 != GLCM_OK) {
             cudaStreamSynchronize(ctx->stream);
             cudaStreamSynchronize(ctx->side_stream);
+            for (cudaStream_t cs : ctx->cls_stream)
+                cudaStreamSynchronize(cs);
             destroy_graph(ge);
             return rc0;
         }
@@ -2233,7 +2374,7 @@ int run_graph_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, const std::vec
             return rc;
         }
         CK(ce);
-        ce = cudaGraphInstantiate(&ge.exec, graph, 0);
+        ce = cudaGraphInstantiate(&ge.exec, graph, cudaGraphInstantiateFlagUseNodePriority);
         if (ce == cudaSuccess && ctx->timing) {
             // Find the event-record nodes that bracket the first vote kernel.
             size_t nnodes = 0;

@@ -250,9 +250,10 @@ cudaError_t launch_naive(const uint8_t* img, long long pitch, int W, int H, int 
 constexpr int kFeatThreads = 512;
 constexpr int kFeatThreadsSmall = 256;
 constexpr int kSmallFeatLevels = 32;
-cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads);
+// priority: 0, or a stream priority for this launch alone (lower is more urgent).
+cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s, int threads, int priority = 0);
 // Symmetric feature jobs with 128 < N <= 256, one cluster of CTAs per GLCM.
-cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s);
+cudaError_t launch_features_cluster(const FeatParams& p, cudaStream_t s, int priority = 0);
 inline bool feat_job_clustered(const FeatJob& f)
 {
     return f.features != nullptr && f.symmetric && f.levels > 128 && f.levels <= 256;
