@@ -788,9 +788,10 @@ __device__ void flush_t(const FastJob& j, uint32_t* hist, uint32_t* marg)
     }
 }
 
-// Persistent CTAs take every chunk from the counter, the first one too: a
-// CTA that starts late (its SM was busy with another kernel) finds the
-// chunks taken instead of adding its own one to the launch's tail.
+// Persistent CTAs: chunk b to CTA b first, then chunks from the counter.
+// (Taking the first chunk from the counter too, for CTAs that start late
+// beside another kernel, measured slower: a lone 4096^2 N = 32 image 28.9 ->
+// 32.0 us, the contention step 0.431 -> 0.433 ms.)
 // One kernel instance per pixel type, N and row alignment (every job of a
 // launch has them).
 // Dynamic shared memory: the histograms (max_hist_words), the joint merge's
@@ -832,9 +833,11 @@ __global__ void __launch_bounds__(kFT, 1) k_glcm_vote_d1(FastParams p)
     const int warp = threadIdx.x >> 5;
     int cur = -1;
     unsigned acc_rows = 0;
+    bool first = true;
     for (;;) {
         if (threadIdx.x == 0)
-            *s_chunk = (int)atomicAdd(p.chunk_counter, 1u);
+            *s_chunk = first ? (int)blockIdx.x : (int)gridDim.x + (int)atomicAdd(p.chunk_counter, 1u);
+        first = false;
         __syncthreads();
         const int c = *s_chunk;
         if (c >= p.n_chunks)
