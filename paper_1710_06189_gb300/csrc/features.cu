@@ -861,7 +861,14 @@ __host__ __device__ inline FeatLayout feat_layout(int N)
     return L;
 }
 
-__global__ void __launch_bounds__(kFeatThreads, 1) k_haralick(FeatParams p, int maxN)
+constexpr int kFeatSmallPerSM = 4;  // CTAs per SM of the N <= 32 instance
+
+// MINB: CTAs per SM the register budget allows -- 1 for the 512-thread
+// launch, more for the 256-thread one of GLCMs with N <= 32 (a short,
+// barrier-bound epilogue: more CTAs per SM hide each other's waits).  The
+// arithmetic is the same in every instance.
+template <int THREADS, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_haralick(FeatParams p, int maxN)
 {
     const FeatJob J = p.jobs[blockIdx.x];
     const int N = J.levels;
@@ -1641,11 +1648,19 @@ cudaError_t launch_features(const FeatParams& p, int max_levels, cudaStream_t s,
     if (threads != kFeatThreads && (threads != kFeatThreadsSmall || max_levels > kSmallFeatLevels))
         return cudaErrorInvalidValue;
     const size_t smem = features_smem_bytes(max_levels);
+    if (threads == kFeatThreadsSmall) {
+        static SmemLimit lim_small;
+        const cudaError_t e = lim_small.raise((const void*)k_haralick<kFeatThreadsSmall, kFeatSmallPerSM>, smem);
+        if (e != cudaSuccess)
+            return e;
+        return launch_prio(k_haralick<kFeatThreadsSmall, kFeatSmallPerSM>, dim3(p.n_jobs), dim3(threads), smem, s,
+                           priority, p, max_levels);
+    }
     static SmemLimit lim;
-    const cudaError_t e = lim.raise((const void*)k_haralick, smem);
+    const cudaError_t e = lim.raise((const void*)k_haralick<kFeatThreads, 1>, smem);
     if (e != cudaSuccess)
         return e;
-    return launch_prio(k_haralick, dim3(p.n_jobs), dim3(threads), smem, s, priority, p, max_levels);
+    return launch_prio(k_haralick<kFeatThreads, 1>, dim3(p.n_jobs), dim3(threads), smem, s, priority, p, max_levels);
 }
 
 }  // namespace glcm

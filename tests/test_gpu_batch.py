@@ -127,3 +127,36 @@ def test_prepared_batch_repeats(gctx):
             assert np.array_equal(h["features"].numpy(), wf.cpu().numpy())
             assert np.array_equal(ft.cpu().numpy(), wf.cpu().numpy())
             assert np.array_equal(h["normalized"].numpy(), wn.cpu().numpy())
+
+
+def test_light_classes_side_by_side(gctx):
+    """A batch of N <= 32 uint8 images only: its column-walk classes vote side
+    by side, one stream per N (an N with rows at 16-byte starts and at odd
+    starts has two classes on one stream), and each N's epilogue follows its
+    own votes; some images ask for counts only.  Every result equals the
+    oracle and the image alone, on the direct run and on graph replays."""
+    rng = np.random.default_rng(77)
+    jobs = []
+    for k in range(12):
+        n = (8, 16, 32)[k % 3]
+        h = int(rng.integers(40, 400))
+        w = 512 if k % 2 == 0 else int(rng.integers(33, 900)) | 1  # aligned rows, odd widths
+        img = S.image(["iid", "smooth", "constant"][k % 3], 300 + k, h, w, np.uint8, sigma=3.0)
+        feats = k % 4 != 3
+        jobs.append((img, n, feats))
+    spec = [dict(image=torch.from_numpy(im).cuda(), levels=n, offsets=S.CONTENTION_OFFSETS,
+                 flags=G.GLCM_SYMMETRIC, normalized=f, features=f) for im, n, f in jobs]
+    for rep in range(3):
+        outs = gctx.batch(spec)
+        torch.cuda.synchronize()
+        for (im, n, f), (c, nm, ft) in zip(jobs, outs):
+            P = oracle.glcm(im, n, S.CONTENTION_OFFSETS)
+            assert np.array_equal(to_u32(c), P), (im.shape, n, rep)
+            if not f:
+                continue
+            alone = gctx.compute(torch.from_numpy(im).cuda(), n, S.CONTENTION_OFFSETS, G.GLCM_SYMMETRIC)
+            fa = gctx.features(alone, n, symmetric=True)
+            torch.cuda.synchronize()
+            assert np.array_equal(ft.cpu().numpy(), fa.cpu().numpy()), (im.shape, n, rep)
+            assert_normalized(nm.cpu().numpy(), oracle.normalize(oracle.symmetrize(P)))
+            assert_features(ft.cpu().numpy(), oracle.haralick_batch(P, True), n, what=f"{im.shape} N={n}")
