@@ -614,26 +614,27 @@ __device__ __forceinline__ void walk_strip(const FastJob& j, int x0, int y0, int
     }
 }
 
-// Items of a job: first the interior strips (1 .. n_strips - 2) of every
-// band, then the edge strips (the first and the last), so that a chunk's
+// Items of a job: first the edge strips (the first and the last) of every
+// band, then the interior strips (1 .. n_strips - 2), so that a chunk's
 // items, one per warp, cost about the same and no warp waits long at the
-// chunk's barrier for an edge strip.
+// chunk's barrier for an edge strip, and a job's last chunks -- a launch's
+// tail -- are its cheaper interior ones.
 template <int BPP, int LOG2N, bool ALIGNED>
 __device__ __forceinline__ void walk_item(const FastJob& j, int item, uint32_t hb, uint32_t* ring)
 {
     constexpr int PX = 16 / BPP;
     const int n_int = max(0, j.n_strips - 2);
+    const int n_edge = min(2, j.n_strips);
     const int n_bands = (j.y_end - j.y_begin + j.band - 1) / j.band;
     int local = item - j.item0;
     int band, strip;
-    if (local < n_int * n_bands) {
-        band = local / n_int;
-        strip = 1 + (local - band * n_int);
-    } else {
-        local -= n_int * n_bands;
-        const int n_edge = min(2, j.n_strips);
+    if (local < n_edge * n_bands) {
         band = local / n_edge;
         strip = (local - band * n_edge) == 0 ? 0 : j.n_strips - 1;
+    } else {
+        local -= n_edge * n_bands;
+        band = local / n_int;
+        strip = 1 + (local - band * n_int);
     }
     const int x0 = strip * 32 * PX;
     const int y0 = j.y_begin + band * j.band;
