@@ -2001,7 +2001,9 @@ int enqueue_batch_split(glcm_ctx* ctx, const SplitBatch& h, const DevBuf* th, Sp
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side_stream, ctx->ev_fork, 0));
     TRY(enqueue_features(ctx, h.feats, th[2], h.max_levels, capturing, ge, ctx->side_stream));
-    r.p8.max_ctas = r.p16.max_ctas = std::max(1, ctx->sm_count - split_reserve(ctx, (int)h.feats.size()));
+    // The rest votes on every SM: the heavy epilogue, launched first, has
+    // taken its SMs before the rest's CTAs queue for them.
+    r.p8.max_ctas = r.p16.max_ctas = 0;
     ClassStreams cs;
     if (!plan_empty(r.p8))
         TRY(enqueue_vote(ctx, r.p8, tr[0], tr[1], r.c8, true, capturing, ge, nullptr,
@@ -2337,7 +2339,7 @@ int run_graph_batch(glcm_ctx* ctx, const glcm_desc* descs, int n, const std::vec
             rc0 = prepare_batch(ctx, heavy.data(), (int)heavy.size(), sb, ge.jobs, ge.offs, ge.feat);
             if (rc0 == GLCM_OK)
                 rc0 = prepare_batch(ctx, rest.data(), (int)rest.size(), sb2, ge.jobs2, ge.offs2, ge.feat2,
-                                    launch_ctas(ctx, ctx->sm_count - split_reserve(ctx, n_heavy_glcm)));
+                                    launch_ctas(ctx));
         } else if (n > 0) {
             rc0 = prepare_batch(ctx, descs, n, sb, ge.jobs, ge.offs, ge.feat);
         } else {
