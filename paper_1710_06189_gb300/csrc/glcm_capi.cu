@@ -528,8 +528,10 @@ int launch_ctas(const glcm_ctx* ctx, int max_ctas = 0)
     return std::max(1, c);
 }
 
-// SMs the rest of a split batch leaves to the expensive epilogues of its
-// first part (n_glcm GLCMs) while it votes.
+// SMs the later groups of a host-buffer batch leave to the expensive
+// epilogues of its first groups (n_glcm GLCMs) while they vote.  (A device
+// batch's light part votes on every SM: its heavy epilogue is launched
+// first and takes its SMs before the light CTAs queue for them.)
 int split_reserve(const glcm_ctx* ctx, int n_glcm)
 {
     return std::min(n_glcm, ctx->sm_count / 4);
